@@ -1,0 +1,271 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module only *describes* problems: the block lattice (sizes, spacing,
+boundary kinds, block numbering) and initial conditions given as primitive
+states (rho, u, v, w, p) turned into conserved arrays.  It contains none of the
+hydrodynamics method (no reconstruction, no Riemann solver, no update, no
+time-step rule), and it imports neither the product package nor ``oracle/``.
+
+Block storage layout (the layout both sides consume):
+    U[nblocks][5][nz + 2*gz][ny + 2*g][nx + 2*g]   float64, x fastest
+with variables (rho, rho*u, rho*v, rho*w, E); gz = g in 3-D and 0 in 2-D.
+Block ids are lexicographic over the lattice, x fastest:
+    b = bi + nbx * (bj + nby * bk).
+The domain is the unit square / cube; cell widths are 1/(nb_d * n_d).
+
+The problems follow the workloads of the block-structured hydrodynamics runs
+the paper generates code for (Sec. 4.2: equal-size blocks with a halo of
+guard cells, Sec. 2.2): a 2-D Sod shock tube, a 3-D Sedov blast, periodic
+Sod / Kelvin-Helmholtz ensembles with log-normal density noise, and random
+valid states for brute-force checks.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Tuple
+
+import numpy as np
+
+OUTFLOW = "outflow"
+PERIODIC = "periodic"
+
+
+@dataclass(frozen=True)
+class Lattice:
+    """A uniform lattice of equal blocks covering [0,1]^ndim."""
+
+    ndim: int
+    nb: Tuple[int, int, int]          # blocks per dimension (nb[2] == 1 in 2-D)
+    n: Tuple[int, int, int]           # interior cells per block (n[2] == 1 in 2-D)
+    ng: int = 4                       # guard cells per side (x, y; z too in 3-D)
+    bc: Tuple[str, str, str] = (OUTFLOW, OUTFLOW, OUTFLOW)
+    extent: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+
+    def __post_init__(self):
+        if self.ndim not in (2, 3):
+            raise ValueError("ndim must be 2 or 3")
+        if self.ndim == 2 and (self.nb[2] != 1 or self.n[2] != 1):
+            raise ValueError("2-D lattices have nb[2] == n[2] == 1")
+        for b in self.bc:
+            if b not in (OUTFLOW, PERIODIC):
+                raise ValueError(f"unknown boundary kind {b!r}")
+
+    @property
+    def gz(self) -> int:
+        return self.ng if self.ndim == 3 else 0
+
+    @property
+    def nblocks(self) -> int:
+        return self.nb[0] * self.nb[1] * self.nb[2]
+
+    @property
+    def padded(self) -> Tuple[int, int, int]:
+        """(nz_pad, ny_pad, nx_pad)."""
+        return (self.n[2] + 2 * self.gz, self.n[1] + 2 * self.ng, self.n[0] + 2 * self.ng)
+
+    @property
+    def shape(self) -> Tuple[int, int, int, int, int]:
+        return (self.nblocks, 5) + self.padded
+
+    @property
+    def global_cells(self) -> Tuple[int, int, int]:
+        return tuple(self.nb[d] * self.n[d] for d in range(3))
+
+    @property
+    def dx(self) -> Tuple[float, float, float]:
+        return tuple(self.extent[d] / (self.nb[d] * self.n[d]) for d in range(3))
+
+    @property
+    def interior_cells(self) -> int:
+        g = self.global_cells
+        return g[0] * g[1] * g[2]
+
+    def block_coords(self, b: int) -> Tuple[int, int, int]:
+        bi = b % self.nb[0]
+        bj = (b // self.nb[0]) % self.nb[1]
+        bk = b // (self.nb[0] * self.nb[1])
+        return bi, bj, bk
+
+    def interior_slices(self):
+        """Index of the interior cells inside a padded block (z, y, x)."""
+        gz, g = self.gz, self.ng
+        return (slice(gz, gz + self.n[2]), slice(g, g + self.n[1]), slice(g, g + self.n[0]))
+
+
+def lattice_2d(nbx, nby, nxb=16, nyb=16, ng=4, bc=OUTFLOW) -> Lattice:
+    bcs = (bc, bc, OUTFLOW) if isinstance(bc, str) else tuple(bc) + (OUTFLOW,)
+    return Lattice(2, (nbx, nby, 1), (nxb, nyb, 1), ng, bcs)
+
+
+def lattice_3d(nbx, nby, nbz, nxb=16, nyb=16, nzb=16, ng=4, bc=OUTFLOW) -> Lattice:
+    bcs = (bc, bc, bc) if isinstance(bc, str) else tuple(bc)
+    return Lattice(3, (nbx, nby, nbz), (nxb, nyb, nzb), ng, bcs)
+
+
+def cell_centers(lat: Lattice):
+    """Cell-centre coordinates X, Y, Z of every padded cell, shape (nblk, nz, ny, nx)."""
+    nzp, nyp, nxp = lat.padded
+    dx = lat.dx
+    X = np.empty((lat.nblocks, nzp, nyp, nxp))
+    Y = np.empty_like(X)
+    Z = np.empty_like(X)
+    ii = np.arange(nxp) - lat.ng
+    jj = np.arange(nyp) - lat.ng
+    kk = np.arange(nzp) - lat.gz
+    for b in range(lat.nblocks):
+        bi, bj, bk = lat.block_coords(b)
+        x = (bi * lat.n[0] + ii + 0.5) * dx[0]
+        y = (bj * lat.n[1] + jj + 0.5) * dx[1]
+        z = (bk * lat.n[2] + kk + 0.5) * dx[2] if lat.ndim == 3 else np.full(nzp, 0.5 * dx[2])
+        Z[b], Y[b], X[b] = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def conserved(rho, u, v, w, p, gamma):
+    """Conserved (rho, rho u, rho v, rho w, E) of a primitive ideal-gas state.
+
+    This is the definition of the initial data (total energy of the stated
+    state), not part of the method being tested.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    U = np.empty((5,) + rho.shape)
+    U[0] = rho
+    U[1] = rho * u
+    U[2] = rho * v
+    U[3] = rho * w
+    U[4] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return U
+
+
+def _assemble(lat: Lattice, rho, u, v, w, p, gamma):
+    U = conserved(rho, u, v, w, p, gamma)          # (5, nblk, nz, ny, nx)
+    return np.ascontiguousarray(np.moveaxis(U, 0, 1))
+
+
+# ----------------------------------------------------------------------------
+# Initial conditions
+# ----------------------------------------------------------------------------
+
+SOD_LEFT = (1.0, 0.0, 1.0)      # (rho, u, p) for x < 1/2
+SOD_RIGHT = (0.125, 0.0, 0.1)
+
+
+def sod(lat: Lattice, gamma: float = 1.4, x0: float = 0.5, axis: int = 0):
+    """Sod shock tube along ``axis``: (rho,p) = (1,1) left of x0, (0.125,0.1) right."""
+    X, Y, Z = cell_centers(lat)
+    s = (X, Y, Z)[axis]
+    left = s < x0
+    rho = np.where(left, SOD_LEFT[0], SOD_RIGHT[0])
+    p = np.where(left, SOD_LEFT[2], SOD_RIGHT[2])
+    zero = np.zeros_like(rho)
+    return _assemble(lat, rho, zero, zero, zero, p, gamma)
+
+
+def sedov_cells(lat: Lattice, r_cells: float = 3.5):
+    """Mask of the cells whose centres lie within r_cells cell widths of the centre."""
+    X, Y, Z = cell_centers(lat)
+    dx = lat.dx[0]
+    c = [0.5 * lat.extent[d] for d in range(3)]
+    r2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2
+    if lat.ndim == 3:
+        r2 = r2 + (Z - c[2]) ** 2
+    mask = r2 <= (r_cells * dx) ** 2
+    # only interior cells carry the deposit
+    inner = np.zeros_like(mask)
+    zs, ys, xs = lat.interior_slices()
+    inner[:, zs, ys, xs] = True
+    return mask & inner
+
+
+def sedov(lat: Lattice, gamma: float = 1.4, energy: float = 1.0, r_cells: float = 3.5,
+          p_ambient: float = 1e-5, rho_ambient: float = 1.0):
+    """Sedov blast: energy deposited as uniform pressure in the cells within r_cells.
+
+    The deposit pressure is p = (gamma-1) * energy / (n_dep * cell_volume), so the
+    deposited internal energy equals ``energy`` exactly; elsewhere p = p_ambient.
+    """
+    mask = sedov_cells(lat, r_cells)
+    ndep = int(mask.sum())
+    vol = float(np.prod(lat.dx[: lat.ndim]))
+    p_dep = (gamma - 1.0) * energy / (ndep * vol)
+    rho = np.full(mask.shape, rho_ambient)
+    p = np.where(mask, p_dep, p_ambient)
+    zero = np.zeros_like(rho)
+    return _assemble(lat, rho, zero, zero, zero, p, gamma)
+
+
+def kelvin_helmholtz(lat: Lattice, gamma: float = 1.4, seed: int = 0, sigma: float = 0.1):
+    """2-D Kelvin-Helmholtz shear layer with log-normal density noise (periodic)."""
+    X, Y, _ = cell_centers(lat)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    inner = np.abs(Y - 0.5) < 0.25
+    rho = np.where(inner, 2.0, 1.0)
+    u = np.where(inner, 0.5, -0.5)
+    v = 0.01 * np.sin(4.0 * np.pi * X)
+    p = np.full(rho.shape, 2.5)
+    rho = rho * np.exp(sigma * rng.standard_normal(rho.shape))
+    return _assemble(lat, rho, u, v, np.zeros_like(rho), p, gamma)
+
+
+def sod_periodic(lat: Lattice, gamma: float = 1.4, seed: int = 0, sigma: float = 0.1):
+    """Sod layout on a periodic domain (two interfaces) with log-normal density noise."""
+    X, _, _ = cell_centers(lat)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    left = X < 0.5
+    rho = np.where(left, SOD_LEFT[0], SOD_RIGHT[0]) * np.exp(sigma * rng.standard_normal(X.shape))
+    p = np.where(left, SOD_LEFT[2], SOD_RIGHT[2])
+    zero = np.zeros_like(rho)
+    return _assemble(lat, rho, zero, zero, zero, p, gamma)
+
+
+def random_state(lat: Lattice, seed: int, gamma: float = 1.4, rough: bool = True,
+                 mach: float = 0.8):
+    """Random valid state: positive density/pressure, velocities up to ~mach.
+
+    rough=True draws independent values per cell (discontinuous everywhere);
+    rough=False draws a few random Fourier modes (smooth).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (lat.nblocks,) + lat.padded
+    if rough:
+        rho = rng.uniform(0.5, 2.0, shape)
+        p = rng.uniform(0.5, 2.0, shape)
+        vel = rng.uniform(-mach, mach, (3,) + shape)
+    else:
+        X, Y, Z = cell_centers(lat)
+        def field(lo, hi):
+            f = np.zeros(shape)
+            for _ in range(3):
+                kx, ky, kz = rng.integers(1, 4, 3)
+                ph = rng.uniform(0, 2 * np.pi)
+                f += np.sin(2 * np.pi * (kx * X + ky * Y + (kz * Z if lat.ndim == 3 else 0)) + ph)
+            return lo + (hi - lo) * (f / 6.0 + 0.5)
+        rho = field(0.5, 2.0)
+        p = field(0.5, 2.0)
+        vel = np.stack([field(-mach, mach) for _ in range(3)])
+    if lat.ndim == 2:
+        vel[2] = 0.0
+    return _assemble(lat, rho, vel[0], vel[1], vel[2], p, gamma)
+
+
+def poison_guards(U: np.ndarray, lat: Lattice, value: float = np.nan, corners_only: bool = False):
+    """Overwrite guard cells (all, or only edge/corner regions) with ``value``."""
+    U = U.copy()
+    nzp, nyp, nxp = lat.padded
+    g, gz = lat.ng, lat.gz
+    k = np.arange(nzp)
+    j = np.arange(nyp)
+    i = np.arange(nxp)
+    ox = (i < g).astype(int) + (i >= g + lat.n[0]).astype(int)
+    oy = (j < g).astype(int) + (j >= g + lat.n[1]).astype(int)
+    oz = ((k < gz).astype(int) + (k >= gz + lat.n[2]).astype(int)) if lat.ndim == 3 else np.zeros(nzp, int)
+    nout = oz[:, None, None] + oy[None, :, None] + ox[None, None, :]
+    sel = nout >= 2 if corners_only else nout >= 1
+    U[:, :, sel] = value
+    return U
+
+
+def ensemble_sizes(count: int = 96, seed: int = 0, choices=(64, 128, 256, 512)):
+    """Problem sizes for the batched-ensemble workload (uniform draw, seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(choices[i]) for i in rng.integers(0, len(choices), count)]

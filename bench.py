@@ -1,0 +1,375 @@
+"""Benchmark: FP64 zone-updates/s of the block-structured Euler update.
+
+Workload: 3-D Sedov blast at 256^3 = 4096 blocks of 16^3 interior cells + 4
+guard cells, gamma 1.4, CFL 0.8, SSP-RK2 with MC-limited PLM and HLLC, dt on
+the device every step.  A step = one full SSP-RK2 time step (two stage kernels
+with the guard fill fused, the CFL reduction fused into the second) on the
+whole domain.  The state (2.26 GB) is larger than L2 (129 MB), so no flush
+is needed between steps.
+
+One JSON line on rank 0.  Under torchrun every rank advances its own replica
+(the method's only exchanges are guard cells and the dt minimum inside one
+domain on one GPU), and `value` sums all ranks' zones over the slowest
+rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+same scheme, same config and metric), rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 zone-updates/s (3D Sedov 256^3, SSP-RK2 PLM-MC HLLC)"
+UNIT = "zone-updates/s"
+WORKLOAD = ("3D Sedov blast 256^3: 4096 blocks of 16^3 + 4 guard cells, FP64, gamma 1.4, CFL 0.8, "
+            "SSP-RK2 (non-telescoping), MC-limited PLM, HLLC, CFL dt on device each step")
+# Algorithmic FP64 operations per zone-update (+, -, *, /, sqrt = 1 each),
+# counted on the oracle's arithmetic by oracle/opcount.cpp: stage 1 570,
+# stage 2 585 + 24 for the CFL signal speed of the new state.
+FLOPS_STAGE1 = 570
+FLOPS_STAGE2 = 585 + 24
+# FP64 peak derived from the nominal GB300 rate (1.25 TFLOP/s) at 152 SMs and
+# 2070 MHz: 2 FP64 FMA lanes per SM per clock -> 152 * 2 * 2 * 2.07e9.
+FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2.07e9
+ALG_BYTES_PER_ZONE = 200  # stage 1: read U^n, write U1 (80 B); stage 2: read U1, U^n, write U^{n+1} (120 B)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def aggregate(local_seconds: float, local_units: float, world: int, group=None):
+    """(max seconds over ranks, total units over ranks) -- the job's clock and work."""
+    if world == 1:
+        return local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_seconds], dtype=torch.float64)
+    u = torch.tensor([local_units], dtype=torch.float64)
+    if dist.get_backend(group) == "nccl":
+        t, u = t.cuda(), u.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), float(u.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for rel in ("gbh_stage.cu", "gbh_device.cuh", "gbh_internal.h"):
+        with open(os.path.join(ROOT, "paper_2401_03378_gb300", "csrc", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(zones: int):
+    """DRAM bytes per stage-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash():
+        return None
+    per_zone = rec["dram_bytes_per_launch"] / rec["zones"]
+    return per_zone * zones
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def make_problem(nb: int):
+    import workloads as wl
+    lat = wl.lattice_3d(nb, nb, nb, 16, 16, 16, 4)
+    return lat, wl.sedov(lat)
+
+
+def fp64_probe_tflops(gb, torch):
+    sms = gb.sm_count()
+    blocks, threads, iters = sms * 8, 256, 20000
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    gb.fp64_probe(blocks, threads, 100, out)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gb.fp64_probe(blocks, threads, iters, out)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        best = max(best, 16.0 * iters * blocks * threads / s)
+    return best
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import paper_2401_03378_gb300 as gb
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lat, U0 = make_problem(args.nb)
+    zones = lat.interior_cells
+    h = gb.Hydro.from_lattice(lat)
+    U = torch.from_numpy(U0).cuda()
+    dt = h.compute_dt(U)
+    for _ in range(args.warmup):
+        h.step_cfl(U, dt)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    h.set_kernel_timing(True)
+    h.stage_kernel_time()  # clear
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.step_cfl(U, dt)
+        e1.record(stream)
+        barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    stage_ms, stage_launches = h.stage_kernel_time()
+    h.set_kernel_timing(False)
+    clocks = clk.summary()
+    tmax, units = aggregate(secs, float(zones) * args.steps, world)
+    value = units / tmax
+    nbad = h.check_state(U)
+
+    # end to end through the host-buffer C-ABI call: every step copies the
+    # state in from pinned host memory and the updated state back out
+    e2e = None
+    if args.e2e_steps > 0:
+        Uh = torch.from_numpy(U0.copy()).pin_memory()
+        hist = np.zeros(1)
+        h.advance_host(Uh, 1, hist)  # warm (allocates the device buffer)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h.advance_host(Uh, 1, hist)
+        barrier()
+        esecs = time.perf_counter() - t0
+        etmax, eunits = aggregate(esecs, float(zones) * args.e2e_steps, world)
+        nbytes = h.lib.gbh_state_bytes(h.ctx)
+        e2e = {"value": eunits / etmax, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
+               "d2h_bytes_per_step": int(nbytes), "steps": args.e2e_steps}
+
+    # roofline of the dominant kernel (the fused stage kernel, both stages)
+    flops_per_launch = 0.5 * (FLOPS_STAGE1 + FLOPS_STAGE2) * zones
+    ms_per_launch = stage_ms / max(stage_launches, 1)
+    achieved = flops_per_launch / (ms_per_launch / 1e3)
+    probe = fp64_probe_tflops(gb, torch) if rank == 0 else None
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs")
+    traffic = measured_traffic(zones)
+    roof = {
+        "kernel": "gbh stage_kernel<16,3D> (both SSP-RK2 stages, fused halo gather, dt epilogue)",
+        "bound": "alu",
+        "achieved": achieved / 1e12,
+        "peak": FP64_PEAK_NOMINAL / 1e12,
+        "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_NOMINAL,
+        "peak_source": "derived: nominal GB300 FP64 1.25 TFLOP/s = 152 SMs x 2 FMA lanes x 2 flops x 2.07 GHz",
+        "peak_probe_measured": probe / 1e12 if probe else None,
+        "frac_of_probe": achieved / probe if probe else None,
+        "flops_per_zone_update": FLOPS_STAGE1 + FLOPS_STAGE2,
+        "launches": stage_launches,
+        "ms_per_launch": ms_per_launch,
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": ALG_BYTES_PER_ZONE / 2 * zones,
+        "hbm_frac": (ALG_BYTES_PER_ZONE / 2 * zones / (ms_per_launch / 1e3)) / (hbm * 1e9) if hbm else None,
+    }
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * tmax / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded Sedov initial condition)",
+        "config": {"workload": WORKLOAD, "zones": zones, "blocks": lat.nblocks,
+                   "l2": "state 2.26 GB per array > 129 MB L2: no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "e2e": e2e,
+        "unphysical_cells": nbad,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, U0, lat)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def oracle_step_rate(lat, U0, nsteps, threads=0):
+    """Time `nsteps` oracle SSP-RK2 steps (dt from the oracle) on the host cores."""
+    from oracle import oracle as orc
+    used = orc.set_threads(threads)
+    o = orc.Oracle(lat)
+    U = U0.copy()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        dt = o.compute_dt(U)
+        o.step(U, dt)
+    secs = time.perf_counter() - t0
+    return lat.interior_cells * nsteps / secs, used, secs
+
+
+def cpu_baseline(args, U0, lat):
+    rate, used, secs = oracle_step_rate(lat, U0, args.cpu_steps)
+    return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{args.cpu_steps} oracle SSP-RK2 step(s) of the full 256^3 workload "
+                      f"({secs:.1f} s, OpenMP over blocks, {used} threads)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    lat, U0 = make_problem(args.nb)
+    from oracle import oracle as orc
+    used = orc.set_threads(0)
+    o = orc.Oracle(lat)
+    U = U0.copy()
+    for _ in range(args.warmup):
+        o.step(U, o.compute_dt(U))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(U, o.compute_dt(U))
+    secs = time.perf_counter() - t0
+    value = lat.interior_cells * args.steps / secs
+    sample = (f"{args.steps} oracle SSP-RK2 step(s) of the {lat.global_cells[0]}^3 Sedov lattice "
+              f"({lat.nblocks} blocks of 16^3), OpenMP over blocks, {used} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Sedov initial condition)",
+        "config": {"workload": WORKLOAD if args.nb == 16 else f"{WORKLOAD} (sampled at {lat.global_cells[0]}^3)",
+                   "zones": lat.interior_cells},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gbhydro", "reference"], default="gbhydro")
+    ap.add_argument("--nb", type=int, default=16, help="blocks per dimension (16 -> 256^3)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        log("note: at least 3 warm-up steps are required; using 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

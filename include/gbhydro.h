@@ -1,0 +1,170 @@
+/*
+ * gbhydro.h -- C ABI of libgbhydro.so: the per-block finite-volume update of
+ * the compressible Euler equations on a block-structured mesh, on one GB300
+ * GPU (sm_103a), in FP64.
+ *
+ * The paper (CG-Kit, Flash-X Spark variants) describes the work as a
+ * block-structured grid of equal blocks, each surrounded by guard cells
+ * (Sec. 2.2), advanced by an SSP Runge-Kutta time stepper that fills the
+ * guard cells before every stage and then runs, on every block, the
+ * intra-stage calculations calcLims -> calcFlux -> updSoln -> calcEos
+ * (Sec. 4.2, non-telescoping listing; Alg. "Intra stage calculations for
+ * Spark"; Alg. "Block initializations for Spark").  The paper names neither
+ * the reconstruction, the Riemann solver, the RK order nor the time-step
+ * rule.  This library uses piecewise-linear reconstruction of primitive
+ * variables with the monotonized-central limiter, the HLLC flux with
+ * Einfeldt / Roe-average wave speeds, two-stage SSP-RK (Shu-Osher), and the
+ * CFL rule dt = cfl / max_cells sum_d (|u_d| + c) / dx_d.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: GBH_OK (0) or a negative GBH_ERR_* code; gbh_last_error()
+ *    gives a message.  Nothing throws or aborts across this boundary.
+ *  - State arrays are caller-owned DEVICE pointers to FP64 data laid out as
+ *        U[nblocks][5][nzb + 2*gz][nyb + 2*ng][nxb + 2*ng]   (x fastest)
+ *    with variables (rho, rho*u, rho*v, rho*w, E), gz = ng in 3-D, 0 in 2-D.
+ *    Pointers must be 8-byte aligned; distinct arrays must not overlap unless
+ *    an entry point says so.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it and the call returns without synchronising, except where
+ *    an entry point says it synchronises.
+ *  - Interior cells are the result.  After hydro_step / hydro_step_cfl /
+ *    hydro_advance the guard cells of U hold unspecified (stale) values;
+ *    call hydro_fill_guardcells if they are wanted.
+ *  - A context is used from one host thread and one stream at a time.
+ */
+#ifndef GBHYDRO_H
+#define GBHYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBH_OK 0
+#define GBH_ERR_INVAL (-1)        /* bad argument: sizes, nguard < 2, dt <= 0 or non-finite, table entry out of range */
+#define GBH_ERR_CUDA (-2)         /* a CUDA launch or runtime call failed; the message keeps the CUDA error string */
+#define GBH_ERR_UNPHYSICAL (-3)   /* density or pressure at/below its floor, or a non-finite value */
+#define GBH_ERR_NOMEM (-4)        /* device or host allocation failed */
+#define GBH_ERR_UNSUPPORTED (-5)  /* valid request that this build does not implement (e.g. block shape) */
+
+/* Neighbour-table code for a block face on the domain boundary with a
+ * zero-gradient (outflow) condition.  Periodic boundaries are expressed by
+ * the caller as the id of the wrapped block. */
+#define GBH_BC_OUTFLOW (-1)
+
+typedef struct gbh_ctx gbh_ctx;
+
+typedef struct gbh_params {
+  int ndim;               /* 2 or 3 */
+  int nxb, nyb, nzb;      /* interior cells per block; this build supports nxb == nyb in {4, 8, 16},
+                             nzb == 1 when ndim == 2, nzb >= 2 when ndim == 3 */
+  int nguard;             /* guard cells per side, >= 2 and <= min(nxb, nyb[, nzb]) (4 in the standard setups) */
+  int nblocks;            /* >= 1 */
+  double gamma;           /* ratio of specific heats, > 1 */
+  double cfl;             /* Courant number for hydro_compute_dt / hydro_step_cfl, in (0, 1] */
+  double small_rho;       /* density floor used when converting conserved -> primitive (e.g. 1e-12) */
+  double small_p;         /* pressure floor, same use (e.g. 1e-14) */
+  const int32_t *nbr;     /* HOST [nblocks][3^ndim]: block id (>= 0) of the neighbour at lattice offset
+                             (ox, oy[, oz]) in {-1,0,1}^ndim, entry index (oz+1)*9 + (oy+1)*3 + (ox+1)
+                             (2-D: (oy+1)*3 + (ox+1)); the centre entry is the block itself; GBH_BC_OUTFLOW
+                             where the offset leaves the domain.  Copied at gbh_create. */
+  const double *dx;       /* HOST [nblocks][3]: cell widths of each block (dz ignored in 2-D), > 0.  Copied. */
+} gbh_params;
+
+/* Create a context: validates params (GBH_ERR_INVAL, GBH_ERR_UNSUPPORTED),
+ * copies the tables to the current CUDA device and allocates the stage
+ * scratch (one state-sized buffer) and a few device words.  Synchronous.
+ * *out is set to NULL on failure. */
+int gbh_create(const gbh_params *params, gbh_ctx **out);
+
+/* Release everything gbh_create allocated.  Synchronises the device.  NULL is a no-op. */
+int gbh_destroy(gbh_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed gbh_create when ctx is NULL). */
+const char *gbh_last_error(const gbh_ctx *ctx);
+
+/* Bytes of one state array U for this context's layout. */
+long long gbh_state_bytes(const gbh_ctx *ctx);
+
+/* fill_guardcells (Sec. 4.2, called before every RK stage in the
+ * non-telescoping variant): every guard cell of every block is set, in place,
+ * from the neighbour block's interior; at an outflow domain edge the nearest
+ * interior value is copied, dimension by dimension in the order x, y, z (so
+ * edge and corner guards are defined too).  Reads interior cells only. */
+int hydro_fill_guardcells(gbh_ctx *ctx, double *U, void *stream);
+
+/* CFL time step of the state U (interior cells of all blocks):
+ * *dt_dev = cfl / max sum_d (|u_d| + c) / dx_d, written to the DEVICE double
+ * dt_dev.  No synchronisation. */
+int hydro_compute_dt(gbh_ctx *ctx, const double *U, double *dt_dev, void *stream);
+
+/* One RK stage in Shu-Osher form on the interior of every block:
+ *     Uout = a * Un + b * (Uin + dt * L(Uin)),
+ * L = the flux-difference operator of the intra-stage calculations (calcLims,
+ * calcFlux, updSoln).  With a == 0 and b == 1 this is Uin + dt L(Uin) and Un
+ * is not read (may be NULL).  Guard data of Uin are gathered from the
+ * neighbour blocks' interiors through the neighbour table (Uin's own guard
+ * cells are not read).  Uout may equal Un but must not overlap Uin.
+ * dt must be finite and > 0. */
+int hydro_stage(gbh_ctx *ctx, const double *Uin, const double *Un, double *Uout, double dt, double a,
+                double b, void *stream);
+
+/* The same stage, but reading the guard data from Uin's own guard cells
+ * (for callers that filled them, e.g. with hydro_fill_guardcells). */
+int hydro_stage_guarded(gbh_ctx *ctx, const double *Uin, const double *Un, double *Uout, double dt,
+                        double a, double b, void *stream);
+
+/* One full SSP-RK2 step in place with a host-given dt:
+ *     U1 = U + dt L(U);   U <- 1/2 U + 1/2 (U1 + dt L(U1)).
+ * U1 lives in the context's scratch buffer. */
+int hydro_step(gbh_ctx *ctx, double *U, double dt, void *stream);
+
+/* One SSP-RK2 step in place whose dt is read from the DEVICE double *dt_dev
+ * (which must hold the CFL time step of U, e.g. from hydro_compute_dt or the
+ * previous call); on return the stream holds work that overwrites *dt_dev
+ * with the CFL time step of the new state (computed in the second stage's
+ * epilogue).  No host synchronisation: the loop can be captured or pipelined. */
+int hydro_step_cfl(gbh_ctx *ctx, double *U, double *dt_dev, void *stream);
+
+/* nsteps calls of hydro_step_cfl.  If dt_hist_dev is not NULL it receives the
+ * dt used by each step (DEVICE array of nsteps doubles). */
+int hydro_advance(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, double *dt_hist_dev, void *stream);
+
+/* Host-buffer variant for callers whose state lives in host memory:
+ * copies U_host (pinned or pageable, one state array) to a context-owned
+ * device buffer (allocated on first use), computes dt, advances nsteps, and
+ * copies the interior-updated state back into U_host and the dt of each step
+ * into dt_hist_host (nsteps doubles, may be NULL).  Synchronises the stream. */
+int hydro_advance_host(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist_host, void *stream);
+
+/* Scan the interior of U: counts cells whose density <= small_rho, pressure
+ * <= small_p, or any variable is non-finite.  Synchronises the stream, writes
+ * the count to *nbad_host and returns GBH_ERR_UNPHYSICAL if it is non-zero. */
+int hydro_check_state(gbh_ctx *ctx, const double *U, long long *nbad_host, void *stream);
+
+/* Number of floor applications (small_rho / small_p) on interior cells during
+ * stages since the last call; resets the counter.  Synchronises the stream. */
+int hydro_floor_hits(gbh_ctx *ctx, long long *hits_host, void *stream);
+
+/* Kernel timing for measurement: when enabled, CUDA events are recorded on
+ * the stream around every stage-kernel launch.  gbh_stage_kernel_time
+ * synchronises the stream, returns the summed stage-kernel time (ms) and
+ * launch count since the previous call, and clears them. */
+int gbh_set_kernel_timing(gbh_ctx *ctx, int enable);
+int gbh_stage_kernel_time(gbh_ctx *ctx, double *ms_host, long long *launches_host, void *stream);
+
+/* FP64 throughput probe (not part of the method): launches blocks x threads
+ * threads, each running 8 independent chains of iters fused multiply-adds,
+ * and writes one double per thread to out_dev (blocks*threads doubles).
+ * FP64 flops executed = 16 * iters * blocks * threads. */
+int gbh_fp64_probe(int blocks, int threads, int iters, double *out_dev, void *stream);
+
+/* Number of SMs of the current device (for sizing probes), or a negative error. */
+int gbh_device_sm_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBHYDRO_H */

@@ -1,0 +1,96 @@
+"""ctypes declarations of the C ABI in include/gbhydro.h (marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbhydro.so")
+
+GBH_OK = 0
+GBH_ERR_INVAL = -1
+GBH_ERR_CUDA = -2
+GBH_ERR_UNPHYSICAL = -3
+GBH_ERR_NOMEM = -4
+GBH_ERR_UNSUPPORTED = -5
+GBH_BC_OUTFLOW = -1
+
+ERROR_NAMES = {
+    GBH_ERR_INVAL: "GBH_ERR_INVAL",
+    GBH_ERR_CUDA: "GBH_ERR_CUDA",
+    GBH_ERR_UNPHYSICAL: "GBH_ERR_UNPHYSICAL",
+    GBH_ERR_NOMEM: "GBH_ERR_NOMEM",
+    GBH_ERR_UNSUPPORTED: "GBH_ERR_UNSUPPORTED",
+}
+
+
+class GbhParams(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int),
+        ("nxb", C.c_int),
+        ("nyb", C.c_int),
+        ("nzb", C.c_int),
+        ("nguard", C.c_int),
+        ("nblocks", C.c_int),
+        ("gamma", C.c_double),
+        ("cfl", C.c_double),
+        ("small_rho", C.c_double),
+        ("small_p", C.c_double),
+        ("nbr", C.POINTER(C.c_int32)),
+        ("dx", C.POINTER(C.c_double)),
+    ]
+
+
+# name -> (restype, argtypes); the exported symbols of libgbhydro.so
+_vp = C.c_void_p
+_dp = C.c_void_p          # device or host double* passed as an address
+SIGNATURES = {
+    "gbh_create": (C.c_int, [C.POINTER(GbhParams), C.POINTER(_vp)]),
+    "gbh_destroy": (C.c_int, [_vp]),
+    "gbh_last_error": (C.c_char_p, [_vp]),
+    "gbh_state_bytes": (C.c_longlong, [_vp]),
+    "hydro_fill_guardcells": (C.c_int, [_vp, _dp, _vp]),
+    "hydro_compute_dt": (C.c_int, [_vp, _dp, _dp, _vp]),
+    "hydro_stage": (C.c_int, [_vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _vp]),
+    "hydro_stage_guarded": (C.c_int, [_vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _vp]),
+    "hydro_step": (C.c_int, [_vp, _dp, C.c_double, _vp]),
+    "hydro_step_cfl": (C.c_int, [_vp, _dp, _dp, _vp]),
+    "hydro_advance": (C.c_int, [_vp, _dp, C.c_int, _dp, _dp, _vp]),
+    "hydro_advance_host": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
+    "hydro_check_state": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), _vp]),
+    "hydro_floor_hits": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),
+    "gbh_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "gbh_stage_kernel_time": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _vp]),
+    "gbh_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _vp]),
+    "gbh_device_sm_count": (C.c_int, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GbhError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        self.code = code
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+
+
+def load(path: str | None = None):
+    """Load libgbhydro.so (built in-tree).  Raises if it is missing: there is
+    no fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    f"{p} is missing: build it with `python -m paper_2401_03378_gb300.build` "
+                    "(there is no CPU fallback)")
+            lib = C.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib

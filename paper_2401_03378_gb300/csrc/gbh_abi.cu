@@ -1,0 +1,450 @@
+// gbh_abi.cu -- the C ABI of libgbhydro.so (declared in include/gbhydro.h).
+//
+// The context owns: the device copies of the neighbour tables and inverse
+// cell widths, one state-sized scratch buffer (the intermediate SSP-RK2 stage
+// U1), and a few device words (signal-speed accumulator, floor counter, check
+// counter).  Every entry point validates its arguments before enqueuing work
+// and reports failures as GBH_ERR_* codes with a message; no host
+// synchronisation happens unless the entry point says so.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gbhydro.h"
+#include "gbh_internal.h"
+
+using gbh::Eos;
+using gbh::Layout;
+
+struct gbh_ctx {
+  Layout lay{};
+  Eos eos{};
+  double cfl = 0.0;
+  int device = 0;
+  int* d_nbr = nullptr;            // [nblocks][3^ndim]
+  int* d_face = nullptr;           // [nblocks][6]
+  double* d_inv_dx = nullptr;      // [nblocks][3]
+  double* d_scratch = nullptr;     // U1 of SSP-RK2, one state
+  unsigned long long* d_words = nullptr;  // [0] smax accumulator, [1] floor count, [2] check count
+  // host-buffer path (allocated on first use)
+  double* d_host_state = nullptr;
+  double* d_host_dt = nullptr;
+  double* d_host_hist = nullptr;
+  int host_hist_cap = 0;
+  // kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;     // pairs (start, stop)
+  size_t ev_used = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_create_err[512] = {0};
+
+int set_err(gbh_ctx* c, int code, const char* fmt, ...) {
+  char* buf = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_err(gbh_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GBH_OK;
+  return set_err(c, GBH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+long long state_elems(const Layout& L) { return (long long)L.nblocks * L.bstride; }
+
+int check_ctx(gbh_ctx* c) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_err(c, e, "cudaGetDevice");
+  if (dev != c->device)
+    return set_err(c, GBH_ERR_INVAL, "current device %d differs from the context's device %d", dev, c->device);
+  return GBH_OK;
+}
+
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+int check_dt(gbh_ctx* c, double dt) {
+  if (!std::isfinite(dt) || !(dt > 0.0)) return set_err(c, GBH_ERR_INVAL, "dt must be finite and > 0 (got %g)", dt);
+  return GBH_OK;
+}
+
+int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
+  *stop = nullptr;
+  if (!c->timing) return GBH_OK;
+  if (c->ev_used + 2 > c->ev.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+      return set_err(c, GBH_ERR_CUDA, "cudaEventCreate failed");
+    c->ev.push_back(a);
+    c->ev.push_back(b);
+  }
+  cudaEvent_t a = c->ev[c->ev_used], b = c->ev[c->ev_used + 1];
+  c->ev_used += 2;
+  *stop = b;
+  return cuda_err(c, cudaEventRecord(a, s), "cudaEventRecord");
+}
+
+int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
+                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s) {
+  gbh::StageArgs A{};
+  A.Uin = Uin;
+  A.Un = Un;
+  A.Uout = Uout;
+  A.face_nbr = c->d_face;
+  A.inv_dx = c->d_inv_dx;
+  A.dt_dev = dt_dev;
+  A.dt = dt;
+  A.a = a;
+  A.b = b;
+  A.combine = (a == 0.0 && b == 1.0) ? 0 : 1;
+  A.gather = gather ? 1 : 0;
+  A.lay = c->lay;
+  A.eos = c->eos;
+  if (c->lay.ndim == 3) {
+    A.kchunk = c->lay.nz;   // one CTA per block
+    A.nchunks = 1;
+  } else {
+    A.kchunk = 1;
+    A.nchunks = 1;
+  }
+  A.smax_acc = dt_epilogue ? c->d_words : nullptr;
+  A.floor_count = c->d_words + 1;
+  cudaEvent_t stop;
+  int rc = record_start(c, s, &stop);
+  if (rc) return rc;
+  rc = cuda_err(c, gbh::launch_stage(A, s), "stage kernel launch");
+  if (rc) return rc;
+  if (stop) rc = cuda_err(c, cudaEventRecord(stop, s), "cudaEventRecord");
+  return rc;
+}
+
+int validate(const gbh_params* p) {
+  if (!p) return set_err(nullptr, GBH_ERR_INVAL, "params is NULL");
+  if (p->ndim != 2 && p->ndim != 3) return set_err(nullptr, GBH_ERR_INVAL, "ndim must be 2 or 3 (got %d)", p->ndim);
+  if (p->nblocks < 1) return set_err(nullptr, GBH_ERR_INVAL, "nblocks must be >= 1");
+  if (p->nxb < 1 || p->nyb < 1 || p->nzb < 1) return set_err(nullptr, GBH_ERR_INVAL, "block sizes must be >= 1");
+  if (p->ndim == 2 && p->nzb != 1) return set_err(nullptr, GBH_ERR_INVAL, "2-D requires nzb == 1");
+  if (p->ndim == 3 && p->nzb < 2) return set_err(nullptr, GBH_ERR_INVAL, "3-D requires nzb >= 2");
+  if (p->nguard < 2) return set_err(nullptr, GBH_ERR_INVAL, "nguard must be >= 2 (the stencil reads 2 cells)");
+  int nmin = p->nxb < p->nyb ? p->nxb : p->nyb;
+  if (p->ndim == 3 && p->nzb < nmin) nmin = p->nzb;
+  if (p->nguard > nmin) return set_err(nullptr, GBH_ERR_INVAL, "nguard (%d) must not exceed the block size (%d)", p->nguard, nmin);
+  if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return set_err(nullptr, GBH_ERR_INVAL, "gamma must be > 1");
+  if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return set_err(nullptr, GBH_ERR_INVAL, "cfl must be in (0, 1]");
+  if (!(p->small_rho > 0.0) || !(p->small_p > 0.0)) return set_err(nullptr, GBH_ERR_INVAL, "floors must be > 0");
+  if (!p->nbr || !p->dx) return set_err(nullptr, GBH_ERR_INVAL, "nbr and dx tables are required");
+  const int nn = p->ndim == 3 ? 27 : 9;
+  const int centre = p->ndim == 3 ? 13 : 4;
+  for (long long b = 0; b < p->nblocks; ++b) {
+    for (int e = 0; e < nn; ++e) {
+      const int v = p->nbr[b * nn + e];
+      if (v >= p->nblocks || (v < 0 && v != GBH_BC_OUTFLOW))
+        return set_err(nullptr, GBH_ERR_INVAL, "nbr[%lld][%d] = %d is out of range", b, e, v);
+    }
+    if (p->nbr[b * nn + centre] != (int)b)
+      return set_err(nullptr, GBH_ERR_INVAL, "nbr[%lld] centre entry must be the block itself", b);
+    for (int d = 0; d < 3; ++d) {
+      const double h = p->dx[b * 3 + d];
+      if (d < p->ndim && !(h > 0.0 && std::isfinite(h)))
+        return set_err(nullptr, GBH_ERR_INVAL, "dx[%lld][%d] must be finite and > 0", b, d);
+    }
+  }
+  if (p->nxb != p->nyb || (p->nxb != 4 && p->nxb != 8 && p->nxb != 16))
+    return set_err(nullptr, GBH_ERR_UNSUPPORTED, "this build supports nxb == nyb in {4, 8, 16} (got %d x %d)", p->nxb, p->nyb);
+  return GBH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbh_create(const gbh_params* p, gbh_ctx** out) {
+  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  gbh_ctx* c = new (std::nothrow) gbh_ctx();
+  if (!c) return set_err(nullptr, GBH_ERR_NOMEM, "host allocation failed");
+  Layout& L = c->lay;
+  L.ndim = p->ndim;
+  L.nx = p->nxb;
+  L.ny = p->nyb;
+  L.nz = p->nzb;
+  L.g = p->nguard;
+  L.gz = p->ndim == 3 ? p->nguard : 0;
+  L.nxp = L.nx + 2 * L.g;
+  L.nyp = L.ny + 2 * L.g;
+  L.nzp = L.nz + 2 * L.gz;
+  L.nblocks = p->nblocks;
+  L.vstride = (long long)L.nxp * L.nyp * L.nzp;
+  L.bstride = 5 * L.vstride;
+  c->eos.gamma = p->gamma;
+  c->eos.gm1 = p->gamma - 1.0;
+  c->eos.inv_gm1 = 1.0 / (p->gamma - 1.0);
+  c->eos.small_rho = p->small_rho;
+  c->eos.small_p = p->small_p;
+  c->cfl = p->cfl;
+
+  const int nn = p->ndim == 3 ? 27 : 9;
+  std::vector<int> face(6 * (size_t)p->nblocks, GBH_BC_OUTFLOW);
+  std::vector<double> inv(3 * (size_t)p->nblocks, 0.0);
+  for (long long b = 0; b < p->nblocks; ++b) {
+    const int32_t* row = p->nbr + b * nn;
+    auto at = [&](int ox, int oy, int oz) {
+      return p->ndim == 3 ? row[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] : row[(oy + 1) * 3 + (ox + 1)];
+    };
+    face[6 * b + 0] = at(-1, 0, 0);
+    face[6 * b + 1] = at(1, 0, 0);
+    face[6 * b + 2] = at(0, -1, 0);
+    face[6 * b + 3] = at(0, 1, 0);
+    if (p->ndim == 3) {
+      face[6 * b + 4] = at(0, 0, -1);
+      face[6 * b + 5] = at(0, 0, 1);
+    }
+    for (int d = 0; d < 3; ++d) inv[3 * b + d] = (d < p->ndim) ? 1.0 / p->dx[3 * b + d] : 0.0;
+  }
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_nbr, sizeof(int) * nn * (size_t)p->nblocks);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_face, sizeof(int) * face.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_inv_dx, sizeof(double) * inv.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_words, sizeof(unsigned long long) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, sizeof(double) * state_elems(L));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_nbr, p->nbr, sizeof(int) * nn * (size_t)p->nblocks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_face, face.data(), sizeof(int) * face.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_inv_dx, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_words, 0, sizeof(unsigned long long) * 4);
+  if (e == cudaSuccess) e = gbh::stage_prepare(L.nx, L.ndim);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
+    set_err(nullptr, code, "gbh_create: %s", cudaGetErrorString(e));
+    gbh_destroy(c);
+    return code;
+  }
+  *out = c;
+  return GBH_OK;
+}
+
+int gbh_destroy(gbh_ctx* c) {
+  if (!c) return GBH_OK;
+  cudaDeviceSynchronize();
+  cudaFree(c->d_nbr);
+  cudaFree(c->d_face);
+  cudaFree(c->d_inv_dx);
+  cudaFree(c->d_words);
+  cudaFree(c->d_scratch);
+  cudaFree(c->d_host_state);
+  cudaFree(c->d_host_dt);
+  cudaFree(c->d_host_hist);
+  for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
+  delete c;
+  return GBH_OK;
+}
+
+const char* gbh_last_error(const gbh_ctx* c) { return c ? c->err : g_create_err; }
+
+long long gbh_state_bytes(const gbh_ctx* c) {
+  return c ? (long long)sizeof(double) * state_elems(c->lay) : -1;
+}
+
+int hydro_fill_guardcells(gbh_ctx* c, double* U, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "U must be a non-null 8-byte aligned device pointer");
+  gbh::FillArgs A{U, c->d_nbr, c->d_face, c->lay};
+  return cuda_err(c, gbh::launch_fill(A, (cudaStream_t)stream), "fill kernel launch");
+}
+
+int hydro_compute_dt(gbh_ctx* c, const double* U, double* dt_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  gbh::DtArgs A{U, c->d_inv_dx, c->lay, c->eos, c->d_words};
+  rc = cuda_err(c, gbh::launch_dt_reduce(A, s), "dt reduce launch");
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
+}
+
+static int stage_common(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, double dt, double a,
+                        double b, bool gather, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = check_dt(c, dt))) return rc;
+  if (!Uin || !Uout || !aligned8(Uin) || !aligned8(Uout)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
+  if (!std::isfinite(a) || !std::isfinite(b)) return set_err(c, GBH_ERR_INVAL, "a and b must be finite");
+  const bool combine = !(a == 0.0 && b == 1.0);
+  if (combine && (!Un || !aligned8(Un))) return set_err(c, GBH_ERR_INVAL, "Un is required when (a, b) != (0, 1)");
+  const long long n = state_elems(c->lay);
+  if (Uin < Uout + n && Uout < Uin + n) return set_err(c, GBH_ERR_INVAL, "Uout must not overlap Uin");
+  return stage_launch(c, Uin, combine ? Un : nullptr, Uout, nullptr, dt, a, b, gather, false, (cudaStream_t)stream);
+}
+
+int hydro_stage(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, double dt, double a, double b,
+                void* stream) {
+  return stage_common(c, Uin, Un, Uout, dt, a, b, true, stream);
+}
+
+int hydro_stage_guarded(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, double dt, double a,
+                        double b, void* stream) {
+  return stage_common(c, Uin, Un, Uout, dt, a, b, false, stream);
+}
+
+int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = check_dt(c, dt))) return rc;
+  if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
+  if (rc) return rc;
+  return stage_launch(c, c->d_scratch, U, U, nullptr, dt, 0.5, 0.5, true, false, s);
+}
+
+static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
+  int rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
+  if (rc) return rc;
+  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
+}
+
+int hydro_step_cfl(gbh_ctx* c, double* U, double* dt_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  return step_cfl(c, U, dt_dev, (cudaStream_t)stream);
+}
+
+int hydro_advance(gbh_ctx* c, double* U, int nsteps, double* dt_dev, double* dt_hist_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (nsteps < 0) return set_err(c, GBH_ERR_INVAL, "nsteps must be >= 0");
+  if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int n = 0; n < nsteps; ++n) {
+    if (dt_hist_dev) {
+      rc = cuda_err(c, cudaMemcpyAsync(dt_hist_dev + n, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, s),
+                    "dt history copy");
+      if (rc) return rc;
+    }
+    rc = step_cfl(c, U, dt_dev, s);
+    if (rc) return rc;
+  }
+  return GBH_OK;
+}
+
+int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U_host || nsteps < 0) return set_err(c, GBH_ERR_INVAL, "U_host must be non-null and nsteps >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * state_elems(c->lay);
+  cudaError_t e = cudaSuccess;
+  if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
+  if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double));
+  if (e == cudaSuccess && nsteps > c->host_hist_cap) {
+    cudaFree(c->d_host_hist);
+    c->d_host_hist = nullptr;
+    e = cudaMalloc(&c->d_host_hist, sizeof(double) * nsteps);
+    if (e == cudaSuccess) c->host_hist_cap = nsteps;
+  }
+  if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+  if ((rc = cuda_err(c, cudaMemcpyAsync(c->d_host_state, U_host, bytes, cudaMemcpyHostToDevice, s), "H2D copy")))
+    return rc;
+  if ((rc = hydro_compute_dt(c, c->d_host_state, c->d_host_dt, stream))) return rc;
+  if ((rc = hydro_advance(c, c->d_host_state, nsteps, c->d_host_dt, nsteps ? c->d_host_hist : nullptr, stream)))
+    return rc;
+  if ((rc = cuda_err(c, cudaMemcpyAsync(U_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, s), "D2H copy")))
+    return rc;
+  if (dt_hist_host && nsteps > 0 &&
+      (rc = cuda_err(c, cudaMemcpyAsync(dt_hist_host, c->d_host_hist, sizeof(double) * nsteps,
+                                        cudaMemcpyDeviceToHost, s), "D2H dt copy")))
+    return rc;
+  return cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+}
+
+int hydro_check_state(gbh_ctx* c, const double* U, long long* nbad_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !aligned8(U) || !nbad_host) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h = 0;
+  if ((rc = cuda_err(c, cudaMemsetAsync(c->d_words + 2, 0, sizeof(unsigned long long), s), "memset"))) return rc;
+  if ((rc = cuda_err(c, gbh::launch_check(U, c->lay, c->eos, c->d_words + 2, s), "check kernel launch"))) return rc;
+  if ((rc = cuda_err(c, cudaMemcpyAsync(&h, c->d_words + 2, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H copy")))
+    return rc;
+  if ((rc = cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return rc;
+  *nbad_host = (long long)h;
+  if (h) return set_err(c, GBH_ERR_UNPHYSICAL, "%llu interior cells are unphysical or non-finite", h);
+  return GBH_OK;
+}
+
+int hydro_floor_hits(gbh_ctx* c, long long* hits_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!hits_host) return set_err(c, GBH_ERR_INVAL, "hits_host is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h = 0;
+  if ((rc = cuda_err(c, cudaMemcpyAsync(&h, c->d_words + 1, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H copy")))
+    return rc;
+  if ((rc = cuda_err(c, cudaMemsetAsync(c->d_words + 1, 0, sizeof(h), s), "memset"))) return rc;
+  if ((rc = cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return rc;
+  *hits_host = (long long)h;
+  return GBH_OK;
+}
+
+int gbh_set_kernel_timing(gbh_ctx* c, int enable) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  c->timing = enable != 0;
+  c->ev_used = 0;
+  return GBH_OK;
+}
+
+int gbh_stage_kernel_time(gbh_ctx* c, double* ms_host, long long* launches_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!ms_host || !launches_host) return set_err(c, GBH_ERR_INVAL, "null output pointer");
+  if ((rc = cuda_err(c, cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize"))) return rc;
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if ((rc = cuda_err(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime"))) return rc;
+    total += ms;
+  }
+  *ms_host = total;
+  *launches_host = (long long)(c->ev_used / 2);
+  c->ev_used = 0;
+  return GBH_OK;
+}
+
+int gbh_fp64_probe(int blocks, int threads, int iters, double* out_dev, void* stream) {
+  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || !out_dev)
+    return set_err(nullptr, GBH_ERR_INVAL, "invalid probe arguments");
+  cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, out_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "probe launch: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
+int gbh_device_sm_count(void) {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GBH_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GBH_ERR_CUDA;
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// gbh_aux.cu -- guard-cell fill, CFL time-step reduction, state check and the
+// FP64 throughput probe.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbh_device.cuh"
+#include "gbh_internal.h"
+
+namespace gbh {
+namespace {
+
+constexpr int kThreads = 256;
+
+// fill_guardcells (Sec. 4.2).  One thread per (block, padded cell); interior
+// cells are skipped.  The value of a guard cell is resolved directly, without
+// passes that depend on one another:
+//  1. for each dimension d in which the cell lies outside the block and the
+//     block's face in that direction is an outflow edge, its coordinate is
+//     clamped to the nearest interior index (outflow is applied in the order
+//     x, then y, then z; clamps in different dimensions commute);
+//  2. the remaining outside dimensions give a lattice offset; the cell is the
+//     interior cell of the neighbour block at that offset (full table).
+// Every source is an interior cell, so the in-place fill has no read/write
+// overlap.  An offset with no neighbour and no outflow face is left untouched.
+__global__ void fill_kernel(const FillArgs a) {
+  const Layout& L = a.lay;
+  const long long cells = (long long)L.nzp * L.nyp * L.nxp;
+  const long long total = cells * L.nblocks;
+  const int nn = L.ndim == 3 ? 27 : 9;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / cells);
+    long long r = t - (long long)b * cells;
+    const int ii = (int)(r % L.nxp);
+    r /= L.nxp;
+    const int jj = (int)(r % L.nyp);
+    const int kk = (int)(r / L.nyp);
+    int c[3] = {ii - L.g, jj - L.g, kk - L.gz};
+    int o[3];
+    bool interior = true;
+    for (int d = 0; d < 3; ++d) {
+      o[d] = c[d] < 0 ? -1 : (c[d] >= n[d] ? 1 : 0);
+      if (o[d] != 0) interior = false;
+    }
+    if (interior) continue;
+    for (int d = 0; d < L.ndim; ++d) {
+      if (o[d] == 0) continue;
+      const int f = 2 * d + (o[d] > 0 ? 1 : 0);
+      if (__ldg(a.face_nbr + 6 * b + f) == -1) {   // outflow face
+        c[d] = o[d] < 0 ? 0 : n[d] - 1;
+        o[d] = 0;
+      }
+    }
+    int src = b;
+    if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+      const int e = L.ndim == 3 ? (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
+      src = __ldg(a.nbr + (long long)nn * b + e);
+      if (src < 0) continue;
+      for (int d = 0; d < 3; ++d) c[d] -= o[d] * n[d];
+    }
+    const long long so =
+        (long long)src * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g);
+    const long long dof = (long long)b * L.bstride + ((long long)kk * L.nyp + jj) * L.nxp + ii;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a.U[dof + v * L.vstride] = a.U[so + v * L.vstride];
+  }
+}
+
+// CFL reduction: max over interior cells of the signal-speed sum, one
+// atomicMax per CTA on the bit pattern (order-preserving for doubles >= 0).
+__global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
+  const Layout& L = a.lay;
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * L.nblocks;
+  const bool d3 = L.ndim == 3;
+  double smax = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    long long r = t - (long long)b * per;
+    const int i = (int)(r % L.nx);
+    r /= L.nx;
+    const int j = (int)(r % L.ny);
+    const int k = (int)(r / L.ny);
+    const long long o = (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+    double U[5], W[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
+    cons_to_prim(U, W, a.eos);
+    const double s = signal_speed(W, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
+                                  __ldg(a.inv_dx + 3 * b + 2), d3);
+    smax = fmax(smax, s);
+  }
+  __shared__ double red[kThreads];
+  red[threadIdx.x] = smax;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// dt = cfl / smax; also records it and clears the accumulator for its next use.
+__global__ void dt_finalize_kernel(unsigned long long* acc, double cfl, double* dt_out, double* hist) {
+  const double smax = __longlong_as_double((long long)*acc);
+  const double dt = cfl / smax;
+  *dt_out = dt;
+  if (hist) *hist = dt;
+  *acc = 0ull;
+}
+
+__global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const Layout L, const Eos e,
+                                                         unsigned long long* count) {
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * L.nblocks;
+  unsigned long long bad = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    long long r = t - (long long)b * per;
+    const int i = (int)(r % L.nx);
+    r /= L.nx;
+    const int j = (int)(r % L.ny);
+    const int k = (int)(r / L.ny);
+    const long long o = (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+    double u[5];
+    bool finite = true;
+    for (int v = 0; v < 5; ++v) {
+      u[v] = U[o + v * L.vstride];
+      finite = finite && isfinite(u[v]);
+    }
+    const double p = e.gm1 * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+    if (!finite || !(u[0] > e.small_rho) || !(p > e.small_p)) ++bad;
+  }
+  if (bad) atomicAdd(count, bad);
+}
+
+// 8 independent FMA chains per thread; the multiplier and addend keep the
+// values bounded (fixed point 1.0).
+__global__ void fp64_probe_kernel(int iters, double* out) {
+  const double m = 0.999999999, c = 1e-9;
+  double x0 = 1.0 + 1e-3 * threadIdx.x, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
+  double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, m, c); x1 = fma(x1, m, c); x2 = fma(x2, m, c); x3 = fma(x3, m, c);
+    x4 = fma(x4, m, c); x5 = fma(x5, m, c); x6 = fma(x6, m, c); x7 = fma(x7, m, c);
+  }
+  out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+int grid_for(long long work, int threads) {
+  long long g = (work + threads - 1) / threads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
+  const long long work = (long long)a.lay.nblocks * a.lay.nzp * a.lay.nyp * a.lay.nxp;
+  fill_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s) {
+  const long long work = (long long)a.lay.nblocks * a.lay.nx * a.lay.ny * a.lay.nz;
+  dt_reduce_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_out, double* hist,
+                               cudaStream_t s) {
+  dt_finalize_kernel<<<1, 1, 0, s>>>(acc, cfl, dt_out, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
+                         cudaStream_t s) {
+  const long long work = (long long)lay.nblocks * lay.nx * lay.ny * lay.nz;
+  check_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(U, lay, eos, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s) {
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(iters, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gbh

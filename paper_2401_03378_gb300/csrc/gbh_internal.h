@@ -1,0 +1,74 @@
+// gbh_internal.h -- launch interfaces shared by the translation units of
+// libgbhydro.so (not part of the public ABI; see include/gbhydro.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbh {
+
+// Face order used by the compact face-neighbour table: x-, x+, y-, y+, z-, z+.
+enum { FACE_XM = 0, FACE_XP, FACE_YM, FACE_YP, FACE_ZM, FACE_ZP };
+
+struct Layout {
+  int ndim;
+  int nx, ny, nz;        // interior cells per block
+  int g, gz;             // guard widths (gz = g in 3-D, 0 in 2-D)
+  int nxp, nyp, nzp;     // padded extents
+  int nblocks;
+  long long vstride;     // nzp*nyp*nxp
+  long long bstride;     // 5*vstride
+};
+
+struct Eos {
+  double gamma, gm1, inv_gm1, small_rho, small_p;
+};
+
+// Arguments of one RK-stage launch: Uout = a*Un + b*(Uin + dt*L(Uin)).
+struct StageArgs {
+  const double* Uin;
+  const double* Un;      // may alias Uout (read and written by the same thread)
+  double* Uout;
+  const int* face_nbr;   // [nblocks][6]
+  const double* inv_dx;  // [nblocks][3]
+  const double* dt_dev;  // if non-null, dt = *dt_dev
+  double dt;
+  double a, b;
+  int combine;           // 0: Uout = Uin + dt*L; 1: a*Un + b*(Uin + dt*L)
+  int gather;            // 1: halo from neighbour interiors; 0: from Uin's own guard cells
+  int kchunk, nchunks;   // z planes per CTA (3-D), CTAs per block
+  Layout lay;
+  Eos eos;
+  unsigned long long* smax_acc;     // if non-null: max signal-speed sum of Uout (bit pattern)
+  unsigned long long* floor_count;  // floor applications on interior cells
+};
+
+cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
+size_t stage_smem_bytes(int nx);
+cudaError_t stage_prepare(int nx, int ndim);  // opt-in to the dynamic shared memory size
+
+struct FillArgs {
+  double* U;
+  const int* nbr;        // [nblocks][3^ndim]
+  const int* face_nbr;   // [nblocks][6]
+  Layout lay;
+};
+cudaError_t launch_fill(const FillArgs& a, cudaStream_t s);
+
+struct DtArgs {
+  const double* U;
+  const double* inv_dx;
+  Layout lay;
+  Eos eos;
+  unsigned long long* smax_acc;
+};
+cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s);
+cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_out, double* hist,
+                               cudaStream_t s);
+
+cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
+                         cudaStream_t s);
+
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
+
+}  // namespace gbh

@@ -1,0 +1,339 @@
+// gbh_stage.cu -- the fused RK-stage kernel (one launch per stage).
+//
+// One stage of the non-telescoping SSP-RK method (Sec. 4.2): for every block,
+// the intra-stage calculations calcLims -> calcFlux -> updSoln -> calcEos
+// (Alg. "Intra stage calculations for Spark") followed by the Shu-Osher RK
+// combine Uout = a*Un + b*(Uin + dt*L(Uin)); initSoln (Alg. "Block
+// initializations for Spark") is the caller keeping Un.  The guard-cell fill
+// that precedes every stage is fused: the halo cells the face stencil reads
+// (a 2-deep slab across each face) are gathered straight from the neighbour
+// blocks' interiors through the face-neighbour table, or, at an outflow
+// domain edge, from the nearest interior cell.
+//
+// Work decomposition (one CTA = one block, or a z-chunk of one, N*N threads):
+//  - the CTA marches through the z planes of its chunk; thread (i, j) keeps
+//    the primitive variables of its own column at planes k, k+1 and the z
+//    face state / z flux of the previous plane in registers, so each z face
+//    is reconstructed and solved exactly once;
+//  - per plane, the primitives of the plane plus its 2-deep x/y rims go to
+//    shared memory; MC face states of the (N+2)*N x-slope cells and
+//    N*(N+2) y-slope cells, then the (N+1)*N x faces and N*(N+1) y faces are
+//    processed as flat work lists over all threads (full warps);
+//  - the update of the plane reads its x/y fluxes from shared memory and its
+//    z fluxes from registers and writes Uout.
+// Optional epilogue (second RK stage): max over the CTA of the CFL signal
+// speed of Uout, one 64-bit atomicMax per CTA on the bit pattern of the
+// non-negative double.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbh_device.cuh"
+#include "gbh_internal.h"
+
+namespace gbh {
+namespace {
+
+// Offset (in doubles, relative to the array base) of cell (i, j, k) of block
+// b, given in interior coordinates that may lie outside the block in at most
+// one dimension by at most 2 cells.  In gather mode such a cell is read from
+// the face neighbour's interior, or, at an outflow edge (GBH_BC_OUTFLOW), from
+// the nearest interior cell of b; in guard mode from b's own guard cells.
+template <int N>
+__device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int i, int j, int k) {
+  const Layout& L = a.lay;
+  int blk = b;
+  if (a.gather) {
+    int f = -1;
+    if (i < 0) f = FACE_XM;
+    else if (i >= N) f = FACE_XP;
+    else if (j < 0) f = FACE_YM;
+    else if (j >= N) f = FACE_YP;
+    else if (k < 0) f = FACE_ZM;
+    else if (k >= L.nz) f = FACE_ZP;
+    if (f >= 0) {
+      const int nb = __ldg(a.face_nbr + 6 * b + f);
+      if (nb >= 0) {
+        blk = nb;
+        switch (f) {
+          case FACE_XM: i += N; break;
+          case FACE_XP: i -= N; break;
+          case FACE_YM: j += N; break;
+          case FACE_YP: j -= N; break;
+          case FACE_ZM: k += L.nz; break;
+          default: k -= L.nz; break;
+        }
+      } else {
+        switch (f) {
+          case FACE_XM: i = 0; break;
+          case FACE_XP: i = N - 1; break;
+          case FACE_YM: j = 0; break;
+          case FACE_YP: j = N - 1; break;
+          case FACE_ZM: k = 0; break;
+          default: k = L.nz - 1; break;
+        }
+      }
+    }
+  }
+  return (long long)blk * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+}
+
+template <int N>
+__device__ __forceinline__ int load_prim(const StageArgs& a, int b, int i, int j, int k, double W[5]) {
+  const long long o = cell_offset<N>(a, b, i, j, k);
+  double U[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * a.lay.vstride);
+  return cons_to_prim(U, W, a.eos);
+}
+
+template <int N, bool DIM3>
+__global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
+  constexpr int NT = N * N;
+  constexpr int P = N + 4;                  // plane with 2-deep x/y rims
+  constexpr int QX = N * (N + 2);           // x-slope cells of a plane
+  constexpr int FX = N * (N + 1);           // x faces of a plane
+  extern __shared__ double smem[];
+  double* sW = smem;                        // [5][P][P] primitives of the plane
+  double* sQx = sW + 5 * P * P;             // [2][5][N][N+2] x face states (minus, plus)
+  double* sQy = sQx + 2 * 5 * QX;           // [2][5][N+2][N] y face states
+  double* sFx = sQy + 2 * 5 * QX;           // [5][N][N+1] x fluxes
+  double* sFy = sFx + 5 * FX;               // [5][N+1][N] y fluxes
+  __shared__ double s_red[NT];
+
+  const Layout& L = a.lay;
+  const int tid = threadIdx.x;
+  const int tx = tid % N, ty = tid / N;
+  const int b = blockIdx.x / a.nchunks;
+  const int chunk = blockIdx.x - b * a.nchunks;
+  const int k0 = DIM3 ? chunk * a.kchunk : 0;
+  const int k1 = DIM3 ? min(L.nz, k0 + a.kchunk) : 1;
+  const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+  const double idx = __ldg(a.inv_dx + 3 * b), idy = __ldg(a.inv_dx + 3 * b + 1);
+  const double idz = DIM3 ? __ldg(a.inv_dx + 3 * b + 2) : 0.0;
+  const Eos& e = a.eos;
+
+  int hits = 0;
+  double smax = 0.0;
+  double W0[5], Wp1[5], qpz[5], Fzm[5];     // column state carried along z
+
+  if (DIM3) {
+    double Wm2[5], Wm1[5], qpm1[5], qm0[5];
+    load_prim<N>(a, b, tx, ty, k0 - 2, Wm2);
+    load_prim<N>(a, b, tx, ty, k0 - 1, Wm1);
+    hits += load_prim<N>(a, b, tx, ty, k0, W0);
+    const int h1 = load_prim<N>(a, b, tx, ty, k0 + 1, Wp1);
+    if (k0 + 1 < k1) hits += h1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qpm1[v] = Wm1[v] + mc_half_slope(Wm2[v], Wm1[v], W0[v]);
+      const double h = mc_half_slope(Wm1[v], W0[v], Wp1[v]);
+      qm0[v] = W0[v] - h;
+      qpz[v] = W0[v] + h;
+    }
+    // z face k0 - 1/2; rotated order (rho, w, u, v, p)
+    double wl[5] = {qpm1[0], qpm1[3], qpm1[1], qpm1[2], qpm1[4]};
+    double wr[5] = {qm0[0], qm0[3], qm0[1], qm0[2], qm0[4]};
+    double f[5];
+    hllc_flux(wl, wr, e, f);
+    Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
+  } else {
+    hits += load_prim<N>(a, b, tx, ty, 0, W0);
+  }
+
+  for (int k = k0; k < k1; ++k) {
+    double Fzp[5], Wn[5], qpn[5];
+    if (DIM3) {
+      // own column: primitives at k+2, face states of k+1, z flux at k + 1/2
+      const int hn = load_prim<N>(a, b, tx, ty, k + 2, Wn);
+      if (k + 2 < k1) hits += hn;
+      double qmz[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double h = mc_half_slope(W0[v], Wp1[v], Wn[v]);
+        qmz[v] = Wp1[v] - h;
+        qpn[v] = Wp1[v] + h;
+      }
+      double wl[5] = {qpz[0], qpz[3], qpz[1], qpz[2], qpz[4]};
+      double wr[5] = {qmz[0], qmz[3], qmz[1], qmz[2], qmz[4]};
+      double f[5];
+      hllc_flux(wl, wr, e, f);
+      Fzp[0] = f[0]; Fzp[1] = f[2]; Fzp[2] = f[3]; Fzp[3] = f[1]; Fzp[4] = f[4];
+    }
+
+    // (A) primitives of plane k and its 2-deep x/y rims -> shared memory
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sW[(v * P + ty + 2) * P + tx + 2] = W0[v];
+    for (int r = tid; r < 8 * N; r += NT) {
+      const int q = r / (2 * N), t = r - q * 2 * N;
+      const int depth = t / N, pos = t - depth * N;
+      int i, j;
+      if (q == 0) { i = -1 - depth; j = pos; }
+      else if (q == 1) { i = N + depth; j = pos; }
+      else if (q == 2) { i = pos; j = -1 - depth; }
+      else { i = pos; j = N + depth; }
+      double W[5];
+      load_prim<N>(a, b, i, j, k, W);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sW[(v * P + j + 2) * P + i + 2] = W[v];
+    }
+    __syncthreads();
+
+    // (B) MC face states: x-slope cells i in [-1, N], y-slope cells j in [-1, N]
+    for (int s = tid; s < 2 * QX; s += NT) {
+      if (s < QX) {
+        const int ii = s % (N + 2), j = s / (N + 2);   // slope cell i = ii - 1
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double* row = sW + (v * P + j + 2) * P + ii;
+          const double q0 = row[1];
+          const double h = mc_half_slope(row[0], q0, row[2]);
+          sQx[(v * N + j) * (N + 2) + ii] = q0 - h;
+          sQx[((5 + v) * N + j) * (N + 2) + ii] = q0 + h;
+        }
+      } else {
+        const int s2 = s - QX;
+        const int i = s2 % N, jj = s2 / N;             // slope cell j = jj - 1
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double* col = sW + (v * P + jj) * P + i + 2;
+          const double q0 = col[P];
+          const double h = mc_half_slope(col[0], q0, col[2 * P]);
+          sQy[(v * (N + 2) + jj) * N + i] = q0 - h;
+          sQy[((5 + v) * (N + 2) + jj) * N + i] = q0 + h;
+        }
+      }
+    }
+    __syncthreads();
+
+    // (C) HLLC on the x faces (i - 1/2, i in [0, N]) and y faces (j - 1/2, j in [0, N])
+    for (int f = tid; f < 2 * FX; f += NT) {
+      const bool xf = f < FX;
+      int i, j;
+      const double *ql, *qr;       // minus/plus state arrays, var stride vs
+      int vs, ol, orr;
+      if (xf) {
+        i = f % (N + 1); j = f / (N + 1);
+        vs = N * (N + 2);
+        ol = 5 * vs + j * (N + 2) + i;        // plus state of cell i-1 (slot i)
+        orr = j * (N + 2) + i + 1;            // minus state of cell i (slot i+1)
+        ql = sQx; qr = sQx;
+      } else {
+        const int f2 = f - FX;
+        i = f2 % N; j = f2 / N;
+        vs = (N + 2) * N;
+        ol = 5 * vs + j * N + i;              // plus state of cell j-1 (slot j)
+        orr = (j + 1) * N + i;                // minus state of cell j (slot j+1)
+        ql = sQy; qr = sQy;
+      }
+      const int vn = xf ? 1 : 2, vt = xf ? 2 : 1;   // normal and first tangential momentum
+      double wl[5] = {ql[ol], ql[ol + vn * vs], ql[ol + vt * vs], ql[ol + 3 * vs], ql[ol + 4 * vs]};
+      double wr[5] = {qr[orr], qr[orr + vn * vs], qr[orr + vt * vs], qr[orr + 3 * vs], qr[orr + 4 * vs]};
+      double F[5];
+      hllc_flux(wl, wr, e, F);
+      if (xf) {
+        double* o = sFx + j * (N + 1) + i;
+        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+      } else {
+        double* o = sFy + j * N + i;
+        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+      }
+    }
+    __syncthreads();
+
+    // (D) updSoln + RK combine for cell (tx, ty, k)
+    const long long base =
+        (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (ty + L.g)) * L.nxp + (tx + L.g);
+    double out[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double fx = sFx[(v * N + ty) * (N + 1) + tx + 1] - sFx[(v * N + ty) * (N + 1) + tx];
+      const double fy = sFy[(v * (N + 1) + ty + 1) * N + tx] - sFy[(v * (N + 1) + ty) * N + tx];
+      double Lv = -fx * idx;
+      Lv = Lv - fy * idy;
+      if (DIM3) Lv = Lv - (Fzp[v] - Fzm[v]) * idz;
+      const long long o = base + v * L.vstride;
+      const double uin = __ldg(a.Uin + o);
+      out[v] = a.combine ? a.a * a.Un[o] + a.b * (uin + dt * Lv) : uin + dt * Lv;
+      a.Uout[o] = out[v];
+    }
+    if (a.smax_acc) {
+      double W[5];
+      cons_to_prim(out, W, e);
+      smax = fmax(smax, signal_speed(W, e, idx, idy, idz, DIM3));
+    }
+
+    if (DIM3) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        W0[v] = Wp1[v];
+        Wp1[v] = Wn[v];
+        qpz[v] = qpn[v];
+        Fzm[v] = Fzp[v];
+      }
+    }
+  }
+
+  if (hits) atomicAdd(a.floor_count, (unsigned long long)hits);
+  if (a.smax_acc) {
+    s_red[tid] = smax;
+    __syncthreads();
+#pragma unroll
+    for (int w = NT / 2; w > 0; w >>= 1) {
+      if (tid < w) s_red[tid] = fmax(s_red[tid], s_red[tid + w]);
+      __syncthreads();
+    }
+    if (tid == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(s_red[0]));
+  }
+}
+
+template <int N>
+size_t smem_for() {
+  constexpr int P = N + 4;
+  return sizeof(double) * (5 * P * P + 4 * 5 * N * (N + 2) + 2 * 5 * N * (N + 1));
+}
+
+template <int N, bool D3>
+cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)a.lay.nblocks * (unsigned)a.nchunks;
+  stage_kernel<N, D3><<<grid, N * N, smem_for<N>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, bool D3>
+cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(stage_kernel<N, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_for<N>());
+}
+
+}  // namespace
+
+size_t stage_smem_bytes(int nx) {
+  switch (nx) {
+    case 4: return smem_for<4>();
+    case 8: return smem_for<8>();
+    case 16: return smem_for<16>();
+    default: return 0;
+  }
+}
+
+cudaError_t stage_prepare(int nx, int ndim) {
+  const bool d3 = ndim == 3;
+  switch (nx) {
+    case 4: return d3 ? prepare_t<4, true>() : prepare_t<4, false>();
+    case 8: return d3 ? prepare_t<8, true>() : prepare_t<8, false>();
+    case 16: return d3 ? prepare_t<16, true>() : prepare_t<16, false>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) {
+  const bool d3 = a.lay.ndim == 3;
+  switch (a.lay.nx) {
+    case 4: return d3 ? launch_t<4, true>(a, s) : launch_t<4, false>(a, s);
+    case 8: return d3 ? launch_t<8, true>(a, s) : launch_t<8, false>(a, s);
+    case 16: return d3 ? launch_t<16, true>(a, s) : launch_t<16, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gbh

@@ -1,0 +1,188 @@
+"""Thin Python binding of libgbhydro.so for PyTorch CUDA tensors.
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  Tensors are float64, C-contiguous, on the context's CUDA
+device, shaped (nblocks, 5, nz_pad, ny_pad, nx_pad); work is enqueued on
+torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _abi
+from .grid import neighbour_table, uniform_widths
+
+
+def _stream_handle() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Hydro:
+    """One block-structured Euler problem bound to the current CUDA device.
+
+    Parameters mirror ``gbh_params``: block sizes, guard width, gamma, CFL
+    number, floors, and either an explicit neighbour table / cell widths or a
+    rectangular lattice (``nb`` blocks per dimension, ``periodic`` flags,
+    domain ``extent``) from which they are built.
+    """
+
+    def __init__(self, ndim: int, n: Sequence[int], nguard: int = 4, *,
+                 nb: Optional[Sequence[int]] = None, periodic=(False, False, False),
+                 extent=(1.0, 1.0, 1.0), nbr: Optional[np.ndarray] = None,
+                 dx: Optional[np.ndarray] = None, gamma: float = 1.4, cfl: float = 0.8,
+                 small_rho: float = 1e-12, small_p: float = 1e-14):
+        self.lib = _abi.load()
+        self.ndim = int(ndim)
+        nx, ny, nz = (int(n[0]), int(n[1]), int(n[2]) if ndim == 3 else 1)
+        if nbr is None:
+            if nb is None:
+                raise ValueError("give either nbr/dx tables or a lattice (nb)")
+            nbr = neighbour_table(ndim, nb, periodic)
+            nblk = nbr.shape[0]
+            cells = (nb[0] * nx, nb[1] * ny, (nb[2] if ndim == 3 else 1) * nz)
+            dx = uniform_widths(nblk, [extent[d] / cells[d] for d in range(3)])
+        self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        self.dx = np.ascontiguousarray(dx, dtype=np.float64)
+        self.nblocks = int(self.nbr.shape[0])
+        self.n = (nx, ny, nz)
+        self.nguard = int(nguard)
+        gz = self.nguard if ndim == 3 else 0
+        self.shape = (self.nblocks, 5, nz + 2 * gz, ny + 2 * self.nguard, nx + 2 * self.nguard)
+        p = _abi.GbhParams()
+        p.ndim, p.nxb, p.nyb, p.nzb = self.ndim, nx, ny, nz
+        p.nguard, p.nblocks = self.nguard, self.nblocks
+        p.gamma, p.cfl, p.small_rho, p.small_p = gamma, cfl, small_rho, small_p
+        p.nbr = self.nbr.ctypes.data_as(C.POINTER(C.c_int32))
+        p.dx = self.dx.ctypes.data_as(C.POINTER(C.c_double))
+        ctx = C.c_void_p()
+        rc = self.lib.gbh_create(C.byref(p), C.byref(ctx))
+        if rc != 0:
+            raise _abi.GbhError(rc, self.lib.gbh_last_error(None).decode())
+        self.ctx = ctx
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_lattice(cls, lat, **kw):
+        """Build from any object with ndim, nb, n, ng, bc, extent (e.g. workloads.Lattice)."""
+        return cls(lat.ndim, lat.n, lat.ng, nb=lat.nb,
+                   periodic=tuple(b == "periodic" for b in lat.bc), extent=lat.extent, **kw)
+
+    # -- helpers -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.gbh_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise _abi.GbhError(rc, self.lib.gbh_last_error(self.ctx).decode())
+
+    def _state(self, U: torch.Tensor, name="U") -> int:
+        if not isinstance(U, torch.Tensor) or U.dtype != torch.float64 or not U.is_cuda:
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        if tuple(U.shape) != self.shape or not U.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {self.shape}, got {tuple(U.shape)}")
+        return U.data_ptr()
+
+    def _scalar(self, t: torch.Tensor, name="dt") -> int:
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or t.numel() < 1:
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        return t.data_ptr()
+
+    def empty_state(self) -> torch.Tensor:
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    # -- the ABI -----------------------------------------------------------
+    def fill_guardcells(self, U):
+        self._check(self.lib.hydro_fill_guardcells(self.ctx, self._state(U), _stream_handle()))
+        return U
+
+    def compute_dt(self, U, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device="cuda")
+        self._check(self.lib.hydro_compute_dt(self.ctx, self._state(U), self._scalar(out), _stream_handle()))
+        return out
+
+    def stage(self, Uin, Un, Uout, dt: float, a: float, b: float, guarded: bool = False):
+        fn = self.lib.hydro_stage_guarded if guarded else self.lib.hydro_stage
+        un = self._state(Un, "Un") if Un is not None else None
+        self._check(fn(self.ctx, self._state(Uin, "Uin"), un, self._state(Uout, "Uout"),
+                       float(dt), float(a), float(b), _stream_handle()))
+        return Uout
+
+    def step(self, U, dt: float):
+        self._check(self.lib.hydro_step(self.ctx, self._state(U), float(dt), _stream_handle()))
+        return U
+
+    def step_cfl(self, U, dt_dev: torch.Tensor):
+        self._check(self.lib.hydro_step_cfl(self.ctx, self._state(U), self._scalar(dt_dev), _stream_handle()))
+        return U
+
+    def advance(self, U, nsteps: int, dt_dev: torch.Tensor, dt_hist: Optional[torch.Tensor] = None):
+        h = None
+        if dt_hist is not None:
+            if dt_hist.numel() < nsteps:
+                raise ValueError("dt_hist is too short")
+            h = self._scalar(dt_hist, "dt_hist")
+        self._check(self.lib.hydro_advance(self.ctx, self._state(U), int(nsteps), self._scalar(dt_dev), h,
+                                           _stream_handle()))
+        return U
+
+    def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
+        """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
+        if isinstance(U_host, torch.Tensor):
+            if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous():
+                raise TypeError("U_host must be a contiguous float64 CPU tensor")
+            ptr = U_host.data_ptr()
+        else:
+            if U_host.dtype != np.float64 or not U_host.flags.c_contiguous:
+                raise TypeError("U_host must be a C-contiguous float64 array")
+            ptr = U_host.ctypes.data
+        if tuple(U_host.shape) != self.shape:
+            raise ValueError(f"U_host must have shape {self.shape}")
+        h = None
+        if dt_hist_host is not None:
+            h = dt_hist_host.ctypes.data if isinstance(dt_hist_host, np.ndarray) else dt_hist_host.data_ptr()
+        self._check(self.lib.hydro_advance_host(self.ctx, ptr, int(nsteps), h, _stream_handle()))
+        return U_host
+
+    def check_state(self, U) -> int:
+        n = C.c_longlong(0)
+        rc = self.lib.hydro_check_state(self.ctx, self._state(U), C.byref(n), _stream_handle())
+        if rc not in (0, _abi.GBH_ERR_UNPHYSICAL):
+            self._check(rc)
+        return int(n.value)
+
+    def floor_hits(self) -> int:
+        n = C.c_longlong(0)
+        self._check(self.lib.hydro_floor_hits(self.ctx, C.byref(n), _stream_handle()))
+        return int(n.value)
+
+    def set_kernel_timing(self, on: bool):
+        self._check(self.lib.gbh_set_kernel_timing(self.ctx, 1 if on else 0))
+
+    def stage_kernel_time(self):
+        ms, n = C.c_double(0), C.c_longlong(0)
+        self._check(self.lib.gbh_stage_kernel_time(self.ctx, C.byref(ms), C.byref(n), _stream_handle()))
+        return float(ms.value), int(n.value)
+
+
+def fp64_probe(blocks: int, threads: int, iters: int, out: torch.Tensor):
+    lib = _abi.load()
+    rc = lib.gbh_fp64_probe(int(blocks), int(threads), int(iters), out.data_ptr(), _stream_handle())
+    if rc != 0:
+        raise _abi.GbhError(rc, lib.gbh_last_error(None).decode())
+
+
+def sm_count() -> int:
+    return int(_abi.load().gbh_device_sm_count())

@@ -1,0 +1,140 @@
+"""CPU checks of the C ABI library: it builds, loads, exports every symbol the
+header declares, and rejects invalid parameters before touching the GPU; plus
+the host-side neighbour-table builder."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbhydro.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_03378_gb300 import build, _abi
+    build.build()
+    return _abi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+def test_header_lists_the_abi():
+    names = declared_functions()
+    for required in ("hydro_fill_guardcells", "hydro_compute_dt", "hydro_step", "gbh_create"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2401_03378_gb300 import _abi
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in declared_functions():
+        assert name in exported, name
+        assert name in _abi.SIGNATURES, f"binding lacks {name}"
+
+
+def _params(**over):
+    from paper_2401_03378_gb300 import _abi, neighbour_table, uniform_widths
+    nbr = neighbour_table(3, (2, 2, 2), (False, False, False))
+    dx = uniform_widths(8, (0.1, 0.1, 0.1))
+    p = _abi.GbhParams()
+    p.ndim, p.nxb, p.nyb, p.nzb, p.nguard, p.nblocks = 3, 16, 16, 16, 4, 8
+    p.gamma, p.cfl, p.small_rho, p.small_p = 1.4, 0.8, 1e-12, 1e-14
+    for k, v in over.items():
+        if k in ("nbr", "dx"):
+            continue
+        setattr(p, k, v)
+    nbr = over.get("nbr", nbr)
+    dx = over.get("dx", dx)
+    keep = (np.ascontiguousarray(nbr, dtype=np.int32), np.ascontiguousarray(dx))
+    p.nbr = keep[0].ctypes.data_as(C.POINTER(C.c_int32))
+    p.dx = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+    return p, keep
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(ndim=4), -1),
+    (dict(nguard=1), -1),
+    (dict(nguard=17), -1),
+    (dict(gamma=1.0), -1),
+    (dict(cfl=0.0), -1),
+    (dict(nblocks=0), -1),
+    (dict(nzb=1), -1),
+    (dict(nxb=12, nyb=12), -5),
+    (dict(nxb=16, nyb=8, nguard=4), -5),
+])
+def test_create_rejects_invalid_params_without_gpu(lib, over, code):
+    p, keep = _params(**over)
+    ctx = C.c_void_p()
+    assert lib.gbh_create(C.byref(p), C.byref(ctx)) == code
+    assert ctx.value is None
+    assert lib.gbh_last_error(None)
+
+
+def test_create_rejects_bad_tables_without_gpu(lib):
+    from paper_2401_03378_gb300 import neighbour_table
+    nbr = neighbour_table(3, (2, 2, 2), (False, False, False)).copy()
+    nbr[3, 5] = 99
+    p, keep = _params(nbr=nbr)
+    ctx = C.c_void_p()
+    assert lib.gbh_create(C.byref(p), C.byref(ctx)) == -1
+    nbr = neighbour_table(3, (2, 2, 2), (False, False, False)).copy()
+    nbr[2, 13] = 1
+    p, keep = _params(nbr=nbr)
+    assert lib.gbh_create(C.byref(p), C.byref(ctx)) == -1
+    dx = np.full((8, 3), 0.1)
+    dx[4, 1] = -0.1
+    p, keep = _params(dx=dx)
+    assert lib.gbh_create(C.byref(p), C.byref(ctx)) == -1
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.hydro_step(None, None, 1.0, None) == -1
+    assert lib.gbh_destroy(None) == 0
+
+
+@pytest.mark.parametrize("ndim,nb,per", [
+    (2, (3, 2, 1), (False, False, False)),
+    (2, (4, 3, 1), (True, False, False)),
+    (3, (3, 2, 2), (False, True, True)),
+    (3, (1, 2, 3), (True, True, True)),
+])
+def test_neighbour_table_geometry(ndim, nb, per):
+    """Every entry is the block whose lattice coordinates differ by the offset
+    (wrapped when periodic); the table is symmetric under offset negation."""
+    from paper_2401_03378_gb300 import neighbour_table
+    tab = neighbour_table(ndim, nb, per)
+    nbz = nb[2] if ndim == 3 else 1
+    nblk = nb[0] * nb[1] * nbz
+    assert tab.shape == (nblk, 27 if ndim == 3 else 9)
+    offs = [(ox, oy, oz) for oz in ((-1, 0, 1) if ndim == 3 else (0,)) for oy in (-1, 0, 1) for ox in (-1, 0, 1)]
+    coords = [(b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])) for b in range(nblk)]
+    dims = (nb[0], nb[1], nbz)
+    for b in range(nblk):
+        for e, o in enumerate(offs):
+            target = []
+            inside = True
+            for d in range(3):
+                x = coords[b][d] + o[d]
+                if not 0 <= x < dims[d]:
+                    if per[d]:
+                        x %= dims[d]
+                    else:
+                        inside = False
+                target.append(x)
+            if inside:
+                assert coords[tab[b, e]] == tuple(target)
+                back = offs.index(tuple(-x for x in o))
+                assert tab[tab[b, e], back] == b or any(
+                    dims[d] <= 2 and per[d] for d in range(3))
+            else:
+                assert tab[b, e] == -1

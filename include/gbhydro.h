@@ -160,6 +160,13 @@ int gbh_stage_kernel_time(gbh_ctx *ctx, double *ms_host, long long *launches_hos
  * FP64 flops executed = 16 * iters * blocks * threads. */
 int gbh_fp64_probe(int blocks, int threads, int iters, double *out_dev, void *stream);
 
+/* Self-test of the FP64 reciprocal / reciprocal-square-root / square-root
+ * building blocks the kernels use (hardware seed + one refinement step):
+ * for n positive, normal, finite DEVICE doubles x_dev writes 6*n DEVICE
+ * doubles out_dev = [refined 1/x | IEEE 1/x | refined 1/sqrt(x) |
+ * IEEE 1/sqrt(x) | refined sqrt(x) | IEEE sqrt(x)].  Not part of the method. */
+int gbh_fastmath_selftest(const double *x_dev, double *out_dev, long long n, void *stream);
+
 /* Number of SMs of the current device (for sizing probes), or a negative error. */
 int gbh_device_sm_count(void);
 

@@ -194,6 +194,7 @@ int gbh_create(const gbh_params* p, gbh_ctx** out) {
   c->eos.gamma = p->gamma;
   c->eos.gm1 = p->gamma - 1.0;
   c->eos.inv_gm1 = 1.0 / (p->gamma - 1.0);
+  c->eos.g_gm1 = p->gamma / (p->gamma - 1.0);
   c->eos.small_rho = p->small_rho;
   c->eos.small_p = p->small_p;
   c->cfl = p->cfl;
@@ -437,6 +438,13 @@ int gbh_fp64_probe(int blocks, int threads, int iters, double* out_dev, void* st
     return set_err(nullptr, GBH_ERR_INVAL, "invalid probe arguments");
   cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, out_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "probe launch: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
+int gbh_fastmath_selftest(const double* x_dev, double* out_dev, long long n, void* stream) {
+  if (!x_dev || !out_dev || n < 1) return set_err(nullptr, GBH_ERR_INVAL, "invalid self-test arguments");
+  cudaError_t e = gbh::launch_fastmath_selftest(x_dev, out_dev, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "self-test launch: %s", cudaGetErrorString(e));
   return GBH_OK;
 }
 

@@ -150,6 +150,20 @@ __global__ void fp64_probe_kernel(int iters, double* out) {
   out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// Self-test of the refined reciprocal / square roots: out[6][n] =
+// rcp_nr, 1.0/x, rsqrt_nr, 1.0/sqrt(x), sqrt_nr, sqrt(x).
+__global__ void fastmath_selftest_kernel(const double* x, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[i] = rcp_nr(v);
+    out[n + i] = 1.0 / v;
+    out[2 * n + i] = rsqrt_nr(v);
+    out[3 * n + i] = 1.0 / sqrt(v);
+    out[4 * n + i] = sqrt_nr(v);
+    out[5 * n + i] = sqrt(v);
+  }
+}
+
 int grid_for(long long work, int threads) {
   long long g = (work + threads - 1) / threads;
   if (g > 152LL * 16) g = 152LL * 16;
@@ -181,6 +195,11 @@ cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long lon
                          cudaStream_t s) {
   const long long work = (long long)lay.nblocks * lay.nx * lay.ny * lay.nz;
   check_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(U, lay, eos, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s) {
+  fastmath_selftest_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(x, out, n);
   return cudaGetLastError();
 }
 

@@ -7,46 +7,64 @@
 // ideal-gas EOS with floors, MC-limited piecewise-linear reconstruction of
 // primitive variables, and the HLLC flux (Toro's star state, Einfeldt /
 // Roe-average wave-speed bounds).
+//
+// The formulas are arranged to minimise FP64 instructions (the kernel is
+// bound by the FP64 pipe): one reciprocal per primitive conversion, one
+// reciprocal square root per face side giving both sqrt(rho) and 1/rho, the
+// HLLC star state reduced to a single reciprocal, and every comparison done
+// on bit patterns (gbh_fastmath.cuh).  Results agree with the plain
+// formulas to rounding.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gbh_fastmath.cuh"
 #include "gbh_internal.h"
 
 namespace gbh {
 
-// calcEos role: conserved (rho, mx, my, mz, E) -> primitive (rho, u, v, w, p).
-// Floors rho at small_rho and p at small_p; returns 1 when a floor applied.
+// calcEos role: conserved (rho, mx, my, mz, E) -> primitive (rho, u, v, w, p),
+// p = (gamma-1) (E - (mx u + my v + mz w)/2).  Floors rho at small_rho and p
+// at small_p; returns 1 when a floor applied.
 __device__ __forceinline__ int cons_to_prim(const double U[5], double W[5], const Eos& e) {
   int hit = 0;
   double rho = U[0];
-  if (rho < e.small_rho) { rho = e.small_rho; hit = 1; }
-  const double ir = 1.0 / rho;
+  if (less_d(rho, e.small_rho)) { rho = e.small_rho; hit = 1; }
+  const double ir = rcp_nr(rho);
   const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-  const double ek = 0.5 * (U[1] * u + U[2] * v + U[3] * w);
-  double p = e.gm1 * (U[4] - ek);
-  if (p < e.small_p) { p = e.small_p; hit = 1; }
+  const double m2 = fma(U[3], w, fma(U[2], v, U[1] * u));
+  double p = e.gm1 * fma(-0.5, m2, U[4]);
+  if (less_d(p, e.small_p)) { p = e.small_p; hit = 1; }
   W[0] = rho; W[1] = u; W[2] = v; W[3] = w; W[4] = p;
   return hit;
 }
 
 // calcLims role: half of the MC-limited slope at q0,
 //   sigma/2 = sign(dp) * min(|dm+dp|/4, |dm|, |dp|) if dm, dp have the same strict sign, else 0,
-// so that the face values are q0 -/+ sigma/2.
+// so that the face values are q0 -/+ sigma/2.  Sign test and minimum on bit
+// patterns (magnitudes of doubles order like unsigned integers).
 __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp) {
   const double dm = q0 - qm;
   const double dp = qp - q0;
-  const double h = fmin(0.25 * fabs(dm + dp), fmin(fabs(dm), fabs(dp)));
-  return (dm * dp > 0.0) ? copysign(h, dp) : 0.0;
+  const double s4 = 0.25 * (dm + dp);
+  const long long bm = dbits(dm), bp = dbits(dp);
+  const unsigned long long mask = 0x7fffffffffffffffULL;
+  const unsigned long long am = (unsigned long long)bm & mask, ap = (unsigned long long)bp & mask;
+  const unsigned long long as = (unsigned long long)dbits(s4) & mask;
+  unsigned long long m = am < ap ? am : ap;
+  m = as < m ? as : m;
+  const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
+  return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
 }
 
-// Signal-speed sum of one cell for the CFL rule.
+// Signal-speed sum of one cell for the CFL rule (W from cons_to_prim).
 __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, double idx,
                                                double idy, double idz, bool dim3) {
-  const double c = sqrt(e.gamma * W[4] / W[0]);
-  double s = (fabs(W[1]) + c) * idx + (fabs(W[2]) + c) * idy;
-  if (dim3) s += (fabs(W[3]) + c) * idz;
+  const double c = sqrt_nr(e.gamma * W[4] * rcp_nr(W[0]));
+  double s = (fabs(W[1]) + c) * idx;
+  s = fma(fabs(W[2]) + c, idy, s);
+  if (dim3) s = fma(fabs(W[3]) + c, idz, s);
   return s;
 }
 
@@ -54,53 +72,62 @@ __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, 
 // component of the rotated states WL (low side) and WR (high side):
 // W = (rho, u_n, u_t1, u_t2, p).  F is returned in the same rotated order.
 //
-// Region choice follows the sign of the contact speed S*: side K = L when
-// S* >= 0, else R.  The flux is F_K + S_K (U*_K - U_K), with the correction
-// switched off (coefficient exactly 0) when the whole fan lies on one side
-// (S_L >= 0 or S_R <= 0), which then returns F_K exactly.
+// Wave speeds: S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~)
+// with Roe averages (sqrt(rho) weights); contact speed
+// S* = (p_R - p_L + m_L u_L - m_R u_R) / (m_L - m_R), m_K = rho_K (S_K - u_K).
+// Side K = L when S* >= 0, else R.  With delta = (S* - u_K) / (S_K - S*),
+// Toro's star state satisfies
+//   U*_K - U_K = delta [rho_K, rho_K S_K, rho_K v_K, rho_K w_K, h_K + m_K S*]
+// (h = E + p), so F = F_K + S_K (U*_K - U_K) becomes, with g = S_K delta,
+//   F0 = rho_K u_K + g rho_K,  F1 = rho_K u_K^2 + p_K + g rho_K S_K,
+//   F2 = v_K F0,  F3 = w_K F0,  F4 = u_K h_K + g (h_K + m_K S*).
+// When the whole fan lies on one side (S_L >= 0, or S_R <= 0) g = 0 and
+// F = F_K.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
 
-  const double EL = pL * e.inv_gm1 + 0.5 * rL * (uL * uL + vL * vL + wL * wL);
-  const double ER = pR * e.inv_gm1 + 0.5 * rR * (uR * uR + vR * vR + wR * wR);
-  const double cL = sqrt(e.gamma * pL / rL);
-  const double cR = sqrt(e.gamma * pR / rR);
+  const double aL = rsqrt_nr(rL), aR = rsqrt_nr(rR);    // 1/sqrt(rho)
+  const double sL = rL * aL, sR = rR * aR;              // sqrt(rho)
+  const double iL = aL * aL, iR = aR * aR;              // 1/rho
 
-  // Roe averages (sqrt(rho) weights)
-  const double sL = sqrt(rL), sR = sqrt(rR);
-  const double inv = 1.0 / (sL + sR);
-  const double HL = (EL + pL) / rL, HR = (ER + pR) / rR;
-  const double ut = (sL * uL + sR * uR) * inv;
-  const double vt = (sL * vL + sR * vR) * inv;
-  const double wt = (sL * wL + sR * wR) * inv;
-  const double Ht = (sL * HL + sR * HR) * inv;
-  const double ct = sqrt(e.gm1 * (Ht - 0.5 * (ut * ut + vt * vt + wt * wt)));
+  const double kL = fma(wL, wL, fma(vL, vL, uL * uL));
+  const double kR = fma(wR, wR, fma(vR, vR, uR * uR));
+  const double hL = fma(0.5 * rL, kL, e.g_gm1 * pL);    // E + p
+  const double hR = fma(0.5 * rR, kR, e.g_gm1 * pR);
+  const double cL = sqrt_nr(e.gamma * pL * iL);
+  const double cR = sqrt_nr(e.gamma * pR * iR);
 
-  const double SL = fmin(uL - cL, ut - ct);
-  const double SR = fmax(uR + cR, ut + ct);
+  const double w = rcp_nr(sL + sR);
+  const double wl = sL * w, wr = sR * w;
+  const double ut = fma(wl, uL, wr * uR);
+  const double vt = fma(wl, vL, wr * vR);
+  const double wt = fma(wl, wL, wr * wR);
+  const double Ht = fma(hL, aL, hR * aR) * w;           // sqrt(rho) H = h / sqrt(rho)
+  const double kt = fma(wt, wt, fma(vt, vt, ut * ut));
+  const double ct = sqrt_nr(e.gm1 * fma(-0.5, kt, Ht));
+
+  const double SL = min_d(uL - cL, ut - ct);
+  const double SR = max_d(uR + cR, ut + ct);
   const double mL = rL * (SL - uL);
   const double mR = rR * (SR - uR);
-  const double Ss = (pR - pL + mL * uL - mR * uR) / (mL - mR);
+  const double Ss = fma(-mR, uR, fma(mL, uL, pR - pL)) * rcp_nr(mL - mR);
 
-  const bool left = Ss >= 0.0;
-  const double rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR, wK = left ? wL : wR;
-  const double pK = left ? pL : pR, EK = left ? EL : ER, SK = left ? SL : SR, mK = left ? mL : mR;
-  const bool fan = left ? (SL < 0.0) : (SR > 0.0);
+  const bool left = ge0(Ss);
+  const double rK = sel(left, rL, rR), uK = sel(left, uL, uR), vK = sel(left, vL, vR);
+  const double wK = sel(left, wL, wR), pK = sel(left, pL, pR), hK = sel(left, hL, hR);
+  const double SK = sel(left, SL, SR), mK = sel(left, mL, mR);
+  const bool fan = left ? lt0(SL) : gt0(SR);
 
+  const double delta = (Ss - uK) * rcp_nr(SK - Ss);
+  const double g = sel(fan, SK, 0.0) * delta;
   const double mass = rK * uK;
-  const double FK0 = mass, FK1 = mass * uK + pK, FK2 = mass * vK, FK3 = mass * wK;
-  const double FK4 = uK * (EK + pK);
-
-  const double fac = mK / (SK - Ss);
-  const double es = EK / rK + (Ss - uK) * (Ss + pK / mK);
-  const double coef = fan ? SK : 0.0;
-  F[0] = FK0 + coef * (fac - rK);
-  F[1] = FK1 + coef * (fac * Ss - mass);
-  F[2] = FK2 + coef * (fac * vK - rK * vK);
-  F[3] = FK3 + coef * (fac * wK - rK * wK);
-  F[4] = FK4 + coef * (fac * es - EK);
+  F[0] = fma(g, rK, mass);
+  F[1] = fma(g, rK * SK, fma(mass, uK, pK));
+  F[2] = vK * F[0];
+  F[3] = wK * F[0];
+  F[4] = fma(g, fma(mK, Ss, hK), uK * hK);
 }
 
 }  // namespace gbh

@@ -21,7 +21,7 @@ struct Layout {
 };
 
 struct Eos {
-  double gamma, gm1, inv_gm1, small_rho, small_p;
+  double gamma, gm1, inv_gm1, g_gm1, small_rho, small_p;  // g_gm1 = gamma / (gamma - 1)
 };
 
 // Arguments of one RK-stage launch: Uout = a*Un + b*(Uin + dt*L(Uin)).
@@ -69,6 +69,7 @@ cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_o
 cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
                          cudaStream_t s);
 
+cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
 
 }  // namespace gbh

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
   const double dt = a.dt_dev ? *a.dt_dev : a.dt;
   const double idx = __ldg(a.inv_dx + 3 * b), idy = __ldg(a.inv_dx + 3 * b + 1);
   const double idz = DIM3 ? __ldg(a.inv_dx + 3 * b + 2) : 0.0;
+  const double dtx = dt * idx, dty = dt * idy, dtz = dt * idz;
   const Eos& e = a.eos;
 
   int hits = 0;
@@ -240,7 +241,8 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
     }
     __syncthreads();
 
-    // (D) updSoln + RK combine for cell (tx, ty, k)
+    // (D) updSoln + RK combine for cell (tx, ty, k):
+    //     Uin + dt L = Uin - dt/dx dFx - dt/dy dFy - dt/dz dFz
     const long long base =
         (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (ty + L.g)) * L.nxp + (tx + L.g);
     double out[5];
@@ -248,12 +250,11 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
     for (int v = 0; v < 5; ++v) {
       const double fx = sFx[(v * N + ty) * (N + 1) + tx + 1] - sFx[(v * N + ty) * (N + 1) + tx];
       const double fy = sFy[(v * (N + 1) + ty + 1) * N + tx] - sFy[(v * (N + 1) + ty) * N + tx];
-      double Lv = -fx * idx;
-      Lv = Lv - fy * idy;
-      if (DIM3) Lv = Lv - (Fzp[v] - Fzm[v]) * idz;
       const long long o = base + v * L.vstride;
-      const double uin = __ldg(a.Uin + o);
-      out[v] = a.combine ? a.a * a.Un[o] + a.b * (uin + dt * Lv) : uin + dt * Lv;
+      double r = fma(-dtx, fx, __ldg(a.Uin + o));
+      r = fma(-dty, fy, r);
+      if (DIM3) r = fma(-dtz, Fzp[v] - Fzm[v], r);
+      out[v] = a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
       a.Uout[o] = out[v];
     }
     if (a.smax_acc) {

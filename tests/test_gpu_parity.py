@@ -279,3 +279,23 @@ def test_fp64_probe_runs(gb):
     out = torch.zeros(152 * 4 * 256, dtype=torch.float64, device="cuda")
     gb.fp64_probe(152 * 4, 256, 1000, out)
     assert torch.isfinite(out).all()
+
+
+def test_refined_reciprocal_and_roots_within_two_ulp(gb):
+    """The kernels' reciprocal, 1/sqrt and sqrt (hardware seed + one
+    third-order refinement) stay within 2 ulp of the IEEE results over the
+    value ranges the scheme produces (and far beyond)."""
+    import ctypes
+    rng = np.random.default_rng(21)
+    x = np.concatenate([10.0 ** rng.uniform(-14, 14, 400000), rng.uniform(0.5, 2.0, 100000),
+                        np.array([1.0, 2.0, 0.5, 3.0, 1e-14, 1e14])])
+    xd = dev(x)
+    out = torch.empty(6 * len(x), dtype=torch.float64, device="cuda")
+    lib = gb.load()
+    assert lib.gbh_fastmath_selftest(xd.data_ptr(), out.data_ptr(), len(x),
+                                     torch.cuda.current_stream().cuda_stream) == 0
+    o = host(out).reshape(6, -1)
+    for k in range(3):
+        fast, ieee = o[2 * k], o[2 * k + 1]
+        ulp = np.abs(fast - ieee) / np.spacing(np.abs(ieee))
+        assert np.max(ulp) <= 2.0, (k, np.max(ulp))

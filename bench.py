@@ -168,7 +168,7 @@ def fp64_probe_tflops(gb, torch):
     sms = gb.sm_count()
     blocks, threads, iters = sms * 8, 256, 20000
     out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
-    gb.fp64_probe(blocks, threads, 100, out)
+    gb.fp64_probe(blocks, threads, 100, out, 32)
     torch.cuda.synchronize()
     best = 0.0
     for _ in range(3):

@@ -155,10 +155,11 @@ int gbh_set_kernel_timing(gbh_ctx *ctx, int enable);
 int gbh_stage_kernel_time(gbh_ctx *ctx, double *ms_host, long long *launches_host, void *stream);
 
 /* FP64 throughput probe (not part of the method): launches blocks x threads
- * threads, each running 8 independent chains of iters fused multiply-adds,
- * and writes one double per thread to out_dev (blocks*threads doubles).
- * FP64 flops executed = 16 * iters * blocks * threads. */
-int gbh_fp64_probe(int blocks, int threads, int iters, double *out_dev, void *stream);
+ * threads; in every warp the first `lanes` (1..32) lanes run 8 independent
+ * chains of iters fused multiply-adds, the others none.  Writes one double
+ * per thread to out_dev (blocks*threads doubles).  FP64 flops executed =
+ * 16 * iters * blocks * (threads/32) * lanes for threads a multiple of 32. */
+int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, double *out_dev, void *stream);
 
 /* Self-test of the FP64 reciprocal / reciprocal-square-root / square-root
  * building blocks the kernels use (hardware seed + one refinement step):

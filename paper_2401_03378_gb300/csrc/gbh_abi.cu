@@ -433,10 +433,10 @@ int gbh_stage_kernel_time(gbh_ctx* c, double* ms_host, long long* launches_host,
   return GBH_OK;
 }
 
-int gbh_fp64_probe(int blocks, int threads, int iters, double* out_dev, void* stream) {
-  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || !out_dev)
+int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, double* out_dev, void* stream) {
+  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || lanes < 1 || lanes > 32 || !out_dev)
     return set_err(nullptr, GBH_ERR_INVAL, "invalid probe arguments");
-  cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, out_dev, (cudaStream_t)stream);
+  cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, lanes, out_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "probe launch: %s", cudaGetErrorString(e));
   return GBH_OK;
 }

@@ -138,12 +138,14 @@ __global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const 
 }
 
 // 8 independent FMA chains per thread; the multiplier and addend keep the
-// values bounded (fixed point 1.0).
-__global__ void fp64_probe_kernel(int iters, double* out) {
+// values bounded (fixed point 1.0).  Only the first `lanes` lanes of each
+// warp run the chains (to measure how the FP64 pipe charges partial warps).
+__global__ void fp64_probe_kernel(int iters, int lanes, double* out) {
   const double m = 0.999999999, c = 1e-9;
   double x0 = 1.0 + 1e-3 * threadIdx.x, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
   double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
-  for (int i = 0; i < iters; ++i) {
+  const int n = (int)(threadIdx.x & 31) < lanes ? iters : 0;
+  for (int i = 0; i < n; ++i) {
     x0 = fma(x0, m, c); x1 = fma(x1, m, c); x2 = fma(x2, m, c); x3 = fma(x3, m, c);
     x4 = fma(x4, m, c); x5 = fma(x5, m, c); x6 = fma(x6, m, c); x7 = fma(x7, m, c);
   }
@@ -203,8 +205,8 @@ cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s) {
-  fp64_probe_kernel<<<blocks, threads, 0, s>>>(iters, out);
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, double* out, cudaStream_t s) {
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(iters, lanes, out);
   return cudaGetLastError();
 }
 

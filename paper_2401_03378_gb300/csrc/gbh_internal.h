@@ -70,6 +70,6 @@ cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long lon
                          cudaStream_t s);
 
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);
-cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, double* out, cudaStream_t s);
 
 }  // namespace gbh

@@ -177,9 +177,9 @@ class Hydro:
         return float(ms.value), int(n.value)
 
 
-def fp64_probe(blocks: int, threads: int, iters: int, out: torch.Tensor):
+def fp64_probe(blocks: int, threads: int, iters: int, out: torch.Tensor, lanes: int = 32):
     lib = _abi.load()
-    rc = lib.gbh_fp64_probe(int(blocks), int(threads), int(iters), out.data_ptr(), _stream_handle())
+    rc = lib.gbh_fp64_probe(int(blocks), int(threads), int(iters), int(lanes), out.data_ptr(), _stream_handle())
     if rc != 0:
         raise _abi.GbhError(rc, lib.gbh_last_error(None).decode())
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "hydro_stage": (C.c_int, [_vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _vp]),
     "hydro_stage_guarded": (C.c_int, [_vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _vp]),
     "hydro_step": (C.c_int, [_vp, _dp, C.c_double, _vp]),
+    "hydro_step_static": (C.c_int, [C.POINTER(GbhParams), _dp, C.c_double, _vp]),
     "hydro_step_cfl": (C.c_int, [_vp, _dp, _dp, _vp]),
     "hydro_advance": (C.c_int, [_vp, _dp, C.c_int, _dp, _dp, _vp]),
     "hydro_advance_host": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),

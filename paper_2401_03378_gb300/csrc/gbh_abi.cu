@@ -111,15 +111,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   A.b = b;
   A.combine = (a == 0.0 && b == 1.0) ? 0 : 1;
   A.gather = gather ? 1 : 0;
-  A.lay = c->lay;
-  A.eos = c->eos;
-  if (c->lay.ndim == 3) {
-    A.kchunk = c->lay.nz;   // one CTA per block
-    A.nchunks = 1;
-  } else {
-    A.kchunk = 1;
-    A.nchunks = 1;
-  }
+  gbh::stage_args_common(&A, c->lay, c->eos);
   A.smax_acc = dt_epilogue ? c->d_words : nullptr;
   A.floor_count = c->d_words + 1;
   cudaEvent_t stop;
@@ -131,7 +123,11 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   return rc;
 }
 
-int validate(const gbh_params* p) {
+}  // namespace
+
+namespace gbh {
+
+int validate_params(const gbh_params* p) {
   if (!p) return set_err(nullptr, GBH_ERR_INVAL, "params is NULL");
   if (p->ndim != 2 && p->ndim != 3) return set_err(nullptr, GBH_ERR_INVAL, "ndim must be 2 or 3 (got %d)", p->ndim);
   if (p->nblocks < 1) return set_err(nullptr, GBH_ERR_INVAL, "nblocks must be >= 1");
@@ -167,56 +163,72 @@ int validate(const gbh_params* p) {
   return GBH_OK;
 }
 
-}  // namespace
+void layout_from_params(const gbh_params* p, Layout* L, Eos* e) {
+  L->ndim = p->ndim;
+  L->nx = p->nxb;
+  L->ny = p->nyb;
+  L->nz = p->nzb;
+  L->g = p->nguard;
+  L->gz = p->ndim == 3 ? p->nguard : 0;
+  L->nxp = L->nx + 2 * L->g;
+  L->nyp = L->ny + 2 * L->g;
+  L->nzp = L->nz + 2 * L->gz;
+  L->nblocks = p->nblocks;
+  L->vstride = (long long)L->nxp * L->nyp * L->nzp;
+  L->bstride = 5 * L->vstride;
+  e->gamma = p->gamma;
+  e->gm1 = p->gamma - 1.0;
+  e->inv_gm1 = 1.0 / (p->gamma - 1.0);
+  e->g_gm1 = p->gamma / (p->gamma - 1.0);
+  e->small_rho = p->small_rho;
+  e->small_p = p->small_p;
+}
+
+void face_table_from_params(const gbh_params* p, long long b, int face[6], double inv_dx[3]) {
+  const int nn = p->ndim == 3 ? 27 : 9;
+  const int32_t* row = p->nbr + b * nn;
+  auto at = [&](int ox, int oy, int oz) {
+    return p->ndim == 3 ? row[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] : row[(oy + 1) * 3 + (ox + 1)];
+  };
+  face[0] = at(-1, 0, 0);
+  face[1] = at(1, 0, 0);
+  face[2] = at(0, -1, 0);
+  face[3] = at(0, 1, 0);
+  face[4] = p->ndim == 3 ? at(0, 0, -1) : GBH_BC_OUTFLOW;
+  face[5] = p->ndim == 3 ? at(0, 0, 1) : GBH_BC_OUTFLOW;
+  for (int d = 0; d < 3; ++d) inv_dx[d] = (d < p->ndim) ? 1.0 / p->dx[3 * b + d] : 0.0;
+}
+
+void stage_args_common(StageArgs* A, const Layout& L, const Eos& e) {
+  A->lay = L;
+  A->eos = e;
+  A->kchunk = L.ndim == 3 ? L.nz : 1;   // one CTA per block
+  A->nchunks = 1;
+}
+
+int set_create_error(int code, const char* msg) { return set_err(nullptr, code, "%s", msg); }
+
+}  // namespace gbh
+
+using gbh::validate_params;
 
 extern "C" {
 
 int gbh_create(const gbh_params* p, gbh_ctx** out) {
   if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
   *out = nullptr;
-  int rc = validate(p);
+  int rc = validate_params(p);
   if (rc) return rc;
   gbh_ctx* c = new (std::nothrow) gbh_ctx();
   if (!c) return set_err(nullptr, GBH_ERR_NOMEM, "host allocation failed");
-  Layout& L = c->lay;
-  L.ndim = p->ndim;
-  L.nx = p->nxb;
-  L.ny = p->nyb;
-  L.nz = p->nzb;
-  L.g = p->nguard;
-  L.gz = p->ndim == 3 ? p->nguard : 0;
-  L.nxp = L.nx + 2 * L.g;
-  L.nyp = L.ny + 2 * L.g;
-  L.nzp = L.nz + 2 * L.gz;
-  L.nblocks = p->nblocks;
-  L.vstride = (long long)L.nxp * L.nyp * L.nzp;
-  L.bstride = 5 * L.vstride;
-  c->eos.gamma = p->gamma;
-  c->eos.gm1 = p->gamma - 1.0;
-  c->eos.inv_gm1 = 1.0 / (p->gamma - 1.0);
-  c->eos.g_gm1 = p->gamma / (p->gamma - 1.0);
-  c->eos.small_rho = p->small_rho;
-  c->eos.small_p = p->small_p;
+  gbh::layout_from_params(p, &c->lay, &c->eos);
+  const Layout& L = c->lay;
   c->cfl = p->cfl;
 
   const int nn = p->ndim == 3 ? 27 : 9;
   std::vector<int> face(6 * (size_t)p->nblocks, GBH_BC_OUTFLOW);
   std::vector<double> inv(3 * (size_t)p->nblocks, 0.0);
-  for (long long b = 0; b < p->nblocks; ++b) {
-    const int32_t* row = p->nbr + b * nn;
-    auto at = [&](int ox, int oy, int oz) {
-      return p->ndim == 3 ? row[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] : row[(oy + 1) * 3 + (ox + 1)];
-    };
-    face[6 * b + 0] = at(-1, 0, 0);
-    face[6 * b + 1] = at(1, 0, 0);
-    face[6 * b + 2] = at(0, -1, 0);
-    face[6 * b + 3] = at(0, 1, 0);
-    if (p->ndim == 3) {
-      face[6 * b + 4] = at(0, 0, -1);
-      face[6 * b + 5] = at(0, 0, 1);
-    }
-    for (int d = 0; d < 3; ++d) inv[3 * b + d] = (d < p->ndim) ? 1.0 / p->dx[3 * b + d] : 0.0;
-  }
+  for (long long b = 0; b < p->nblocks; ++b) gbh::face_table_from_params(p, b, &face[6 * b], &inv[3 * b]);
 
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_nbr, sizeof(int) * nn * (size_t)p->nblocks);

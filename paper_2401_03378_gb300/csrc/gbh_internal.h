@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gbhydro.h"
+
 namespace gbh {
 
 // Face order used by the compact face-neighbour table: x-, x+, y-, y+, z-, z+.
@@ -44,6 +46,13 @@ struct StageArgs {
 };
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
+
+// Host helpers shared by the entry points (gbh_abi.cu).
+int validate_params(const gbh_params* p);     // GBH_OK or an error code; message in gbh_last_error(NULL)
+void layout_from_params(const gbh_params* p, Layout* L, Eos* e);
+void face_table_from_params(const gbh_params* p, long long b, int face[6], double inv_dx[3]);
+void stage_args_common(StageArgs* A, const Layout& L, const Eos& e);
+int set_create_error(int code, const char* msg);
 size_t stage_smem_bytes(int nx);
 cudaError_t stage_prepare(int nx, int ndim);  // opt-in to the dynamic shared memory size
 

@@ -39,6 +39,9 @@
 #include "oracle_pointwise.h"
 
 extern "C" {
+struct OrcAmr2 {
+  int lo[3], hi[3];  /* fine region in coarse-block units, [lo, hi) per dimension */
+};
 struct OrcGrid {
   int ndim;          /* 2 or 3 */
   int nb[3];         /* blocks per dimension (nb[2] = 1 in 2-D) */
@@ -334,6 +337,348 @@ ll step(const OrcGrid& G, double* U, double dt) {
   return hits;
 }
 
+// ---------------------------------------------------------------------------
+// Two-level composite grid (refinement ratio 2, one dt for both levels).
+//
+// Sec. 4.2, all-levels listing: every leaf block of every level is advanced
+// in one sweep, then the fluxes at coarse-fine boundaries are communicated
+// and the coarse side is corrected; Sec. 2.2: blocks of all levels have the
+// same cell counts, only the cell width differs.  Readings (the paper gives
+// no formulas):
+//   - restriction: a covered coarse cell holds the mean of its 2^d children;
+//   - prolongation into fine guard cells across the coarse-fine boundary:
+//     u_f = u_c + sum_d s_d sigma_d / 4 (s_d = -1 for the lower child, +1 for
+//     the upper) with MC slopes sigma_d of the conserved coarse variables --
+//     conservative (the children average to the parent);
+//   - flux correction: at a coarse face on the boundary of the fine region
+//     the coarse flux is replaced by the mean of the 2^(d-1) fine fluxes
+//     through it, in every RK stage, weighted like the stage's L term.
+// Layout: coarse blocks 0..n0-1 (the complete coarse lattice; covered blocks
+// hold restricted data), then fine blocks n0..n0+n1-1 (lattice over the fine
+// region, x fastest).  The fine region is a box of whole coarse blocks at
+// least one block away from the domain boundary.
+struct Amr2 {
+  OrcGrid C, F;
+  int lo[3], hi[3];
+  ll n0, n1;
+};
+
+Amr2 make_amr2(const OrcGrid& C, const int lo[3], const int hi[3]) {
+  Amr2 A;
+  A.C = C;
+  A.F = C;
+  for (int d = 0; d < 3; ++d) {
+    A.lo[d] = d < C.ndim ? lo[d] : 0;
+    A.hi[d] = d < C.ndim ? hi[d] : 1;
+    A.F.nb[d] = d < C.ndim ? 2 * (A.hi[d] - A.lo[d]) : 1;
+    A.F.dx[d] = C.dx[d] * 0.5;
+    A.F.periodic[d] = 0;
+  }
+  A.n0 = (ll)C.nb[0] * C.nb[1] * C.nb[2];
+  A.n1 = (ll)A.F.nb[0] * A.F.nb[1] * A.F.nb[2];
+  return A;
+}
+
+bool covered(const Amr2& A, const Geo& gc, ll b) {
+  int c[3];
+  gc.coords(b, c);
+  for (int d = 0; d < 3; ++d)
+    if (c[d] < A.lo[d] || c[d] >= A.hi[d]) return false;
+  return true;
+}
+
+int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+/* value of coarse interior cell at global coarse cell coordinates X */
+double coarse_value(const Geo& gc, const double* U, int v, const int X[3]) {
+  int bc[3], loc[3];
+  for (int d = 0; d < 3; ++d) {
+    bc[d] = X[d] / gc.n[d];
+    loc[d] = X[d] - bc[d] * gc.n[d] + gc.g[d];
+  }
+  const ll b = bc[0] + (ll)gc.nb[0] * (bc[1] + (ll)gc.nb[1] * bc[2]);
+  return U[gc.at(b, v, loc[2], loc[1], loc[0])];
+}
+
+/* fine block f's global fine-cell coordinates of its padded cell (i, j, k) */
+void fine_global(const Geo& gf, ll f, int i, int j, int k, int X[3]) {
+  int c[3];
+  gf.coords(f, c);
+  const int p[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d) X[d] = c[d] * gf.n[d] + p[d] - gf.g[d];
+}
+
+void amr2_restrict(const Amr2& A, double* U) {
+  const Geo gc(A.C), gf(A.F);
+  const int nd = A.C.ndim;
+  const double w = nd == 3 ? 0.125 : 0.25;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (ll b = 0; b < A.n0; ++b) {
+    if (!covered(A, gc, b)) continue;
+    int c[3];
+    gc.coords(b, c);
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < gc.n[2]; ++k)
+        for (int j = 0; j < gc.n[1]; ++j)
+          for (int i = 0; i < gc.n[0]; ++i) {
+            const int X[3] = {c[0] * gc.n[0] + i, c[1] * gc.n[1] + j, c[2] * gc.n[2] + k};
+            int fX[3];
+            for (int d = 0; d < 3; ++d) fX[d] = d < nd ? 2 * (X[d] - A.lo[d] * gc.n[d]) : 0;
+            double s = 0.0;
+            for (int dz = 0; dz < (nd == 3 ? 2 : 1); ++dz)
+              for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                  const int Y[3] = {fX[0] + dx, fX[1] + dy, fX[2] + dz};
+                  int fb[3], loc[3];
+                  for (int d = 0; d < 3; ++d) {
+                    fb[d] = Y[d] / gf.n[d];
+                    loc[d] = Y[d] - fb[d] * gf.n[d] + gf.g[d];
+                  }
+                  const ll f = fb[0] + (ll)gf.nb[0] * (fb[1] + (ll)gf.nb[1] * fb[2]);
+                  s = s + U[gc.at(A.n0 + f, v, loc[2], loc[1], loc[0])];
+                }
+            U[gc.at(b, v, k + gc.g[2], j + gc.g[1], i + gc.g[0])] = s * w;
+          }
+  }
+}
+
+/* guard cells of every fine block: same-level copies where the fine
+ * neighbour exists, conservative linear prolongation from the coarse level
+ * elsewhere.  The coarse level's interior must be current (restricted). */
+void amr2_fill_fine(const Amr2& A, double* U) {
+  const Geo gc(A.C), gf(A.F);
+  const int nd = A.C.ndim;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (ll f = 0; f < A.n1; ++f) {
+    for (int k = 0; k < gf.p[2]; ++k)
+      for (int j = 0; j < gf.p[1]; ++j)
+        for (int i = 0; i < gf.p[0]; ++i) {
+          const int x[3] = {i, j, k};
+          int o[3];
+          bool interior = true;
+          for (int d = 0; d < 3; ++d) {
+            o[d] = x[d] < gf.g[d] ? -1 : (x[d] >= gf.g[d] + gf.n[d] ? 1 : 0);
+            if (o[d]) interior = false;
+          }
+          if (interior) continue;
+          const ll nb = gf.neighbour(f, o);
+          if (nb >= 0) {
+            for (int v = 0; v < 5; ++v)
+              U[gf.at(A.n0 + f, v, k, j, i)] =
+                  U[gf.at(A.n0 + nb, v, k - o[2] * gf.n[2], j - o[1] * gf.n[1], i - o[0] * gf.n[0])];
+            continue;
+          }
+          int X[3], P[3], sgn[3];
+          fine_global(gf, f, i, j, k, X);
+          for (int d = 0; d < 3; ++d) {
+            if (d < nd) {
+              const int h = fdiv(X[d], 2);
+              P[d] = A.lo[d] * gc.n[d] + h;
+              sgn[d] = (X[d] - 2 * h) == 0 ? -1 : 1;
+            } else {
+              P[d] = 0;
+              sgn[d] = 0;
+            }
+          }
+          for (int v = 0; v < 5; ++v) {
+            double val = coarse_value(gc, U, v, P);
+            for (int d = 0; d < nd; ++d) {
+              int Pm[3] = {P[0], P[1], P[2]}, Pp[3] = {P[0], P[1], P[2]};
+              Pm[d] -= 1;
+              Pp[d] += 1;
+              const double sig = orc::mc_slope(coarse_value(gc, U, v, Pm), coarse_value(gc, U, v, P),
+                                               coarse_value(gc, U, v, Pp));
+              val = val + 0.25 * sig * (double)sgn[d];
+            }
+            U[gf.at(A.n0 + f, v, k, j, i)] = val;
+          }
+        }
+  }
+}
+
+/* Flux registers: the fluxes through the boundary faces of the fine region
+ * (fine side) and through the coarse faces adjacent to it (coarse side). */
+struct FluxReg {
+  std::vector<std::vector<double>> face;   /* [(block)*6 + face] -> [5][t2][t1] or empty */
+};
+
+void tangential(int d, int& t1, int& t2) {
+  t1 = d == 0 ? 1 : 0;
+  t2 = d == 2 ? 1 : 2;
+}
+
+void record_face(const Geo& g, const Work& w, int d, int side, std::vector<double>& out) {
+  int t1, t2;
+  tangential(d, t1, t2);
+  const int n1 = g.n[t1], n2 = g.n[t2];
+  out.assign((size_t)5 * n1 * n2, 0.0);
+  const ll cells = g.cells;
+  for (int v = 0; v < 5; ++v)
+    for (int b2 = 0; b2 < n2; ++b2)
+      for (int b1 = 0; b1 < n1; ++b1) {
+        int x[3];
+        x[d] = side ? g.g[d] + g.n[d] : g.g[d];   /* F[d][c]: face between c - e_d and c */
+        x[t1] = g.g[t1] + b1;
+        x[t2] = g.g[t2] + b2;
+        out[((size_t)v * n2 + b2) * n1 + b1] = w.F[d][v * cells + g.cell(x[2], x[1], x[0])];
+      }
+}
+
+ll amr2_stage(const Amr2& A, const double* Uin, const double* Un, double* Uout, double dt, double a, double bcoef,
+              FluxReg& R) {
+  const Geo gc(A.C), gf(A.F);
+  const ll total = A.n0 + A.n1;
+  R.face.assign(total * 6, std::vector<double>());
+  ll hits = 0;
+#pragma omp parallel reduction(+ : hits)
+  {
+    Work w;
+    w.resize(gc.cells);
+#pragma omp for schedule(dynamic, 1)
+    for (ll t = 0; t < total; ++t) {
+      if (t < A.n0) {
+        if (covered(A, gc, t)) continue;
+        hits += stage_block(A.C, gc, t, Uin, Un, Uout, dt, a, bcoef, w);
+        for (int d = 0; d < A.C.ndim; ++d)
+          for (int side = 0; side < 2; ++side) {
+            int o[3] = {0, 0, 0};
+            o[d] = side ? 1 : -1;
+            const ll nb = gc.neighbour(t, o);
+            if (nb >= 0 && covered(A, gc, nb)) record_face(gc, w, d, side, R.face[t * 6 + 2 * d + side]);
+          }
+      } else {
+        const ll f = t - A.n0;
+        hits += stage_block(A.F, gf, t, Uin, Un, Uout, dt, a, bcoef, w);
+        for (int d = 0; d < A.C.ndim; ++d)
+          for (int side = 0; side < 2; ++side) {
+            int o[3] = {0, 0, 0};
+            o[d] = side ? 1 : -1;
+            if (gf.neighbour(f, o) < 0) record_face(gf, w, d, side, R.face[t * 6 + 2 * d + side]);
+          }
+      }
+    }
+  }
+  return hits;
+}
+
+/* Replace, on the coarse side, the flux through every coarse face on the
+ * boundary of the fine region by the mean of the fine fluxes through it:
+ * U += coef * dt * (F_coarse - mean F_fine) / dx on the low side of the
+ * face, with the opposite sign on the high side (coef = the stage's b). */
+void amr2_reflux(const Amr2& A, double* U, double dt, double coef, const FluxReg& R) {
+  const Geo gc(A.C), gf(A.F);
+  const int nd = A.C.ndim;
+  for (ll b = 0; b < A.n0; ++b) {
+    if (covered(A, gc, b)) continue;
+    int c[3];
+    gc.coords(b, c);
+    for (int d = 0; d < nd; ++d)
+      for (int side = 0; side < 2; ++side) {
+        const std::vector<double>& Fc = R.face[b * 6 + 2 * d + side];
+        if (Fc.empty()) continue;
+        int t1, t2;
+        tangential(d, t1, t2);
+        const int n1 = gc.n[t1], n2 = gc.n[t2];
+        const double idx = 1.0 / A.C.dx[d];
+        /* the fine region lies on the `side` of this face; its boundary
+         * faces there are the fine blocks' faces of the opposite side */
+        const int fside = 1 - side;
+        const int nfine = nd == 3 ? 4 : 2;
+        for (int b2 = 0; b2 < n2; ++b2)
+          for (int b1 = 0; b1 < n1; ++b1) {
+            int T[3];                                 /* global coarse coordinates of the face cell's tangentials */
+            T[t1] = c[t1] * gc.n[t1] + b1;
+            T[t2] = c[t2] * gc.n[t2] + b2;
+            /* fine face position along d: first / last fine cell of the fine region */
+            const int fd = side ? 0 : gf.nb[d] * gf.n[d] - 1;
+            double fsum[5] = {0, 0, 0, 0, 0};
+            for (int q2 = 0; q2 < (nd == 3 ? 2 : 1); ++q2)
+              for (int q1 = 0; q1 < 2; ++q1) {
+                int Y[3];
+                Y[d] = fd;
+                Y[t1] = 2 * (T[t1] - A.lo[t1] * gc.n[t1]) + q1;
+                Y[t2] = nd == 3 || t2 < nd ? 2 * (T[t2] - A.lo[t2] * gc.n[t2]) + q2 : 0;
+                int fb[3], loc[3];
+                for (int e = 0; e < 3; ++e) {
+                  fb[e] = Y[e] / gf.n[e];
+                  loc[e] = Y[e] - fb[e] * gf.n[e];
+                }
+                const ll f = fb[0] + (ll)gf.nb[0] * (fb[1] + (ll)gf.nb[1] * fb[2]);
+                const std::vector<double>& Ff = R.face[(A.n0 + f) * 6 + 2 * d + fside];
+                const int fn1 = gf.n[t1], fn2 = gf.n[t2];
+                for (int v = 0; v < 5; ++v) fsum[v] = fsum[v] + Ff[((size_t)v * fn2 + loc[t2]) * fn1 + loc[t1]];
+                (void)fn2;
+              }
+            int x[3];
+            x[d] = side ? gc.g[d] + gc.n[d] - 1 : gc.g[d];
+            x[t1] = gc.g[t1] + b1;
+            x[t2] = gc.g[t2] + b2;
+            for (int v = 0; v < 5; ++v) {
+              const double fmean = fsum[v] / (double)nfine;
+              const double fcv = Fc[((size_t)v * n2 + b2) * n1 + b1];
+              const double corr = side ? (fcv - fmean) : (fmean - fcv);
+              U[gc.at(b, v, x[2], x[1], x[0])] += coef * dt * corr * idx;
+            }
+          }
+      }
+  }
+}
+
+double amr2_compute_dt(const Amr2& A, const double* U) {
+  const Geo gc(A.C);
+  double smax = 0.0;
+  for (int lev = 0; lev < 2; ++lev) {
+    const OrcGrid& G = lev ? A.F : A.C;
+    const double idx = 1.0 / G.dx[0], idy = 1.0 / G.dx[1], idz = 1.0 / G.dx[2];
+    const ll b0 = lev ? A.n0 : 0, b1 = lev ? A.n0 + A.n1 : A.n0;
+    for (ll b = b0; b < b1; ++b) {
+      if (!lev && covered(A, gc, b)) continue;
+      for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
+        for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
+          for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
+            double u5[5], W[5];
+            load_cons(gc, U, b, k, j, i, u5);
+            orc::prim_from_cons(u5, A.C.gamma, A.C.small_rho, A.C.small_p, W);
+            smax = std::max(smax, orc::signal_speed(gc.ndim, W, A.C.gamma, idx, idy, idz));
+          }
+    }
+  }
+  return A.C.cfl / smax;
+}
+
+void amr2_prepare(const Amr2& A, double* U) {
+  amr2_restrict(A, U);
+  fill_guardcells(A.C, U);   /* coarse lattice = the first n0 blocks */
+  amr2_fill_fine(A, U);
+}
+
+ll amr2_step(const Amr2& A, double* U, double dt) {
+  const Geo gc(A.C);
+  const ll total = (A.n0 + A.n1) * 5 * gc.cells;
+  std::vector<double> U1(U, U + total), U2(total);
+  FluxReg R;
+  ll hits = 0;
+  amr2_prepare(A, U);
+  hits += amr2_stage(A, U, nullptr, U1.data(), dt, 0.0, 1.0, R);
+  amr2_reflux(A, U1.data(), dt, 1.0, R);
+  amr2_prepare(A, U1.data());
+  std::memcpy(U2.data(), U1.data(), total * sizeof(double));
+  hits += amr2_stage(A, U1.data(), U, U2.data(), dt, 0.5, 0.5, R);
+  amr2_reflux(A, U2.data(), dt, 0.5, R);
+  for (ll b = 0; b < A.n0 + A.n1; ++b) {
+    if (b < A.n0 && covered(A, gc, b)) continue;
+    for (int v = 0; v < 5; ++v)
+      for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
+        for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
+          for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
+            const ll o = gc.at(b, v, k, j, i);
+            U[o] = U2[o];
+          }
+  }
+  amr2_restrict(A, U);
+  return hits;
+}
+
 }  // namespace
 
 extern "C" {
@@ -395,6 +740,44 @@ long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist) {
     const double dt = compute_dt(*G, U);
     if (dt_hist) dt_hist[s] = dt;
     hits += step(*G, U, dt);
+  }
+  return hits;
+}
+
+/* ---- two-level composite grid (coarse blocks first, then fine blocks) ---- */
+
+void orc2_restrict(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_restrict(make_amr2(*G, R->lo, R->hi), U); }
+
+void orc2_fill(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_prepare(make_amr2(*G, R->lo, R->hi), U); }
+
+double orc2_compute_dt(const OrcGrid* G, const OrcAmr2* R, const double* U) {
+  return amr2_compute_dt(make_amr2(*G, R->lo, R->hi), U);
+}
+
+long long orc2_step(const OrcGrid* G, const OrcAmr2* R, double* U, double dt) {
+  return amr2_step(make_amr2(*G, R->lo, R->hi), U, dt);
+}
+
+/* One stage without flux correction (reflux = 0) or with it (reflux = 1):
+ * prepares Uin (restriction + guard fills) and writes the leaf blocks of Uout. */
+long long orc2_stage(const OrcGrid* G, const OrcAmr2* R, double* Uin, const double* Un, double* Uout, double dt,
+                     double a, double b, int reflux) {
+  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  FluxReg reg;
+  amr2_prepare(A, Uin);
+  const ll hits = amr2_stage(A, Uin, Un, Uout, dt, a, b, reg);
+  if (reflux) amr2_reflux(A, Uout, dt, b, reg);
+  return hits;
+}
+
+long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist) {
+  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  long long hits = 0;
+  amr2_restrict(A, U);
+  for (int s = 0; s < nsteps; ++s) {
+    const double dt = amr2_compute_dt(A, U);
+    if (dt_hist) dt_hist[s] = dt;
+    hits += amr2_step(A, U, dt);
   }
   return hits;
 }

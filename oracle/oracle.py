@@ -17,6 +17,10 @@ _lock = threading.Lock()
 _lib = None
 
 
+class OrcAmr2(C.Structure):
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3)]
+
+
 class OrcGrid(C.Structure):
     _fields_ = [
         ("ndim", C.c_int),
@@ -62,6 +66,19 @@ def lib():
             L.orc_step.restype = C.c_longlong
             L.orc_run.argtypes = [gp, dp, C.c_int, dp]
             L.orc_run.restype = C.c_longlong
+            ap = C.POINTER(OrcAmr2)
+            L.orc2_restrict.argtypes = [gp, ap, dp]
+            L.orc2_restrict.restype = None
+            L.orc2_fill.argtypes = [gp, ap, dp]
+            L.orc2_fill.restype = None
+            L.orc2_compute_dt.argtypes = [gp, ap, dp]
+            L.orc2_compute_dt.restype = C.c_double
+            L.orc2_step.argtypes = [gp, ap, dp, C.c_double]
+            L.orc2_step.restype = C.c_longlong
+            L.orc2_stage.argtypes = [gp, ap, dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_int]
+            L.orc2_stage.restype = C.c_longlong
+            L.orc2_run.argtypes = [gp, ap, dp, C.c_int, dp]
+            L.orc2_run.restype = C.c_longlong
             _lib = L
     return _lib
 
@@ -136,6 +153,54 @@ class Oracle:
         _check(U, self.lat)
         hist = np.zeros(max(nsteps, 1))
         hits = int(self.L.orc_run(C.byref(self.g), _dp(U), int(nsteps), _dp(hist)))
+        return hist[:nsteps], hits
+
+
+class Oracle2:
+    """The oracle on a two-level composite grid (workloads.TwoLevel)."""
+
+    def __init__(self, tl, gamma=1.4, cfl=0.8, small_rho=1e-12, small_p=1e-14):
+        self.tl = tl
+        self.g = grid(tl.coarse, gamma, cfl, small_rho, small_p)
+        self.r = OrcAmr2()
+        for d in range(3):
+            self.r.lo[d] = tl.lo[d]
+            self.r.hi[d] = tl.hi[d]
+        self.L = lib()
+
+    def _chk(self, U):
+        if U.shape != self.tl.shape or U.dtype != np.float64 or not U.flags.c_contiguous:
+            raise ValueError(f"U must be C-contiguous float64 of shape {self.tl.shape}")
+
+    def restrict(self, U):
+        self._chk(U)
+        self.L.orc2_restrict(C.byref(self.g), C.byref(self.r), _dp(U))
+        return U
+
+    def fill(self, U):
+        """restriction, coarse guard fill, fine guard fill (copies + prolongation)"""
+        self._chk(U)
+        self.L.orc2_fill(C.byref(self.g), C.byref(self.r), _dp(U))
+        return U
+
+    def compute_dt(self, U):
+        self._chk(U)
+        return float(self.L.orc2_compute_dt(C.byref(self.g), C.byref(self.r), _dp(U)))
+
+    def stage(self, Uin, Un, Uout, dt, a, b, reflux=True):
+        for X in (Uin, Uout) + ((Un,) if Un is not None else ()):
+            self._chk(X)
+        return int(self.L.orc2_stage(C.byref(self.g), C.byref(self.r), _dp(Uin), _dp(Un), _dp(Uout),
+                                     dt, a, b, 1 if reflux else 0))
+
+    def step(self, U, dt):
+        self._chk(U)
+        return int(self.L.orc2_step(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
+
+    def run(self, U, nsteps):
+        self._chk(U)
+        hist = np.zeros(max(nsteps, 1))
+        hits = int(self.L.orc2_run(C.byref(self.g), C.byref(self.r), _dp(U), int(nsteps), _dp(hist)))
         return hist[:nsteps], hits
 
 

@@ -40,6 +40,7 @@ class Lattice:
     ng: int = 4                       # guard cells per side (x, y; z too in 3-D)
     bc: Tuple[str, str, str] = (OUTFLOW, OUTFLOW, OUTFLOW)
     extent: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+    origin: Tuple[float, float, float] = (0.0, 0.0, 0.0)
 
     def __post_init__(self):
         if self.ndim not in (2, 3):
@@ -114,9 +115,9 @@ def cell_centers(lat: Lattice):
     kk = np.arange(nzp) - lat.gz
     for b in range(lat.nblocks):
         bi, bj, bk = lat.block_coords(b)
-        x = (bi * lat.n[0] + ii + 0.5) * dx[0]
-        y = (bj * lat.n[1] + jj + 0.5) * dx[1]
-        z = (bk * lat.n[2] + kk + 0.5) * dx[2] if lat.ndim == 3 else np.full(nzp, 0.5 * dx[2])
+        x = lat.origin[0] + (bi * lat.n[0] + ii + 0.5) * dx[0]
+        y = lat.origin[1] + (bj * lat.n[1] + jj + 0.5) * dx[1]
+        z = (lat.origin[2] + (bk * lat.n[2] + kk + 0.5) * dx[2]) if lat.ndim == 3 else np.full(nzp, 0.5 * dx[2])
         Z[b], Y[b], X[b] = np.meshgrid(z, y, x, indexing="ij")
     return X, Y, Z
 
@@ -165,7 +166,7 @@ def sedov_cells(lat: Lattice, r_cells: float = 3.5):
     """Mask of the cells whose centres lie within r_cells cell widths of the centre."""
     X, Y, Z = cell_centers(lat)
     dx = lat.dx[0]
-    c = [0.5 * lat.extent[d] for d in range(3)]
+    c = [lat.origin[d] + 0.5 * lat.extent[d] for d in range(3)]
     r2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2
     if lat.ndim == 3:
         r2 = r2 + (Z - c[2]) ** 2
@@ -263,6 +264,99 @@ def poison_guards(U: np.ndarray, lat: Lattice, value: float = np.nan, corners_on
     sel = nout >= 2 if corners_only else nout >= 1
     U[:, :, sel] = value
     return U
+
+
+# ----------------------------------------------------------------------------
+# Two-level composite grids (refinement ratio 2)
+# ----------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class TwoLevel:
+    """A complete coarse lattice plus a fine lattice at twice the resolution over
+    the box of coarse blocks [lo, hi) (at least one block from the domain edge).
+    Composite arrays hold the coarse blocks first, then the fine blocks."""
+
+    coarse: Lattice
+    lo: Tuple[int, int, int]
+    hi: Tuple[int, int, int]
+
+    def __post_init__(self):
+        for d in range(self.coarse.ndim):
+            if not (1 <= self.lo[d] < self.hi[d] <= self.coarse.nb[d] - 1):
+                raise ValueError("the fine region must be a box of coarse blocks away from the domain edge")
+
+    @property
+    def fine(self) -> Lattice:
+        c = self.coarse
+        nd = c.ndim
+        dx = c.dx
+        nb = tuple(2 * (self.hi[d] - self.lo[d]) if d < nd else 1 for d in range(3))
+        origin = tuple(self.lo[d] * c.n[d] * dx[d] if d < nd else 0.0 for d in range(3))
+        extent = tuple((self.hi[d] - self.lo[d]) * c.n[d] * dx[d] if d < nd else c.extent[d] for d in range(3))
+        return Lattice(nd, nb, c.n, c.ng, (OUTFLOW, OUTFLOW, OUTFLOW), extent, origin)
+
+    @property
+    def n0(self) -> int:
+        return self.coarse.nblocks
+
+    @property
+    def n1(self) -> int:
+        return self.fine.nblocks
+
+    @property
+    def nblocks(self) -> int:
+        return self.n0 + self.n1
+
+    @property
+    def shape(self):
+        return (self.nblocks, 5) + self.coarse.padded
+
+    def covered(self, b: int) -> bool:
+        c = self.coarse.block_coords(b)
+        return all(self.lo[d] <= c[d] < self.hi[d] for d in range(3))
+
+    @property
+    def leaf_cells(self) -> int:
+        c = self.coarse
+        per = c.n[0] * c.n[1] * c.n[2]
+        ncov = sum(1 for b in range(self.n0) if self.covered(b))
+        return (self.n0 - ncov + self.n1) * per
+
+
+def two_level(coarse: Lattice, lo, hi) -> TwoLevel:
+    lo = tuple(lo) + (0,) * (3 - len(lo))
+    hi = tuple(hi) + (1,) * (3 - len(hi))
+    return TwoLevel(coarse, lo, hi)
+
+
+def two_level_state(tl: TwoLevel, prim_fn, gamma: float = 1.4):
+    """Composite conserved array from a primitive-state function of (X, Y, Z)."""
+    parts = []
+    for lat in (tl.coarse, tl.fine):
+        X, Y, Z = cell_centers(lat)
+        rho, u, v, w, p = prim_fn(X, Y, Z)
+        parts.append(_assemble(lat, rho, u, v, w, p, gamma))
+    return np.ascontiguousarray(np.concatenate(parts, axis=0))
+
+
+def sedov_two_level(tl: TwoLevel, gamma: float = 1.4, energy: float = 1.0, r_cells: float = 3.5,
+                    p_ambient: float = 1e-5):
+    """Sedov blast on a composite grid: the energy sits in the fine cells within
+    r_cells FINE cell widths of the centre (which the fine region must contain);
+    every other cell is ambient (covered coarse cells are restricted by the solver)."""
+    fine = tl.fine
+    mask = sedov_cells(fine, r_cells)
+    ndep = int(mask.sum())
+    vol = float(np.prod(fine.dx[: fine.ndim]))
+    p_dep = (gamma - 1.0) * energy / (ndep * vol)
+    shape_c = (tl.coarse.nblocks,) + tl.coarse.padded
+    zc = np.zeros(shape_c)
+    Uc = _assemble(tl.coarse, np.ones(shape_c), zc, zc, zc, np.full(shape_c, p_ambient), gamma)
+    rho = np.ones(mask.shape)
+    p = np.where(mask, p_dep, p_ambient)
+    zero = np.zeros_like(rho)
+    Uf = _assemble(fine, rho, zero, zero, zero, p, gamma)
+    return np.ascontiguousarray(np.concatenate([Uc, Uf], axis=0))
 
 
 def ensemble_sizes(count: int = 96, seed: int = 0, choices=(64, 128, 256, 512)):

@@ -53,6 +53,11 @@ extern "C" {
  * the caller as the id of the wrapped block. */
 #define GBH_BC_OUTFLOW (-1)
 
+/* Neighbour-table code of a fine block whose region at that offset lies on
+ * the next coarser level (two-level composite grids, gbh_create_refined):
+ * the guard cells there are filled by prolongation from the parent level. */
+#define GBH_NBR_COARSER (-2)
+
 typedef struct gbh_ctx gbh_ctx;
 
 typedef struct gbh_params {
@@ -77,6 +82,36 @@ typedef struct gbh_params {
  * scratch (one state-sized buffer) and a few device words.  Synchronous.
  * *out is set to NULL on failure. */
 int gbh_create(const gbh_params *params, gbh_ctx **out);
+
+/* Two-level composite grids (refinement ratio 2, one dt for all levels).
+ * Sec. 4.2 of the paper, all-levels variant: every leaf block of every level
+ * is advanced in one sweep, then the fluxes through coarse-fine boundaries are
+ * communicated and the coarse side corrected.  params describes all blocks of
+ * both levels in one state array (same padded block shape); nbr entries of a
+ * fine block whose region lies on the coarser level are GBH_NBR_COARSER; dx of
+ * a fine block is half its parent's.  The tables (HOST, copied):
+ *   parent   [nblocks][4]: parent block id and the offset of this block's
+ *            origin in parent cells (0 or n/2 per dimension); (-1,0,0,0) on
+ *            level 0;
+ *   children [nblocks][8]: the 2^ndim children of a covered (refined) block in
+ *            octant order x + 2y + 4z (x fastest), -1 elsewhere.
+ * On such a context every stage restricts the covered blocks (mean of their
+ * children), prolongs into the fine guard cells facing the coarser level
+ * (u_c + sum_d s_d sigma_d / 4, MC slopes of the conserved coarse variables),
+ * updates the leaf blocks and replaces the coarse flux through each face on
+ * the fine-region boundary by the mean of the fine fluxes through it.
+ * hydro_step / hydro_step_cfl / hydro_advance[_host] end with a restriction;
+ * hydro_compute_dt uses leaf cells only; hydro_fill_guardcells restricts and
+ * then fills every guard cell (prolongation where the region is coarser).
+ * hydro_stage / hydro_stage_guarded return GBH_ERR_UNSUPPORTED on such a
+ * context.  Supported: exactly two levels, cubic (3-D) or square (2-D) blocks
+ * of even size, fine blocks not on the domain boundary. */
+typedef struct gbh_refinement {
+  const int32_t *parent;
+  const int32_t *children;
+} gbh_refinement;
+
+int gbh_create_refined(const gbh_params *params, const gbh_refinement *refinement, gbh_ctx **out);
 
 /* Release everything gbh_create allocated.  Synchronises the device.  NULL is a no-op. */
 int gbh_destroy(gbh_ctx *ctx);

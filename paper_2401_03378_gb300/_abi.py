@@ -15,6 +15,7 @@ GBH_ERR_UNPHYSICAL = -3
 GBH_ERR_NOMEM = -4
 GBH_ERR_UNSUPPORTED = -5
 GBH_BC_OUTFLOW = -1
+GBH_NBR_COARSER = -2
 
 ERROR_NAMES = {
     GBH_ERR_INVAL: "GBH_ERR_INVAL",
@@ -42,11 +43,16 @@ class GbhParams(C.Structure):
     ]
 
 
+class GbhRefinement(C.Structure):
+    _fields_ = [("parent", C.POINTER(C.c_int32)), ("children", C.POINTER(C.c_int32))]
+
+
 # name -> (restype, argtypes); the exported symbols of libgbhydro.so
 _vp = C.c_void_p
 _dp = C.c_void_p          # device or host double* passed as an address
 SIGNATURES = {
     "gbh_create": (C.c_int, [C.POINTER(GbhParams), C.POINTER(_vp)]),
+    "gbh_create_refined": (C.c_int, [C.POINTER(GbhParams), C.POINTER(GbhRefinement), C.POINTER(_vp)]),
     "gbh_destroy": (C.c_int, [_vp]),
     "gbh_last_error": (C.c_char_p, [_vp]),
     "gbh_state_bytes": (C.c_longlong, [_vp]),

@@ -37,6 +37,18 @@ struct gbh_ctx {
   double* d_host_dt = nullptr;
   double* d_host_hist = nullptr;
   int host_hist_cap = 0;
+  // two-level composite grid (gbh_create_refined)
+  bool refined = false;
+  int* d_parent = nullptr;
+  int* d_children = nullptr;
+  int* d_active = nullptr;          // leaf blocks
+  int nactive = 0;
+  int* d_covered = nullptr;
+  int* d_fine = nullptr;
+  int* d_flux_slot = nullptr;       // [nblocks][6]
+  double* d_flux_reg = nullptr;
+  gbh::RefluxEntry* d_reflux = nullptr;
+  gbh::AmrArgs amr{};
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -114,6 +126,12 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   gbh::stage_args_common(&A, c->lay, c->eos);
   A.smax_acc = dt_epilogue ? c->d_words : nullptr;
   A.floor_count = c->d_words + 1;
+  if (c->refined) {
+    A.block_list = c->d_active;
+    A.nlist = c->nactive;
+    A.flux_slot = c->d_flux_slot;
+    A.flux_reg = c->d_flux_reg;
+  }
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
   if (rc) return rc;
@@ -123,11 +141,46 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   return rc;
 }
 
+// One stage on a two-level composite grid (all-levels variant): restrict the
+// covered coarse blocks of Uin, prolong into the fine guard slabs that face
+// the coarser level, update the leaf blocks (writing the boundary fluxes to
+// the flux registers), and correct the coarse side of the fine-region
+// boundary.  Uin's covered blocks and fine guard cells are rewritten.
+int refined_stage(gbh_ctx* c, double* Uin, const double* Un, double* Uout, const double* dt_dev, double dt,
+                  double a, double b, cudaStream_t s) {
+  int rc = cuda_err(c, gbh::launch_restrict(Uin, c->amr, s), "restrict launch");
+  if (rc) return rc;
+  rc = cuda_err(c, gbh::launch_prolong(Uin, c->amr, 2, true, s), "prolong launch");
+  if (rc) return rc;
+  rc = stage_launch(c, Uin, Un, Uout, dt_dev, dt, a, b, true, false, s);
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, s), "reflux launch");
+}
+
+// One SSP-RK2 step on a two-level grid; ends with the restriction of the new
+// state so that covered coarse cells hold the mean of their children.
+int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
+  int rc = refined_stage(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, s);
+  if (rc) return rc;
+  rc = refined_stage(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, s);
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
+}
+
+gbh::DtArgs dt_args(gbh_ctx* c, const double* U) {
+  gbh::DtArgs A{U, c->d_inv_dx, c->lay, c->eos, c->d_words, nullptr, 0};
+  if (c->refined) {
+    A.block_list = c->d_active;
+    A.nlist = c->nactive;
+  }
+  return A;
+}
+
 }  // namespace
 
 namespace gbh {
 
-int validate_params(const gbh_params* p) {
+int validate_params(const gbh_params* p, bool allow_coarser) {
   if (!p) return set_err(nullptr, GBH_ERR_INVAL, "params is NULL");
   if (p->ndim != 2 && p->ndim != 3) return set_err(nullptr, GBH_ERR_INVAL, "ndim must be 2 or 3 (got %d)", p->ndim);
   if (p->nblocks < 1) return set_err(nullptr, GBH_ERR_INVAL, "nblocks must be >= 1");
@@ -147,7 +200,7 @@ int validate_params(const gbh_params* p) {
   for (long long b = 0; b < p->nblocks; ++b) {
     for (int e = 0; e < nn; ++e) {
       const int v = p->nbr[b * nn + e];
-      if (v >= p->nblocks || (v < 0 && v != GBH_BC_OUTFLOW))
+      if (v >= p->nblocks || (v < 0 && v != GBH_BC_OUTFLOW && !(allow_coarser && v == GBH_NBR_COARSER)))
         return set_err(nullptr, GBH_ERR_INVAL, "nbr[%lld][%d] = %d is out of range", b, e, v);
     }
     if (p->nbr[b * nn + centre] != (int)b)
@@ -212,13 +265,10 @@ int set_create_error(int code, const char* msg) { return set_err(nullptr, code, 
 
 using gbh::validate_params;
 
-extern "C" {
+static int create_common(const gbh_params* p, gbh_ctx** out);
+extern "C" int gbh_destroy(gbh_ctx* c);
 
-int gbh_create(const gbh_params* p, gbh_ctx** out) {
-  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
-  *out = nullptr;
-  int rc = validate_params(p);
-  if (rc) return rc;
+static int create_common(const gbh_params* p, gbh_ctx** out) {
   gbh_ctx* c = new (std::nothrow) gbh_ctx();
   if (!c) return set_err(nullptr, GBH_ERR_NOMEM, "host allocation failed");
   gbh::layout_from_params(p, &c->lay, &c->eos);
@@ -252,6 +302,148 @@ int gbh_create(const gbh_params* p, gbh_ctx** out) {
   return GBH_OK;
 }
 
+
+extern "C" {
+
+int gbh_create(const gbh_params* p, gbh_ctx** out) {
+  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_params(p, false);
+  if (rc) return rc;
+  return create_common(p, out);
+}
+
+int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** out) {
+  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_params(p, true);
+  if (rc) return rc;
+  if (!r || !r->parent || !r->children) return set_err(nullptr, GBH_ERR_INVAL, "refinement tables are required");
+  const int nd = p->ndim, nn = nd == 3 ? 27 : 9, nch = nd == 3 ? 8 : 4;
+  const int n[3] = {p->nxb, p->nyb, p->nzb};
+  if (p->nxb % 2 || (nd == 3 && p->nzb != p->nxb))
+    return set_err(nullptr, GBH_ERR_UNSUPPORTED, "two-level grids need even, cubic (3-D) or square (2-D) blocks");
+  const long long NB = p->nblocks;
+  const int32_t* par = r->parent;
+  const int32_t* chl = r->children;
+  for (long long b = 0; b < NB; ++b) {
+    const int P = par[4 * b];
+    if (P < 0) {
+      if (P != -1 || par[4 * b + 1] || par[4 * b + 2] || par[4 * b + 3])
+        return set_err(nullptr, GBH_ERR_INVAL, "parent[%lld] of a level-0 block must be (-1, 0, 0, 0)", b);
+      for (int e = 0; e < nn; ++e)
+        if (p->nbr[b * nn + e] == GBH_NBR_COARSER)
+          return set_err(nullptr, GBH_ERR_INVAL, "level-0 block %lld has a GBH_NBR_COARSER entry", b);
+      continue;
+    }
+    if (P >= NB || par[4 * P] != -1)
+      return set_err(nullptr, GBH_ERR_UNSUPPORTED, "block %lld: only two levels are supported", b);
+    int oct = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int o = par[4 * b + 1 + d];
+      if (d >= nd ? o != 0 : (o != 0 && o != n[d] / 2))
+        return set_err(nullptr, GBH_ERR_INVAL, "parent offset of block %lld is not 0 or n/2", b);
+      if (o) oct |= 1 << d;
+      if (d < nd && std::fabs(p->dx[3 * b + d] * 2.0 - p->dx[3 * P + d]) > 1e-14 * p->dx[3 * P + d])
+        return set_err(nullptr, GBH_ERR_INVAL, "block %lld: cell width must be half its parent's", b);
+    }
+    if (chl[8 * P + oct] != (int)b)
+      return set_err(nullptr, GBH_ERR_INVAL, "children of %d do not list block %lld", P, b);
+  }
+  for (long long b = 0; b < NB; ++b) {
+    const bool has = chl[8 * b] >= 0;
+    for (int o = 0; o < 8; ++o) {
+      const int ch = chl[8 * b + o];
+      if (!has || o >= nch) {
+        if (ch != -1) return set_err(nullptr, GBH_ERR_INVAL, "children[%lld][%d] must be -1", b, o);
+      } else if (ch < 0 || ch >= NB || par[4 * ch] != (int)b) {
+        return set_err(nullptr, GBH_ERR_INVAL, "children[%lld][%d] = %d is not a child of it", b, o, ch);
+      }
+    }
+  }
+  // lists, flux-register slots and the flux-correction entries
+  std::vector<int> active, covered, fine, slot(6 * (size_t)NB, -1);
+  std::vector<gbh::RefluxEntry> refl;
+  std::vector<int> face(6 * (size_t)NB);
+  std::vector<double> inv(3);
+  for (long long b = 0; b < NB; ++b) gbh::face_table_from_params(p, b, &face[6 * b], inv.data());
+  int nslots = 0;
+  for (long long b = 0; b < NB; ++b) {
+    (chl[8 * b] >= 0 ? covered : active).push_back((int)b);
+    if (par[4 * b] < 0) continue;
+    bool any = false;
+    for (int e = 0; e < nn; ++e) any = any || p->nbr[b * nn + e] == GBH_NBR_COARSER;
+    if (any) fine.push_back((int)b);
+    for (int f = 0; f < 2 * nd; ++f)
+      if (face[6 * b + f] == GBH_NBR_COARSER) slot[6 * b + f] = nslots++;
+  }
+  for (long long b = 0; b < NB; ++b) {
+    if (par[4 * b] >= 0 || chl[8 * b] >= 0) continue;
+    for (int f = 0; f < 2 * nd; ++f) {
+      const int nb = face[6 * b + f];
+      if (nb < 0 || chl[8 * nb] < 0) continue;
+      gbh::RefluxEntry en{};
+      en.block = (int)b;
+      en.face = f;
+      en.coarse_slot = slot[6 * b + f] = nslots++;
+      const int d = f >> 1, side = f & 1;
+      const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+      for (int q = 0; q < 4; ++q) en.fine_slot[q] = -1;
+      for (int q2 = 0; q2 < (nd == 3 ? 2 : 1); ++q2)
+        for (int q1 = 0; q1 < 2; ++q1) {
+          const int oct = ((side ? 0 : 1) << d) | (q1 << t1d) | (nd == 3 ? (q2 << t2d) : 0);
+          const int ch = chl[8 * nb + oct];
+          const int fs = slot[6 * (size_t)ch + 2 * d + (1 - side)];
+          if (fs < 0)
+            return set_err(nullptr, GBH_ERR_INVAL, "fine block %d facing coarse block %lld is not marked GBH_NBR_COARSER", ch, b);
+          en.fine_slot[q1 + 2 * q2] = fs;
+        }
+      refl.push_back(en);
+    }
+  }
+  gbh_ctx* c = nullptr;
+  if ((rc = create_common(p, &c))) return rc;
+  c->refined = true;
+  c->nactive = (int)active.size();
+  const size_t fstride = 5 * (size_t)p->nxb * (nd == 3 ? p->nxb : 1);
+  cudaError_t e = cudaMalloc(&c->d_parent, sizeof(int) * 4 * NB);
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    if (e != cudaSuccess) return;
+    if (bytes == 0) bytes = 8;
+    e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess && src) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_parent, par, sizeof(int) * 4 * NB, cudaMemcpyHostToDevice);
+  up((void**)&c->d_children, chl, sizeof(int) * 8 * NB);
+  up((void**)&c->d_active, active.data(), sizeof(int) * active.size());
+  up((void**)&c->d_covered, covered.empty() ? nullptr : covered.data(), sizeof(int) * covered.size());
+  up((void**)&c->d_fine, fine.empty() ? nullptr : fine.data(), sizeof(int) * fine.size());
+  up((void**)&c->d_flux_slot, slot.data(), sizeof(int) * slot.size());
+  up((void**)&c->d_flux_reg, nullptr, sizeof(double) * fstride * (size_t)(nslots ? nslots : 1));
+  up((void**)&c->d_reflux, refl.empty() ? nullptr : refl.data(), sizeof(gbh::RefluxEntry) * refl.size());
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
+    set_err(nullptr, code, "gbh_create_refined: %s", cudaGetErrorString(e));
+    gbh_destroy(c);
+    return code;
+  }
+  gbh::AmrArgs& A = c->amr;
+  A.lay = c->lay;
+  A.nbr = c->d_nbr;
+  A.parent = c->d_parent;
+  A.children = c->d_children;
+  A.covered = c->d_covered;
+  A.ncovered = (int)covered.size();
+  A.fine = c->d_fine;
+  A.nfine = (int)fine.size();
+  A.reflux = c->d_reflux;
+  A.nreflux = (int)refl.size();
+  A.flux_reg = c->d_flux_reg;
+  A.inv_dx = c->d_inv_dx;
+  *out = c;
+  return GBH_OK;
+}
+
 int gbh_destroy(gbh_ctx* c) {
   if (!c) return GBH_OK;
   cudaDeviceSynchronize();
@@ -263,6 +455,14 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_host_state);
   cudaFree(c->d_host_dt);
   cudaFree(c->d_host_hist);
+  cudaFree(c->d_parent);
+  cudaFree(c->d_children);
+  cudaFree(c->d_active);
+  cudaFree(c->d_covered);
+  cudaFree(c->d_fine);
+  cudaFree(c->d_flux_slot);
+  cudaFree(c->d_flux_reg);
+  cudaFree(c->d_reflux);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
   return GBH_OK;
@@ -278,8 +478,12 @@ int hydro_fill_guardcells(gbh_ctx* c, double* U, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "U must be a non-null 8-byte aligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->refined && (rc = cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch"))) return rc;
   gbh::FillArgs A{U, c->d_nbr, c->d_face, c->lay};
-  return cuda_err(c, gbh::launch_fill(A, (cudaStream_t)stream), "fill kernel launch");
+  if ((rc = cuda_err(c, gbh::launch_fill(A, s), "fill kernel launch"))) return rc;
+  if (c->refined) return cuda_err(c, gbh::launch_prolong(U, c->amr, c->lay.g, false, s), "prolong launch");
+  return GBH_OK;
 }
 
 int hydro_compute_dt(gbh_ctx* c, const double* U, double* dt_dev, void* stream) {
@@ -287,8 +491,7 @@ int hydro_compute_dt(gbh_ctx* c, const double* U, double* dt_dev, void* stream) 
   if (rc) return rc;
   if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  gbh::DtArgs A{U, c->d_inv_dx, c->lay, c->eos, c->d_words};
-  rc = cuda_err(c, gbh::launch_dt_reduce(A, s), "dt reduce launch");
+  rc = cuda_err(c, gbh::launch_dt_reduce(dt_args(c, U), s), "dt reduce launch");
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
 }
@@ -297,6 +500,7 @@ static int stage_common(gbh_ctx* c, const double* Uin, const double* Un, double*
                         double b, bool gather, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "single stages are not exposed on two-level contexts");
   if ((rc = check_dt(c, dt))) return rc;
   if (!Uin || !Uout || !aligned8(Uin) || !aligned8(Uout)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   if (!std::isfinite(a) || !std::isfinite(b)) return set_err(c, GBH_ERR_INVAL, "a and b must be finite");
@@ -323,12 +527,20 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if ((rc = check_dt(c, dt))) return rc;
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->refined) return refined_step(c, U, nullptr, dt, s);
   rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
   if (rc) return rc;
   return stage_launch(c, c->d_scratch, U, U, nullptr, dt, 0.5, 0.5, true, false, s);
 }
 
 static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
+  if (c->refined) {
+    // the CFL speed must see the flux-corrected state: separate reduction
+    int rc = refined_step(c, U, dt_dev, 0.0, s);
+    if (rc) return rc;
+    if ((rc = cuda_err(c, gbh::launch_dt_reduce(dt_args(c, U), s), "dt reduce launch"))) return rc;
+    return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
+  }
   int rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
   if (rc) return rc;
   rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);

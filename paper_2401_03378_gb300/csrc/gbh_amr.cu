@@ -1,0 +1,224 @@
+// gbh_amr.cu -- two-level composite grid: restriction, prolongation into fine
+// guard cells, and the coarse-side flux correction.
+//
+// Sec. 4.2 of the paper (all-levels listing): every leaf block of every level
+// is advanced in one sweep; then the fluxes through coarse-fine boundaries are
+// communicated and the coarse side corrected; Sec. 2.2: blocks of all levels
+// hold the same number of cells, only the cell width differs.  The formulas
+// are not in the paper; the readings used (refinement ratio 2, one dt):
+//  - restriction: a covered coarse cell = mean of its 2^d children, summed in
+//    the order (z, y, x) of the child offsets;
+//  - prolongation: a fine guard cell whose region lies on the coarser level =
+//    u_c + sum_d s_d sigma_d / 4 (s_d = -1 for the lower child, +1 for the
+//    upper), sigma_d the MC slope of the conserved coarse variable;
+//  - flux correction: the coarse flux through a face on the boundary of the
+//    fine region is replaced by the mean of the fine fluxes through it:
+//    U += b dt (F_c - mean F_f) / dx (low side of the face; opposite sign on
+//    the high side), b = the stage's weight of L.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbh_device.cuh"
+#include "gbh_internal.h"
+
+namespace gbh {
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+__device__ __forceinline__ long long at(const Layout& L, int b, int v, int i, int j, int k) {
+  return (long long)b * L.bstride + v * L.vstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+}
+
+// Restriction: one thread per (covered block, interior cell); 5 variables.
+__global__ void restrict_kernel(double* U, const AmrArgs a) {
+  const Layout& L = a.lay;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  const int h[3] = {L.nx / 2, L.ny / 2, L.ndim == 3 ? L.nz / 2 : 1};
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * a.ncovered;
+  const double w = L.ndim == 3 ? 0.125 : 0.25;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int cb = __ldg(a.covered + t / per);
+    long long r = t % per;
+    const int i = (int)(r % n[0]);
+    r /= n[0];
+    const int j = (int)(r % n[1]);
+    const int k = (int)(r / n[1]);
+    const int oct = (i / h[0]) + 2 * (j / h[1]) + (L.ndim == 3 ? 4 * (k / h[2]) : 0);
+    const int child = __ldg(a.children + 8 * cb + oct);
+    const int fi = 2 * (i % h[0]), fj = 2 * (j % h[1]), fk = L.ndim == 3 ? 2 * (k % h[2]) : 0;
+    for (int v = 0; v < 5; ++v) {
+      double s = 0.0;
+      for (int dz = 0; dz < (L.ndim == 3 ? 2 : 1); ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) s = __dadd_rn(s, U[at(L, child, v, fi + dx, fj + dy, fk + dz)]);
+      U[at(L, cb, v, i, j, k)] = __dmul_rn(s, w);
+    }
+  }
+}
+
+// Coarse cell at parent-local coordinates (x, y, z), which may lie outside
+// the parent block in any direction by at most one block: resolved through
+// the parent's 27-entry neighbour table (clamped at an outflow edge).
+__device__ __forceinline__ long long coarse_offset(const AmrArgs& a, int parent, int x, int y, int z) {
+  const Layout& L = a.lay;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  int c[3] = {x, y, z};
+  int o[3];
+  for (int d = 0; d < 3; ++d) o[d] = c[d] < 0 ? -1 : (c[d] >= n[d] ? 1 : 0);
+  int blk = parent;
+  if (o[0] | o[1] | o[2]) {
+    const int e = L.ndim == 3 ? (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
+    const int nb = __ldg(a.nbr + (long long)(L.ndim == 3 ? 27 : 9) * parent + e);
+    if (nb >= 0) {
+      blk = nb;
+      for (int d = 0; d < 3; ++d) c[d] -= o[d] * n[d];
+    } else {
+      for (int d = 0; d < 3; ++d) c[d] = c[d] < 0 ? 0 : (c[d] >= n[d] ? n[d] - 1 : c[d]);
+    }
+  }
+  return (long long)blk * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g);
+}
+
+__device__ __forceinline__ int floor_div2(int x) { return x >= 0 ? x / 2 : -((1 - x) / 2); }
+
+// Prolongation into the guard cells of fine blocks whose region lies on the
+// coarser level (neighbour code GBH_NBR_COARSER).  One thread per (task,
+// cell): a task is one fine block; `depth` limits the guard depth and
+// `faces_only` restricts to the face slabs (what the stage kernel reads).
+__global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_only) {
+  const Layout& L = a.lay;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  const int gg[3] = {depth, depth, L.ndim == 3 ? depth : 0};
+  const int ex[3] = {n[0] + 2 * gg[0], n[1] + 2 * gg[1], n[2] + 2 * gg[2]};
+  const long long per = (long long)ex[0] * ex[1] * ex[2];
+  const long long total = per * a.nfine;
+  const int nn = L.ndim == 3 ? 27 : 9;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int fb = __ldg(a.fine + t / per);
+    long long r = t % per;
+    int c[3];
+    c[0] = (int)(r % ex[0]) - gg[0];
+    r /= ex[0];
+    c[1] = (int)(r % ex[1]) - gg[1];
+    c[2] = (int)(r / ex[1]) - gg[2];
+    int o[3], nout = 0;
+    for (int d = 0; d < 3; ++d) {
+      o[d] = c[d] < 0 ? -1 : (c[d] >= n[d] ? 1 : 0);
+      nout += o[d] != 0;
+    }
+    if (nout == 0 || (faces_only && nout != 1)) continue;
+    const int e = L.ndim == 3 ? (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
+    if (__ldg(a.nbr + (long long)nn * fb + e) != GBH_NBR_COARSER) continue;
+    const int parent = __ldg(a.parent + 4 * fb);
+    int P[3], s[3];
+    for (int d = 0; d < 3; ++d) {
+      if (d < L.ndim) {
+        const int hh = floor_div2(c[d]);
+        P[d] = __ldg(a.parent + 4 * fb + 1 + d) + hh;
+        s[d] = (c[d] - 2 * hh) == 0 ? -1 : 1;
+      } else {
+        P[d] = 0;
+        s[d] = 0;
+      }
+    }
+    const long long oc = coarse_offset(a, parent, P[0], P[1], P[2]);
+    long long om[3], op[3];
+    for (int d = 0; d < L.ndim; ++d) {
+      int Pm[3] = {P[0], P[1], P[2]}, Pp[3] = {P[0], P[1], P[2]};
+      Pm[d] -= 1;
+      Pp[d] += 1;
+      om[d] = coarse_offset(a, parent, Pm[0], Pm[1], Pm[2]);
+      op[d] = coarse_offset(a, parent, Pp[0], Pp[1], Pp[2]);
+    }
+    for (int v = 0; v < 5; ++v) {
+      const long long vo = v * L.vstride;
+      const double q0 = U[oc + vo];
+      double val = q0;
+      for (int d = 0; d < L.ndim; ++d) {
+        const double h = mc_half_slope(U[om[d] + vo], q0, U[op[d] + vo]);   // sigma / 2
+        val = __dadd_rn(val, __dmul_rn(0.5 * h, (double)s[d]));
+      }
+      U[at(L, fb, v, c[0], c[1], c[2])] = val;
+    }
+  }
+}
+
+// Flux correction on the coarse side of the fine-region boundary.  One
+// thread per (interface face, face cell).
+__global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, double dt_val, double coef) {
+  const Layout& L = a.lay;
+  const int N = L.nx;
+  const int n2 = L.ndim == 3 ? N : 1;
+  const int half = N / 2;
+  const long long per = (long long)N * n2;
+  const long long total = per * a.nreflux;
+  const double dt = dt_dev ? *dt_dev : dt_val;
+  const long long sstride = 5LL * N * n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const RefluxEntry en = a.reflux[t / per];
+    const int r = (int)(t % per);
+    const int t1 = r % N, t2 = r / N;
+    const int d = en.face >> 1, side = en.face & 1;
+    // coarse cell adjacent to the face
+    int x[3];
+    const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+    x[d] = side ? (d == 0 ? L.nx : d == 1 ? L.ny : L.nz) - 1 : 0;
+    x[t1d] = t1;
+    x[t2d] = L.ndim == 3 ? t2 : 0;
+    const int q1 = t1 / half, q2 = L.ndim == 3 ? t2 / half : 0;
+    const int fs = en.fine_slot[q1 + 2 * q2];
+    const int f1 = 2 * (t1 % half), f2 = L.ndim == 3 ? 2 * (t2 % half) : 0;
+    const double* Fc = a.flux_reg + (long long)en.coarse_slot * sstride;
+    const double* Ff = a.flux_reg + (long long)fs * sstride;
+    const double idx = __ldg(a.inv_dx + 3 * en.block + d);
+    const double nfine = L.ndim == 3 ? 0.25 : 0.5;
+    for (int v = 0; v < 5; ++v) {
+      double fsum = 0.0;
+      for (int b2 = 0; b2 < (L.ndim == 3 ? 2 : 1); ++b2)
+        for (int b1 = 0; b1 < 2; ++b1)
+          fsum = __dadd_rn(fsum, Ff[((long long)v * n2 + f2 + b2) * N + f1 + b1]);
+      const double fmean = __dmul_rn(fsum, nfine);
+      const double fc = Fc[((long long)v * n2 + (L.ndim == 3 ? t2 : 0)) * N + t1];
+      const double corr = side ? __dsub_rn(fc, fmean) : __dsub_rn(fmean, fc);
+      const long long o = at(L, en.block, v, x[0], x[1], x[2]);
+      U[o] = __dadd_rn(U[o], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s) {
+  if (a.ncovered == 0) return cudaSuccess;
+  restrict_kernel<<<grid_for((long long)a.ncovered * a.lay.nx * a.lay.ny * a.lay.nz), kThreads, 0, s>>>(U, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s) {
+  if (a.nfine == 0) return cudaSuccess;
+  const Layout& L = a.lay;
+  const long long per = (long long)(L.nx + 2 * depth) * (L.ny + 2 * depth) * (L.ndim == 3 ? L.nz + 2 * depth : 1);
+  prolong_kernel<<<grid_for(per * a.nfine), kThreads, 0, s>>>(U, a, depth, faces_only ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, double dt, double coef,
+                          cudaStream_t s) {
+  if (a.nreflux == 0) return cudaSuccess;
+  const long long per = (long long)a.lay.nx * (a.lay.ndim == 3 ? a.lay.nx : 1);
+  reflux_kernel<<<grid_for(per * a.nreflux), kThreads, 0, s>>>(U, a, dt_dev, dt, coef);
+  return cudaGetLastError();
+}
+
+}  // namespace gbh

@@ -72,13 +72,13 @@ __global__ void fill_kernel(const FillArgs a) {
 __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
   const Layout& L = a.lay;
   const long long per = (long long)L.nx * L.ny * L.nz;
-  const long long total = per * L.nblocks;
+  const long long total = per * (a.block_list ? a.nlist : L.nblocks);
   const bool d3 = L.ndim == 3;
   double smax = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / per);
-    long long r = t - (long long)b * per;
+    const int b = a.block_list ? __ldg(a.block_list + t / per) : (int)(t / per);
+    long long r = t % per;
     const int i = (int)(r % L.nx);
     r /= L.nx;
     const int j = (int)(r % L.ny);

@@ -43,12 +43,45 @@ struct StageArgs {
   Eos eos;
   unsigned long long* smax_acc;     // if non-null: max signal-speed sum of Uout (bit pattern)
   unsigned long long* floor_count;  // floor applications on interior cells
+  // two-level composite grids (all null on a uniform grid)
+  const int* block_list;            // blocks to update (leaf blocks); null = all blocks
+  int nlist;                        // entries of block_list
+  const int* flux_slot;             // [nblocks][6] flux-register slot of a face, or -1
+  double* flux_reg;                 // [slots][5][n_t2][N] face fluxes (t1 fastest)
 };
+
+// One coarse face on the boundary of the fine region: the coarse block, its
+// face (2*dim + side), its flux-register slot and the slots of the 2^(d-1)
+// fine faces covering it (quadrant index q1 + 2*q2 of the tangential halves).
+struct RefluxEntry {
+  int block, face, coarse_slot;
+  int fine_slot[4];
+};
+
+struct AmrArgs {
+  Layout lay;
+  const int* nbr;        // [nblocks][3^ndim]
+  const int* parent;     // [nblocks][4]: parent id, offset in parent cells (x, y, z)
+  const int* children;   // [nblocks][8]
+  const int* covered;    // covered (non-leaf) coarse blocks
+  int ncovered;
+  const int* fine;       // fine blocks with at least one region on the coarser level
+  int nfine;
+  const RefluxEntry* reflux;
+  int nreflux;
+  double* flux_reg;
+  const double* inv_dx;
+};
+
+cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s);
+cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s);
+cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, double dt, double coef,
+                          cudaStream_t s);
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 
 // Host helpers shared by the entry points (gbh_abi.cu).
-int validate_params(const gbh_params* p);     // GBH_OK or an error code; message in gbh_last_error(NULL)
+int validate_params(const gbh_params* p, bool allow_coarser);  // GBH_OK or an error code; message in gbh_last_error(NULL)
 void layout_from_params(const gbh_params* p, Layout* L, Eos* e);
 void face_table_from_params(const gbh_params* p, long long b, int face[6], double inv_dx[3]);
 void stage_args_common(StageArgs* A, const Layout& L, const Eos& e);
@@ -70,6 +103,8 @@ struct DtArgs {
   Layout lay;
   Eos eos;
   unsigned long long* smax_acc;
+  const int* block_list;   // blocks to include (null = all)
+  int nlist;
 };
 cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s);
 cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_out, double* hist,

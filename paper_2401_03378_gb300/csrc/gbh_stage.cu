@@ -37,7 +37,9 @@ namespace {
 // b, given in interior coordinates that may lie outside the block in at most
 // one dimension by at most 2 cells.  In gather mode such a cell is read from
 // the face neighbour's interior, or, at an outflow edge (GBH_BC_OUTFLOW), from
-// the nearest interior cell of b; in guard mode from b's own guard cells.
+// the nearest interior cell of b, or, across a coarse-fine boundary
+// (GBH_NBR_COARSER), from b's own (prolonged) guard cells; in guard mode
+// always from b's own guard cells.
 template <int N>
 __device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int i, int j, int k) {
   const Layout& L = a.lay;
@@ -62,7 +64,7 @@ __device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int 
           case FACE_ZM: k += L.nz; break;
           default: k -= L.nz; break;
         }
-      } else {
+      } else if (nb == GBH_BC_OUTFLOW) {
         switch (f) {
           case FACE_XM: i = 0; break;
           case FACE_XP: i = N - 1; break;
@@ -72,6 +74,9 @@ __device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int 
           default: k = L.nz - 1; break;
         }
       }
+      // GBH_NBR_COARSER: the region lies on the coarser level; b's own guard
+      // cells hold the prolonged data
+
     }
   }
   return (long long)blk * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
@@ -103,8 +108,9 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
   const Layout& L = a.lay;
   const int tid = threadIdx.x;
   const int tx = tid % N, ty = tid / N;
-  const int b = blockIdx.x / a.nchunks;
-  const int chunk = blockIdx.x - b * a.nchunks;
+  const int slot_idx = blockIdx.x / a.nchunks;
+  const int chunk = blockIdx.x - slot_idx * a.nchunks;
+  const int b = a.block_list ? __ldg(a.block_list + slot_idx) : slot_idx;
   const int k0 = DIM3 ? chunk * a.kchunk : 0;
   const int k1 = DIM3 ? min(L.nz, k0 + a.kchunk) : 1;
   const double dt = a.dt_dev ? *a.dt_dev : a.dt;
@@ -257,6 +263,29 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
       out[v] = a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
       a.Uout[o] = out[v];
     }
+    if (a.flux_slot) {
+      // fluxBuff: fluxes through faces on a coarse-fine boundary, for the correction
+      const long long n2 = DIM3 ? N : 1;
+      const long long ss = 5 * n2 * N;
+      const int* fsl = a.flux_slot + 6 * b;
+      const int t2k = DIM3 ? k : 0;
+      if (tx == 0 && fsl[FACE_XM] >= 0)
+        for (int v = 0; v < 5; ++v)
+          a.flux_reg[fsl[FACE_XM] * ss + (v * n2 + t2k) * N + ty] = sFx[(v * N + ty) * (N + 1)];
+      if (tx == N - 1 && fsl[FACE_XP] >= 0)
+        for (int v = 0; v < 5; ++v)
+          a.flux_reg[fsl[FACE_XP] * ss + (v * n2 + t2k) * N + ty] = sFx[(v * N + ty) * (N + 1) + N];
+      if (ty == 0 && fsl[FACE_YM] >= 0)
+        for (int v = 0; v < 5; ++v)
+          a.flux_reg[fsl[FACE_YM] * ss + (v * n2 + t2k) * N + tx] = sFy[(v * (N + 1)) * N + tx];
+      if (ty == N - 1 && fsl[FACE_YP] >= 0)
+        for (int v = 0; v < 5; ++v)
+          a.flux_reg[fsl[FACE_YP] * ss + (v * n2 + t2k) * N + tx] = sFy[(v * (N + 1) + N) * N + tx];
+      if (DIM3 && k == 0 && fsl[FACE_ZM] >= 0)
+        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZM] * ss + (v * n2 + ty) * N + tx] = Fzm[v];
+      if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
+        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + ty) * N + tx] = Fzp[v];
+    }
     if (a.smax_acc) {
       double W[5];
       cons_to_prim(out, W, e);
@@ -295,7 +324,7 @@ size_t smem_for() {
 
 template <int N, bool D3>
 cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
-  const unsigned grid = (unsigned)a.lay.nblocks * (unsigned)a.nchunks;
+  const unsigned grid = (unsigned)(a.block_list ? a.nlist : a.lay.nblocks) * (unsigned)a.nchunks;
   stage_kernel<N, D3><<<grid, N * N, smem_for<N>(), s>>>(a);
   return cudaGetLastError();
 }

@@ -71,7 +71,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 }  // namespace
 
 extern "C" int hydro_step_static(const gbh_params* params, double* U, double dt, void* stream) {
-  int rc = gbh::validate_params(params);
+  int rc = gbh::validate_params(params, false);
   if (rc) return rc;
   if (!U || ((uintptr_t)U & 7u)) return fail(GBH_ERR_INVAL, "U must be a non-null 8-byte aligned device pointer");
   if (!std::isfinite(dt) || !(dt > 0.0)) return fail(GBH_ERR_INVAL, "dt must be finite and > 0");

@@ -11,6 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 GBH_BC_OUTFLOW = -1
+GBH_NBR_COARSER = -2
 
 
 def neighbour_table(ndim: int, nb, periodic) -> np.ndarray:
@@ -45,3 +46,39 @@ def uniform_widths(nblocks: int, dx) -> np.ndarray:
     w = np.empty((nblocks, 3), dtype=np.float64)
     w[:] = np.asarray(dx, dtype=np.float64)
     return w
+
+
+def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
+    """Tables of a two-level composite grid: the complete coarse lattice nb0
+    (blocks 0..n0-1) plus a fine lattice at half the cell width over the coarse
+    blocks [lo, hi) (blocks n0.., lexicographic over the fine lattice).
+
+    Returns (nbr, dx, parent, children) in the layout gbh_create_refined takes.
+    """
+    nd = int(ndim)
+    nb0 = tuple(int(x) for x in nb0) + (1,) * (3 - len(nb0))
+    lo = tuple(int(x) for x in lo) + (0,) * (3 - len(lo))
+    hi = tuple(int(x) for x in hi) + (1,) * (3 - len(hi))
+    n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
+    nb1 = tuple(2 * (hi[d] - lo[d]) if d < nd else 1 for d in range(3))
+    n0 = nb0[0] * nb0[1] * nb0[2]
+    n1 = nb1[0] * nb1[1] * nb1[2]
+    cnbr = neighbour_table(nd, nb0, periodic)
+    fnbr = neighbour_table(nd, nb1, (False, False, False)).astype(np.int64)
+    fnbr = np.where(fnbr >= 0, fnbr + n0, GBH_NBR_COARSER).astype(np.int32)
+    nbr = np.concatenate([cnbr, fnbr], axis=0)
+    dx = np.empty((n0 + n1, 3))
+    dx[:n0] = np.asarray(dx0, dtype=np.float64)
+    dx[n0:] = np.asarray(dx0, dtype=np.float64) * 0.5
+    parent = np.zeros((n0 + n1, 4), dtype=np.int32)
+    parent[:n0, 0] = -1
+    children = np.full((n0 + n1, 8), -1, dtype=np.int32)
+    for f in range(n1):
+        fc = (f % nb1[0], (f // nb1[0]) % nb1[1], f // (nb1[0] * nb1[1]))
+        pc = tuple(lo[d] + fc[d] // 2 if d < nd else 0 for d in range(3))
+        pid = pc[0] + nb0[0] * (pc[1] + nb0[1] * pc[2])
+        off = tuple((fc[d] % 2) * (n[d] // 2) if d < nd else 0 for d in range(3))
+        parent[n0 + f] = (pid, *off)
+        oct_ = sum((fc[d] % 2) << d for d in range(nd))
+        children[pid, oct_] = n0 + f
+    return nbr, dx, parent, children

@@ -34,7 +34,8 @@ class Hydro:
                  nb: Optional[Sequence[int]] = None, periodic=(False, False, False),
                  extent=(1.0, 1.0, 1.0), nbr: Optional[np.ndarray] = None,
                  dx: Optional[np.ndarray] = None, gamma: float = 1.4, cfl: float = 0.8,
-                 small_rho: float = 1e-12, small_p: float = 1e-14):
+                 small_rho: float = 1e-12, small_p: float = 1e-14,
+                 parent: Optional[np.ndarray] = None, children: Optional[np.ndarray] = None):
         self.lib = _abi.load()
         self.ndim = int(ndim)
         nx, ny, nz = (int(n[0]), int(n[1]), int(n[2]) if ndim == 3 else 1)
@@ -59,7 +60,16 @@ class Hydro:
         p.nbr = self.nbr.ctypes.data_as(C.POINTER(C.c_int32))
         p.dx = self.dx.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()
-        rc = self.lib.gbh_create(C.byref(p), C.byref(ctx))
+        self.refined = parent is not None
+        if self.refined:
+            self.parent = np.ascontiguousarray(parent, dtype=np.int32)
+            self.children = np.ascontiguousarray(children, dtype=np.int32)
+            r = _abi.GbhRefinement()
+            r.parent = self.parent.ctypes.data_as(C.POINTER(C.c_int32))
+            r.children = self.children.ctypes.data_as(C.POINTER(C.c_int32))
+            rc = self.lib.gbh_create_refined(C.byref(p), C.byref(r), C.byref(ctx))
+        else:
+            rc = self.lib.gbh_create(C.byref(p), C.byref(ctx))
         if rc != 0:
             raise _abi.GbhError(rc, self.lib.gbh_last_error(None).decode())
         self.ctx = ctx
@@ -70,6 +80,16 @@ class Hydro:
         """Build from any object with ndim, nb, n, ng, bc, extent (e.g. workloads.Lattice)."""
         return cls(lat.ndim, lat.n, lat.ng, nb=lat.nb,
                    periodic=tuple(b == "periodic" for b in lat.bc), extent=lat.extent, **kw)
+
+    @classmethod
+    def from_two_level(cls, tl, **kw):
+        """Two-level composite grid: any object with `coarse` (a lattice), `lo`, `hi`
+        (the fine region in coarse blocks), e.g. workloads.TwoLevel."""
+        from .grid import two_level_tables
+        c = tl.coarse
+        nbr, dx, parent, children = two_level_tables(
+            c.ndim, c.nb, c.n, tl.lo, tl.hi, tuple(b == "periodic" for b in c.bc), c.dx)
+        return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children, **kw)
 
     # -- helpers -----------------------------------------------------------
     def close(self):

@@ -138,3 +138,53 @@ def test_neighbour_table_geometry(ndim, nb, per):
                     dims[d] <= 2 and per[d] for d in range(3))
             else:
                 assert tab[b, e] == -1
+
+
+def test_two_level_tables_structure():
+    from paper_2401_03378_gb300.grid import two_level_tables
+    nbr, dx, parent, children = two_level_tables(3, (4, 4, 4), (8, 8, 8), (1, 1, 1), (3, 3, 3),
+                                                 (False, False, False), (1 / 32, 1 / 32, 1 / 32))
+    n0 = 64
+    assert nbr.shape == (128, 27)
+    # every covered coarse block has 8 children whose parent is it, at the right offsets
+    for b in range(n0):
+        ch = children[b]
+        c = (b % 4, (b // 4) % 4, b // 16)
+        inside = all(1 <= c[d] < 3 for d in range(3))
+        assert (ch >= 0).all() == inside and ((ch < 0).all() or inside)
+        for o, f in enumerate(ch if inside else []):
+            assert parent[f, 0] == b
+            assert tuple(parent[f, 1:]) == tuple(((o >> d) & 1) * 4 for d in range(3))
+    # fine blocks: GBH_NBR_COARSER exactly where the fine lattice ends
+    fine_faces = nbr[n0:][:, [12, 14, 10, 16, 4, 22]]
+    assert (fine_faces == -2).sum() == 6 * 16
+    assert np.all(dx[n0:] == dx[:n0][0] * 0.5)
+
+
+def test_create_refined_rejects_bad_tables_without_gpu(lib):
+    from paper_2401_03378_gb300 import _abi
+    from paper_2401_03378_gb300.grid import two_level_tables
+    nbr, dx, parent, children = two_level_tables(3, (4, 4, 4), (8, 8, 8), (1, 1, 1), (3, 3, 3),
+                                                 (False, False, False), (1 / 32,) * 3)
+    def attempt(nbr_, dx_, parent_, children_):
+        keep = [np.ascontiguousarray(x) for x in (nbr_, dx_, parent_, children_)]
+        p = _abi.GbhParams()
+        p.ndim, p.nxb, p.nyb, p.nzb, p.nguard, p.nblocks = 3, 8, 8, 8, 4, keep[0].shape[0]
+        p.gamma, p.cfl, p.small_rho, p.small_p = 1.4, 0.8, 1e-12, 1e-14
+        p.nbr = keep[0].ctypes.data_as(C.POINTER(C.c_int32))
+        p.dx = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+        r = _abi.GbhRefinement()
+        r.parent = keep[2].ctypes.data_as(C.POINTER(C.c_int32))
+        r.children = keep[3].ctypes.data_as(C.POINTER(C.c_int32))
+        ctx = C.c_void_p()
+        return lib.gbh_create_refined(C.byref(p), C.byref(r), C.byref(ctx))
+    bad = children.copy(); bad[21, 3] = 7
+    assert attempt(nbr, dx, parent, bad) == -1
+    bad = parent.copy(); bad[70, 1] = 3
+    assert attempt(nbr, dx, bad, children) == -1
+    bad = dx.copy(); bad[90, 0] *= 1.5
+    assert attempt(nbr, bad, parent, children) == -1
+    bad = nbr.copy(); bad[5, 13 + 1] = -2
+    assert attempt(bad, dx, parent, children) == -1
+    bad = nbr.copy(); bad[64][bad[64] == -2] = -1   # a fine block claims an outflow edge
+    assert attempt(bad, dx, parent, children) == -1

@@ -121,9 +121,11 @@ class ClockSampler:
         sm = [num(r[1]) for r in rows if num(r[1])]
         mx = [num(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        counts = {names[i]: sum(1 for r in rows if r[5 + i].lower() == "active") for i in range(4)}
+        reasons = sorted(k for k, v in counts.items() if v)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons,
+                "reason_samples": {k: v for k, v in counts.items() if v}, "samples": len(rows),
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
@@ -244,6 +246,13 @@ def run_gpu(args):
         e2e = {"value": eunits / etmax, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(nbytes), "steps": args.e2e_steps}
 
+    two_level = None
+    if args.two_level_steps > 0:
+        two_level = run_two_level(args, gb, torch, barrier)
+    ensemble = None
+    if args.ensemble_steps > 0:
+        ensemble = run_ensemble(args, gb, torch, barrier)
+
     # roofline of the dominant kernel (the fused stage kernel, both stages)
     flops_per_launch = 0.5 * (FLOPS_STAGE1 + FLOPS_STAGE2) * zones
     ms_per_launch = stage_ms / max(stage_launches, 1)
@@ -289,6 +298,8 @@ def run_gpu(args):
         "clocks": clocks,
         "roofline": roof,
         "e2e": e2e,
+        "two_level": two_level,
+        "ensemble": ensemble,
         "unphysical_cells": nbad,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,6 +309,98 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_two_level(args, gb, torch, barrier):
+    """The two-level variant of the workload: 4096 coarse blocks (256^3) plus 4096
+    fine blocks at half the cell width over the central eighth of the volume,
+    one dt for both levels; zone-updates counted over leaf cells."""
+    import workloads as wl
+    nb = args.nb
+    tl = wl.two_level(wl.lattice_3d(nb, nb, nb, 16, 16, 16, 4), (nb // 4,) * 3, (3 * nb // 4,) * 3)
+    U0 = wl.sedov_two_level(tl)
+    h = gb.Hydro.from_two_level(tl)
+    U = torch.from_numpy(U0).cuda()
+    h.fill_guardcells(U)
+    dt = h.compute_dt(U)
+    for _ in range(args.warmup):
+        h.step_cfl(U, dt)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.two_level_steps):
+        h.step_cfl(U, dt)
+    e1.record(stream)
+    barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    nbad = h.check_state(U)
+    h.close()
+    del U
+    torch.cuda.empty_cache()
+    return {"workload": f"{WORKLOAD} -- two-level variant: {tl.n0} coarse + {tl.n1} fine blocks, "
+                        "restriction/prolongation in the guard fill, flux correction every stage",
+            "value": tl.leaf_cells * args.two_level_steps / secs, "unit": UNIT, "zones": tl.leaf_cells,
+            "steps": args.two_level_steps, "ms_per_step": 1e3 * secs / args.two_level_steps,
+            "launches_per_step": 11, "unphysical_cells": nbad}
+
+
+def run_ensemble(args, gb, torch, barrier):
+    """Batched ensemble: 96 independent periodic 2-D problems of sizes drawn from
+    {64^2, 128^2, 256^2, 512^2} in 16^2 blocks (Sod / Kelvin-Helmholtz with
+    log-normal density noise), each with its own dt, advanced together as one
+    CUDA graph of batched launches -- against one launch per problem per stage."""
+    import numpy as np
+    import workloads as wl
+    probs = wl.ensemble(count=96, seed=0)
+    lats = [l for l, _ in probs]
+    zones = sum(l.interior_cells for l in lats)
+    n = args.ensemble_steps
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    h = gb.Hydro.from_batch(lats)
+    U0 = np.concatenate([u for _, u in probs])
+    U = torch.from_numpy(U0).cuda()
+    kc, ipc = h.autotune(U)
+    dt = h.compute_dt(U)
+    h.advance_graph(U, n, dt)          # capture + warm-up run
+    U.copy_(torch.from_numpy(U0))
+    h.compute_dt(U, dt)
+    batched = timed(lambda: h.advance_graph(U, n, dt))
+    h.close()
+    del U
+    # baseline: a context per problem, one launch per problem per stage
+    ctxs = [(gb.Hydro.from_lattice(l), torch.from_numpy(u).cuda()) for l, u in probs]
+    dts = [c.compute_dt(u) for c, u in ctxs]
+    for (c, u), d in zip(ctxs, dts):
+        c.step_cfl(u, d)
+    def loop():
+        for _ in range(n):
+            for (c, u), d in zip(ctxs, dts):
+                c.step_cfl(u, d)
+    separate = timed(loop)
+    for c, _ in ctxs:
+        c.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    return {"workload": "96 independent periodic 2-D problems, sizes drawn from {64^2,128^2,256^2,512^2} "
+                        "(seed 0) in 16^2 blocks + 4 guards, Sod / Kelvin-Helmholtz with log-normal density "
+                        "noise (sigma 0.1, seeds 1000+i), own CFL dt each, FP64",
+            "zones": zones, "blocks": sum(l.nblocks for l in lats), "steps": n,
+            "batched_graph": {"value": zones * n / batched, "unit": UNIT, "ms_per_step": 1e3 * batched / n,
+                              "launches_per_step": 3, "graph_launches": 1, "kchunk": kc, "items_per_cta": ipc},
+            "one_launch_per_problem": {"value": zones * n / separate, "unit": UNIT,
+                                       "ms_per_step": 1e3 * separate / n, "launches_per_step": 3 * len(lats)},
+            "speedup": separate / batched}
 
 
 def oracle_step_rate(lat, U0, nsteps, threads=0):
@@ -359,6 +462,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gbhydro", "reference"], default="gbhydro")
     ap.add_argument("--nb", type=int, default=16, help="blocks per dimension (16 -> 256^3)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--two-level-steps", type=int, default=20)
+    ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

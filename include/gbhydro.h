@@ -113,6 +113,36 @@ typedef struct gbh_refinement {
 
 int gbh_create_refined(const gbh_params *params, const gbh_refinement *refinement, gbh_ctx **out);
 
+/* Batched ensembles: many independent problems in one context and one state
+ * array, advanced together (the concurrent-data pattern of Sec. 3.2 of the
+ * paper; independent simulations instead of blocks of one domain).
+ * problem[b] (HOST, [nblocks], copied) is the problem id (0..nproblems-1) of
+ * block b; the neighbour table must not connect blocks of different problems
+ * (GBH_ERR_INVAL).  Every problem has its own CFL time step: on such a
+ * context hydro_compute_dt, hydro_step_cfl, hydro_advance[_graph] read and
+ * write dt_dev[nproblems], hydro_advance's history is [nsteps][nproblems],
+ * and hydro_advance_host's is too; hydro_step / hydro_stage apply their one
+ * host dt to all problems.  The paper has no batched mode. */
+int gbh_create_batched(const gbh_params *params, const int32_t *problem, int nproblems, gbh_ctx **out);
+
+/* Work decomposition of the stage kernel: kchunk = z planes per work item
+ * (3-D; 0 or nzb = the whole block) and items_per_cta = consecutive work
+ * items one CTA processes (1 = a CTA per item; a grid of about two CTAs per
+ * SM makes the kernel persistent).  Results do not depend on it (bitwise).
+ * gbh_autotune times the candidates on U (stage launches into the context's
+ * scratch; U is not modified; synchronises the stream; clears the floor
+ * counter) and keeps the fastest; gbh_set_decomposition sets one directly.
+ * The chosen values are written to *kchunk_out / *items_out if not NULL. */
+int gbh_autotune(gbh_ctx *ctx, const double *U, int *kchunk_out, int *items_out, void *stream);
+int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
+
+/* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
+ * private stream; re-captured when U, dt_dev or nsteps change, or the
+ * decomposition changes) and launched on `stream` as one graph.  Kernel
+ * timing must be off.  The first call captures: make it outside any capture
+ * of the caller's own. */
+int hydro_advance_graph(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, void *stream);
+
 /* Release everything gbh_create allocated.  Synchronises the device.  NULL is a no-op. */
 int gbh_destroy(gbh_ctx *ctx);
 

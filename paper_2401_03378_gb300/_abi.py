@@ -53,6 +53,10 @@ _dp = C.c_void_p          # device or host double* passed as an address
 SIGNATURES = {
     "gbh_create": (C.c_int, [C.POINTER(GbhParams), C.POINTER(_vp)]),
     "gbh_create_refined": (C.c_int, [C.POINTER(GbhParams), C.POINTER(GbhRefinement), C.POINTER(_vp)]),
+    "gbh_create_batched": (C.c_int, [C.POINTER(GbhParams), C.POINTER(C.c_int32), C.c_int, C.POINTER(_vp)]),
+    "gbh_autotune": (C.c_int, [_vp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int), _vp]),
+    "gbh_set_decomposition": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "gbh_destroy": (C.c_int, [_vp]),
     "gbh_last_error": (C.c_char_p, [_vp]),
     "gbh_state_bytes": (C.c_longlong, [_vp]),

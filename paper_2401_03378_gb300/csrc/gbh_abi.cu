@@ -48,7 +48,22 @@ struct gbh_ctx {
   int* d_flux_slot = nullptr;       // [nblocks][6]
   double* d_flux_reg = nullptr;
   gbh::RefluxEntry* d_reflux = nullptr;
+  int2* d_cf_faces = nullptr;
   gbh::AmrArgs amr{};
+  // batched ensembles (gbh_create_batched): per-block problem id, per-problem CFL accumulators
+  int nproblems = 1;
+  int* d_problem = nullptr;
+  unsigned long long* d_smax = nullptr;  // [nproblems]; points into d_words for a single problem
+  unsigned long long* d_smax_own = nullptr;
+  // stage-kernel work decomposition (gbh_autotune)
+  int kchunk = 0;                   // z planes per work item (3-D); 0 = the whole block
+  int items_per_cta = 1;
+  // CUDA graph of hydro_advance_graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  const double* graph_U = nullptr;
+  const double* graph_dt = nullptr;
+  int graph_steps = 0;
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -124,8 +139,14 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   A.combine = (a == 0.0 && b == 1.0) ? 0 : 1;
   A.gather = gather ? 1 : 0;
   gbh::stage_args_common(&A, c->lay, c->eos);
-  A.smax_acc = dt_epilogue ? c->d_words : nullptr;
+  A.smax_acc = dt_epilogue ? c->d_smax : nullptr;
   A.floor_count = c->d_words + 1;
+  A.problem = c->d_problem;
+  if (c->lay.ndim == 3 && c->kchunk > 0) {
+    A.kchunk = c->kchunk;
+    A.nchunks = (c->lay.nz + c->kchunk - 1) / c->kchunk;
+  }
+  A.items_per_cta = c->items_per_cta;
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
@@ -168,12 +189,30 @@ int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStr
 }
 
 gbh::DtArgs dt_args(gbh_ctx* c, const double* U) {
-  gbh::DtArgs A{U, c->d_inv_dx, c->lay, c->eos, c->d_words, nullptr, 0};
+  gbh::DtArgs A{U, c->d_inv_dx, c->lay, c->eos, c->d_smax, nullptr, 0};
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
   }
   return A;
+}
+
+// CFL time step(s) of U into dt_dev (one per problem) and, if given, hist.
+int reduce_dt(gbh_ctx* c, const double* U, double* dt_dev, double* hist, cudaStream_t s) {
+  cudaError_t e = c->d_problem ? gbh::launch_dt_reduce_blocks(dt_args(c, U), c->d_problem, s)
+                               : gbh::launch_dt_reduce(dt_args(c, U), s);
+  int rc = cuda_err(c, e, "dt reduce launch");
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, hist, s, c->nproblems),
+                  "dt finalize launch");
+}
+
+void drop_graph(gbh_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_U = nullptr;
+  c->graph_dt = nullptr;
+  c->graph_steps = 0;
 }
 
 }  // namespace
@@ -255,8 +294,9 @@ void face_table_from_params(const gbh_params* p, long long b, int face[6], doubl
 void stage_args_common(StageArgs* A, const Layout& L, const Eos& e) {
   A->lay = L;
   A->eos = e;
-  A->kchunk = L.ndim == 3 ? L.nz : 1;   // one CTA per block
+  A->kchunk = L.ndim == 3 ? L.nz : 1;   // one work item per block
   A->nchunks = 1;
+  A->items_per_cta = 1;
 }
 
 int set_create_error(int code, const char* msg) { return set_err(nullptr, code, "%s", msg); }
@@ -267,6 +307,23 @@ using gbh::validate_params;
 
 static int create_common(const gbh_params* p, gbh_ctx** out);
 extern "C" int gbh_destroy(gbh_ctx* c);
+
+static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
+  if (c->refined) {
+    // the CFL speed must see the flux-corrected state: separate reduction
+    int rc = refined_step(c, U, dt_dev, 0.0, s);
+    if (rc) return rc;
+    return reduce_dt(c, U, dt_dev, nullptr, s);
+  }
+  int rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
+  if (rc) return rc;
+  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
+  if (rc) return rc;
+  return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
+                  "dt finalize launch");
+}
+
+
 
 static int create_common(const gbh_params* p, gbh_ctx** out) {
   gbh_ctx* c = new (std::nothrow) gbh_ctx();
@@ -298,6 +355,7 @@ static int create_common(const gbh_params* p, gbh_ctx** out) {
     gbh_destroy(c);
     return code;
   }
+  c->d_smax = c->d_words;
   *out = c;
   return GBH_OK;
 }
@@ -364,6 +422,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   // lists, flux-register slots and the flux-correction entries
   std::vector<int> active, covered, fine, slot(6 * (size_t)NB, -1);
   std::vector<gbh::RefluxEntry> refl;
+  std::vector<int2> cf_faces;
   std::vector<int> face(6 * (size_t)NB);
   std::vector<double> inv(3);
   for (long long b = 0; b < NB; ++b) gbh::face_table_from_params(p, b, &face[6 * b], inv.data());
@@ -375,7 +434,10 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
     for (int e = 0; e < nn; ++e) any = any || p->nbr[b * nn + e] == GBH_NBR_COARSER;
     if (any) fine.push_back((int)b);
     for (int f = 0; f < 2 * nd; ++f)
-      if (face[6 * b + f] == GBH_NBR_COARSER) slot[6 * b + f] = nslots++;
+      if (face[6 * b + f] == GBH_NBR_COARSER) {
+        slot[6 * b + f] = nslots++;
+        cf_faces.push_back(make_int2((int)b, f));
+      }
   }
   for (long long b = 0; b < NB; ++b) {
     if (par[4 * b] >= 0 || chl[8 * b] >= 0) continue;
@@ -421,6 +483,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   up((void**)&c->d_flux_slot, slot.data(), sizeof(int) * slot.size());
   up((void**)&c->d_flux_reg, nullptr, sizeof(double) * fstride * (size_t)(nslots ? nslots : 1));
   up((void**)&c->d_reflux, refl.empty() ? nullptr : refl.data(), sizeof(gbh::RefluxEntry) * refl.size());
+  up((void**)&c->d_cf_faces, cf_faces.empty() ? nullptr : cf_faces.data(), sizeof(int2) * cf_faces.size());
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
     set_err(nullptr, code, "gbh_create_refined: %s", cudaGetErrorString(e));
@@ -438,10 +501,145 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.nfine = (int)fine.size();
   A.reflux = c->d_reflux;
   A.nreflux = (int)refl.size();
+  A.cf_faces = c->d_cf_faces;
+  A.ncf_faces = (int)cf_faces.size();
   A.flux_reg = c->d_flux_reg;
   A.inv_dx = c->d_inv_dx;
   *out = c;
   return GBH_OK;
+}
+
+int gbh_create_batched(const gbh_params* p, const int32_t* problem, int nproblems, gbh_ctx** out) {
+  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_params(p, false);
+  if (rc) return rc;
+  if (!problem || nproblems < 1) return set_err(nullptr, GBH_ERR_INVAL, "problem table and nproblems >= 1 are required");
+  const int nn = p->ndim == 3 ? 27 : 9;
+  for (long long b = 0; b < p->nblocks; ++b) {
+    const int pb = problem[b];
+    if (pb < 0 || pb >= nproblems) return set_err(nullptr, GBH_ERR_INVAL, "problem[%lld] = %d out of range", b, pb);
+    for (int e = 0; e < nn; ++e) {
+      const int v = p->nbr[b * nn + e];
+      if (v >= 0 && problem[v] != pb)
+        return set_err(nullptr, GBH_ERR_INVAL, "block %lld and its neighbour %d belong to different problems", b, v);
+    }
+  }
+  gbh_ctx* c = nullptr;
+  if ((rc = create_common(p, &c))) return rc;
+  cudaError_t e = cudaMalloc(&c->d_problem, sizeof(int) * (size_t)p->nblocks);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_problem, problem, sizeof(int) * (size_t)p->nblocks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_smax_own, sizeof(unsigned long long) * nproblems);
+  if (e == cudaSuccess) e = cudaMemset(c->d_smax_own, 0, sizeof(unsigned long long) * nproblems);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
+    set_err(nullptr, code, "gbh_create_batched: %s", cudaGetErrorString(e));
+    gbh_destroy(c);
+    return code;
+  }
+  c->d_smax = c->d_smax_own;
+  c->nproblems = nproblems;
+  *out = c;
+  return GBH_OK;
+}
+
+int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool timing = c->timing;
+  c->timing = false;
+  drop_graph(c);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<int> kcs = {0};
+  if (c->lay.ndim == 3 && c->lay.nz >= 8 && c->lay.nz % 2 == 0) kcs.push_back(c->lay.nz / 2);
+  const long long nlist = c->refined ? c->nactive : c->lay.nblocks;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_err(c, GBH_ERR_CUDA, "cudaEventCreate failed");
+  float best = 1e30f;
+  int best_kc = 0, best_ipc = 1;
+  for (int kc : kcs) {
+    const long long nitems = nlist * (kc > 0 ? (c->lay.nz + kc - 1) / kc : 1);
+    const long long persistent = (nitems + 2LL * sms - 1) / (2LL * sms);
+    std::vector<int> ipcs = {1, 2, 4};
+    if (persistent > 4) ipcs.push_back((int)persistent);
+    for (int ipc : ipcs) {
+      c->kchunk = kc;
+      c->items_per_cta = ipc;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && rc == GBH_OK; ++rep) {
+        if (rep == 1) rc = cuda_err(c, cudaEventRecord(e0, s), "cudaEventRecord");
+        if (!rc) rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, 1e-300, 0.0, 1.0, true, false, s);
+      }
+      if (!rc) rc = cuda_err(c, cudaEventRecord(e1, s), "cudaEventRecord");
+      if (!rc) rc = cuda_err(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+      if (!rc) rc = cuda_err(c, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        best_kc = kc;
+        best_ipc = ipc;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->kchunk = best_kc;
+  c->items_per_cta = best_ipc;
+  c->timing = timing;
+  cudaMemsetAsync(c->d_words + 1, 0, sizeof(unsigned long long), s);   // trial launches may count floors
+  if (rc) return rc;
+  if (kchunk_out) *kchunk_out = best_kc > 0 ? best_kc : c->lay.nz;
+  if (items_out) *items_out = best_ipc;
+  return GBH_OK;
+}
+
+int gbh_set_decomposition(gbh_ctx* c, int kchunk, int items_per_cta) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  if (items_per_cta < 1 || kchunk < 0 || (kchunk > 0 && (c->lay.ndim != 3 || kchunk < 2 || kchunk > c->lay.nz)))
+    return set_err(c, GBH_ERR_INVAL, "invalid decomposition (kchunk %d, items per CTA %d)", kchunk, items_per_cta);
+  drop_graph(c);
+  c->kchunk = (kchunk == c->lay.nz) ? 0 : kchunk;
+  c->items_per_cta = items_per_cta;
+  return GBH_OK;
+}
+
+int hydro_advance_graph(gbh_ctx* c, double* U, int nsteps, double* dt_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (nsteps < 1) return set_err(c, GBH_ERR_INVAL, "nsteps must be >= 1");
+  if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  if (c->timing) return set_err(c, GBH_ERR_INVAL, "disable kernel timing before capturing a graph");
+  if (!(c->graph_exec && c->graph_U == U && c->graph_dt == dt_dev && c->graph_steps == nsteps)) {
+    drop_graph(c);
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(c, e, "begin capture");
+    for (int n = 0; n < nsteps && rc == GBH_OK; ++n) rc = step_cfl(c, U, dt_dev, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return cuda_err(c, e, "graph instantiate");
+    }
+    c->graph_U = U;
+    c->graph_dt = dt_dev;
+    c->graph_steps = nsteps;
+  }
+  return cuda_err(c, cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream), "graph launch");
 }
 
 int gbh_destroy(gbh_ctx* c) {
@@ -463,6 +661,11 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_flux_slot);
   cudaFree(c->d_flux_reg);
   cudaFree(c->d_reflux);
+  cudaFree(c->d_cf_faces);
+  cudaFree(c->d_problem);
+  cudaFree(c->d_smax_own);
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
   return GBH_OK;
@@ -490,10 +693,7 @@ int hydro_compute_dt(gbh_ctx* c, const double* U, double* dt_dev, void* stream) 
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
-  cudaStream_t s = (cudaStream_t)stream;
-  rc = cuda_err(c, gbh::launch_dt_reduce(dt_args(c, U), s), "dt reduce launch");
-  if (rc) return rc;
-  return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
+  return reduce_dt(c, U, dt_dev, nullptr, (cudaStream_t)stream);
 }
 
 static int stage_common(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, double dt, double a,
@@ -533,21 +733,6 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   return stage_launch(c, c->d_scratch, U, U, nullptr, dt, 0.5, 0.5, true, false, s);
 }
 
-static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
-  if (c->refined) {
-    // the CFL speed must see the flux-corrected state: separate reduction
-    int rc = refined_step(c, U, dt_dev, 0.0, s);
-    if (rc) return rc;
-    if ((rc = cuda_err(c, gbh::launch_dt_reduce(dt_args(c, U), s), "dt reduce launch"))) return rc;
-    return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
-  }
-  int rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
-  if (rc) return rc;
-  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
-  if (rc) return rc;
-  return cuda_err(c, gbh::launch_dt_finalize(c->d_words, c->cfl, dt_dev, nullptr, s), "dt finalize launch");
-}
-
 int hydro_step_cfl(gbh_ctx* c, double* U, double* dt_dev, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -563,7 +748,8 @@ int hydro_advance(gbh_ctx* c, double* U, int nsteps, double* dt_dev, double* dt_
   cudaStream_t s = (cudaStream_t)stream;
   for (int n = 0; n < nsteps; ++n) {
     if (dt_hist_dev) {
-      rc = cuda_err(c, cudaMemcpyAsync(dt_hist_dev + n, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, s),
+      rc = cuda_err(c, cudaMemcpyAsync(dt_hist_dev + (size_t)n * c->nproblems, dt_dev,
+                                       sizeof(double) * c->nproblems, cudaMemcpyDeviceToDevice, s),
                     "dt history copy");
       if (rc) return rc;
     }
@@ -581,11 +767,11 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
   const size_t bytes = sizeof(double) * state_elems(c->lay);
   cudaError_t e = cudaSuccess;
   if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
-  if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double));
+  if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double) * c->nproblems);
   if (e == cudaSuccess && nsteps > c->host_hist_cap) {
     cudaFree(c->d_host_hist);
     c->d_host_hist = nullptr;
-    e = cudaMalloc(&c->d_host_hist, sizeof(double) * nsteps);
+    e = cudaMalloc(&c->d_host_hist, sizeof(double) * nsteps * c->nproblems);
     if (e == cudaSuccess) c->host_hist_cap = nsteps;
   }
   if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "device allocation failed: %s", cudaGetErrorString(e));
@@ -597,7 +783,7 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
   if ((rc = cuda_err(c, cudaMemcpyAsync(U_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, s), "D2H copy")))
     return rc;
   if (dt_hist_host && nsteps > 0 &&
-      (rc = cuda_err(c, cudaMemcpyAsync(dt_hist_host, c->d_host_hist, sizeof(double) * nsteps,
+      (rc = cuda_err(c, cudaMemcpyAsync(dt_hist_host, c->d_host_hist, sizeof(double) * nsteps * c->nproblems,
                                         cudaMemcpyDeviceToHost, s), "D2H dt copy")))
     return rc;
   return cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");

@@ -153,6 +153,60 @@ __global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_
   }
 }
 
+// Prolongation into the 2-deep face slabs that the stage kernel reads, for a
+// list of (fine block, face) pairs whose face neighbour lies on the coarser
+// level: one thread per (pair, slab cell).
+__global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
+  const Layout& L = a.lay;
+  const int N = L.nx;
+  const int n2 = L.ndim == 3 ? N : 1;
+  const long long per = 2LL * N * n2;
+  const long long total = per * a.ncf_faces;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int2 ff = a.cf_faces[t / per];
+    const int fb = ff.x, d = ff.y >> 1, side = ff.y & 1;
+    const int r = (int)(t % per);
+    const int depth = r % 2, t1 = (r / 2) % N, t2 = r / (2 * N);
+    const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+    int c[3];
+    c[d] = side ? N + depth : -1 - depth;
+    c[t1d] = t1;
+    c[t2d] = L.ndim == 3 ? t2 : 0;
+    const int parent = __ldg(a.parent + 4 * fb);
+    int P[3], sg[3];
+    for (int e = 0; e < 3; ++e) {
+      if (e < L.ndim) {
+        const int hh = floor_div2(c[e]);
+        P[e] = __ldg(a.parent + 4 * fb + 1 + e) + hh;
+        sg[e] = (c[e] - 2 * hh) == 0 ? -1 : 1;
+      } else {
+        P[e] = 0;
+        sg[e] = 0;
+      }
+    }
+    const long long oc = coarse_offset(a, parent, P[0], P[1], P[2]);
+    long long om[3], op[3];
+    for (int e = 0; e < L.ndim; ++e) {
+      int Pm[3] = {P[0], P[1], P[2]}, Pp[3] = {P[0], P[1], P[2]};
+      Pm[e] -= 1;
+      Pp[e] += 1;
+      om[e] = coarse_offset(a, parent, Pm[0], Pm[1], Pm[2]);
+      op[e] = coarse_offset(a, parent, Pp[0], Pp[1], Pp[2]);
+    }
+    for (int v = 0; v < 5; ++v) {
+      const long long vo = v * L.vstride;
+      const double q0 = U[oc + vo];
+      double val = q0;
+      for (int e = 0; e < L.ndim; ++e) {
+        const double h = mc_half_slope(U[om[e] + vo], q0, U[op[e] + vo]);
+        val = __dadd_rn(val, __dmul_rn(0.5 * h, (double)sg[e]));
+      }
+      U[at(L, fb, v, c[0], c[1], c[2])] = val;
+    }
+  }
+}
+
 // Flux correction on the coarse side of the fine-region boundary.  One
 // thread per (interface face, face cell).
 __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, double dt_val, double coef) {
@@ -207,6 +261,11 @@ cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s) {
 
 cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s) {
   if (a.nfine == 0) return cudaSuccess;
+  if (faces_only && depth == 2 && a.cf_faces) {
+    const long long per = 2LL * a.lay.nx * (a.lay.ndim == 3 ? a.lay.nx : 1);
+    prolong_faces_kernel<<<grid_for(per * a.ncf_faces), kThreads, 0, s>>>(U, a);
+    return cudaGetLastError();
+  }
   const Layout& L = a.lay;
   const long long per = (long long)(L.nx + 2 * depth) * (L.ny + 2 * depth) * (L.ndim == 3 ? L.nz + 2 * depth : 1);
   prolong_kernel<<<grid_for(per * a.nfine), kThreads, 0, s>>>(U, a, depth, faces_only ? 1 : 0);

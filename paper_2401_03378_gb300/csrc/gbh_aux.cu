@@ -102,13 +102,49 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
   if (threadIdx.x == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(red[0]));
 }
 
-// dt = cfl / smax; also records it and clears the accumulator for its next use.
-__global__ void dt_finalize_kernel(unsigned long long* acc, double cfl, double* dt_out, double* hist) {
-  const double smax = __longlong_as_double((long long)*acc);
-  const double dt = cfl / smax;
-  *dt_out = dt;
-  if (hist) *hist = dt;
-  *acc = 0ull;
+// dt = cfl / smax per problem; also records it and clears the accumulator for
+// its next use.
+__global__ void dt_finalize_kernel(unsigned long long* acc, double cfl, double* dt_out, double* hist, int n) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const double smax = __longlong_as_double((long long)acc[p]);
+    const double dt = cfl / smax;
+    dt_out[p] = dt;
+    if (hist) hist[p] = dt;
+    acc[p] = 0ull;
+  }
+}
+
+// Segmented CFL reduction for batched ensembles: one CTA per block at a time
+// (grid-stride over blocks), one atomicMax into the block's problem slot.
+__global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs a, const int* problem) {
+  const Layout& L = a.lay;
+  const int per = L.nx * L.ny * L.nz;
+  const bool d3 = L.ndim == 3;
+  __shared__ double red[kThreads];
+  const int nb = a.block_list ? a.nlist : L.nblocks;
+  for (int s = blockIdx.x; s < nb; s += gridDim.x) {
+    const int b = a.block_list ? __ldg(a.block_list + s) : s;
+    double smax = 0.0;
+    for (int t = threadIdx.x; t < per; t += blockDim.x) {
+      const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+      const long long o =
+          (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+      double U[5], W[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
+      cons_to_prim(U, W, a.eos);
+      smax = fmax(smax, signal_speed(W, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
+                                     __ldg(a.inv_dx + 3 * b + 2), d3));
+    }
+    red[threadIdx.x] = smax;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(a.smax_acc + __ldg(problem + b), (unsigned long long)__double_as_longlong(red[0]));
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const Layout L, const Eos e,
@@ -188,8 +224,14 @@ cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_out, double* hist,
-                               cudaStream_t s) {
-  dt_finalize_kernel<<<1, 1, 0, s>>>(acc, cfl, dt_out, hist);
+                               cudaStream_t s, int n) {
+  dt_finalize_kernel<<<(n + 255) / 256, n < 256 ? n : 256, 0, s>>>(acc, cfl, dt_out, hist, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_reduce_blocks(const DtArgs& a, const int* problem, cudaStream_t s) {
+  const int nb = a.block_list ? a.nlist : a.lay.nblocks;
+  dt_reduce_blocks_kernel<<<nb < 152 * 8 ? nb : 152 * 8, kThreads, 0, s>>>(a, problem);
   return cudaGetLastError();
 }
 

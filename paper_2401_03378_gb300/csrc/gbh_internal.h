@@ -38,7 +38,10 @@ struct StageArgs {
   double a, b;
   int combine;           // 0: Uout = Uin + dt*L; 1: a*Un + b*(Uin + dt*L)
   int gather;            // 1: halo from neighbour interiors; 0: from Uin's own guard cells
-  int kchunk, nchunks;   // z planes per CTA (3-D), CTAs per block
+  int kchunk, nchunks;   // z planes per work item (3-D), work items per block
+  int items_per_cta;     // consecutive work items processed by one CTA (>= 1)
+  const int* problem;    // [nblocks] problem of each block (batched ensembles), or null
+                         // (then dt_dev and smax_acc have one entry)
   Layout lay;
   Eos eos;
   unsigned long long* smax_acc;     // if non-null: max signal-speed sum of Uout (bit pattern)
@@ -67,6 +70,8 @@ struct AmrArgs {
   int ncovered;
   const int* fine;       // fine blocks with at least one region on the coarser level
   int nfine;
+  const int2* cf_faces;  // (fine block, face) pairs whose face neighbour is on the coarser level
+  int ncf_faces;
   const RefluxEntry* reflux;
   int nreflux;
   double* flux_reg;
@@ -108,7 +113,8 @@ struct DtArgs {
 };
 cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s);
 cudaError_t launch_dt_finalize(unsigned long long* acc, double cfl, double* dt_out, double* hist,
-                               cudaStream_t s);
+                               cudaStream_t s, int n = 1);
+cudaError_t launch_dt_reduce_blocks(const DtArgs& a, const int* problem, cudaStream_t s);
 
 cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
                          cudaStream_t s);

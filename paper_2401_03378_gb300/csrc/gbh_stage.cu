@@ -91,29 +91,30 @@ __device__ __forceinline__ int load_prim(const StageArgs& a, int b, int i, int j
   return cons_to_prim(U, W, a.eos);
 }
 
+// One work item: block `b` of the list (or of the lattice) and z-chunk
+// `chunk`.  Uses the caller's shared memory; ends with the per-item atomics.
 template <int N, bool DIM3>
-__global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
+__device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red) {
   constexpr int NT = N * N;
   constexpr int P = N + 4;                  // plane with 2-deep x/y rims
   constexpr int QX = N * (N + 2);           // x-slope cells of a plane
   constexpr int FX = N * (N + 1);           // x faces of a plane
-  extern __shared__ double smem[];
   double* sW = smem;                        // [5][P][P] primitives of the plane
   double* sQx = sW + 5 * P * P;             // [2][5][N][N+2] x face states (minus, plus)
   double* sQy = sQx + 2 * 5 * QX;           // [2][5][N+2][N] y face states
   double* sFx = sQy + 2 * 5 * QX;           // [5][N][N+1] x fluxes
   double* sFy = sFx + 5 * FX;               // [5][N+1][N] y fluxes
-  __shared__ double s_red[NT];
 
   const Layout& L = a.lay;
   const int tid = threadIdx.x;
   const int tx = tid % N, ty = tid / N;
-  const int slot_idx = blockIdx.x / a.nchunks;
-  const int chunk = blockIdx.x - slot_idx * a.nchunks;
+  const int slot_idx = item / a.nchunks;
+  const int chunk = item - slot_idx * a.nchunks;
   const int b = a.block_list ? __ldg(a.block_list + slot_idx) : slot_idx;
+  const int prob = a.problem ? __ldg(a.problem + b) : 0;
   const int k0 = DIM3 ? chunk * a.kchunk : 0;
   const int k1 = DIM3 ? min(L.nz, k0 + a.kchunk) : 1;
-  const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+  const double dt = a.dt_dev ? a.dt_dev[prob] : a.dt;
   const double idx = __ldg(a.inv_dx + 3 * b), idy = __ldg(a.inv_dx + 3 * b + 1);
   const double idz = DIM3 ? __ldg(a.inv_dx + 3 * b + 2) : 0.0;
   const double dtx = dt * idx, dty = dt * idy, dtz = dt * idz;
@@ -312,7 +313,23 @@ __global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
       if (tid < w) s_red[tid] = fmax(s_red[tid], s_red[tid + w]);
       __syncthreads();
     }
-    if (tid == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(s_red[0]));
+    if (tid == 0) atomicMax(a.smax_acc + prob, (unsigned long long)__double_as_longlong(s_red[0]));
+  }
+}
+
+// Work list: items (block, z-chunk) in order; each CTA processes
+// `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
+// grid makes the kernel persistent).  No CTA waits on another.
+template <int N, bool DIM3>
+__global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
+  extern __shared__ double smem[];
+  __shared__ double s_red[N * N];
+  const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
+  const int first = blockIdx.x * a.items_per_cta;
+  const int last = min(nitems, first + a.items_per_cta);
+  for (int item = first; item < last; ++item) {
+    stage_item<N, DIM3>(a, item, smem, s_red);
+    __syncthreads();
   }
 }
 
@@ -324,7 +341,9 @@ size_t smem_for() {
 
 template <int N, bool D3>
 cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
-  const unsigned grid = (unsigned)(a.block_list ? a.nlist : a.lay.nblocks) * (unsigned)a.nchunks;
+  const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
+  const int per = a.items_per_cta > 0 ? a.items_per_cta : 1;
+  const unsigned grid = (unsigned)((nitems + per - 1) / per);
   stage_kernel<N, D3><<<grid, N * N, smem_for<N>(), s>>>(a);
   return cudaGetLastError();
 }

@@ -82,3 +82,22 @@ def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
         oct_ = sum((fc[d] % 2) << d for d in range(nd))
         children[pid, oct_] = n0 + f
     return nbr, dx, parent, children
+
+
+def batched_tables(problems):
+    """Tables of independent problems in one state array.
+
+    problems: sequence of (ndim, nb, periodic, dx) uniform lattices (same block
+    shape).  Blocks of problem i follow those of problem i-1.  Returns
+    (nbr, dx, problem) for gbh_create_batched.
+    """
+    nbrs, dxs, ids = [], [], []
+    off = 0
+    for i, (ndim, nb, periodic, dx) in enumerate(problems):
+        t = neighbour_table(ndim, nb, periodic).astype(np.int64)
+        t = np.where(t >= 0, t + off, t).astype(np.int32)
+        nbrs.append(t)
+        dxs.append(uniform_widths(t.shape[0], dx))
+        ids.append(np.full(t.shape[0], i, dtype=np.int32))
+        off += t.shape[0]
+    return np.concatenate(nbrs), np.concatenate(dxs), np.concatenate(ids)

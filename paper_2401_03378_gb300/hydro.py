@@ -35,7 +35,8 @@ class Hydro:
                  extent=(1.0, 1.0, 1.0), nbr: Optional[np.ndarray] = None,
                  dx: Optional[np.ndarray] = None, gamma: float = 1.4, cfl: float = 0.8,
                  small_rho: float = 1e-12, small_p: float = 1e-14,
-                 parent: Optional[np.ndarray] = None, children: Optional[np.ndarray] = None):
+                 parent: Optional[np.ndarray] = None, children: Optional[np.ndarray] = None,
+                 problem: Optional[np.ndarray] = None, nproblems: int = 1):
         self.lib = _abi.load()
         self.ndim = int(ndim)
         nx, ny, nz = (int(n[0]), int(n[1]), int(n[2]) if ndim == 3 else 1)
@@ -61,7 +62,12 @@ class Hydro:
         p.dx = self.dx.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()
         self.refined = parent is not None
-        if self.refined:
+        self.nproblems = int(nproblems) if problem is not None else 1
+        if problem is not None:
+            self.problem = np.ascontiguousarray(problem, dtype=np.int32)
+            rc = self.lib.gbh_create_batched(C.byref(p), self.problem.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             self.nproblems, C.byref(ctx))
+        elif self.refined:
             self.parent = np.ascontiguousarray(parent, dtype=np.int32)
             self.children = np.ascontiguousarray(children, dtype=np.int32)
             r = _abi.GbhRefinement()
@@ -90,6 +96,17 @@ class Hydro:
         nbr, dx, parent, children = two_level_tables(
             c.ndim, c.nb, c.n, tl.lo, tl.hi, tuple(b == "periodic" for b in c.bc), c.dx)
         return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children, **kw)
+
+    @classmethod
+    def from_batch(cls, lattices, **kw):
+        """Independent problems (uniform lattices with equal block shapes) in one
+        context; the state array holds their blocks one problem after another."""
+        from .grid import batched_tables
+        lats = list(lattices)
+        c = lats[0]
+        nbr, dx, problem = batched_tables(
+            [(l.ndim, l.nb, tuple(b == "periodic" for b in l.bc), l.dx) for l in lats])
+        return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, problem=problem, nproblems=len(lats), **kw)
 
     # -- helpers -----------------------------------------------------------
     def close(self):
@@ -129,7 +146,7 @@ class Hydro:
 
     def compute_dt(self, U, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
-            out = torch.empty(1, dtype=torch.float64, device="cuda")
+            out = torch.empty(self.nproblems, dtype=torch.float64, device="cuda")
         self._check(self.lib.hydro_compute_dt(self.ctx, self._state(U), self._scalar(out), _stream_handle()))
         return out
 
@@ -157,6 +174,20 @@ class Hydro:
         self._check(self.lib.hydro_advance(self.ctx, self._state(U), int(nsteps), self._scalar(dt_dev), h,
                                            _stream_handle()))
         return U
+
+    def advance_graph(self, U, nsteps: int, dt_dev: torch.Tensor):
+        """nsteps of step_cfl as one CUDA graph (captured on first use)."""
+        self._check(self.lib.hydro_advance_graph(self.ctx, self._state(U), int(nsteps), self._scalar(dt_dev),
+                                                 _stream_handle()))
+        return U
+
+    def autotune(self, U):
+        kc, ipc = C.c_int(0), C.c_int(0)
+        self._check(self.lib.gbh_autotune(self.ctx, self._state(U), C.byref(kc), C.byref(ipc), _stream_handle()))
+        return int(kc.value), int(ipc.value)
+
+    def set_decomposition(self, kchunk: int, items_per_cta: int):
+        self._check(self.lib.gbh_set_decomposition(self.ctx, int(kchunk), int(items_per_cta)))
 
     def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
         """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""

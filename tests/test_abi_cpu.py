@@ -188,3 +188,23 @@ def test_create_refined_rejects_bad_tables_without_gpu(lib):
     assert attempt(bad, dx, parent, children) == -1
     bad = nbr.copy(); bad[64][bad[64] == -2] = -1   # a fine block claims an outflow edge
     assert attempt(bad, dx, parent, children) == -1
+
+
+def test_create_batched_rejects_cross_problem_neighbours_without_gpu(lib):
+    from paper_2401_03378_gb300 import _abi
+    from paper_2401_03378_gb300.grid import batched_tables
+    nbr, dx, prob = batched_tables([(2, (2, 2, 1), (True, True, False), (0.1, 0.1, 0.1)),
+                                    (2, (3, 3, 1), (True, True, False), (0.05, 0.05, 0.1))])
+    assert nbr.shape == (13, 9) and list(prob) == [0] * 4 + [1] * 9
+    assert nbr[:4].max() < 4 and nbr[4:].min() >= 4
+    bad = nbr.copy()
+    bad[1, 5] = 7
+    keep = [np.ascontiguousarray(bad), np.ascontiguousarray(dx), np.ascontiguousarray(prob)]
+    p = _abi.GbhParams()
+    p.ndim, p.nxb, p.nyb, p.nzb, p.nguard, p.nblocks = 2, 16, 16, 1, 4, 13
+    p.gamma, p.cfl, p.small_rho, p.small_p = 1.4, 0.8, 1e-12, 1e-14
+    p.nbr = keep[0].ctypes.data_as(C.POINTER(C.c_int32))
+    p.dx = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+    ctx = C.c_void_p()
+    rc = lib.gbh_create_batched(C.byref(p), keep[2].ctypes.data_as(C.POINTER(C.c_int32)), 2, C.byref(ctx))
+    assert rc == -1 and b"different problems" in lib.gbh_last_error(None)

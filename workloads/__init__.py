@@ -363,3 +363,18 @@ def ensemble_sizes(count: int = 96, seed: int = 0, choices=(64, 128, 256, 512)):
     """Problem sizes for the batched-ensemble workload (uniform draw, seeded)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return [int(choices[i]) for i in rng.integers(0, len(choices), count)]
+
+
+def ensemble(count: int = 96, seed: int = 0, nxb: int = 16, ng: int = 4, choices=(64, 128, 256, 512)):
+    """Batched-ensemble workload: `count` independent periodic 2-D problems of
+    sizes drawn from `choices` (seed `seed`) in nxb^2 blocks; problem i starts
+    from the periodic Sod layout (i even) or the Kelvin-Helmholtz layer (i odd),
+    each with log-normal density noise of sigma 0.1 drawn with seed 1000 + i.
+    Returns a list of (Lattice, U)."""
+    out = []
+    for i, size in enumerate(ensemble_sizes(count, seed, choices)):
+        nb = size // nxb
+        lat = lattice_2d(nb, nb, nxb, nxb, ng, bc=PERIODIC)
+        U = sod_periodic(lat, seed=1000 + i) if i % 2 == 0 else kelvin_helmholtz(lat, seed=1000 + i)
+        out.append((lat, U))
+    return out

@@ -131,7 +131,7 @@ class ClockSampler:
 
 def source_hash():
     h = hashlib.sha256()
-    for rel in ("gbh_stage.cu", "gbh_device.cuh", "gbh_internal.h"):
+    for rel in ("gbh_stage.cu", "gbh_device.cuh", "gbh_gather.cuh", "gbh_internal.h"):
         with open(os.path.join(ROOT, "paper_2401_03378_gb300", "csrc", rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -252,6 +252,9 @@ def run_gpu(args):
     ensemble = None
     if args.ensemble_steps > 0:
         ensemble = run_ensemble(args, gb, torch, barrier)
+    adjoint = None
+    if args.adjoint_steps > 0:
+        adjoint = run_adjoint(args, gb, torch, barrier)
 
     # roofline of the dominant kernel (the fused stage kernel, both stages)
     flops_per_launch = 0.5 * (FLOPS_STAGE1 + FLOPS_STAGE2) * zones
@@ -300,6 +303,7 @@ def run_gpu(args):
         "e2e": e2e,
         "two_level": two_level,
         "ensemble": ensemble,
+        "adjoint": adjoint,
         "unphysical_cells": nbad,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -403,6 +407,38 @@ def run_ensemble(args, gb, torch, barrier):
             "speedup": separate / batched}
 
 
+def run_adjoint(args, gb, torch, barrier):
+    """Gradient workload: 2-D Sod-like 256^2 in 16^2 blocks, 50 steps, checkpoint
+    every 10; forward (with checkpoints) and adjoint sweep timed separately."""
+    import numpy as np
+    import workloads as wl
+    from paper_2401_03378_gb300.adjoint import CheckpointedRun
+    lat = wl.lattice_2d(16, 16, 16, 16, 4)
+    n = args.adjoint_steps
+    h = gb.Hydro.from_lattice(lat)
+    U0 = torch.from_numpy(wl.sod_smooth(lat)).cuda()
+    rng = np.random.default_rng(7)
+    lam = torch.from_numpy(rng.standard_normal(lat.shape)).cuda()
+    run = CheckpointedRun(h, n, every=10)
+    run.forward(U0)
+    run.backward(lam)           # warm-up (allocates the adjoint buffers)
+    stream = torch.cuda.current_stream()
+    times = []
+    for fn in (lambda: run.forward(U0), lambda: run.backward(lam)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+    h.close()
+    return {"workload": "2-D Sod-like (tanh-smoothed jump, smooth 2-D modulations) 256^2 in 16^2 blocks + 4 guards, "
+                        f"{n} steps, checkpoint every 10, dt held fixed, FP64",
+            "forward_ms": times[0], "adjoint_ms": times[1], "adjoint_over_forward": times[1] / times[0],
+            "target_ratio": 4.0}
+
+
 def oracle_step_rate(lat, U0, nsteps, threads=0):
     """Time `nsteps` oracle SSP-RK2 steps (dt from the oracle) on the host cores."""
     from oracle import oracle as orc
@@ -464,6 +500,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--two-level-steps", type=int, default=20)
     ap.add_argument("--ensemble-steps", type=int, default=100)
+    ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

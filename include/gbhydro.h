@@ -143,6 +143,30 @@ int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
  * of the caller's own. */
 int hydro_advance_graph(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, void *stream);
 
+/* Adjoint (vector-Jacobian products) for gradients of a loss of the final
+ * state with respect to the initial fields.  Conventions: dt is held fixed
+ * (a constant of each step), and every branch keeps the decision the forward
+ * evaluation took (floors, MC limiter case, HLLC side and fan, the min / max
+ * of the wave-speed bounds).  Uniform single-problem contexts only
+ * (GBH_ERR_UNSUPPORTED otherwise).  All arrays are DEVICE state arrays; only
+ * interior cells are read or written.  The paper has no adjoint.
+ *
+ * hydro_stage_vjp: out = cA*A + cB*B + J_L(U)^T (scale*M), L the stage's
+ *   flux-difference operator evaluated at U (guard data gathered from the
+ *   neighbours as in hydro_stage).  A and B may be NULL; out may equal A or B
+ *   but must not overlap U or M.
+ * hydro_step_adjoint: given lam_next = dJ/dU^{n+1} of one hydro_step(Un, dt),
+ *   writes lam_prev = dJ/dU^n (recomputes the intermediate stage; lam_prev
+ *   may equal lam_next, must not overlap Un).
+ * hydro_prim_to_cons: U = conserved(W) on interior cells, W = (rho, u, v, w, p)
+ *   in the state layout; hydro_prim_to_cons_vjp: lamW = (dU/dW)^T lamU. */
+int hydro_stage_vjp(gbh_ctx *ctx, const double *U, const double *M, double scale, const double *A, double cA,
+                    const double *B, double cB, double *out, void *stream);
+int hydro_step_adjoint(gbh_ctx *ctx, const double *Un, double dt, const double *lam_next, double *lam_prev,
+                       void *stream);
+int hydro_prim_to_cons(gbh_ctx *ctx, const double *W, double *U, void *stream);
+int hydro_prim_to_cons_vjp(gbh_ctx *ctx, const double *W, const double *lamU, double *lamW, void *stream);
+
 /* Release everything gbh_create allocated.  Synchronises the device.  NULL is a no-op. */
 int gbh_destroy(gbh_ctx *ctx);
 

@@ -679,6 +679,170 @@ ll amr2_step(const Amr2& A, double* U, double dt) {
   return hits;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the stage and of the SSP-RK2 step (dt held fixed, branches as in
+// the forward evaluation).  Each face's flux is differentiated with respect
+// to the conserved values of its 4 stencil cells by forward-mode dual
+// numbers over the oracle's own pointwise functions (oracle_pointwise.h):
+// comparisons act on the values, so every branch keeps its forward decision.
+// The transposed data flow (faces -> stencil cells -> guard fill -> sources)
+// is then summed plainly.
+template <int K>
+struct Dual {
+  double v;
+  double d[K];
+  Dual(double x = 0.0) : v(x) { for (int i = 0; i < K; ++i) d[i] = 0.0; }
+};
+template <int K> Dual<K> operator+(const Dual<K>& a, const Dual<K>& b) { Dual<K> r(a.v + b.v); for (int i = 0; i < K; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int K> Dual<K> operator-(const Dual<K>& a, const Dual<K>& b) { Dual<K> r(a.v - b.v); for (int i = 0; i < K; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int K> Dual<K> operator-(const Dual<K>& a) { Dual<K> r(-a.v); for (int i = 0; i < K; ++i) r.d[i] = -a.d[i]; return r; }
+template <int K> Dual<K> operator*(const Dual<K>& a, const Dual<K>& b) { Dual<K> r(a.v * b.v); for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int K> Dual<K> operator/(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r(a.v / b.v);
+  for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+template <int K> Dual<K> sqrt(const Dual<K>& a) { Dual<K> r(std::sqrt(a.v)); for (int i = 0; i < K; ++i) r.d[i] = a.d[i] / (2.0 * r.v); return r; }
+template <int K> bool operator<(const Dual<K>& a, const Dual<K>& b) { return a.v < b.v; }
+template <int K> bool operator<=(const Dual<K>& a, const Dual<K>& b) { return a.v <= b.v; }
+template <int K> bool operator>(const Dual<K>& a, const Dual<K>& b) { return a.v > b.v; }
+template <int K> bool operator==(const Dual<K>& a, const Dual<K>& b) { return a.v == b.v; }
+
+using D20 = Dual<20>;
+
+/* J_L(U)^T (scale M) on the interior of every block; U must have its guard
+ * cells filled.  out is written on interior cells. */
+void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale, double* out) {
+  const Geo geo(G);
+  const ll nbk = geo.nblocks();
+  const ll cells = geo.cells;
+  const int nd = geo.ndim;
+  std::vector<double> ext(nbk * 5 * cells, 0.0);   /* adjoint of the conserved stencil inputs */
+  const ll stride[3] = {1, geo.p[0], (ll)geo.p[0] * geo.p[1]};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (ll b = 0; b < nbk; ++b) {
+    for (int d = 0; d < nd; ++d) {
+      const double idx = 1.0 / G.dx[d];
+      const int t1 = d == 0 ? 2 : 1, t2 = d == 2 ? 2 : 3;
+      const int vmap[5] = {0, 1 + d, t1, t2, 4};
+      for (int k = 0; k < geo.p[2]; ++k)
+        for (int j = 0; j < geo.p[1]; ++j)
+          for (int i = 0; i < geo.p[0]; ++i) {
+            const int x[3] = {i, j, k};
+            bool ok = x[d] >= geo.g[d] && x[d] <= geo.g[d] + geo.n[d];
+            for (int e = 0; e < 3; ++e)
+              if (e != d && !inside(geo, e, x[e])) ok = false;
+            if (!ok) continue;
+            const ll c = geo.cell(k, j, i);
+            /* flux adjoint from this block's own cells c - e_d and c */
+            double lamF[5];
+            for (int v = 0; v < 5; ++v) {
+              const double mc = inside(geo, d, x[d]) ? M[geo.at(b, v, k, j, i) ] : 0.0;
+              const int xm = x[d] - 1;
+              const double mm = inside(geo, d, xm) ? M[geo.at(b, v, k, j, i) - stride[d]] : 0.0;
+              lamF[v] = scale * idx * (mc - mm);
+            }
+            /* the 4 stencil cells c-2e, c-e, c, c+e as dual inputs (20 slots) */
+            D20 W[4][5];
+            for (int s = 0; s < 4; ++s) {
+              D20 u5[5];
+              const ll cs = c + (s - 2) * stride[d];
+              for (int v = 0; v < 5; ++v) {
+                u5[v] = D20(U[b * 5 * cells + v * cells + cs]);
+                u5[v].d[5 * s + v] = 1.0;
+              }
+              orc::prim_from_cons(u5, D20(G.gamma), D20(G.small_rho), D20(G.small_p), W[s]);
+            }
+            D20 WL[5], WR[5], F[5];
+            for (int q = 0; q < 5; ++q) {
+              const int v = vmap[q];
+              const D20 sL = orc::mc_slope(W[0][v], W[1][v], W[2][v]);
+              const D20 sR = orc::mc_slope(W[1][v], W[2][v], W[3][v]);
+              WL[q] = W[1][v] + D20(0.5) * sL;
+              WR[q] = W[2][v] - D20(0.5) * sR;
+            }
+            orc::hllc(WL, WR, D20(G.gamma), F);
+            for (int s = 0; s < 4; ++s) {
+              const ll cs = c + (s - 2) * stride[d];
+              for (int v = 0; v < 5; ++v) {
+                double acc = 0.0;
+                for (int q = 0; q < 5; ++q) acc += lamF[vmap[q]] * F[q].d[5 * s + v];
+                ext[b * 5 * cells + v * cells + cs] += acc;
+              }
+            }
+          }
+    }
+  }
+  /* adjoint of the guard fill (face slabs only: the stencil reads no
+   * corners): a guard position hands its adjoint to the interior cell it was
+   * copied from -- the neighbour's, or the block's own boundary cell at an
+   * outflow edge */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (ll b = 0; b < nbk; ++b)
+    for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+      for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+        for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i)
+          for (int v = 0; v < 5; ++v) out[geo.at(b, v, k, j, i)] = ext[geo.at(b, v, k, j, i)];
+  for (ll b = 0; b < nbk; ++b)
+    for (int d = 0; d < nd; ++d)
+      for (int side = 0; side < 2; ++side) {
+        int o[3] = {0, 0, 0};
+        o[d] = side ? 1 : -1;
+        const ll nb = geo.neighbour(b, o);
+        for (int k = 0; k < geo.p[2]; ++k)
+          for (int j = 0; j < geo.p[1]; ++j)
+            for (int i = 0; i < geo.p[0]; ++i) {
+              const int x[3] = {i, j, k};
+              bool slab = side ? (x[d] >= geo.g[d] + geo.n[d] && x[d] < geo.g[d] + geo.n[d] + 2)
+                               : (x[d] >= geo.g[d] - 2 && x[d] < geo.g[d]);
+              for (int e = 0; e < 3; ++e)
+                if (e != d && !inside(geo, e, x[e])) slab = false;
+              if (!slab) continue;
+              int src[3] = {i, j, k};
+              ll sb = b;
+              if (nb >= 0) {
+                sb = nb;
+                src[d] = x[d] - o[d] * geo.n[d];
+              } else {
+                src[d] = side ? geo.g[d] + geo.n[d] - 1 : geo.g[d];
+              }
+              for (int v = 0; v < 5; ++v)
+                out[geo.at(sb, v, src[2], src[1], src[0])] += ext[geo.at(b, v, k, j, i)];
+            }
+      }
+}
+
+/* dJ/dU^n of one SSP-RK2 step (dt held fixed) from dJ/dU^{n+1}. */
+void step_adjoint(const OrcGrid& G, const double* Un, double dt, const double* lam, double* lam_prev) {
+  const Geo geo(G);
+  const ll total = geo.nblocks() * 5 * geo.cells;
+  std::vector<double> U0(Un, Un + total), U1(total), tmp(total, 0.0), j1(total, 0.0), j0(total, 0.0);
+  fill_guardcells(G, U0.data());
+  std::memcpy(U1.data(), U0.data(), total * sizeof(double));
+  stage(G, U0.data(), nullptr, U1.data(), dt, 0.0, 1.0, nullptr, 0);
+  fill_guardcells(G, U1.data());
+  /* lam_U1 = 1/2 lam + J_L(U1)^T (dt/2 lam) */
+  stage_vjp(G, U1.data(), lam, 0.5 * dt, j1.data());
+  for (ll b = 0; b < geo.nblocks(); ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+            const ll o = geo.at(b, v, k, j, i);
+            tmp[o] = 0.5 * lam[o] + j1[o];
+          }
+  /* lam_n = 1/2 lam + lam_U1 + J_L(U^n)^T (dt lam_U1) */
+  stage_vjp(G, U0.data(), tmp.data(), dt, j0.data());
+  for (ll b = 0; b < geo.nblocks(); ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+            const ll o = geo.at(b, v, k, j, i);
+            lam_prev[o] = 0.5 * lam[o] + tmp[o] + j0[o];
+          }
+}
+
 }  // namespace
 
 extern "C" {
@@ -780,6 +944,21 @@ long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, do
     hits += amr2_step(A, U, dt);
   }
   return hits;
+}
+
+/* ---- adjoint (dt held fixed) ---- */
+
+/* out = J_L(U)^T (scale M) on interior cells; U's guard cells are filled here
+ * on a copy. */
+void orc_stage_vjp(const OrcGrid* G, const double* U, const double* M, double scale, double* out) {
+  const Geo geo(*G);
+  std::vector<double> Uf(U, U + geo.nblocks() * 5 * geo.cells);
+  fill_guardcells(*G, Uf.data());
+  stage_vjp(*G, Uf.data(), M, scale, out);
+}
+
+void orc_step_adjoint(const OrcGrid* G, const double* Un, double dt, const double* lam_next, double* lam_prev) {
+  step_adjoint(*G, Un, dt, lam_next, lam_prev);
 }
 
 }  // extern "C"

@@ -66,6 +66,10 @@ def lib():
             L.orc_step.restype = C.c_longlong
             L.orc_run.argtypes = [gp, dp, C.c_int, dp]
             L.orc_run.restype = C.c_longlong
+            L.orc_stage_vjp.argtypes = [gp, dp, dp, C.c_double, dp]
+            L.orc_stage_vjp.restype = None
+            L.orc_step_adjoint.argtypes = [gp, dp, C.c_double, dp, dp]
+            L.orc_step_adjoint.restype = None
             ap = C.POINTER(OrcAmr2)
             L.orc2_restrict.argtypes = [gp, ap, dp]
             L.orc2_restrict.restype = None
@@ -147,6 +151,22 @@ class Oracle:
     def step(self, U, dt):
         _check(U, self.lat)
         return int(self.L.orc_step(C.byref(self.g), _dp(U), float(dt)))
+
+    def stage_vjp(self, U, M, scale):
+        """J_L(U)^T (scale M) on interior cells (dt held fixed, branches frozen)."""
+        _check(U, self.lat)
+        _check(M, self.lat)
+        out = np.zeros_like(U)
+        self.L.orc_stage_vjp(C.byref(self.g), _dp(U), _dp(M), float(scale), _dp(out))
+        return out
+
+    def step_adjoint(self, Un, dt, lam_next):
+        """dJ/dU^n of one step(Un, dt) from dJ/dU^{n+1} (interior cells)."""
+        _check(Un, self.lat)
+        _check(lam_next, self.lat)
+        out = np.zeros_like(Un)
+        self.L.orc_step_adjoint(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out))
+        return out
 
     def run(self, U, nsteps):
         """Advance U in place by nsteps; returns (dt history, floor hits)."""

@@ -57,6 +57,10 @@ SIGNATURES = {
     "gbh_autotune": (C.c_int, [_vp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int), _vp]),
     "gbh_set_decomposition": (C.c_int, [_vp, C.c_int, C.c_int]),
     "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
+    "hydro_stage_vjp": (C.c_int, [_vp, _dp, _dp, C.c_double, _dp, C.c_double, _dp, C.c_double, _dp, _vp]),
+    "hydro_step_adjoint": (C.c_int, [_vp, _dp, C.c_double, _dp, _dp, _vp]),
+    "hydro_prim_to_cons": (C.c_int, [_vp, _dp, _dp, _vp]),
+    "hydro_prim_to_cons_vjp": (C.c_int, [_vp, _dp, _dp, _dp, _vp]),
     "gbh_destroy": (C.c_int, [_vp]),
     "gbh_last_error": (C.c_char_p, [_vp]),
     "gbh_state_bytes": (C.c_longlong, [_vp]),

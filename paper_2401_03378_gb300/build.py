@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbhydro.so")
-SOURCES = ["gbh_abi.cu", "gbh_stage.cu", "gbh_aux.cu", "gbh_static.cu", "gbh_amr.cu"]
-HEADERS = ["gbh_internal.h", "gbh_device.cuh", "gbh_fastmath.cuh"]
+SOURCES = ["gbh_abi.cu", "gbh_stage.cu", "gbh_aux.cu", "gbh_static.cu", "gbh_amr.cu", "gbh_adjoint.cu"]
+HEADERS = ["gbh_internal.h", "gbh_device.cuh", "gbh_fastmath.cuh", "gbh_gather.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

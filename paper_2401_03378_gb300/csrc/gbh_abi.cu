@@ -64,6 +64,9 @@ struct gbh_ctx {
   const double* graph_U = nullptr;
   const double* graph_dt = nullptr;
   int graph_steps = 0;
+  // adjoint buffers (allocated on first use): per-face adjoint slots, intermediate adjoint
+  double* d_adj_lamW = nullptr;
+  double* d_adj_tmp = nullptr;
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -205,6 +208,31 @@ int reduce_dt(gbh_ctx* c, const double* U, double* dt_dev, double* hist, cudaStr
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, hist, s, c->nproblems),
                   "dt finalize launch");
+}
+
+int ensure_adjoint_buffers(gbh_ctx* c) {
+  const size_t bytes = sizeof(double) * (size_t)state_elems(c->lay);
+  cudaError_t e = cudaSuccess;
+  if (!c->d_adj_lamW) e = cudaMalloc(&c->d_adj_lamW, sizeof(double) * gbh::stage_vjp_scratch_doubles(c->lay));
+  if (e == cudaSuccess && !c->d_adj_tmp) e = cudaMalloc(&c->d_adj_tmp, bytes);
+  if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
+gbh::StageArgs vjp_args(gbh_ctx* c, const double* U) {
+  gbh::StageArgs A{};
+  gbh::stage_args_common(&A, c->lay, c->eos);
+  A.Uin = U;
+  A.face_nbr = c->d_face;
+  A.inv_dx = c->d_inv_dx;
+  A.gather = 1;
+  return A;
+}
+
+int adjoint_supported(gbh_ctx* c) {
+  if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is not implemented on two-level contexts");
+  if (c->nproblems > 1) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint takes one dt: not on batched contexts");
+  return GBH_OK;
 }
 
 void drop_graph(gbh_ctx* c) {
@@ -642,6 +670,63 @@ int hydro_advance_graph(gbh_ctx* c, double* U, int nsteps, double* dt_dev, void*
   return cuda_err(c, cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream), "graph launch");
 }
 
+int hydro_stage_vjp(gbh_ctx* c, const double* U, const double* M, double scale, const double* A, double cA,
+                    const double* B, double cB, double* out, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = adjoint_supported(c))) return rc;
+  if (!U || !M || !out || !aligned8(U) || !aligned8(M) || !aligned8(out) || (A && !aligned8(A)) || (B && !aligned8(B)))
+    return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  if (!std::isfinite(scale) || !std::isfinite(cA) || !std::isfinite(cB)) return set_err(c, GBH_ERR_INVAL, "non-finite coefficient");
+  const long long n = state_elems(c->lay);
+  if ((out < U + n && U < out + n) || (out < M + n && M < out + n))
+    return set_err(c, GBH_ERR_INVAL, "out must not overlap U or M");
+  if ((rc = ensure_adjoint_buffers(c))) return rc;
+  return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, U), M, scale, A, cA, B, cB, c->d_adj_lamW, out,
+                                           (cudaStream_t)stream), "stage VJP launch");
+}
+
+int hydro_step_adjoint(gbh_ctx* c, const double* Un, double dt, const double* lam_next, double* lam_prev,
+                       void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = adjoint_supported(c))) return rc;
+  if ((rc = check_dt(c, dt))) return rc;
+  if (!Un || !lam_next || !lam_prev || !aligned8(Un) || !aligned8(lam_next) || !aligned8(lam_prev))
+    return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  const long long n = state_elems(c->lay);
+  if (lam_prev < Un + n && Un < lam_prev + n) return set_err(c, GBH_ERR_INVAL, "lam_prev must not overlap Un");
+  if ((rc = ensure_adjoint_buffers(c))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // U1 = Un + dt L(Un) (recomputed forward stage)
+  rc = stage_launch(c, Un, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
+  if (rc) return rc;
+  // U^{n+1} = 1/2 Un + 1/2 (U1 + dt L(U1)):  lam_U1 = 1/2 lam + J_L(U1)^T (dt/2 lam)
+  rc = cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, c->d_scratch), lam_next, 0.5 * dt, lam_next, 0.5, nullptr, 0.0,
+                                         c->d_adj_lamW, c->d_adj_tmp, s), "stage VJP launch");
+  if (rc) return rc;
+  // lam_n = 1/2 lam + lam_U1 + J_L(Un)^T (dt lam_U1)
+  return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, Un), c->d_adj_tmp, dt, lam_next, 0.5, c->d_adj_tmp, 1.0,
+                                           c->d_adj_lamW, lam_prev, s), "stage VJP launch");
+}
+
+int hydro_prim_to_cons(gbh_ctx* c, const double* W, double* U, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!W || !U || !aligned8(W) || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  return cuda_err(c, gbh::launch_prim_to_cons(c->lay, c->eos, W, U, nullptr, nullptr, (cudaStream_t)stream),
+                  "prim_to_cons launch");
+}
+
+int hydro_prim_to_cons_vjp(gbh_ctx* c, const double* W, const double* lamU, double* lamW, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!W || !lamU || !lamW || !aligned8(W) || !aligned8(lamU) || !aligned8(lamW))
+    return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
+  return cuda_err(c, gbh::launch_prim_to_cons(c->lay, c->eos, W, nullptr, lamU, lamW, (cudaStream_t)stream),
+                  "prim_to_cons VJP launch");
+}
+
 int gbh_destroy(gbh_ctx* c) {
   if (!c) return GBH_OK;
   cudaDeviceSynchronize();
@@ -663,6 +748,8 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_reflux);
   cudaFree(c->d_cf_faces);
   cudaFree(c->d_problem);
+  cudaFree(c->d_adj_lamW);
+  cudaFree(c->d_adj_tmp);
   cudaFree(c->d_smax_own);
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -189,6 +189,39 @@ class Hydro:
     def set_decomposition(self, kchunk: int, items_per_cta: int):
         self._check(self.lib.gbh_set_decomposition(self.ctx, int(kchunk), int(items_per_cta)))
 
+    # -- adjoint ------------------------------------------------------------
+    def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None):
+        """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen)."""
+        if lam_prev is None:
+            lam_prev = torch.zeros_like(lam_next)
+        self._check(self.lib.hydro_step_adjoint(self.ctx, self._state(Un, "Un"), float(dt),
+                                                self._state(lam_next, "lam_next"), self._state(lam_prev, "lam_prev"),
+                                                _stream_handle()))
+        return lam_prev
+
+    def stage_vjp(self, U, M, scale: float, A=None, cA: float = 0.0, B=None, cB: float = 0.0, out=None):
+        """out = cA A + cB B + J_L(U)^T (scale M) on interior cells."""
+        if out is None:
+            out = torch.zeros_like(U)
+        a = self._state(A, "A") if A is not None else None
+        b = self._state(B, "B") if B is not None else None
+        self._check(self.lib.hydro_stage_vjp(self.ctx, self._state(U), self._state(M, "M"), float(scale), a,
+                                             float(cA), b, float(cB), self._state(out, "out"), _stream_handle()))
+        return out
+
+    def prim_to_cons(self, W, U=None):
+        if U is None:
+            U = torch.zeros_like(W)
+        self._check(self.lib.hydro_prim_to_cons(self.ctx, self._state(W, "W"), self._state(U), _stream_handle()))
+        return U
+
+    def prim_to_cons_vjp(self, W, lamU, lamW=None):
+        if lamW is None:
+            lamW = torch.zeros_like(W)
+        self._check(self.lib.hydro_prim_to_cons_vjp(self.ctx, self._state(W, "W"), self._state(lamU, "lamU"),
+                                                    self._state(lamW, "lamW"), _stream_handle()))
+        return lamW
+
     def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
         """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
         if isinstance(U_host, torch.Tensor):

@@ -1,0 +1,95 @@
+"""Pins of the oracle's adjoint (dual-number Jacobians transposed): central
+finite differences of the oracle's own forward map, dt held fixed."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle.oracle import Oracle
+
+
+def interior_mask(lat):
+    m = np.zeros(lat.shape, dtype=bool)
+    zs, ys, xs = lat.interior_slices()
+    m[:, :, zs, ys, xs] = True
+    return m
+
+
+def pick(lat, n, seed):
+    """Random interior components.  In 2-D the z-momentum is identically zero,
+    so every MC slope of w sits at the limiter's kink (both differences zero);
+    a finite difference through more than one stage then activates those
+    slopes at first order while the frozen-branch adjoint keeps them at zero.
+    Both are valid one-sided linearisations; the comparison uses the others."""
+    rng = np.random.default_rng(seed)
+    m = interior_mask(lat)
+    if lat.ndim == 2:
+        m[:, 3] = False
+    idx = np.argwhere(m)
+    return [tuple(idx[i]) for i in rng.choice(len(idx), n, replace=False)]
+
+
+LATS = [wl.lattice_2d(2, 2, 8, 8, 4), wl.lattice_3d(2, 2, 2, 4, 4, 4, 4, bc="periodic"),
+        wl.lattice_2d(3, 2, 8, 8, 4, bc=("periodic", "outflow"))]
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_stage_vjp_matches_finite_differences(lat):
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=1, rough=False)
+    rng = np.random.default_rng(2)
+    M = rng.normal(size=U.shape) * interior_mask(lat)
+    dt = 0.5 * o.compute_dt(U)
+
+    def G(V):
+        f = V.copy()
+        o.fill_guardcells(f)
+        out = f.copy()
+        o.stage(f, None, out, dt, 0.0, 1.0)
+        return float(np.sum(M * out * interior_mask(lat)))
+
+    grad = M + o.stage_vjp(U, M, dt)
+    scale = np.max(np.abs(grad))
+    for c in pick(lat, 12, 3):
+        h = 1e-6 * max(1.0, abs(U[c]))
+        Up, Um = U.copy(), U.copy()
+        Up[c] += h
+        Um[c] -= h
+        fd = (G(Up) - G(Um)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+@pytest.mark.parametrize("lat", LATS[:2])
+def test_step_adjoint_matches_finite_differences(lat):
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=4, rough=False)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+
+    def G(V):
+        X = V.copy()
+        o.step(X, dt)
+        return float(np.sum(w * X * interior_mask(lat)))
+
+    grad = o.step_adjoint(U, dt, w)
+    scale = np.max(np.abs(grad))
+    for c in pick(lat, 12, 6):
+        h = 1e-6 * max(1.0, abs(U[c]))
+        Up, Um = U.copy(), U.copy()
+        Up[c] += h
+        Um[c] -= h
+        fd = (G(Up) - G(Um)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+def test_step_adjoint_linear_in_the_cotangent():
+    lat = LATS[0]
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=7, rough=True)
+    rng = np.random.default_rng(8)
+    a = rng.normal(size=U.shape) * interior_mask(lat)
+    b = rng.normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+    lhs = o.step_adjoint(U, dt, 2.0 * a - 3.0 * b)
+    rhs = 2.0 * o.step_adjoint(U, dt, a) - 3.0 * o.step_adjoint(U, dt, b)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))

@@ -359,6 +359,28 @@ def sedov_two_level(tl: TwoLevel, gamma: float = 1.4, energy: float = 1.0, r_cel
     return np.ascontiguousarray(np.concatenate([Uc, Uf], axis=0))
 
 
+def sod_smooth(lat: Lattice, gamma: float = 1.4, width_cells: float = 2.0, amp: float = 0.05,
+               primitive: bool = False):
+    """Sod-like 2-D data for gradient checks: the Sod jump at x = 1/2 smoothed by
+    tanh over `width_cells` cells, with smooth 2-D modulations of every field
+    (amplitude `amp`) so that no field is locally constant (the MC limiter is
+    not differentiable where both one-sided differences vanish).  Returns the
+    conserved array, or with primitive=True the (rho, u, v, w, p) array in the
+    same layout."""
+    X, Y, _ = cell_centers(lat)
+    dx = lat.dx[0]
+    s = 0.5 * (1.0 - np.tanh((X - 0.5) / (width_cells * dx)))      # 1 left, 0 right
+    mod = 1.0 + amp * np.sin(2 * np.pi * X + 0.3) * np.sin(2 * np.pi * Y + 0.7)
+    rho = (SOD_RIGHT[0] + (SOD_LEFT[0] - SOD_RIGHT[0]) * s) * mod
+    p = (SOD_RIGHT[2] + (SOD_LEFT[2] - SOD_RIGHT[2]) * s) * (2.0 - mod)
+    u = amp * np.sin(2 * np.pi * Y + 0.2) * np.cos(np.pi * X + 0.1)
+    v = amp * np.cos(2 * np.pi * X + 0.4) * np.sin(2 * np.pi * Y + 0.9)
+    zero = np.zeros_like(rho)
+    if primitive:
+        return np.ascontiguousarray(np.stack([rho, u, v, zero, p], axis=1))
+    return _assemble(lat, rho, u, v, zero, p, gamma)
+
+
 def ensemble_sizes(count: int = 96, seed: int = 0, choices=(64, 128, 256, 512)):
     """Problem sizes for the batched-ensemble workload (uniform draw, seeded)."""
     rng = np.random.Generator(np.random.PCG64(seed))

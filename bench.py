@@ -255,6 +255,9 @@ def run_gpu(args):
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = run_adjoint(args, gb, torch, barrier)
+    telescoping = None
+    if args.telescoping_steps > 0:
+        telescoping = run_telescoping(args, gb, torch, barrier, lat, U0, 1e3 * tmax / args.steps)
 
     # roofline of the dominant kernel (the fused stage kernel, both stages)
     flops_per_launch = 0.5 * (FLOPS_STAGE1 + FLOPS_STAGE2) * zones
@@ -304,6 +307,7 @@ def run_gpu(args):
         "two_level": two_level,
         "ensemble": ensemble,
         "adjoint": adjoint,
+        "telescoping": telescoping,
         "unphysical_cells": nbad,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -313,6 +317,42 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_telescoping(args, gb, torch, barrier, lat, U0, ms_non_telescoping):
+    """The headline workload in the telescoping mode (one guard fill per step;
+    the first stage also updates a 2-cell ring): step time against the
+    non-telescoping step measured above."""
+    h = gb.Hydro.from_lattice(lat)
+    h.set_telescoping(True)
+    U = torch.from_numpy(U0).cuda()
+    dt = h.compute_dt(U)
+    for _ in range(args.warmup):
+        h.step_cfl(U, dt)
+    h.set_kernel_timing(True)
+    h.stage_kernel_time()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.telescoping_steps):
+        h.step_cfl(U, dt)
+    e1.record(stream)
+    barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    stage_ms, launches = h.stage_kernel_time()
+    h.set_kernel_timing(False)
+    nbad = h.check_state(U)
+    h.close()
+    del U
+    torch.cuda.empty_cache()
+    ms = 1e3 * secs / args.telescoping_steps
+    return {"workload": f"{WORKLOAD} -- telescoping mode (fill once per step, ring of 2 in stage 1)",
+            "value": lat.interior_cells * args.telescoping_steps / secs, "unit": UNIT,
+            "steps": args.telescoping_steps, "ms_per_step": ms,
+            "stage_kernels_ms_per_step": stage_ms / args.telescoping_steps,
+            "over_non_telescoping": ms / ms_non_telescoping,
+            "launches_per_step": 4, "unphysical_cells": nbad}
 
 
 def run_two_level(args, gb, torch, barrier):
@@ -501,6 +541,7 @@ def main(argv=None):
     ap.add_argument("--two-level-steps", type=int, default=20)
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--adjoint-steps", type=int, default=50)
+    ap.add_argument("--telescoping-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

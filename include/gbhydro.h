@@ -136,6 +136,23 @@ int gbh_create_batched(const gbh_params *params, const int32_t *problem, int npr
 int gbh_autotune(gbh_ctx *ctx, const double *U, int *kchunk_out, int *items_out, void *stream);
 int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
 
+/* Time-stepping mode (Sec. 4.2, the telescoping variant of the SSP-RK
+ * stepper).  enable = 0 (the default): non-telescoping, the guard cells are
+ * refilled before every stage (fused into the stage kernel as a gather from
+ * the neighbours).  enable != 0: telescoping, one guard fill per step (all 4
+ * guard layers, edges and corners included, written into U's guard cells),
+ * then the first stage updates the interior widened by 2 cells on every side
+ * from U's own guard cells and the second stage reads that ring of the
+ * intermediate state instead of exchanging halos.  Where a neighbour block
+ * supplies the halo the result is the non-telescoping one; at an outflow
+ * domain edge the first stage evolves the zero-gradient copies, so the 2
+ * cells next to that edge differ.  Applies to hydro_step, hydro_step_cfl,
+ * hydro_advance(_graph/_host); not to single stages, hydro_step_static or the
+ * adjoint (which returns GBH_ERR_UNSUPPORTED while the mode is on).
+ * Errors: GBH_ERR_INVAL if nguard < 4; GBH_ERR_UNSUPPORTED on two-level
+ * contexts.  Drops a captured graph. */
+int gbh_set_telescoping(gbh_ctx *ctx, int enable);
+
 /* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
  * private stream; re-captured when U, dt_dev or nsteps change, or the
  * decomposition changes) and launched on `stream` as one graph.  Kernel

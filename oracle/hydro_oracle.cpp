@@ -198,25 +198,44 @@ struct Work {
 
 bool inside(const Geo& geo, int d, int x) { return x >= geo.g[d] && x < geo.g[d] + geo.n[d]; }
 
+/* The box a stage updates: the interior widened by `ext` cells on each side
+ * of every dimension of the problem (ext = 0: the interior). */
+struct Box {
+  int lo[3], hi[3];
+  Box(const Geo& geo, int ext) {
+    for (int d = 0; d < 3; ++d) {
+      const int e = d < geo.ndim ? ext : 0;
+      lo[d] = geo.g[d] - e;
+      hi[d] = geo.g[d] + geo.n[d] + e;
+    }
+  }
+  bool in(int d, int x) const { return x >= lo[d] && x < hi[d]; }
+};
+
 /* One block's intra-stage calculation (Alg. "Intra stage calculations"):
- * calcEos on the cells the stencil reads, calcLims, calcFlux, updSoln.
- * Uin must have its guard cells filled.  Returns floor hits on interior cells. */
+ * calcEos on the cells the stencil reads, calcLims, calcFlux, updSoln, on
+ * the interior widened by `ext` cells (ext = 2: the first stage of the
+ * telescoping mode of Sec. 4.2, which also updates part of the halo).
+ * Uin's guard cells must hold valid data 2 cells beyond that box.  Returns
+ * floor hits on interior cells. */
 ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const double* Un,
-               double* Uout, double dt, double a, double bc, Work& w) {
+               double* Uout, double dt, double a, double bc, Work& w, int ext = 0) {
   const ll cells = geo.cells;
   const int nd = geo.ndim;
+  const Box R(geo, ext);
   ll hits = 0;
-  /* cells read by the face stencil: the interior plus a 2-deep slab across
-   * each face (edges and corners are never read) */
+  /* cells read by the face stencil: the box plus a 2-deep slab across each
+   * of its faces (the box's own edges and corners are never read) */
   for (int k = 0; k < geo.p[2]; ++k)
     for (int j = 0; j < geo.p[1]; ++j)
       for (int i = 0; i < geo.p[0]; ++i) {
         const int x[3] = {i, j, k};
-        int out = 0, far = 0;
+        int out = 0, far = 0, interior = 1;
         for (int d = 0; d < 3; ++d) {
-          if (!inside(geo, d, x[d])) {
+          if (!inside(geo, d, x[d])) interior = 0;
+          if (!R.in(d, x[d])) {
             ++out;
-            const int dist = x[d] < geo.g[d] ? geo.g[d] - x[d] : x[d] - (geo.g[d] + geo.n[d]) + 1;
+            const int dist = x[d] < R.lo[d] ? R.lo[d] - x[d] : x[d] - R.hi[d] + 1;
             if (dist > 2) far = 1;
           }
         }
@@ -226,21 +245,21 @@ ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const 
         double u5[5], W5[5];
         load_cons(geo, Uin, b, k, j, i, u5);
         const int hit = orc::prim_from_cons(u5, G.gamma, G.small_rho, G.small_p, W5);
-        if (out == 0) hits += hit;
+        if (interior) hits += hit;
         for (int v = 0; v < 5; ++v) w.W[v * cells + c] = W5[v];
       }
 
   const ll stride[3] = {1, geo.p[0], (ll)geo.p[0] * geo.p[1]};
-  /* calcLims: MC slopes and face states, per dimension, on the interior and
-   * one cell across each face */
+  /* calcLims: MC slopes and face states, per dimension, on the box and one
+   * cell across each face */
   for (int d = 0; d < nd; ++d)
     for (int k = 0; k < geo.p[2]; ++k)
       for (int j = 0; j < geo.p[1]; ++j)
         for (int i = 0; i < geo.p[0]; ++i) {
           const int x[3] = {i, j, k};
-          bool ok = x[d] >= geo.g[d] - 1 && x[d] <= geo.g[d] + geo.n[d];
+          bool ok = x[d] >= R.lo[d] - 1 && x[d] <= R.hi[d];
           for (int e = 0; e < 3; ++e)
-            if (e != d && !inside(geo, e, x[e])) ok = false;
+            if (e != d && !R.in(e, x[e])) ok = false;
           if (!ok) continue;
           const ll c = geo.cell(k, j, i);
           for (int v = 0; v < 5; ++v) {
@@ -251,8 +270,8 @@ ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const 
           }
         }
 
-  /* calcFlux: HLLC at every face of the interior, F[d][c] is the flux through
-   * the face between c - e_d and c */
+  /* calcFlux: HLLC at every face of the box, F[d][c] is the flux through the
+   * face between c - e_d and c */
   for (int d = 0; d < nd; ++d) {
     /* velocity components in the rotated frame: normal, then the other two */
     const int t1 = d == 0 ? 2 : 1, t2 = d == 2 ? 2 : 3;
@@ -261,9 +280,9 @@ ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const 
       for (int j = 0; j < geo.p[1]; ++j)
         for (int i = 0; i < geo.p[0]; ++i) {
           const int x[3] = {i, j, k};
-          bool ok = x[d] >= geo.g[d] && x[d] <= geo.g[d] + geo.n[d];
+          bool ok = x[d] >= R.lo[d] && x[d] <= R.hi[d];
           for (int e = 0; e < 3; ++e)
-            if (e != d && !inside(geo, e, x[e])) ok = false;
+            if (e != d && !R.in(e, x[e])) ok = false;
           if (!ok) continue;
           const ll c = geo.cell(k, j, i);
           double WL[5], WR[5], Fr[5];
@@ -276,11 +295,11 @@ ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const 
         }
   }
 
-  /* updSoln + RK combine on the interior */
+  /* updSoln + RK combine on the box */
   const double idx = 1.0 / G.dx[0], idy = 1.0 / G.dx[1], idz = 1.0 / G.dx[2];
-  for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
-    for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
-      for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+  for (int k = R.lo[2]; k < R.hi[2]; ++k)
+    for (int j = R.lo[1]; j < R.hi[1]; ++j)
+      for (int i = R.lo[0]; i < R.hi[0]; ++i) {
         const ll c = geo.cell(k, j, i);
         for (int v = 0; v < 5; ++v) {
           const ll o = v * cells + c;
@@ -297,7 +316,7 @@ ll stage_block(const OrcGrid& G, const Geo& geo, ll b, const double* Uin, const 
 }
 
 ll stage(const OrcGrid& G, const double* Uin, const double* Un, double* Uout, double dt, double a,
-         double bc, const ll* blocks, ll nlist) {
+         double bc, const ll* blocks, ll nlist, int ext = 0) {
   const Geo geo(G);
   const ll count = blocks ? nlist : geo.nblocks();
   ll hits = 0;
@@ -308,7 +327,7 @@ ll stage(const OrcGrid& G, const double* Uin, const double* Un, double* Uout, do
 #pragma omp for schedule(dynamic, 1)
     for (ll t = 0; t < count; ++t) {
       const ll b = blocks ? blocks[t] : t;
-      hits += stage_block(G, geo, b, Uin, Un, Uout, dt, a, bc, w);
+      hits += stage_block(G, geo, b, Uin, Un, Uout, dt, a, bc, w, ext);
     }
   }
   return hits;
@@ -326,6 +345,33 @@ ll step(const OrcGrid& G, double* U, double dt) {
   std::memcpy(U2.data(), U1.data(), total * sizeof(double));
   hits += stage(G, U1.data(), U, U2.data(), dt, 0.5, 0.5, nullptr, 0);
   /* copy the new interior back; guard cells keep the values of the first fill */
+  for (ll b = 0; b < geo.nblocks(); ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+            const ll o = geo.at(b, v, k, j, i);
+            U[o] = U2[o];
+          }
+  return hits;
+}
+
+/* One SSP-RK2 step in place in the telescoping mode (Sec. 4.2): one guard
+ * fill, then both stages per block with no exchange between them.  Stage 1
+ * updates the interior widened by 2 cells (the 2-cell reach of the PLM face
+ * stencil), so stage 2 finds U1 in its own guard cells; the fill must supply
+ * 4 guard cells.  Where a neighbour supplies the halo this equals the
+ * non-telescoping step; at an outflow edge the first stage evolves the
+ * zero-gradient copies instead of copying the updated boundary cell. */
+ll step_telescoping(const OrcGrid& G, double* U, double dt) {
+  const Geo geo(G);
+  const ll total = geo.nblocks() * 5 * geo.cells;
+  ll hits = 0;
+  fill_guardcells(G, U);
+  std::vector<double> U1(U, U + total), U2(total);
+  hits += stage(G, U, nullptr, U1.data(), dt, 0.0, 1.0, nullptr, 0, 2);
+  std::memcpy(U2.data(), U1.data(), total * sizeof(double));
+  hits += stage(G, U1.data(), U, U2.data(), dt, 0.5, 0.5, nullptr, 0, 0);
   for (ll b = 0; b < geo.nblocks(); ++b)
     for (int v = 0; v < 5; ++v)
       for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
@@ -897,13 +943,21 @@ long long orc_stage(const OrcGrid* G, const double* Uin, const double* Un, doubl
 
 long long orc_step(const OrcGrid* G, double* U, double dt) { return step(*G, U, dt); }
 
-/* nsteps SSP-RK2 steps, each with dt = compute_dt(U^n); dt_hist[s] receives dt. */
-long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist) {
+/* One telescoping-mode step; -1 if the grid has fewer than 4 guard cells. */
+long long orc_step_telescoping(const OrcGrid* G, double* U, double dt) {
+  if (G->ng < 4) return -1;
+  return step_telescoping(*G, U, dt);
+}
+
+/* nsteps SSP-RK2 steps, each with dt = compute_dt(U^n); dt_hist[s] receives
+ * dt.  telescoping != 0 selects the telescoping mode (needs 4 guard cells). */
+long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist, int telescoping) {
+  if (telescoping && G->ng < 4) return -1;
   long long hits = 0;
   for (int s = 0; s < nsteps; ++s) {
     const double dt = compute_dt(*G, U);
     if (dt_hist) dt_hist[s] = dt;
-    hits += step(*G, U, dt);
+    hits += telescoping ? step_telescoping(*G, U, dt) : step(*G, U, dt);
   }
   return hits;
 }

@@ -64,7 +64,9 @@ def lib():
             L.orc_stage.restype = C.c_longlong
             L.orc_step.argtypes = [gp, dp, C.c_double]
             L.orc_step.restype = C.c_longlong
-            L.orc_run.argtypes = [gp, dp, C.c_int, dp]
+            L.orc_step_telescoping.argtypes = [gp, dp, C.c_double]
+            L.orc_step_telescoping.restype = C.c_longlong
+            L.orc_run.argtypes = [gp, dp, C.c_int, dp, C.c_int]
             L.orc_run.restype = C.c_longlong
             L.orc_stage_vjp.argtypes = [gp, dp, dp, C.c_double, dp]
             L.orc_stage_vjp.restype = None
@@ -148,8 +150,15 @@ class Oracle:
             self._keep = arr
         return int(self.L.orc_stage(C.byref(self.g), _dp(Uin), _dp(Un), _dp(Uout), dt, a, b, lst, nl))
 
-    def step(self, U, dt):
+    def step(self, U, dt, telescoping=False):
+        """One SSP-RK2 step in place; telescoping=True: one guard fill per step
+        and a first stage that also updates a 2-cell ring (needs ng >= 4)."""
         _check(U, self.lat)
+        if telescoping:
+            hits = int(self.L.orc_step_telescoping(C.byref(self.g), _dp(U), float(dt)))
+            if hits < 0:
+                raise ValueError("the telescoping mode needs 4 guard cells")
+            return hits
         return int(self.L.orc_step(C.byref(self.g), _dp(U), float(dt)))
 
     def stage_vjp(self, U, M, scale):
@@ -168,11 +177,13 @@ class Oracle:
         self.L.orc_step_adjoint(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out))
         return out
 
-    def run(self, U, nsteps):
+    def run(self, U, nsteps, telescoping=False):
         """Advance U in place by nsteps; returns (dt history, floor hits)."""
         _check(U, self.lat)
         hist = np.zeros(max(nsteps, 1))
-        hits = int(self.L.orc_run(C.byref(self.g), _dp(U), int(nsteps), _dp(hist)))
+        hits = int(self.L.orc_run(C.byref(self.g), _dp(U), int(nsteps), _dp(hist), int(bool(telescoping))))
+        if hits < 0:
+            raise ValueError("the telescoping mode needs 4 guard cells")
         return hist[:nsteps], hits
 
 

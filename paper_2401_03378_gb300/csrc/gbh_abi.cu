@@ -64,6 +64,8 @@ struct gbh_ctx {
   const double* graph_U = nullptr;
   const double* graph_dt = nullptr;
   int graph_steps = 0;
+  // telescoping mode (gbh_set_telescoping): one guard fill per step
+  bool telescoping = false;
   // adjoint buffers (allocated on first use): per-face adjoint slots, intermediate adjoint
   double* d_adj_lamW = nullptr;
   double* d_adj_tmp = nullptr;
@@ -128,7 +130,7 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
 }
 
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
-                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s) {
+                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, bool ring = false) {
   gbh::StageArgs A{};
   A.Uin = Uin;
   A.Un = Un;
@@ -145,7 +147,12 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   A.smax_acc = dt_epilogue ? c->d_smax : nullptr;
   A.floor_count = c->d_words + 1;
   A.problem = c->d_problem;
-  if (c->lay.ndim == 3 && c->kchunk > 0) {
+  if (ring && c->lay.ndim == 3) {
+    // the first telescoping stage spans nz + 2*ring planes
+    const int span = c->lay.nz + 2 * gbh::TELESCOPE_RING;
+    A.kchunk = c->kchunk > 0 ? c->kchunk : span;
+    A.nchunks = (span + A.kchunk - 1) / A.kchunk;
+  } else if (c->lay.ndim == 3 && c->kchunk > 0) {
     A.kchunk = c->kchunk;
     A.nchunks = (c->lay.nz + c->kchunk - 1) / c->kchunk;
   }
@@ -159,7 +166,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
   if (rc) return rc;
-  rc = cuda_err(c, gbh::launch_stage(A, s), "stage kernel launch");
+  rc = cuda_err(c, ring ? gbh::launch_stage_ring(A, s) : gbh::launch_stage(A, s), "stage kernel launch");
   if (rc) return rc;
   if (stop) rc = cuda_err(c, cudaEventRecord(stop, s), "cudaEventRecord");
   return rc;
@@ -189,6 +196,19 @@ int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStr
   rc = refined_stage(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, s);
   if (rc) return rc;
   return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
+}
+
+// One SSP-RK2 step in the telescoping mode (Sec. 4.2): one guard fill of U
+// (4 cells deep), the first stage on the interior widened by 2 cells into
+// the scratch state, the second stage from the scratch state's own guard
+// cells; no exchange between the stages.
+int telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
+  gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
+  int rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch");
+  if (rc) return rc;
+  rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, false, false, s, true);
+  if (rc) return rc;
+  return stage_launch(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, false, dt_epilogue, s);
 }
 
 gbh::DtArgs dt_args(gbh_ctx* c, const double* U) {
@@ -231,6 +251,7 @@ gbh::StageArgs vjp_args(gbh_ctx* c, const double* U) {
 
 int adjoint_supported(gbh_ctx* c) {
   if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is not implemented on two-level contexts");
+  if (c->telescoping) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping step");
   if (c->nproblems > 1) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint takes one dt: not on batched contexts");
   return GBH_OK;
 }
@@ -343,9 +364,13 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
     if (rc) return rc;
     return reduce_dt(c, U, dt_dev, nullptr, s);
   }
-  int rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
-  if (rc) return rc;
-  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
+  int rc;
+  if (c->telescoping) {
+    rc = telescoping_step(c, U, dt_dev, 0.0, true, s);
+  } else {
+    rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
+    if (!rc) rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
+  }
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
                   "dt finalize launch");
@@ -627,6 +652,17 @@ int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, v
   return GBH_OK;
 }
 
+int gbh_set_telescoping(gbh_ctx* c, int enable) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  if (enable && c->refined)
+    return set_err(c, GBH_ERR_UNSUPPORTED, "the telescoping mode is not implemented on two-level contexts");
+  if (enable && c->lay.g < 4)
+    return set_err(c, GBH_ERR_INVAL, "the telescoping mode needs nguard >= 4 (got %d)", c->lay.g);
+  drop_graph(c);
+  c->telescoping = enable != 0;
+  return GBH_OK;
+}
+
 int gbh_set_decomposition(gbh_ctx* c, int kchunk, int items_per_cta) {
   if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
   if (items_per_cta < 1 || kchunk < 0 || (kchunk > 0 && (c->lay.ndim != 3 || kchunk < 2 || kchunk > c->lay.nz)))
@@ -815,6 +851,7 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->refined) return refined_step(c, U, nullptr, dt, s);
+  if (c->telescoping) return telescoping_step(c, U, nullptr, dt, false, s);
   rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
   if (rc) return rc;
   return stage_launch(c, c->d_scratch, U, U, nullptr, dt, 0.5, 0.5, true, false, s);

@@ -24,6 +24,11 @@
 // Optional epilogue (second RK stage): max over the CTA of the CFL signal
 // speed of Uout, one 64-bit atomicMax per CTA on the bit pattern of the
 // non-negative double.
+//
+// Telescoping mode (Sec. 4.2): the first stage also updates a ring of E = 2
+// guard cells around the interior, from the block's own (filled, 4-deep)
+// guard cells.  The same kernel does it with an (N+2E)^2 plane tile shifted
+// by -E and z planes -E .. nz+E-1; tile position (u, v) is cell (u-E, v-E).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,27 +41,32 @@ namespace {
 
 // One work item: block `b` of the list (or of the lattice) and z-chunk
 // `chunk`.  Uses the caller's shared memory; ends with the per-item atomics.
-template <int N, bool DIM3>
+template <int N, bool DIM3, int E>
 __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red) {
-  constexpr int NT = N * N;
-  constexpr int P = N + 4;                  // plane with 2-deep x/y rims
-  constexpr int QX = N * (N + 2);           // x-slope cells of a plane
-  constexpr int FX = N * (N + 1);           // x faces of a plane
+  constexpr int M = N + 2 * E;              // plane tile (the interior when E = 0)
+  constexpr int NT = M * M;
+  constexpr int P = M + 4;                  // tile with 2-deep x/y rims
+  constexpr int QX = M * (M + 2);           // x-slope cells of a plane
+  constexpr int FX = M * (M + 1);           // x faces of a plane
   double* sW = smem;                        // [5][P][P] primitives of the plane
-  double* sQx = sW + 5 * P * P;             // [2][5][N][N+2] x face states (minus, plus)
-  double* sQy = sQx + 2 * 5 * QX;           // [2][5][N+2][N] y face states
-  double* sFx = sQy + 2 * 5 * QX;           // [5][N][N+1] x fluxes
-  double* sFy = sFx + 5 * FX;               // [5][N+1][N] y fluxes
+  double* sQx = sW + 5 * P * P;             // [2][5][M][M+2] x face states (minus, plus)
+  double* sQy = sQx + 2 * 5 * QX;           // [2][5][M+2][M] y face states
+  double* sFx = sQy + 2 * 5 * QX;           // [5][M][M+1] x fluxes
+  double* sFy = sFx + 5 * FX;               // [5][M+1][M] y fluxes
 
   const Layout& L = a.lay;
   const int tid = threadIdx.x;
-  const int tx = tid % N, ty = tid / N;
+  const int tx = tid % M, ty = tid / M;     // tile position; cell (tx - E, ty - E)
+  const int ci = tx - E, cj = ty - E;
   const int slot_idx = item / a.nchunks;
   const int chunk = item - slot_idx * a.nchunks;
   const int b = a.block_list ? __ldg(a.block_list + slot_idx) : slot_idx;
   const int prob = a.problem ? __ldg(a.problem + b) : 0;
-  const int k0 = DIM3 ? chunk * a.kchunk : 0;
-  const int k1 = DIM3 ? min(L.nz, k0 + a.kchunk) : 1;
+  const int k0 = DIM3 ? chunk * a.kchunk - E : 0;
+  const int k1 = DIM3 ? min(L.nz + E, k0 + a.kchunk) : 1;
+  // floor hits are counted on interior cells only (plane kk of this column)
+  const bool col_in = E == 0 || (ci >= 0 && ci < N && cj >= 0 && cj < N);
+  auto counted = [&](int kk) { return E == 0 ? kk < k1 : (col_in && kk >= 0 && kk < L.nz && kk < k1); };
   const double dt = a.dt_dev ? a.dt_dev[prob] : a.dt;
   const double idx = __ldg(a.inv_dx + 3 * b), idy = __ldg(a.inv_dx + 3 * b + 1);
   const double idz = DIM3 ? __ldg(a.inv_dx + 3 * b + 2) : 0.0;
@@ -69,11 +79,12 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
-    load_prim<N>(a, b, tx, ty, k0 - 2, Wm2);
-    load_prim<N>(a, b, tx, ty, k0 - 1, Wm1);
-    hits += load_prim<N>(a, b, tx, ty, k0, W0);
-    const int h1 = load_prim<N>(a, b, tx, ty, k0 + 1, Wp1);
-    if (k0 + 1 < k1) hits += h1;
+    load_prim<N>(a, b, ci, cj, k0 - 2, Wm2);
+    load_prim<N>(a, b, ci, cj, k0 - 1, Wm1);
+    const int h0 = load_prim<N>(a, b, ci, cj, k0, W0);
+    if (counted(k0)) hits += h0;
+    const int h1 = load_prim<N>(a, b, ci, cj, k0 + 1, Wp1);
+    if (counted(k0 + 1)) hits += h1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       qpm1[v] = Wm1[v] + mc_half_slope(Wm2[v], Wm1[v], W0[v]);
@@ -88,15 +99,16 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     hllc_flux(wl, wr, e, f);
     Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
   } else {
-    hits += load_prim<N>(a, b, tx, ty, 0, W0);
+    const int h0 = load_prim<N>(a, b, ci, cj, 0, W0);
+    if (col_in) hits += h0;
   }
 
   for (int k = k0; k < k1; ++k) {
     double Fzp[5], Wn[5], qpn[5];
     if (DIM3) {
       // own column: primitives at k+2, face states of k+1, z flux at k + 1/2
-      const int hn = load_prim<N>(a, b, tx, ty, k + 2, Wn);
-      if (k + 2 < k1) hits += hn;
+      const int hn = load_prim<N>(a, b, ci, cj, k + 2, Wn);
+      if (counted(k + 2)) hits += hn;
       double qmz[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -112,68 +124,69 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
 
     // (A) primitives of plane k and its 2-deep x/y rims -> shared memory
+    //     (i, j: tile positions)
 #pragma unroll
     for (int v = 0; v < 5; ++v) sW[(v * P + ty + 2) * P + tx + 2] = W0[v];
-    for (int r = tid; r < 8 * N; r += NT) {
-      const int q = r / (2 * N), t = r - q * 2 * N;
-      const int depth = t / N, pos = t - depth * N;
+    for (int r = tid; r < 8 * M; r += NT) {
+      const int q = r / (2 * M), t = r - q * 2 * M;
+      const int depth = t / M, pos = t - depth * M;
       int i, j;
       if (q == 0) { i = -1 - depth; j = pos; }
-      else if (q == 1) { i = N + depth; j = pos; }
+      else if (q == 1) { i = M + depth; j = pos; }
       else if (q == 2) { i = pos; j = -1 - depth; }
-      else { i = pos; j = N + depth; }
+      else { i = pos; j = M + depth; }
       double W[5];
-      load_prim<N>(a, b, i, j, k, W);
+      load_prim<N>(a, b, i - E, j - E, k, W);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sW[(v * P + j + 2) * P + i + 2] = W[v];
     }
     __syncthreads();
 
-    // (B) MC face states: x-slope cells i in [-1, N], y-slope cells j in [-1, N]
+    // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M]
     for (int s = tid; s < 2 * QX; s += NT) {
       if (s < QX) {
-        const int ii = s % (N + 2), j = s / (N + 2);   // slope cell i = ii - 1
+        const int ii = s % (M + 2), j = s / (M + 2);   // slope cell i = ii - 1
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const double* row = sW + (v * P + j + 2) * P + ii;
           const double q0 = row[1];
           const double h = mc_half_slope(row[0], q0, row[2]);
-          sQx[(v * N + j) * (N + 2) + ii] = q0 - h;
-          sQx[((5 + v) * N + j) * (N + 2) + ii] = q0 + h;
+          sQx[(v * M + j) * (M + 2) + ii] = q0 - h;
+          sQx[((5 + v) * M + j) * (M + 2) + ii] = q0 + h;
         }
       } else {
         const int s2 = s - QX;
-        const int i = s2 % N, jj = s2 / N;             // slope cell j = jj - 1
+        const int i = s2 % M, jj = s2 / M;             // slope cell j = jj - 1
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const double* col = sW + (v * P + jj) * P + i + 2;
           const double q0 = col[P];
           const double h = mc_half_slope(col[0], q0, col[2 * P]);
-          sQy[(v * (N + 2) + jj) * N + i] = q0 - h;
-          sQy[((5 + v) * (N + 2) + jj) * N + i] = q0 + h;
+          sQy[(v * (M + 2) + jj) * M + i] = q0 - h;
+          sQy[((5 + v) * (M + 2) + jj) * M + i] = q0 + h;
         }
       }
     }
     __syncthreads();
 
-    // (C) HLLC on the x faces (i - 1/2, i in [0, N]) and y faces (j - 1/2, j in [0, N])
+    // (C) HLLC on the x faces (i - 1/2, i in [0, M]) and y faces (j - 1/2, j in [0, M])
     for (int f = tid; f < 2 * FX; f += NT) {
       const bool xf = f < FX;
       int i, j;
       const double *ql, *qr;       // minus/plus state arrays, var stride vs
       int vs, ol, orr;
       if (xf) {
-        i = f % (N + 1); j = f / (N + 1);
-        vs = N * (N + 2);
-        ol = 5 * vs + j * (N + 2) + i;        // plus state of cell i-1 (slot i)
-        orr = j * (N + 2) + i + 1;            // minus state of cell i (slot i+1)
+        i = f % (M + 1); j = f / (M + 1);
+        vs = M * (M + 2);
+        ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
+        orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
         const int f2 = f - FX;
-        i = f2 % N; j = f2 / N;
-        vs = (N + 2) * N;
-        ol = 5 * vs + j * N + i;              // plus state of cell j-1 (slot j)
-        orr = (j + 1) * N + i;                // minus state of cell j (slot j+1)
+        i = f2 % M; j = f2 / M;
+        vs = (M + 2) * M;
+        ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
+        orr = (j + 1) * M + i;                // minus state of cell j (slot j+1)
         ql = sQy; qr = sQy;
       }
       const int vn = xf ? 1 : 2, vt = xf ? 2 : 1;   // normal and first tangential momentum
@@ -182,24 +195,24 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double F[5];
       hllc_flux(wl, wr, e, F);
       if (xf) {
-        double* o = sFx + j * (N + 1) + i;
+        double* o = sFx + j * (M + 1) + i;
         o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
       } else {
-        double* o = sFy + j * N + i;
+        double* o = sFy + j * M + i;
         o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
       }
     }
     __syncthreads();
 
-    // (D) updSoln + RK combine for cell (tx, ty, k):
+    // (D) updSoln + RK combine for cell (ci, cj, k):
     //     Uin + dt L = Uin - dt/dx dFx - dt/dy dFy - dt/dz dFz
     const long long base =
-        (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (ty + L.g)) * L.nxp + (tx + L.g);
+        (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (cj + L.g)) * L.nxp + (ci + L.g);
     double out[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double fx = sFx[(v * N + ty) * (N + 1) + tx + 1] - sFx[(v * N + ty) * (N + 1) + tx];
-      const double fy = sFy[(v * (N + 1) + ty + 1) * N + tx] - sFy[(v * (N + 1) + ty) * N + tx];
+      const double fx = sFx[(v * M + ty) * (M + 1) + tx + 1] - sFx[(v * M + ty) * (M + 1) + tx];
+      const double fy = sFy[(v * (M + 1) + ty + 1) * M + tx] - sFy[(v * (M + 1) + ty) * M + tx];
       const long long o = base + v * L.vstride;
       double r = fma(-dtx, fx, __ldg(a.Uin + o));
       r = fma(-dty, fy, r);
@@ -207,7 +220,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       out[v] = a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
       a.Uout[o] = out[v];
     }
-    if (a.flux_slot) {
+    if (E == 0 && a.flux_slot) {
       // fluxBuff: fluxes through faces on a coarse-fine boundary, for the correction
       const long long n2 = DIM3 ? N : 1;
       const long long ss = 5 * n2 * N;
@@ -230,7 +243,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
         for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + ty) * N + tx] = Fzp[v];
     }
-    if (a.smax_acc) {
+    if (E == 0 && a.smax_acc) {
       double W[5];
       cons_to_prim(out, W, e);
       smax = fmax(smax, signal_speed(W, e, idx, idy, idz, DIM3));
@@ -248,7 +261,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   }
 
   if (hits) atomicAdd(a.floor_count, (unsigned long long)hits);
-  if (a.smax_acc) {
+  if (E == 0 && a.smax_acc) {
     s_red[tid] = smax;
     __syncthreads();
 #pragma unroll
@@ -263,47 +276,62 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 // Work list: items (block, z-chunk) in order; each CTA processes
 // `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
 // grid makes the kernel persistent).  No CTA waits on another.
-template <int N, bool DIM3>
-__global__ void __launch_bounds__(N * N) stage_kernel(const StageArgs a) {
+template <int N, bool DIM3, int E>
+__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E)) stage_kernel(const StageArgs a) {
   extern __shared__ double smem[];
-  __shared__ double s_red[N * N];
+  __shared__ double s_red[E == 0 ? N * N : 1];
   const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
   const int first = blockIdx.x * a.items_per_cta;
   const int last = min(nitems, first + a.items_per_cta);
   for (int item = first; item < last; ++item) {
-    stage_item<N, DIM3>(a, item, smem, s_red);
+    stage_item<N, DIM3, E>(a, item, smem, s_red);
     __syncthreads();
   }
 }
 
-template <int N>
+template <int N, int E>
 size_t smem_for() {
-  constexpr int P = N + 4;
-  return sizeof(double) * (5 * P * P + 4 * 5 * N * (N + 2) + 2 * 5 * N * (N + 1));
+  constexpr int M = N + 2 * E;
+  constexpr int P = M + 4;
+  return sizeof(double) * (5 * P * P + 4 * 5 * M * (M + 2) + 2 * 5 * M * (M + 1));
 }
 
-template <int N, bool D3>
+template <int N, bool D3, int E>
 cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
   const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
   const int per = a.items_per_cta > 0 ? a.items_per_cta : 1;
   const unsigned grid = (unsigned)((nitems + per - 1) / per);
-  stage_kernel<N, D3><<<grid, N * N, smem_for<N>(), s>>>(a);
+  stage_kernel<N, D3, E><<<grid, (N + 2 * E) * (N + 2 * E), smem_for<N, E>(), s>>>(a);
   return cudaGetLastError();
 }
 
 template <int N, bool D3>
 cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(stage_kernel<N, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_for<N>());
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<N, D3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_for<N, 0>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(stage_kernel<N, D3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_for<N, 2>());
+}
+
+template <int E>
+cudaError_t launch_e(const StageArgs& a, cudaStream_t s) {
+  const bool d3 = a.lay.ndim == 3;
+  switch (a.lay.nx) {
+    case 4: return d3 ? launch_t<4, true, E>(a, s) : launch_t<4, false, E>(a, s);
+    case 8: return d3 ? launch_t<8, true, E>(a, s) : launch_t<8, false, E>(a, s);
+    case 16: return d3 ? launch_t<16, true, E>(a, s) : launch_t<16, false, E>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 size_t stage_smem_bytes(int nx) {
   switch (nx) {
-    case 4: return smem_for<4>();
-    case 8: return smem_for<8>();
-    case 16: return smem_for<16>();
+    case 4: return smem_for<4, 0>();
+    case 8: return smem_for<8, 0>();
+    case 16: return smem_for<16, 0>();
     default: return 0;
   }
 }
@@ -318,14 +346,11 @@ cudaError_t stage_prepare(int nx, int ndim) {
   }
 }
 
-cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) {
-  const bool d3 = a.lay.ndim == 3;
-  switch (a.lay.nx) {
-    case 4: return d3 ? launch_t<4, true>(a, s) : launch_t<4, false>(a, s);
-    case 8: return d3 ? launch_t<8, true>(a, s) : launch_t<8, false>(a, s);
-    case 16: return d3 ? launch_t<16, true>(a, s) : launch_t<16, false>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0>(a, s); }
+
+cudaError_t launch_stage_ring(const StageArgs& a, cudaStream_t s) {
+  if (a.gather || a.combine || a.smax_acc || a.flux_slot || a.lay.g < 4) return cudaErrorInvalidValue;
+  return launch_e<TELESCOPE_RING>(a, s);
 }
 
 }  // namespace gbh

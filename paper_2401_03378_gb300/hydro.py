@@ -189,6 +189,10 @@ class Hydro:
     def set_decomposition(self, kchunk: int, items_per_cta: int):
         self._check(self.lib.gbh_set_decomposition(self.ctx, int(kchunk), int(items_per_cta)))
 
+    def set_telescoping(self, enable: bool = True):
+        """Telescoping SSP-RK2 (one guard fill per step; needs nguard >= 4)."""
+        self._check(self.lib.gbh_set_telescoping(self.ctx, int(bool(enable))))
+
     # -- adjoint ------------------------------------------------------------
     def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None):
         """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen)."""

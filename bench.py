@@ -379,6 +379,21 @@ def run_two_level(args, gb, torch, barrier):
     barrier()
     secs = e0.elapsed_time(e1) / 1e3
     nbad = h.check_state(U)
+    # the same grid in the level-by-level telescoping variant
+    h.set_telescoping(True)
+    U.copy_(torch.from_numpy(U0))
+    h.fill_guardcells(U)
+    h.compute_dt(U, dt)
+    for _ in range(args.warmup):
+        h.step_cfl(U, dt)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.two_level_steps):
+        h.step_cfl(U, dt)
+    e1.record(stream)
+    barrier()
+    tsecs = e0.elapsed_time(e1) / 1e3
+    tbad = h.check_state(U)
     h.close()
     del U
     torch.cuda.empty_cache()
@@ -386,7 +401,11 @@ def run_two_level(args, gb, torch, barrier):
                         "restriction/prolongation in the guard fill, flux correction every stage",
             "value": tl.leaf_cells * args.two_level_steps / secs, "unit": UNIT, "zones": tl.leaf_cells,
             "steps": args.two_level_steps, "ms_per_step": 1e3 * secs / args.two_level_steps,
-            "launches_per_step": 11, "unphysical_cells": nbad}
+            "launches_per_step": 11, "unphysical_cells": nbad,
+            "level_by_level_telescoping": {
+                "value": tl.leaf_cells * args.two_level_steps / tsecs, "unit": UNIT,
+                "ms_per_step": 1e3 * tsecs / args.two_level_steps, "launches_per_step": 10,
+                "unphysical_cells": tbad}}
 
 
 def run_ensemble(args, gb, torch, barrier):

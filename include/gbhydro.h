@@ -146,11 +146,20 @@ int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
  * intermediate state instead of exchanging halos.  Where a neighbour block
  * supplies the halo the result is the non-telescoping one; at an outflow
  * domain edge the first stage evolves the zero-gradient copies, so the 2
- * cells next to that edge differ.  Applies to hydro_step, hydro_step_cfl,
- * hydro_advance(_graph/_host); not to single stages, hydro_step_static or the
- * adjoint (which returns GBH_ERR_UNSUPPORTED while the mode is on).
- * Errors: GBH_ERR_INVAL if nguard < 4; GBH_ERR_UNSUPPORTED on two-level
- * contexts.  Drops a captured graph. */
+ * cells next to that edge differ.
+ * On a two-level context (gbh_create_refined) the mode is the paper's
+ * level-by-level telescoping variant (Fig. "Level-by-levels, Telescoping"):
+ * one fill for both levels (restriction, same-level copies, prolongation of
+ * all guard layers from the coarser level), both stages of every leaf block
+ * from its own guard data with the fluxes through coarse-fine faces of each
+ * stage kept, then the coarse side of the fine region corrected once with
+ * weight 1/2 per stage, and the restriction.
+ * Applies to hydro_step, hydro_step_cfl, hydro_advance(_graph/_host); not to
+ * single stages, hydro_step_static or the adjoint (which returns
+ * GBH_ERR_UNSUPPORTED while the mode is on).
+ * Errors: GBH_ERR_INVAL if nguard < 4; GBH_ERR_NOMEM if the second set of
+ * flux registers (two-level contexts) cannot be allocated.  Drops a captured
+ * graph. */
 int gbh_set_telescoping(gbh_ctx *ctx, int enable);
 
 /* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a

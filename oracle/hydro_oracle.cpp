@@ -570,6 +570,23 @@ void record_face(const Geo& g, const Work& w, int d, int side, std::vector<doubl
       }
 }
 
+/* Record the fluxes of block t's faces on a coarse-fine boundary: a coarse
+ * leaf block's faces towards a covered block, a fine block's faces with no
+ * fine neighbour. */
+void record_cf_faces(const Amr2& A, const Geo& gc, const Geo& gf, ll t, const Work& w, FluxReg& R) {
+  for (int d = 0; d < A.C.ndim; ++d)
+    for (int side = 0; side < 2; ++side) {
+      int o[3] = {0, 0, 0};
+      o[d] = side ? 1 : -1;
+      if (t < A.n0) {
+        const ll nb = gc.neighbour(t, o);
+        if (nb >= 0 && covered(A, gc, nb)) record_face(gc, w, d, side, R.face[t * 6 + 2 * d + side]);
+      } else if (gf.neighbour(t - A.n0, o) < 0) {
+        record_face(gf, w, d, side, R.face[t * 6 + 2 * d + side]);
+      }
+    }
+}
+
 ll amr2_stage(const Amr2& A, const double* Uin, const double* Un, double* Uout, double dt, double a, double bcoef,
               FluxReg& R) {
   const Geo gc(A.C), gf(A.F);
@@ -585,23 +602,38 @@ ll amr2_stage(const Amr2& A, const double* Uin, const double* Un, double* Uout, 
       if (t < A.n0) {
         if (covered(A, gc, t)) continue;
         hits += stage_block(A.C, gc, t, Uin, Un, Uout, dt, a, bcoef, w);
-        for (int d = 0; d < A.C.ndim; ++d)
-          for (int side = 0; side < 2; ++side) {
-            int o[3] = {0, 0, 0};
-            o[d] = side ? 1 : -1;
-            const ll nb = gc.neighbour(t, o);
-            if (nb >= 0 && covered(A, gc, nb)) record_face(gc, w, d, side, R.face[t * 6 + 2 * d + side]);
-          }
       } else {
-        const ll f = t - A.n0;
         hits += stage_block(A.F, gf, t, Uin, Un, Uout, dt, a, bcoef, w);
-        for (int d = 0; d < A.C.ndim; ++d)
-          for (int side = 0; side < 2; ++side) {
-            int o[3] = {0, 0, 0};
-            o[d] = side ? 1 : -1;
-            if (gf.neighbour(f, o) < 0) record_face(gf, w, d, side, R.face[t * 6 + 2 * d + side]);
-          }
       }
+      record_cf_faces(A, gc, gf, t, w, R);
+    }
+  }
+  return hits;
+}
+
+/* The leaf blocks of level `lev` (0 coarse, 1 fine) through both stages of a
+ * telescoping step (Fig. "Level-by-levels, Telescoping": per block, every
+ * stage, no exchange in between): stage 1 on the interior widened by 2
+ * (U -> U1), stage 2 from U1's ring (U1, U -> U2).  The fluxes through the
+ * block's coarse-fine faces in stage s go to R[s]. */
+ll amr2_level_telescoping(const Amr2& A, int lev, const double* U, double* U1, double* U2, double dt,
+                          FluxReg R[2]) {
+  const Geo gc(A.C), gf(A.F);
+  const ll b0 = lev ? A.n0 : 0, b1 = lev ? A.n0 + A.n1 : A.n0;
+  const OrcGrid& G = lev ? A.F : A.C;
+  const Geo& geo = lev ? gf : gc;
+  ll hits = 0;
+#pragma omp parallel reduction(+ : hits)
+  {
+    Work w;
+    w.resize(gc.cells);
+#pragma omp for schedule(dynamic, 1)
+    for (ll t = b0; t < b1; ++t) {
+      if (!lev && covered(A, gc, t)) continue;
+      hits += stage_block(G, geo, t, U, nullptr, U1, dt, 0.0, 1.0, w, 2);
+      record_cf_faces(A, gc, gf, t, w, R[0]);
+      hits += stage_block(G, geo, t, U1, U, U2, dt, 0.5, 0.5, w, 0);
+      record_cf_faces(A, gc, gf, t, w, R[1]);
     }
   }
   return hits;
@@ -712,6 +744,41 @@ ll amr2_step(const Amr2& A, double* U, double dt) {
   hits += amr2_stage(A, U1.data(), U, U2.data(), dt, 0.5, 0.5, R);
   amr2_reflux(A, U2.data(), dt, 0.5, R);
   for (ll b = 0; b < A.n0 + A.n1; ++b) {
+    if (b < A.n0 && covered(A, gc, b)) continue;
+    for (int v = 0; v < 5; ++v)
+      for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
+        for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
+          for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
+            const ll o = gc.at(b, v, k, j, i);
+            U[o] = U2[o];
+          }
+  }
+  amr2_restrict(A, U);
+  return hits;
+}
+
+/* One SSP-RK2 step on the two-level grid in the level-by-level, telescoping
+ * variant (Sec. 4.2 and Fig. "Level-by-levels, Telescoping"): one guard fill
+ * for both levels (restriction, coarse fill, fine fill with prolongation of
+ * all guard layers), then the levels from the finest down, each block through
+ * both stages on its own guard data; the coarse side of the fine region is
+ * then corrected with the fine fluxes, stage by stage, each with the weight
+ * its L term has in U^{n+1} (1/2 and 1/2); the step ends with the
+ * restriction.  One dt for both levels.  Needs 4 guard cells. */
+ll amr2_step_telescoping(const Amr2& A, double* U, double dt) {
+  const Geo gc(A.C);
+  const ll nblk = A.n0 + A.n1;
+  const ll total = nblk * 5 * gc.cells;
+  FluxReg R[2];
+  R[0].face.assign(nblk * 6, std::vector<double>());
+  R[1].face.assign(nblk * 6, std::vector<double>());
+  ll hits = 0;
+  amr2_prepare(A, U);
+  std::vector<double> U1(U, U + total), U2(U, U + total);
+  for (int lev = 1; lev >= 0; --lev) hits += amr2_level_telescoping(A, lev, U, U1.data(), U2.data(), dt, R);
+  amr2_reflux(A, U2.data(), dt, 0.5, R[0]);
+  amr2_reflux(A, U2.data(), dt, 0.5, R[1]);
+  for (ll b = 0; b < nblk; ++b) {
     if (b < A.n0 && covered(A, gc, b)) continue;
     for (int v = 0; v < 5; ++v)
       for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
@@ -941,6 +1008,14 @@ long long orc_stage(const OrcGrid* G, const double* Uin, const double* Un, doubl
   return stage(*G, Uin, Un, Uout, dt, a, b, blocks, nlist);
 }
 
+/* The same on the interior widened by ext cells (0 or 2; ext = 2 needs 4
+ * guard cells, the first stage of the telescoping mode); -1 if invalid. */
+long long orc_stage_ext(const OrcGrid* G, const double* Uin, const double* Un, double* Uout, double dt,
+                        double a, double b, int ext) {
+  if (ext < 0 || G->ng < ext + 2) return -1;
+  return stage(*G, Uin, Un, Uout, dt, a, b, nullptr, 0, ext);
+}
+
 long long orc_step(const OrcGrid* G, double* U, double dt) { return step(*G, U, dt); }
 
 /* One telescoping-mode step; -1 if the grid has fewer than 4 guard cells. */
@@ -988,14 +1063,23 @@ long long orc2_stage(const OrcGrid* G, const OrcAmr2* R, double* Uin, const doub
   return hits;
 }
 
-long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist) {
+/* One level-by-level telescoping step; -1 if the grid has fewer than 4 guard cells. */
+long long orc2_step_telescoping(const OrcGrid* G, const OrcAmr2* R, double* U, double dt) {
+  if (G->ng < 4) return -1;
+  return amr2_step_telescoping(make_amr2(*G, R->lo, R->hi), U, dt);
+}
+
+/* nsteps steps with the CFL dt of the leaf cells; telescoping != 0 selects
+ * the level-by-level telescoping variant, else all-levels non-telescoping. */
+long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist, int telescoping) {
+  if (telescoping && G->ng < 4) return -1;
   const Amr2 A = make_amr2(*G, R->lo, R->hi);
   long long hits = 0;
   amr2_restrict(A, U);
   for (int s = 0; s < nsteps; ++s) {
     const double dt = amr2_compute_dt(A, U);
     if (dt_hist) dt_hist[s] = dt;
-    hits += amr2_step(A, U, dt);
+    hits += telescoping ? amr2_step_telescoping(A, U, dt) : amr2_step(A, U, dt);
   }
   return hits;
 }

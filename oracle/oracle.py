@@ -62,6 +62,8 @@ def lib():
             L.orc_stage.argtypes = [gp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
                                     C.POINTER(C.c_longlong), C.c_longlong]
             L.orc_stage.restype = C.c_longlong
+            L.orc_stage_ext.argtypes = [gp, dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_int]
+            L.orc_stage_ext.restype = C.c_longlong
             L.orc_step.argtypes = [gp, dp, C.c_double]
             L.orc_step.restype = C.c_longlong
             L.orc_step_telescoping.argtypes = [gp, dp, C.c_double]
@@ -83,7 +85,9 @@ def lib():
             L.orc2_step.restype = C.c_longlong
             L.orc2_stage.argtypes = [gp, ap, dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_int]
             L.orc2_stage.restype = C.c_longlong
-            L.orc2_run.argtypes = [gp, ap, dp, C.c_int, dp]
+            L.orc2_step_telescoping.argtypes = [gp, ap, dp, C.c_double]
+            L.orc2_step_telescoping.restype = C.c_longlong
+            L.orc2_run.argtypes = [gp, ap, dp, C.c_int, dp, C.c_int]
             L.orc2_run.restype = C.c_longlong
             _lib = L
     return _lib
@@ -137,12 +141,20 @@ class Oracle:
         _check(U, self.lat)
         return float(self.L.orc_compute_dt(C.byref(self.g), _dp(U)))
 
-    def stage(self, Uin, Un, Uout, dt, a, b, blocks=None):
-        """Uout = a Un + b (Uin + dt L(Uin)) on the interior; Uin's guards must be filled."""
+    def stage(self, Uin, Un, Uout, dt, a, b, blocks=None, ext=0):
+        """Uout = a Un + b (Uin + dt L(Uin)) on the interior (widened by ext
+        cells per side); Uin's guards must be filled."""
         _check(Uin, self.lat)
         _check(Uout, self.lat)
         if Un is not None:
             _check(Un, self.lat)
+        if ext:
+            if blocks is not None:
+                raise ValueError("ext and blocks are exclusive")
+            hits = int(self.L.orc_stage_ext(C.byref(self.g), _dp(Uin), _dp(Un), _dp(Uout), dt, a, b, int(ext)))
+            if hits < 0:
+                raise ValueError("invalid ring width for the guard width")
+            return hits
         lst, nl = None, 0
         if blocks is not None:
             arr = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64))
@@ -224,14 +236,24 @@ class Oracle2:
         return int(self.L.orc2_stage(C.byref(self.g), C.byref(self.r), _dp(Uin), _dp(Un), _dp(Uout),
                                      dt, a, b, 1 if reflux else 0))
 
-    def step(self, U, dt):
+    def step(self, U, dt, telescoping=False):
+        """One step: all-levels non-telescoping (default), or level-by-level
+        telescoping (one fill, every stage per block, correction at the end)."""
         self._chk(U)
+        if telescoping:
+            hits = int(self.L.orc2_step_telescoping(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
+            if hits < 0:
+                raise ValueError("the telescoping mode needs 4 guard cells")
+            return hits
         return int(self.L.orc2_step(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
 
-    def run(self, U, nsteps):
+    def run(self, U, nsteps, telescoping=False):
         self._chk(U)
         hist = np.zeros(max(nsteps, 1))
-        hits = int(self.L.orc2_run(C.byref(self.g), C.byref(self.r), _dp(U), int(nsteps), _dp(hist)))
+        hits = int(self.L.orc2_run(C.byref(self.g), C.byref(self.r), _dp(U), int(nsteps), _dp(hist),
+                                   int(bool(telescoping))))
+        if hits < 0:
+            raise ValueError("the telescoping mode needs 4 guard cells")
         return hist[:nsteps], hits
 
 

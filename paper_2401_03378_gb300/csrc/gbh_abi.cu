@@ -47,6 +47,8 @@ struct gbh_ctx {
   int* d_fine = nullptr;
   int* d_flux_slot = nullptr;       // [nblocks][6]
   double* d_flux_reg = nullptr;
+  double* d_flux_reg2 = nullptr;    // second stage's registers (telescoping; allocated on first use)
+  size_t flux_reg_doubles = 0;
   gbh::RefluxEntry* d_reflux = nullptr;
   int2* d_cf_faces = nullptr;
   gbh::AmrArgs amr{};
@@ -130,7 +132,8 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
 }
 
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
-                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, bool ring = false) {
+                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, bool ring = false,
+                 double* flux_reg = nullptr) {
   gbh::StageArgs A{};
   A.Uin = Uin;
   A.Un = Un;
@@ -161,7 +164,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
     A.block_list = c->d_active;
     A.nlist = c->nactive;
     A.flux_slot = c->d_flux_slot;
-    A.flux_reg = c->d_flux_reg;
+    A.flux_reg = flux_reg ? flux_reg : c->d_flux_reg;
   }
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
@@ -209,6 +212,31 @@ int telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, boo
   rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, false, false, s, true);
   if (rc) return rc;
   return stage_launch(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, false, dt_epilogue, s);
+}
+
+// One SSP-RK2 step on a two-level grid in the level-by-level telescoping
+// variant (Sec. 4.2, Fig. "Level-by-levels, Telescoping"): one guard fill for
+// both levels (restriction, same-level copies, prolongation of all guard
+// layers), both stages of every leaf block from its own guard data with the
+// coarse-fine face fluxes of stage s in register set s, the coarse-side
+// correction with weight 1/2 per stage, restriction.  The two levels need no
+// data from each other inside the step, so both go through the same
+// launches; the paper's finest-first level loop orders nothing here.
+int refined_telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
+  int rc = cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
+  if (rc) return rc;
+  gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
+  if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
+  if ((rc = cuda_err(c, gbh::launch_prolong(U, c->amr, c->lay.g, false, s), "prolong launch"))) return rc;
+  rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, false, false, s, true, c->d_flux_reg);
+  if (rc) return rc;
+  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, false, false, s, false, c->d_flux_reg2);
+  if (rc) return rc;
+  if ((rc = cuda_err(c, gbh::launch_reflux(U, c->amr, dt_dev, dt, 0.5, s), "reflux launch"))) return rc;
+  gbh::AmrArgs A2 = c->amr;
+  A2.flux_reg = c->d_flux_reg2;
+  if ((rc = cuda_err(c, gbh::launch_reflux(U, A2, dt_dev, dt, 0.5, s), "reflux launch"))) return rc;
+  return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
 }
 
 gbh::DtArgs dt_args(gbh_ctx* c, const double* U) {
@@ -360,7 +388,7 @@ extern "C" int gbh_destroy(gbh_ctx* c);
 static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
   if (c->refined) {
     // the CFL speed must see the flux-corrected state: separate reduction
-    int rc = refined_step(c, U, dt_dev, 0.0, s);
+    int rc = c->telescoping ? refined_telescoping_step(c, U, dt_dev, 0.0, s) : refined_step(c, U, dt_dev, 0.0, s);
     if (rc) return rc;
     return reduce_dt(c, U, dt_dev, nullptr, s);
   }
@@ -534,7 +562,8 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   up((void**)&c->d_covered, covered.empty() ? nullptr : covered.data(), sizeof(int) * covered.size());
   up((void**)&c->d_fine, fine.empty() ? nullptr : fine.data(), sizeof(int) * fine.size());
   up((void**)&c->d_flux_slot, slot.data(), sizeof(int) * slot.size());
-  up((void**)&c->d_flux_reg, nullptr, sizeof(double) * fstride * (size_t)(nslots ? nslots : 1));
+  c->flux_reg_doubles = fstride * (size_t)(nslots ? nslots : 1);
+  up((void**)&c->d_flux_reg, nullptr, sizeof(double) * c->flux_reg_doubles);
   up((void**)&c->d_reflux, refl.empty() ? nullptr : refl.data(), sizeof(gbh::RefluxEntry) * refl.size());
   up((void**)&c->d_cf_faces, cf_faces.empty() ? nullptr : cf_faces.data(), sizeof(int2) * cf_faces.size());
   if (e != cudaSuccess) {
@@ -653,11 +682,17 @@ int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, v
 }
 
 int gbh_set_telescoping(gbh_ctx* c, int enable) {
-  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
-  if (enable && c->refined)
-    return set_err(c, GBH_ERR_UNSUPPORTED, "the telescoping mode is not implemented on two-level contexts");
+  int rc = check_ctx(c);
+  if (rc) return rc;
   if (enable && c->lay.g < 4)
     return set_err(c, GBH_ERR_INVAL, "the telescoping mode needs nguard >= 4 (got %d)", c->lay.g);
+  if (enable && c->refined && !c->d_flux_reg2) {
+    cudaError_t e = cudaMalloc(&c->d_flux_reg2, sizeof(double) * c->flux_reg_doubles);
+    if (e != cudaSuccess) {
+      c->d_flux_reg2 = nullptr;
+      return set_err(c, GBH_ERR_NOMEM, "flux registers: %s", cudaGetErrorString(e));
+    }
+  }
   drop_graph(c);
   c->telescoping = enable != 0;
   return GBH_OK;
@@ -781,6 +816,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_fine);
   cudaFree(c->d_flux_slot);
   cudaFree(c->d_flux_reg);
+  cudaFree(c->d_flux_reg2);
   cudaFree(c->d_reflux);
   cudaFree(c->d_cf_faces);
   cudaFree(c->d_problem);
@@ -850,7 +886,7 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if ((rc = check_dt(c, dt))) return rc;
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  if (c->refined) return refined_step(c, U, nullptr, dt, s);
+  if (c->refined) return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, s) : refined_step(c, U, nullptr, dt, s);
   if (c->telescoping) return telescoping_step(c, U, nullptr, dt, false, s);
   rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
   if (rc) return rc;

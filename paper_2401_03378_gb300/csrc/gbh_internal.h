@@ -87,8 +87,9 @@ cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 
 // Telescoping mode (Sec. 4.2): the first stage updates the interior widened by
 // TELESCOPE_RING cells from the block's own guard cells (gather = 0), which
-// must hold 2 more cells (nguard >= 4).  No combine, no dt epilogue, no flux
-// registers.  kchunk/nchunks split the nz + 2*TELESCOPE_RING planes.
+// must hold 2 more cells (nguard >= 4).  No combine, no dt epilogue; flux
+// registers as in launch_stage.  kchunk/nchunks split the nz + 2*TELESCOPE_RING
+// planes.
 constexpr int TELESCOPE_RING = 2;
 cudaError_t launch_stage_ring(const StageArgs& a, cudaStream_t s);
 

@@ -220,28 +220,29 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       out[v] = a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
       a.Uout[o] = out[v];
     }
-    if (E == 0 && a.flux_slot) {
-      // fluxBuff: fluxes through faces on a coarse-fine boundary, for the correction
+    if (a.flux_slot && col_in && (E == 0 || (k >= 0 && k < L.nz))) {
+      // fluxBuff: fluxes through the block's faces on a coarse-fine boundary,
+      // for the correction (interior cells next to the face write them)
       const long long n2 = DIM3 ? N : 1;
       const long long ss = 5 * n2 * N;
       const int* fsl = a.flux_slot + 6 * b;
       const int t2k = DIM3 ? k : 0;
-      if (tx == 0 && fsl[FACE_XM] >= 0)
+      if (ci == 0 && fsl[FACE_XM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_XM] * ss + (v * n2 + t2k) * N + ty] = sFx[(v * N + ty) * (N + 1)];
-      if (tx == N - 1 && fsl[FACE_XP] >= 0)
+          a.flux_reg[fsl[FACE_XM] * ss + (v * n2 + t2k) * N + cj] = sFx[(v * M + ty) * (M + 1) + tx];
+      if (ci == N - 1 && fsl[FACE_XP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_XP] * ss + (v * n2 + t2k) * N + ty] = sFx[(v * N + ty) * (N + 1) + N];
-      if (ty == 0 && fsl[FACE_YM] >= 0)
+          a.flux_reg[fsl[FACE_XP] * ss + (v * n2 + t2k) * N + cj] = sFx[(v * M + ty) * (M + 1) + tx + 1];
+      if (cj == 0 && fsl[FACE_YM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_YM] * ss + (v * n2 + t2k) * N + tx] = sFy[(v * (N + 1)) * N + tx];
-      if (ty == N - 1 && fsl[FACE_YP] >= 0)
+          a.flux_reg[fsl[FACE_YM] * ss + (v * n2 + t2k) * N + ci] = sFy[(v * (M + 1) + ty) * M + tx];
+      if (cj == N - 1 && fsl[FACE_YP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_YP] * ss + (v * n2 + t2k) * N + tx] = sFy[(v * (N + 1) + N) * N + tx];
+          a.flux_reg[fsl[FACE_YP] * ss + (v * n2 + t2k) * N + ci] = sFy[(v * (M + 1) + ty + 1) * M + tx];
       if (DIM3 && k == 0 && fsl[FACE_ZM] >= 0)
-        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZM] * ss + (v * n2 + ty) * N + tx] = Fzm[v];
+        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZM] * ss + (v * n2 + cj) * N + ci] = Fzm[v];
       if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
-        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + ty) * N + tx] = Fzp[v];
+        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + cj) * N + ci] = Fzp[v];
     }
     if (E == 0 && a.smax_acc) {
       double W[5];
@@ -349,7 +350,7 @@ cudaError_t stage_prepare(int nx, int ndim) {
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0>(a, s); }
 
 cudaError_t launch_stage_ring(const StageArgs& a, cudaStream_t s) {
-  if (a.gather || a.combine || a.smax_acc || a.flux_slot || a.lay.g < 4) return cudaErrorInvalidValue;
+  if (a.gather || a.combine || a.smax_acc || a.lay.g < 4) return cudaErrorInvalidValue;
   return launch_e<TELESCOPE_RING>(a, s);
 }
 

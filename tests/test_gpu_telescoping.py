@@ -159,7 +159,76 @@ def test_mode_errors(gb):
         h.step_adjoint(U, 1e-4, torch.zeros_like(U))
     h.set_telescoping(False)
     h.step_adjoint(U, 1e-4, torch.zeros_like(U))
-    tl = wl.two_level(wl.lattice_2d(4, 4, 16, 16, 4, bc="periodic"), (1, 1), (3, 3))
+    tl = wl.two_level(wl.lattice_2d(4, 4, 16, 16, 3, bc="periodic"), (1, 1), (3, 3))
     h2 = gb.Hydro.from_two_level(tl)
     with pytest.raises(GbhError):
         h2.set_telescoping(True)
+
+
+# ---- two-level grids: the level-by-level telescoping variant ----------------
+
+from tests.test_gpu_amr import GRIDS, leaf_err, smooth  # noqa: E402
+from oracle.oracle import Oracle2  # noqa: E402
+
+
+@pytest.mark.parametrize("tl", GRIDS)
+def test_two_level_one_step_matches_oracle(gb, tl):
+    U = smooth(tl, 12)
+    o = Oracle2(tl)
+    o.restrict(U)
+    dt = o.compute_dt(U)
+    ref = U.copy()
+    o.step(ref, dt, telescoping=True)
+    h = gb.Hydro.from_two_level(tl)
+    h.set_telescoping(True)
+    Ug = dev(U)
+    h.step(Ug, dt)
+    out = host(Ug)
+    assert np.all(leaf_err(out, ref, tl) <= 1e-13), leaf_err(out, ref, tl)
+    cov = [b for b in range(tl.n0) if tl.covered(b)]
+    zs, ys, xs = tl.coarse.interior_slices()
+    a = np.moveaxis(out[cov][:, :, zs, ys, xs], 1, 0)
+    b = np.moveaxis(ref[cov][:, :, zs, ys, xs], 1, 0)
+    assert np.all(relerr_per_var(a, b) <= 1e-13)
+
+
+def test_two_level_sedov_run_and_conservation(gb):
+    tl = wl.two_level(wl.lattice_3d(8, 8, 8), (2, 2, 2), (6, 6, 6))
+    U0 = wl.sedov_two_level(tl)
+    ref = U0.copy()
+    hist_o, hits = Oracle2(tl).run(ref, 20, telescoping=True)
+    h = gb.Hydro.from_two_level(tl)
+    h.set_telescoping(True)
+    Ug = dev(U0)
+    h.fill_guardcells(Ug)
+    dt = h.compute_dt(Ug)
+    hist = torch.zeros(20, dtype=torch.float64, device="cuda")
+    h.advance(Ug, 20, dt, hist)
+    assert np.max(np.abs(host(hist) / hist_o - 1)) <= 1e-12
+    assert np.all(leaf_err(host(Ug), ref, tl) <= 1e-11)
+    assert hits == 0 and h.floor_hits() == 0
+
+
+def test_two_level_periodic_conservation_and_graph(gb):
+    tl = GRIDS[0]
+    U = smooth(tl, 13)
+    Oracle2(tl).restrict(U)
+
+    def totals(A):
+        zs, ys, xs = tl.coarse.interior_slices()
+        vc, vf = np.prod(tl.coarse.dx), np.prod(tl.fine.dx)
+        t = np.zeros(5)
+        for b in range(tl.nblocks):
+            if b < tl.n0 and tl.covered(b):
+                continue
+            t += A[b][:, zs, ys, xs].sum(axis=(1, 2, 3)) * (vc if b < tl.n0 else vf)
+        return t
+    t0, scale = totals(U), totals(np.abs(U))
+    h = gb.Hydro.from_two_level(tl)
+    h.set_telescoping(True)
+    A, B = dev(U), dev(U)
+    da, db = h.compute_dt(A), h.compute_dt(B)
+    h.advance(A, 10, da)
+    h.advance_graph(B, 10, db)
+    assert torch.equal(A, B) and torch.equal(da, db)
+    assert np.all(np.abs(totals(host(A)) - t0) <= 10 * 64 * np.finfo(float).eps * scale)

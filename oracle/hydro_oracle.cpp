@@ -333,53 +333,81 @@ ll stage(const OrcGrid& G, const double* Uin, const double* Un, double* Uout, do
   return hits;
 }
 
-/* One SSP-RK2 step in place (non-telescoping: fill before every stage). */
-ll step(const OrcGrid& G, double* U, double dt) {
-  const Geo geo(G);
-  const ll total = geo.nblocks() * 5 * geo.cells;
-  std::vector<double> U1(U, U + total), U2(total);
-  ll hits = 0;
-  fill_guardcells(G, U);
-  hits += stage(G, U, nullptr, U1.data(), dt, 0.0, 1.0, nullptr, 0);
-  fill_guardcells(G, U1.data());
-  std::memcpy(U2.data(), U1.data(), total * sizeof(double));
-  hits += stage(G, U1.data(), U, U2.data(), dt, 0.5, 0.5, nullptr, 0);
-  /* copy the new interior back; guard cells keep the values of the first fill */
+/* SSP-RK stages in Shu-Osher form (Sec. 4.2 names SSP-RK, multistage, no
+ * order): stage s forms U(s) = a_s U^n + b_s (U(s-1) + dt L(U(s-1))), U(0) =
+ * U^n, and U^{n+1} = U(S).  Two stages: (0, 1), (1/2, 1/2); three stages:
+ * (0, 1), (3/4, 1/4), (1/3, 2/3). */
+struct Rk {
+  int S;
+  double a[3], b[3];
+};
+
+Rk rk_scheme(int nstages) {
+  if (nstages == 3) return Rk{3, {0.0, 0.75, 1.0 / 3.0}, {1.0, 0.25, 2.0 / 3.0}};
+  return Rk{2, {0.0, 0.5, 0.0}, {1.0, 0.5, 0.0}};
+}
+
+/* the weight of dt L(U(s-1)) of stage s in U^{n+1}: b_s times the b of
+ * every later stage (1/2, 1/2 for two stages; 1/6, 1/6, 2/3 for three) */
+double rk_weight(const Rk& r, int s) {
+  double w = r.b[s];
+  for (int t = s + 1; t < r.S; ++t) w = w * r.b[t];
+  return w;
+}
+
+void copy_interior(const Geo& geo, const double* src, double* dst) {
   for (ll b = 0; b < geo.nblocks(); ++b)
     for (int v = 0; v < 5; ++v)
       for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
         for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
           for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
             const ll o = geo.at(b, v, k, j, i);
-            U[o] = U2[o];
+            dst[o] = src[o];
           }
+}
+
+/* One SSP-RK step in place, non-telescoping (Sec. 4.2: a guard fill before
+ * every stage).  The new interior is copied back; U's guard cells keep the
+ * values of the first fill. */
+ll step(const OrcGrid& G, double* U, double dt, int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
+  const Geo geo(G);
+  const ll total = geo.nblocks() * 5 * geo.cells;
+  std::vector<double> X(U, U + total), Y(total);
+  ll hits = 0;
+  fill_guardcells(G, U);
+  hits += stage(G, U, nullptr, X.data(), dt, r.a[0], r.b[0], nullptr, 0);
+  for (int st = 1; st < r.S; ++st) {
+    fill_guardcells(G, X.data());
+    std::memcpy(Y.data(), X.data(), total * sizeof(double));
+    hits += stage(G, X.data(), U, Y.data(), dt, r.a[st], r.b[st], nullptr, 0);
+    std::swap(X, Y);
+  }
+  copy_interior(geo, X.data(), U);
   return hits;
 }
 
-/* One SSP-RK2 step in place in the telescoping mode (Sec. 4.2): one guard
- * fill, then both stages per block with no exchange between them.  Stage 1
- * updates the interior widened by 2 cells (the 2-cell reach of the PLM face
- * stencil), so stage 2 finds U1 in its own guard cells; the fill must supply
- * 4 guard cells.  Where a neighbour supplies the halo this equals the
- * non-telescoping step; at an outflow edge the first stage evolves the
- * zero-gradient copies instead of copying the updated boundary cell. */
-ll step_telescoping(const OrcGrid& G, double* U, double dt) {
+/* One SSP-RK step in place in the telescoping mode (Sec. 4.2): one guard
+ * fill, then every stage per block with no exchange in between.  Stage s of
+ * S updates the interior widened by 2 (S - s) cells (the PLM face stencil
+ * reaches 2 cells), so each later stage finds its input in its own guard
+ * cells; the fill must supply 2 S guard cells.  Where a neighbour supplies
+ * the halo this equals the non-telescoping step; at an outflow edge the
+ * first stages evolve the zero-gradient copies instead of copying the
+ * updated boundary cell. */
+ll step_telescoping(const OrcGrid& G, double* U, double dt, int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
   const Geo geo(G);
   const ll total = geo.nblocks() * 5 * geo.cells;
   ll hits = 0;
   fill_guardcells(G, U);
-  std::vector<double> U1(U, U + total), U2(total);
-  hits += stage(G, U, nullptr, U1.data(), dt, 0.0, 1.0, nullptr, 0, 2);
-  std::memcpy(U2.data(), U1.data(), total * sizeof(double));
-  hits += stage(G, U1.data(), U, U2.data(), dt, 0.5, 0.5, nullptr, 0, 0);
-  for (ll b = 0; b < geo.nblocks(); ++b)
-    for (int v = 0; v < 5; ++v)
-      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
-        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
-          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
-            const ll o = geo.at(b, v, k, j, i);
-            U[o] = U2[o];
-          }
+  std::vector<double> X(U, U + total), Y(U, U + total);
+  hits += stage(G, U, nullptr, X.data(), dt, r.a[0], r.b[0], nullptr, 0, 2 * (r.S - 1));
+  for (int st = 1; st < r.S; ++st) {
+    hits += stage(G, X.data(), U, Y.data(), dt, r.a[st], r.b[st], nullptr, 0, 2 * (r.S - 1 - st));
+    std::swap(X, Y);
+  }
+  copy_interior(geo, X.data(), U);
   return hits;
 }
 
@@ -611,13 +639,12 @@ ll amr2_stage(const Amr2& A, const double* Uin, const double* Un, double* Uout, 
   return hits;
 }
 
-/* The leaf blocks of level `lev` (0 coarse, 1 fine) through both stages of a
- * telescoping step (Fig. "Level-by-levels, Telescoping": per block, every
- * stage, no exchange in between): stage 1 on the interior widened by 2
- * (U -> U1), stage 2 from U1's ring (U1, U -> U2).  The fluxes through the
+/* The leaf blocks of level `lev` (0 coarse, 1 fine) through every stage of
+ * a telescoping step (Fig. "Level-by-levels, Telescoping": per block, every
+ * stage, no exchange in between): stage s on the interior widened by
+ * 2 (S - s) cells, X[s] -> X[s+1], X[0] = U^n.  The fluxes through the
  * block's coarse-fine faces in stage s go to R[s]. */
-ll amr2_level_telescoping(const Amr2& A, int lev, const double* U, double* U1, double* U2, double dt,
-                          FluxReg R[2]) {
+ll amr2_level_telescoping(const Amr2& A, const Rk& r, int lev, std::vector<double>* X, double dt, FluxReg* R) {
   const Geo gc(A.C), gf(A.F);
   const ll b0 = lev ? A.n0 : 0, b1 = lev ? A.n0 + A.n1 : A.n0;
   const OrcGrid& G = lev ? A.F : A.C;
@@ -630,10 +657,11 @@ ll amr2_level_telescoping(const Amr2& A, int lev, const double* U, double* U1, d
 #pragma omp for schedule(dynamic, 1)
     for (ll t = b0; t < b1; ++t) {
       if (!lev && covered(A, gc, t)) continue;
-      hits += stage_block(G, geo, t, U, nullptr, U1, dt, 0.0, 1.0, w, 2);
-      record_cf_faces(A, gc, gf, t, w, R[0]);
-      hits += stage_block(G, geo, t, U1, U, U2, dt, 0.5, 0.5, w, 0);
-      record_cf_faces(A, gc, gf, t, w, R[1]);
+      for (int st = 0; st < r.S; ++st) {
+        hits += stage_block(G, geo, t, X[st].data(), st ? X[0].data() : nullptr, X[st + 1].data(), dt, r.a[st],
+                            r.b[st], w, 2 * (r.S - 1 - st));
+        record_cf_faces(A, gc, gf, t, w, R[st]);
+      }
     }
   }
   return hits;
@@ -730,19 +758,26 @@ void amr2_prepare(const Amr2& A, double* U) {
   amr2_fill_fine(A, U);
 }
 
-ll amr2_step(const Amr2& A, double* U, double dt) {
+/* One SSP-RK step on the two-level grid, all-levels non-telescoping: every
+ * stage prepares its input (restriction, coarse fill, fine fill), updates the
+ * leaf blocks and corrects the coarse side with weight b_s. */
+ll amr2_step(const Amr2& A, double* U, double dt, int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
   const Geo gc(A.C);
   const ll total = (A.n0 + A.n1) * 5 * gc.cells;
-  std::vector<double> U1(U, U + total), U2(total);
+  std::vector<double> X(U, U + total), Y(total);
   FluxReg R;
   ll hits = 0;
   amr2_prepare(A, U);
-  hits += amr2_stage(A, U, nullptr, U1.data(), dt, 0.0, 1.0, R);
-  amr2_reflux(A, U1.data(), dt, 1.0, R);
-  amr2_prepare(A, U1.data());
-  std::memcpy(U2.data(), U1.data(), total * sizeof(double));
-  hits += amr2_stage(A, U1.data(), U, U2.data(), dt, 0.5, 0.5, R);
-  amr2_reflux(A, U2.data(), dt, 0.5, R);
+  hits += amr2_stage(A, U, nullptr, X.data(), dt, r.a[0], r.b[0], R);
+  amr2_reflux(A, X.data(), dt, r.b[0], R);
+  for (int st = 1; st < r.S; ++st) {
+    amr2_prepare(A, X.data());
+    std::memcpy(Y.data(), X.data(), total * sizeof(double));
+    hits += amr2_stage(A, X.data(), U, Y.data(), dt, r.a[st], r.b[st], R);
+    amr2_reflux(A, Y.data(), dt, r.b[st], R);
+    std::swap(X, Y);
+  }
   for (ll b = 0; b < A.n0 + A.n1; ++b) {
     if (b < A.n0 && covered(A, gc, b)) continue;
     for (int v = 0; v < 5; ++v)
@@ -750,34 +785,35 @@ ll amr2_step(const Amr2& A, double* U, double dt) {
         for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
           for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
             const ll o = gc.at(b, v, k, j, i);
-            U[o] = U2[o];
+            U[o] = X[o];
           }
   }
   amr2_restrict(A, U);
   return hits;
 }
 
-/* One SSP-RK2 step on the two-level grid in the level-by-level, telescoping
+/* One SSP-RK step on the two-level grid in the level-by-level, telescoping
  * variant (Sec. 4.2 and Fig. "Level-by-levels, Telescoping"): one guard fill
  * for both levels (restriction, coarse fill, fine fill with prolongation of
  * all guard layers), then the levels from the finest down, each block through
- * both stages on its own guard data; the coarse side of the fine region is
+ * every stage on its own guard data; the coarse side of the fine region is
  * then corrected with the fine fluxes, stage by stage, each with the weight
- * its L term has in U^{n+1} (1/2 and 1/2); the step ends with the
- * restriction.  One dt for both levels.  Needs 4 guard cells. */
-ll amr2_step_telescoping(const Amr2& A, double* U, double dt) {
+ * its L term has in U^{n+1} (rk_weight); the step ends with the restriction.
+ * One dt for both levels.  Needs 2 S guard cells. */
+ll amr2_step_telescoping(const Amr2& A, double* U, double dt, int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
   const Geo gc(A.C);
   const ll nblk = A.n0 + A.n1;
   const ll total = nblk * 5 * gc.cells;
-  FluxReg R[2];
-  R[0].face.assign(nblk * 6, std::vector<double>());
-  R[1].face.assign(nblk * 6, std::vector<double>());
+  FluxReg R[3];
+  for (int st = 0; st < r.S; ++st) R[st].face.assign(nblk * 6, std::vector<double>());
   ll hits = 0;
   amr2_prepare(A, U);
-  std::vector<double> U1(U, U + total), U2(U, U + total);
-  for (int lev = 1; lev >= 0; --lev) hits += amr2_level_telescoping(A, lev, U, U1.data(), U2.data(), dt, R);
-  amr2_reflux(A, U2.data(), dt, 0.5, R[0]);
-  amr2_reflux(A, U2.data(), dt, 0.5, R[1]);
+  std::vector<double> X[4];
+  for (int st = 0; st <= r.S; ++st) X[st].assign(U, U + total);
+  for (int lev = 1; lev >= 0; --lev) hits += amr2_level_telescoping(A, r, lev, X, dt, R);
+  double* out = X[r.S].data();
+  for (int st = 0; st < r.S; ++st) amr2_reflux(A, out, dt, rk_weight(r, st), R[st]);
   for (ll b = 0; b < nblk; ++b) {
     if (b < A.n0 && covered(A, gc, b)) continue;
     for (int v = 0; v < 5; ++v)
@@ -785,7 +821,7 @@ ll amr2_step_telescoping(const Amr2& A, double* U, double dt) {
         for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
           for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
             const ll o = gc.at(b, v, k, j, i);
-            U[o] = U2[o];
+            U[o] = out[o];
           }
   }
   amr2_restrict(A, U);
@@ -1024,15 +1060,22 @@ long long orc_step_telescoping(const OrcGrid* G, double* U, double dt) {
   return step_telescoping(*G, U, dt);
 }
 
-/* nsteps SSP-RK2 steps, each with dt = compute_dt(U^n); dt_hist[s] receives
- * dt.  telescoping != 0 selects the telescoping mode (needs 4 guard cells). */
-long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist, int telescoping) {
-  if (telescoping && G->ng < 4) return -1;
+/* One step with nstages (2 or 3) stages, telescoping or not; -1 if nstages
+ * is invalid or the telescoping mode lacks its 2 nstages guard cells. */
+long long orc_step_rk(const OrcGrid* G, double* U, double dt, int nstages, int telescoping) {
+  if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
+  return telescoping ? step_telescoping(*G, U, dt, nstages) : step(*G, U, dt, nstages);
+}
+
+/* nsteps steps, each with dt = compute_dt(U^n); dt_hist[s] receives dt.
+ * telescoping != 0 selects the telescoping mode; nstages 2 or 3. */
+long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist, int telescoping, int nstages) {
+  if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
   long long hits = 0;
   for (int s = 0; s < nsteps; ++s) {
     const double dt = compute_dt(*G, U);
     if (dt_hist) dt_hist[s] = dt;
-    hits += telescoping ? step_telescoping(*G, U, dt) : step(*G, U, dt);
+    hits += telescoping ? step_telescoping(*G, U, dt, nstages) : step(*G, U, dt, nstages);
   }
   return hits;
 }
@@ -1069,17 +1112,26 @@ long long orc2_step_telescoping(const OrcGrid* G, const OrcAmr2* R, double* U, d
   return amr2_step_telescoping(make_amr2(*G, R->lo, R->hi), U, dt);
 }
 
+/* One step with nstages stages: all-levels non-telescoping, or (telescoping
+ * != 0) level-by-level telescoping; -1 if invalid. */
+long long orc2_step_rk(const OrcGrid* G, const OrcAmr2* R, double* U, double dt, int nstages, int telescoping) {
+  if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
+  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  return telescoping ? amr2_step_telescoping(A, U, dt, nstages) : amr2_step(A, U, dt, nstages);
+}
+
 /* nsteps steps with the CFL dt of the leaf cells; telescoping != 0 selects
  * the level-by-level telescoping variant, else all-levels non-telescoping. */
-long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist, int telescoping) {
-  if (telescoping && G->ng < 4) return -1;
+long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist, int telescoping,
+                   int nstages) {
+  if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
   const Amr2 A = make_amr2(*G, R->lo, R->hi);
   long long hits = 0;
   amr2_restrict(A, U);
   for (int s = 0; s < nsteps; ++s) {
     const double dt = amr2_compute_dt(A, U);
     if (dt_hist) dt_hist[s] = dt;
-    hits += telescoping ? amr2_step_telescoping(A, U, dt) : amr2_step(A, U, dt);
+    hits += telescoping ? amr2_step_telescoping(A, U, dt, nstages) : amr2_step(A, U, dt, nstages);
   }
   return hits;
 }

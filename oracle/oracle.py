@@ -68,7 +68,9 @@ def lib():
             L.orc_step.restype = C.c_longlong
             L.orc_step_telescoping.argtypes = [gp, dp, C.c_double]
             L.orc_step_telescoping.restype = C.c_longlong
-            L.orc_run.argtypes = [gp, dp, C.c_int, dp, C.c_int]
+            L.orc_step_rk.argtypes = [gp, dp, C.c_double, C.c_int, C.c_int]
+            L.orc_step_rk.restype = C.c_longlong
+            L.orc_run.argtypes = [gp, dp, C.c_int, dp, C.c_int, C.c_int]
             L.orc_run.restype = C.c_longlong
             L.orc_stage_vjp.argtypes = [gp, dp, dp, C.c_double, dp]
             L.orc_stage_vjp.restype = None
@@ -87,7 +89,9 @@ def lib():
             L.orc2_stage.restype = C.c_longlong
             L.orc2_step_telescoping.argtypes = [gp, ap, dp, C.c_double]
             L.orc2_step_telescoping.restype = C.c_longlong
-            L.orc2_run.argtypes = [gp, ap, dp, C.c_int, dp, C.c_int]
+            L.orc2_step_rk.argtypes = [gp, ap, dp, C.c_double, C.c_int, C.c_int]
+            L.orc2_step_rk.restype = C.c_longlong
+            L.orc2_run.argtypes = [gp, ap, dp, C.c_int, dp, C.c_int, C.c_int]
             L.orc2_run.restype = C.c_longlong
             _lib = L
     return _lib
@@ -162,16 +166,17 @@ class Oracle:
             self._keep = arr
         return int(self.L.orc_stage(C.byref(self.g), _dp(Uin), _dp(Un), _dp(Uout), dt, a, b, lst, nl))
 
-    def step(self, U, dt, telescoping=False):
-        """One SSP-RK2 step in place; telescoping=True: one guard fill per step
-        and a first stage that also updates a 2-cell ring (needs ng >= 4)."""
+    def step(self, U, dt, telescoping=False, stages=2):
+        """One SSP-RK step in place (stages 2 or 3); telescoping=True: one guard
+        fill per step and earlier stages that also update a ring of guard cells
+        (needs ng >= 2 * stages)."""
         _check(U, self.lat)
-        if telescoping:
-            hits = int(self.L.orc_step_telescoping(C.byref(self.g), _dp(U), float(dt)))
-            if hits < 0:
-                raise ValueError("the telescoping mode needs 4 guard cells")
-            return hits
-        return int(self.L.orc_step(C.byref(self.g), _dp(U), float(dt)))
+        if stages == 2 and not telescoping:
+            return int(self.L.orc_step(C.byref(self.g), _dp(U), float(dt)))
+        hits = int(self.L.orc_step_rk(C.byref(self.g), _dp(U), float(dt), int(stages), int(bool(telescoping))))
+        if hits < 0:
+            raise ValueError("stages must be 2 or 3; the telescoping mode needs 2 * stages guard cells")
+        return hits
 
     def stage_vjp(self, U, M, scale):
         """J_L(U)^T (scale M) on interior cells (dt held fixed, branches frozen)."""
@@ -189,13 +194,14 @@ class Oracle:
         self.L.orc_step_adjoint(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out))
         return out
 
-    def run(self, U, nsteps, telescoping=False):
+    def run(self, U, nsteps, telescoping=False, stages=2):
         """Advance U in place by nsteps; returns (dt history, floor hits)."""
         _check(U, self.lat)
         hist = np.zeros(max(nsteps, 1))
-        hits = int(self.L.orc_run(C.byref(self.g), _dp(U), int(nsteps), _dp(hist), int(bool(telescoping))))
+        hits = int(self.L.orc_run(C.byref(self.g), _dp(U), int(nsteps), _dp(hist), int(bool(telescoping)),
+                                  int(stages)))
         if hits < 0:
-            raise ValueError("the telescoping mode needs 4 guard cells")
+            raise ValueError("stages must be 2 or 3; the telescoping mode needs 2 * stages guard cells")
         return hist[:nsteps], hits
 
 
@@ -236,24 +242,25 @@ class Oracle2:
         return int(self.L.orc2_stage(C.byref(self.g), C.byref(self.r), _dp(Uin), _dp(Un), _dp(Uout),
                                      dt, a, b, 1 if reflux else 0))
 
-    def step(self, U, dt, telescoping=False):
+    def step(self, U, dt, telescoping=False, stages=2):
         """One step: all-levels non-telescoping (default), or level-by-level
         telescoping (one fill, every stage per block, correction at the end)."""
         self._chk(U)
-        if telescoping:
-            hits = int(self.L.orc2_step_telescoping(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
-            if hits < 0:
-                raise ValueError("the telescoping mode needs 4 guard cells")
-            return hits
-        return int(self.L.orc2_step(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
+        if stages == 2 and not telescoping:
+            return int(self.L.orc2_step(C.byref(self.g), C.byref(self.r), _dp(U), float(dt)))
+        hits = int(self.L.orc2_step_rk(C.byref(self.g), C.byref(self.r), _dp(U), float(dt), int(stages),
+                                       int(bool(telescoping))))
+        if hits < 0:
+            raise ValueError("stages must be 2 or 3; the telescoping mode needs 2 * stages guard cells")
+        return hits
 
-    def run(self, U, nsteps, telescoping=False):
+    def run(self, U, nsteps, telescoping=False, stages=2):
         self._chk(U)
         hist = np.zeros(max(nsteps, 1))
         hits = int(self.L.orc2_run(C.byref(self.g), C.byref(self.r), _dp(U), int(nsteps), _dp(hist),
-                                   int(bool(telescoping))))
+                                   int(bool(telescoping)), int(stages)))
         if hits < 0:
-            raise ValueError("the telescoping mode needs 4 guard cells")
+            raise ValueError("stages must be 2 or 3; the telescoping mode needs 2 * stages guard cells")
         return hist[:nsteps], hits
 
 

@@ -162,6 +162,19 @@ int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
  * graph. */
 int gbh_set_telescoping(gbh_ctx *ctx, int enable);
 
+/* Number of SSP-RK stages (Sec. 4.2 names SSP-RK, multistage, without an
+ * order): 2 (the default; Shu-Osher SSP-RK2) or 3 (Shu-Osher SSP-RK3:
+ * U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U^{n+1} = 1/3 U +
+ * 2/3 (U2 + dt L(U2))).  Applies to every step path of the context:
+ * non-telescoping (a halo gather per stage), telescoping (ring widths 4, 2, 0;
+ * needs nguard >= 6), two-level all-levels (correction every stage with its
+ * b) and level-by-level telescoping (correction weights 1/6, 1/6, 2/3).
+ * Allocates a second scratch state (and flux registers) on first use.
+ * Errors: GBH_ERR_INVAL for other values or too few guard cells for the
+ * telescoping mode; GBH_ERR_NOMEM.  The adjoint is of the two-stage step
+ * (GBH_ERR_UNSUPPORTED otherwise).  Drops a captured graph. */
+int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
+
 /* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
  * private stream; re-captured when U, dt_dev or nsteps change, or the
  * decomposition changes) and launched on `stream` as one graph.  Kernel

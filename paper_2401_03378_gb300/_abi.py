@@ -57,6 +57,7 @@ SIGNATURES = {
     "gbh_autotune": (C.c_int, [_vp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int), _vp]),
     "gbh_set_decomposition": (C.c_int, [_vp, C.c_int, C.c_int]),
     "gbh_set_telescoping": (C.c_int, [_vp, C.c_int]),
+    "gbh_set_rk_stages": (C.c_int, [_vp, C.c_int]),
     "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "hydro_stage_vjp": (C.c_int, [_vp, _dp, _dp, C.c_double, _dp, C.c_double, _dp, C.c_double, _dp, _vp]),
     "hydro_step_adjoint": (C.c_int, [_vp, _dp, C.c_double, _dp, _dp, _vp]),

@@ -30,7 +30,9 @@ struct gbh_ctx {
   int* d_nbr = nullptr;            // [nblocks][3^ndim]
   int* d_face = nullptr;           // [nblocks][6]
   double* d_inv_dx = nullptr;      // [nblocks][3]
-  double* d_scratch = nullptr;     // U1 of SSP-RK2, one state
+  double* d_scratch = nullptr;     // U(1), one state
+  double* d_scratch2 = nullptr;    // U(2) of three-stage SSP-RK (allocated by gbh_set_rk_stages)
+  int nstages = 2;                 // SSP-RK stages (2 or 3)
   unsigned long long* d_words = nullptr;  // [0] smax accumulator, [1] floor count, [2] check count
   // host-buffer path (allocated on first use)
   double* d_host_state = nullptr;
@@ -47,7 +49,8 @@ struct gbh_ctx {
   int* d_fine = nullptr;
   int* d_flux_slot = nullptr;       // [nblocks][6]
   double* d_flux_reg = nullptr;
-  double* d_flux_reg2 = nullptr;    // second stage's registers (telescoping; allocated on first use)
+  double* d_flux_reg2 = nullptr;    // registers of stages 2 and 3 (telescoping; allocated on first use)
+  double* d_flux_reg3 = nullptr;
   size_t flux_reg_doubles = 0;
   gbh::RefluxEntry* d_reflux = nullptr;
   int2* d_cf_faces = nullptr;
@@ -131,8 +134,10 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
   return cuda_err(c, cudaEventRecord(a, s), "cudaEventRecord");
 }
 
+// One stage launch.  ring > 0: the telescoping form that also updates that
+// many guard cells around the interior, from Uin's own guard cells.
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
-                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, bool ring = false,
+                 double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, int ring = 0,
                  double* flux_reg = nullptr) {
   gbh::StageArgs A{};
   A.Uin = Uin;
@@ -150,9 +155,9 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   A.smax_acc = dt_epilogue ? c->d_smax : nullptr;
   A.floor_count = c->d_words + 1;
   A.problem = c->d_problem;
-  if (ring && c->lay.ndim == 3) {
-    // the first telescoping stage spans nz + 2*ring planes
-    const int span = c->lay.nz + 2 * gbh::TELESCOPE_RING;
+  if (ring > 0 && c->lay.ndim == 3) {
+    // a ring-updating stage spans nz + 2*ring planes
+    const int span = c->lay.nz + 2 * ring;
     A.kchunk = c->kchunk > 0 ? c->kchunk : span;
     A.nchunks = (span + A.kchunk - 1) / A.kchunk;
   } else if (c->lay.ndim == 3 && c->kchunk > 0) {
@@ -169,7 +174,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
   if (rc) return rc;
-  rc = cuda_err(c, ring ? gbh::launch_stage_ring(A, s) : gbh::launch_stage(A, s), "stage kernel launch");
+  rc = cuda_err(c, ring > 0 ? gbh::launch_stage_ring(A, ring, s) : gbh::launch_stage(A, s), "stage kernel launch");
   if (rc) return rc;
   if (stop) rc = cuda_err(c, cudaEventRecord(stop, s), "cudaEventRecord");
   return rc;
@@ -191,51 +196,102 @@ int refined_stage(gbh_ctx* c, double* Uin, const double* Un, double* Uout, const
   return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, s), "reflux launch");
 }
 
-// One SSP-RK2 step on a two-level grid; ends with the restriction of the new
-// state so that covered coarse cells hold the mean of their children.
+// Shu-Osher coefficients of the SSP-RK stages: U(s) = a_s U^n + b_s (U(s-1) +
+// dt L(U(s-1))); two stages (0, 1), (1/2, 1/2); three stages (0, 1),
+// (3/4, 1/4), (1/3, 2/3).
+struct RkCoef {
+  int S;
+  double a[3], b[3];
+};
+
+RkCoef rk_coef(int nstages) {
+  if (nstages == 3) return RkCoef{3, {0.0, 0.75, 1.0 / 3.0}, {1.0, 0.25, 2.0 / 3.0}};
+  return RkCoef{2, {0.0, 0.5, 0.0}, {1.0, 0.5, 0.0}};
+}
+
+// weight of stage s's dt L term in U^{n+1}: b_s times the b of every later stage
+double rk_weight(const RkCoef& r, int s) {
+  double w = r.b[s];
+  for (int t = s + 1; t < r.S; ++t) w = w * r.b[t];
+  return w;
+}
+
+// output buffer of stage s: the scratch states, the last stage writes U
+double* stage_out(gbh_ctx* c, int s, double* U) {
+  if (s == c->nstages - 1) return U;
+  return s == 0 ? c->d_scratch : c->d_scratch2;
+}
+
+double* flux_regs(gbh_ctx* c, int s) { return s == 0 ? c->d_flux_reg : s == 1 ? c->d_flux_reg2 : c->d_flux_reg3; }
+
+// One SSP-RK step on a two-level grid, all-levels non-telescoping; ends with
+// the restriction of the new state so that covered coarse cells hold the
+// mean of their children.
 int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
-  int rc = refined_stage(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, s);
-  if (rc) return rc;
-  rc = refined_stage(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, s);
-  if (rc) return rc;
+  const RkCoef r = rk_coef(c->nstages);
+  double* in = U;
+  for (int st = 0; st < r.S; ++st) {
+    double* out = stage_out(c, st, U);
+    int rc = refined_stage(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], s);
+    if (rc) return rc;
+    in = out;
+  }
   return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
 }
 
-// One SSP-RK2 step in the telescoping mode (Sec. 4.2): one guard fill of U
-// (4 cells deep), the first stage on the interior widened by 2 cells into
-// the scratch state, the second stage from the scratch state's own guard
-// cells; no exchange between the stages.
-int telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
-  gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
-  int rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch");
-  if (rc) return rc;
-  rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, false, false, s, true);
-  if (rc) return rc;
-  return stage_launch(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, false, dt_epilogue, s);
+// One SSP-RK step on a uniform (or batched) grid.  Non-telescoping: every
+// stage gathers its halo from the neighbours.  Telescoping (Sec. 4.2): one
+// guard fill of U (all layers), then stage s of S updates the interior
+// widened by 2 (S - s) cells from its input's own guard cells; no exchange
+// between the stages.  The last stage may carry the dt epilogue.
+int uniform_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
+  const RkCoef r = rk_coef(c->nstages);
+  int rc = GBH_OK;
+  if (c->telescoping) {
+    gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
+    if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
+  }
+  const double* in = U;
+  for (int st = 0; st < r.S; ++st) {
+    double* out = stage_out(c, st, U);
+    const bool last = st == r.S - 1;
+    const int ring = c->telescoping ? 2 * (r.S - 1 - st) : 0;
+    rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], !c->telescoping,
+                      last && dt_epilogue, s, ring);
+    if (rc) return rc;
+    in = out;
+  }
+  return GBH_OK;
 }
 
-// One SSP-RK2 step on a two-level grid in the level-by-level telescoping
+// One SSP-RK step on a two-level grid in the level-by-level telescoping
 // variant (Sec. 4.2, Fig. "Level-by-levels, Telescoping"): one guard fill for
 // both levels (restriction, same-level copies, prolongation of all guard
-// layers), both stages of every leaf block from its own guard data with the
+// layers), every stage of every leaf block from its own guard data with the
 // coarse-fine face fluxes of stage s in register set s, the coarse-side
-// correction with weight 1/2 per stage, restriction.  The two levels need no
-// data from each other inside the step, so both go through the same
-// launches; the paper's finest-first level loop orders nothing here.
+// correction with each stage's weight in U^{n+1}, restriction.  The two
+// levels need no data from each other inside the step, so both go through
+// the same launches; the paper's finest-first level loop orders nothing here.
 int refined_telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
+  const RkCoef r = rk_coef(c->nstages);
   int rc = cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
   if (rc) return rc;
   gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
   if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
   if ((rc = cuda_err(c, gbh::launch_prolong(U, c->amr, c->lay.g, false, s), "prolong launch"))) return rc;
-  rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, dt, 0.0, 1.0, false, false, s, true, c->d_flux_reg);
-  if (rc) return rc;
-  rc = stage_launch(c, c->d_scratch, U, U, dt_dev, dt, 0.5, 0.5, false, false, s, false, c->d_flux_reg2);
-  if (rc) return rc;
-  if ((rc = cuda_err(c, gbh::launch_reflux(U, c->amr, dt_dev, dt, 0.5, s), "reflux launch"))) return rc;
-  gbh::AmrArgs A2 = c->amr;
-  A2.flux_reg = c->d_flux_reg2;
-  if ((rc = cuda_err(c, gbh::launch_reflux(U, A2, dt_dev, dt, 0.5, s), "reflux launch"))) return rc;
+  const double* in = U;
+  for (int st = 0; st < r.S; ++st) {
+    double* out = stage_out(c, st, U);
+    rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], false, false, s,
+                      2 * (r.S - 1 - st), flux_regs(c, st));
+    if (rc) return rc;
+    in = out;
+  }
+  for (int st = 0; st < r.S; ++st) {
+    gbh::AmrArgs A = c->amr;
+    A.flux_reg = flux_regs(c, st);
+    if ((rc = cuda_err(c, gbh::launch_reflux(U, A, dt_dev, dt, rk_weight(r, st), s), "reflux launch"))) return rc;
+  }
   return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
 }
 
@@ -279,7 +335,8 @@ gbh::StageArgs vjp_args(gbh_ctx* c, const double* U) {
 
 int adjoint_supported(gbh_ctx* c) {
   if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is not implemented on two-level contexts");
-  if (c->telescoping) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping step");
+  if (c->telescoping || c->nstages != 2)
+    return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping two-stage step");
   if (c->nproblems > 1) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint takes one dt: not on batched contexts");
   return GBH_OK;
 }
@@ -392,13 +449,7 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
     if (rc) return rc;
     return reduce_dt(c, U, dt_dev, nullptr, s);
   }
-  int rc;
-  if (c->telescoping) {
-    rc = telescoping_step(c, U, dt_dev, 0.0, true, s);
-  } else {
-    rc = stage_launch(c, U, nullptr, c->d_scratch, dt_dev, 0.0, 0.0, 1.0, true, false, s);
-    if (!rc) rc = stage_launch(c, c->d_scratch, U, U, dt_dev, 0.0, 0.5, 0.5, true, true, s);
-  }
+  int rc = uniform_step(c, U, dt_dev, 0.0, true, s);
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
                   "dt finalize launch");
@@ -681,20 +732,43 @@ int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, v
   return GBH_OK;
 }
 
+// Buffers a (telescoping, nstages) combination needs: a second scratch state
+// for three stages, one flux-register set per stage on two-level contexts
+// in the telescoping mode.
+static int ensure_step_buffers(gbh_ctx* c, bool telescoping, int nstages) {
+  cudaError_t e = cudaSuccess;
+  if (nstages == 3 && !c->d_scratch2) e = cudaMalloc(&c->d_scratch2, sizeof(double) * state_elems(c->lay));
+  if (e == cudaSuccess && c->refined && telescoping) {
+    if (!c->d_flux_reg2) e = cudaMalloc(&c->d_flux_reg2, sizeof(double) * c->flux_reg_doubles);
+    if (e == cudaSuccess && nstages == 3 && !c->d_flux_reg3)
+      e = cudaMalloc(&c->d_flux_reg3, sizeof(double) * c->flux_reg_doubles);
+  }
+  if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "step buffers: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
 int gbh_set_telescoping(gbh_ctx* c, int enable) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if (enable && c->lay.g < 4)
-    return set_err(c, GBH_ERR_INVAL, "the telescoping mode needs nguard >= 4 (got %d)", c->lay.g);
-  if (enable && c->refined && !c->d_flux_reg2) {
-    cudaError_t e = cudaMalloc(&c->d_flux_reg2, sizeof(double) * c->flux_reg_doubles);
-    if (e != cudaSuccess) {
-      c->d_flux_reg2 = nullptr;
-      return set_err(c, GBH_ERR_NOMEM, "flux registers: %s", cudaGetErrorString(e));
-    }
-  }
+  if (enable && c->lay.g < 2 * c->nstages)
+    return set_err(c, GBH_ERR_INVAL, "the telescoping mode with %d stages needs nguard >= %d (got %d)", c->nstages,
+                   2 * c->nstages, c->lay.g);
+  if ((rc = ensure_step_buffers(c, enable != 0, c->nstages))) return rc;
   drop_graph(c);
   c->telescoping = enable != 0;
+  return GBH_OK;
+}
+
+int gbh_set_rk_stages(gbh_ctx* c, int nstages) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (nstages != 2 && nstages != 3) return set_err(c, GBH_ERR_INVAL, "nstages must be 2 or 3 (got %d)", nstages);
+  if (c->telescoping && c->lay.g < 2 * nstages)
+    return set_err(c, GBH_ERR_INVAL, "the telescoping mode with %d stages needs nguard >= %d (got %d)", nstages,
+                   2 * nstages, c->lay.g);
+  if ((rc = ensure_step_buffers(c, c->telescoping, nstages))) return rc;
+  drop_graph(c);
+  c->nstages = nstages;
   return GBH_OK;
 }
 
@@ -817,6 +891,8 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_flux_slot);
   cudaFree(c->d_flux_reg);
   cudaFree(c->d_flux_reg2);
+  cudaFree(c->d_flux_reg3);
+  cudaFree(c->d_scratch2);
   cudaFree(c->d_reflux);
   cudaFree(c->d_cf_faces);
   cudaFree(c->d_problem);
@@ -887,10 +963,7 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->refined) return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, s) : refined_step(c, U, nullptr, dt, s);
-  if (c->telescoping) return telescoping_step(c, U, nullptr, dt, false, s);
-  rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
-  if (rc) return rc;
-  return stage_launch(c, c->d_scratch, U, U, nullptr, dt, 0.5, 0.5, true, false, s);
+  return uniform_step(c, U, nullptr, dt, false, s);
 }
 
 int hydro_step_cfl(gbh_ctx* c, double* U, double* dt_dev, void* stream) {

@@ -85,13 +85,11 @@ cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, dou
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 
-// Telescoping mode (Sec. 4.2): the first stage updates the interior widened by
-// TELESCOPE_RING cells from the block's own guard cells (gather = 0), which
-// must hold 2 more cells (nguard >= 4).  No combine, no dt epilogue; flux
-// registers as in launch_stage.  kchunk/nchunks split the nz + 2*TELESCOPE_RING
-// planes.
-constexpr int TELESCOPE_RING = 2;
-cudaError_t launch_stage_ring(const StageArgs& a, cudaStream_t s);
+// Telescoping mode (Sec. 4.2): a stage that updates the interior widened by
+// `ring` cells (0, 2 or 4) from the block's own guard cells (gather = 0),
+// which must hold ring + 2 cells.  No dt epilogue; combine and flux registers
+// as in launch_stage.  kchunk/nchunks split the nz + 2*ring planes.
+cudaError_t launch_stage_ring(const StageArgs& a, int ring, cudaStream_t s);
 
 // Host helpers shared by the entry points (gbh_abi.cu).
 int validate_params(const gbh_params* p, bool allow_coarser);  // GBH_OK or an error code; message in gbh_last_error(NULL)

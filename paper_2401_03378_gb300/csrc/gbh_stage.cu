@@ -25,10 +25,11 @@
 // speed of Uout, one 64-bit atomicMax per CTA on the bit pattern of the
 // non-negative double.
 //
-// Telescoping mode (Sec. 4.2): the first stage also updates a ring of E = 2
-// guard cells around the interior, from the block's own (filled, 4-deep)
-// guard cells.  The same kernel does it with an (N+2E)^2 plane tile shifted
-// by -E and z planes -E .. nz+E-1; tile position (u, v) is cell (u-E, v-E).
+// Telescoping mode (Sec. 4.2): the earlier stages also update a ring of E
+// guard cells around the interior (E = 2 (S - s) for stage s of S), from the
+// block's own guard cells.  The same kernel does it with an (N+2E)^2 plane
+// tile shifted by -E and z planes -E .. nz+E-1; tile position (u, v) is cell
+// (u-E, v-E).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -310,9 +311,13 @@ template <int N, bool D3>
 cudaError_t prepare_t() {
   cudaError_t e = cudaFuncSetAttribute(stage_kernel<N, D3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_for<N, 0>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel<N, D3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_for<N, 2>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel<N, D3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_for<N, 2>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage_kernel<N, D3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_for<N, 4>());
+  return e;
 }
 
 template <int E>
@@ -349,9 +354,14 @@ cudaError_t stage_prepare(int nx, int ndim) {
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0>(a, s); }
 
-cudaError_t launch_stage_ring(const StageArgs& a, cudaStream_t s) {
-  if (a.gather || a.combine || a.smax_acc || a.lay.g < 4) return cudaErrorInvalidValue;
-  return launch_e<TELESCOPE_RING>(a, s);
+cudaError_t launch_stage_ring(const StageArgs& a, int ring, cudaStream_t s) {
+  if (a.gather || a.smax_acc || a.lay.g < ring + 2) return cudaErrorInvalidValue;
+  switch (ring) {
+    case 0: return launch_e<0>(a, s);
+    case 2: return launch_e<2>(a, s);
+    case 4: return launch_e<4>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace gbh

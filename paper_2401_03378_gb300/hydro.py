@@ -190,8 +190,12 @@ class Hydro:
         self._check(self.lib.gbh_set_decomposition(self.ctx, int(kchunk), int(items_per_cta)))
 
     def set_telescoping(self, enable: bool = True):
-        """Telescoping SSP-RK2 (one guard fill per step; needs nguard >= 4)."""
+        """Telescoping SSP-RK (one guard fill per step; needs nguard >= 2 * stages)."""
         self._check(self.lib.gbh_set_telescoping(self.ctx, int(bool(enable))))
+
+    def set_rk_stages(self, nstages: int):
+        """2 (SSP-RK2, the default) or 3 (SSP-RK3) Shu-Osher stages per step."""
+        self._check(self.lib.gbh_set_rk_stages(self.ctx, int(nstages)))
 
     # -- adjoint ------------------------------------------------------------
     def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None):

@@ -255,9 +255,9 @@ def run_gpu(args):
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = run_adjoint(args, gb, torch, barrier)
-    telescoping = None
-    if args.telescoping_steps > 0:
-        telescoping = run_telescoping(args, gb, torch, barrier, lat, U0, 1e3 * tmax / args.steps)
+    variants = None
+    if args.variant_steps > 0:
+        variants = run_variants(args, gb, torch, barrier, 1e3 * tmax / args.steps)
 
     # roofline of the dominant kernel (the fused stage kernel, both stages)
     flops_per_launch = 0.5 * (FLOPS_STAGE1 + FLOPS_STAGE2) * zones
@@ -307,7 +307,7 @@ def run_gpu(args):
         "two_level": two_level,
         "ensemble": ensemble,
         "adjoint": adjoint,
-        "telescoping": telescoping,
+        "variants": variants,
         "unphysical_cells": nbad,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,40 +319,51 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_telescoping(args, gb, torch, barrier, lat, U0, ms_non_telescoping):
-    """The headline workload in the telescoping mode (one guard fill per step;
-    the first stage also updates a 2-cell ring): step time against the
-    non-telescoping step measured above."""
-    h = gb.Hydro.from_lattice(lat)
-    h.set_telescoping(True)
-    U = torch.from_numpy(U0).cuda()
-    dt = h.compute_dt(U)
-    for _ in range(args.warmup):
-        h.step_cfl(U, dt)
-    h.set_kernel_timing(True)
-    h.stage_kernel_time()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.telescoping_steps):
-        h.step_cfl(U, dt)
-    e1.record(stream)
-    barrier()
-    secs = e0.elapsed_time(e1) / 1e3
-    stage_ms, launches = h.stage_kernel_time()
-    h.set_kernel_timing(False)
-    nbad = h.check_state(U)
-    h.close()
-    del U
-    torch.cuda.empty_cache()
-    ms = 1e3 * secs / args.telescoping_steps
-    return {"workload": f"{WORKLOAD} -- telescoping mode (fill once per step, ring of 2 in stage 1)",
-            "value": lat.interior_cells * args.telescoping_steps / secs, "unit": UNIT,
-            "steps": args.telescoping_steps, "ms_per_step": ms,
-            "stage_kernels_ms_per_step": stage_ms / args.telescoping_steps,
-            "over_non_telescoping": ms / ms_non_telescoping,
-            "launches_per_step": 4, "unphysical_cells": nbad}
+def run_variants(args, gb, torch, barrier, ms_headline):
+    """The headline workload in the paper's other stepper variants: the
+    telescoping mode (one guard fill per step, earlier stages also update a
+    ring of guard cells) with two stages, and the three-stage SSP-RK without
+    and with telescoping (the latter on 6 guard cells).  Step time against
+    the headline (non-telescoping, two-stage) step measured above."""
+    import workloads as wl
+    nb = args.nb
+    out = {}
+    for name, ng, stages, tele in (("telescoping_rk2", 4, 2, True), ("ssp_rk3", 4, 3, False),
+                                   ("telescoping_rk3", 6, 3, True)):
+        lat = wl.lattice_3d(nb, nb, nb, 16, 16, 16, ng)
+        h = gb.Hydro.from_lattice(lat)
+        h.set_rk_stages(stages)
+        h.set_telescoping(tele)
+        U = torch.from_numpy(wl.sedov(lat)).cuda()
+        dt = h.compute_dt(U)
+        for _ in range(args.warmup):
+            h.step_cfl(U, dt)
+        h.set_kernel_timing(True)
+        h.stage_kernel_time()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.variant_steps):
+            h.step_cfl(U, dt)
+        e1.record(stream)
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        stage_ms, _ = h.stage_kernel_time()
+        h.set_kernel_timing(False)
+        nbad = h.check_state(U)
+        h.close()
+        del U
+        torch.cuda.empty_cache()
+        ms = 1e3 * secs / args.variant_steps
+        out[name] = {"nguard": ng, "stages": stages, "telescoping": tele,
+                     "value": lat.interior_cells * args.variant_steps / secs, "unit": UNIT,
+                     "steps": args.variant_steps, "ms_per_step": ms,
+                     "stage_kernels_ms_per_step": stage_ms / args.variant_steps,
+                     "over_headline_step": ms / ms_headline,
+                     "launches_per_step": stages + 1 + (1 if tele else 0), "unphysical_cells": nbad}
+    out["workload"] = f"{WORKLOAD} -- stepper variants (nguard as listed)"
+    return out
 
 
 def run_two_level(args, gb, torch, barrier):
@@ -560,8 +571,8 @@ def main(argv=None):
     ap.add_argument("--two-level-steps", type=int, default=20)
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--adjoint-steps", type=int, default=50)
-    ap.add_argument("--telescoping-steps", type=int, default=20)
-    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--variant-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

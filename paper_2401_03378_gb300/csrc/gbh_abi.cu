@@ -149,7 +149,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   A.dt = dt;
   A.a = a;
   A.b = b;
-  A.combine = (a == 0.0 && b == 1.0) ? 0 : 1;
+  A.combine = (a == 0.0 && b == 1.0) ? 0 : (a == 0.5 && b == 0.5) ? 2 : 1;
   A.gather = gather ? 1 : 0;
   gbh::stage_args_common(&A, c->lay, c->eos);
   A.smax_acc = dt_epilogue ? c->d_smax : nullptr;
@@ -367,6 +367,8 @@ int validate_params(const gbh_params* p, bool allow_coarser) {
   if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return set_err(nullptr, GBH_ERR_INVAL, "gamma must be > 1");
   if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return set_err(nullptr, GBH_ERR_INVAL, "cfl must be in (0, 1]");
   if (!(p->small_rho > 0.0) || !(p->small_p > 0.0)) return set_err(nullptr, GBH_ERR_INVAL, "floors must be > 0");
+  if (!(p->small_rho >= 1e-300))
+    return set_err(nullptr, GBH_ERR_INVAL, "small_rho must be >= 1e-300 (densities are kept normal numbers)");
   if (!p->nbr || !p->dx) return set_err(nullptr, GBH_ERR_INVAL, "nbr and dx tables are required");
   const int nn = p->ndim == 3 ? 27 : 9;
   const int centre = p->ndim == 3 ? 13 : 4;

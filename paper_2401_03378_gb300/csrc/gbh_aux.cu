@@ -87,8 +87,9 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
     double U[5], W[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
-    cons_to_prim(U, W, a.eos);
-    const double s = signal_speed(W, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
+    double ir;
+    cons_to_prim_ir(U, W, a.eos, ir);
+    const double s = signal_speed_ir(W, ir, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
                                   __ldg(a.inv_dx + 3 * b + 2), d3);
     smax = fmax(smax, s);
   }
@@ -132,8 +133,9 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
       double U[5], W[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
-      cons_to_prim(U, W, a.eos);
-      smax = fmax(smax, signal_speed(W, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
+      double ir;
+      cons_to_prim_ir(U, W, a.eos, ir);
+      smax = fmax(smax, signal_speed_ir(W, ir, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
                                      __ldg(a.inv_dx + 3 * b + 2), d3));
     }
     red[threadIdx.x] = smax;

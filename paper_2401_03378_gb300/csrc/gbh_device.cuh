@@ -27,17 +27,22 @@ namespace gbh {
 // calcEos role: conserved (rho, mx, my, mz, E) -> primitive (rho, u, v, w, p),
 // p = (gamma-1) (E - (mx u + my v + mz w)/2).  Floors rho at small_rho and p
 // at small_p; returns 1 when a floor applied.
-__device__ __forceinline__ int cons_to_prim(const double U[5], double W[5], const Eos& e) {
+__device__ __forceinline__ int cons_to_prim_ir(const double U[5], double W[5], const Eos& e, double& ir) {
   int hit = 0;
   double rho = U[0];
   if (less_d(rho, e.small_rho)) { rho = e.small_rho; hit = 1; }
-  const double ir = rcp_nr(rho);
+  ir = rcp_nr(rho);
   const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
   const double m2 = fma(U[3], w, fma(U[2], v, U[1] * u));
   double p = e.gm1 * fma(-0.5, m2, U[4]);
   if (less_d(p, e.small_p)) { p = e.small_p; hit = 1; }
   W[0] = rho; W[1] = u; W[2] = v; W[3] = w; W[4] = p;
   return hit;
+}
+
+__device__ __forceinline__ int cons_to_prim(const double U[5], double W[5], const Eos& e) {
+  double ir;
+  return cons_to_prim_ir(U, W, e, ir);
 }
 
 // calcLims role: half of the MC-limited slope at q0,
@@ -56,6 +61,50 @@ __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp)
   m = as < m ? as : m;
   const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
   return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+}
+
+// Twice the MC-limited slope, 2 sigma = sign(dp) * min(|dm+dp|, 4|dm|, 4|dp|)
+// if dm, dp have the same strict sign, else 0; the face values q0 -/+ sigma/2
+// are then fma(-/+0.25, 2 sigma, q0), bit for bit the values of
+// mc_half_slope.  The factors 4 are added to the exponent fields (exact for
+// normal numbers; a subnormal |dm| or |dp| would compare as if it were about
+// 2^-1020, which moves the result by less than that), saving the FP64
+// multiply by 1/4.
+__device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
+  const double dm = q0 - qm;
+  const double dp = qp - q0;
+  const double sum = dm + dp;
+  const long long bm = dbits(dm), bp = dbits(dp);
+  const unsigned long long mask = 0x7fffffffffffffffULL;
+  const unsigned long long am = (unsigned long long)bm & mask, ap = (unsigned long long)bp & mask;
+  const unsigned long long as = (unsigned long long)dbits(sum) & mask;
+  unsigned long long m = (am < ap ? am : ap) + (2ULL << 52);   // min(4|dm|, 4|dp|)
+  m = as < m ? as : m;
+  const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
+  return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+}
+
+// x / 2 for a positive normal x >= 2^-1021 (one off the exponent field)
+__device__ __forceinline__ double half_pos(double x) { return bitsd(dbits(x) - (1LL << 52)); }
+
+// x / 2 for any finite x on the integer pipe: one off the exponent field when
+// |x| >= 2^-1021, else the magnitude bits shifted right (exact except that
+// the last bit of a subnormal result is truncated)
+__device__ __forceinline__ double half_any(double x) {
+  const long long b = dbits(x);
+  const long long mag = b & 0x7fffffffffffffffLL;
+  return bitsd(mag >= (2LL << 52) ? b - (1LL << 52) : ((b ^ mag) | (mag >> 1)));
+}
+
+// Signal-speed sum of one cell for the CFL rule; W from cons_to_prim and
+// ir = 1 / W[0] (cons_to_prim_ir returns it).
+__device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, const Eos& e, double idx,
+                                                  double idy, double idz, bool dim3) {
+  const double c = sqrt_nr(e.gamma * W[4] * ir);
+  double s = (fabs(W[1]) + c) * idx;
+  s = fma(fabs(W[2]) + c, idy, s);
+  if (dim3) s = fma(fabs(W[3]) + c, idz, s);
+  return s;
 }
 
 // Signal-speed sum of one cell for the CFL rule (W from cons_to_prim).
@@ -94,8 +143,8 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
 
   const double kL = fma(wL, wL, fma(vL, vL, uL * uL));
   const double kR = fma(wR, wR, fma(vR, vR, uR * uR));
-  const double hL = fma(0.5 * rL, kL, e.g_gm1 * pL);    // E + p
-  const double hR = fma(0.5 * rR, kR, e.g_gm1 * pR);
+  const double hL = fma(half_pos(rL), kL, e.g_gm1 * pL);    // E + p (rho >= small_rho, normal)
+  const double hR = fma(half_pos(rR), kR, e.g_gm1 * pR);
   const double cL = sqrt_nr(e.gamma * pL * iL);
   const double cR = sqrt_nr(e.gamma * pR * iR);
 

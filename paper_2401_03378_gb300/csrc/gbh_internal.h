@@ -36,7 +36,7 @@ struct StageArgs {
   const double* dt_dev;  // if non-null, dt = *dt_dev
   double dt;
   double a, b;
-  int combine;           // 0: Uout = Uin + dt*L; 1: a*Un + b*(Uin + dt*L)
+  int combine;           // 0: Uout = Uin + dt*L; 1: a*Un + b*(Uin + dt*L); 2: the same with a = b = 1/2
   int gather;            // 1: halo from neighbour interiors; 0: from Uin's own guard cells
   int kchunk, nchunks;   // z planes per work item (3-D), work items per block
   int items_per_cta;     // consecutive work items processed by one CTA (>= 1)

@@ -88,10 +88,10 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     if (counted(k0 + 1)) hits += h1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      qpm1[v] = Wm1[v] + mc_half_slope(Wm2[v], Wm1[v], W0[v]);
-      const double h = mc_half_slope(Wm1[v], W0[v], Wp1[v]);
-      qm0[v] = W0[v] - h;
-      qpz[v] = W0[v] + h;
+      qpm1[v] = fma(0.25, mc_slope_x2(Wm2[v], Wm1[v], W0[v]), Wm1[v]);
+      const double t = mc_slope_x2(Wm1[v], W0[v], Wp1[v]);
+      qm0[v] = fma(-0.25, t, W0[v]);
+      qpz[v] = fma(0.25, t, W0[v]);
     }
     // z face k0 - 1/2; rotated order (rho, w, u, v, p)
     double wl[5] = {qpm1[0], qpm1[3], qpm1[1], qpm1[2], qpm1[4]};
@@ -113,9 +113,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double qmz[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double h = mc_half_slope(W0[v], Wp1[v], Wn[v]);
-        qmz[v] = Wp1[v] - h;
-        qpn[v] = Wp1[v] + h;
+        const double t = mc_slope_x2(W0[v], Wp1[v], Wn[v]);
+        qmz[v] = fma(-0.25, t, Wp1[v]);
+        qpn[v] = fma(0.25, t, Wp1[v]);
       }
       double wl[5] = {qpz[0], qpz[3], qpz[1], qpz[2], qpz[4]};
       double wr[5] = {qmz[0], qmz[3], qmz[1], qmz[2], qmz[4]};
@@ -151,9 +151,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         for (int v = 0; v < 5; ++v) {
           const double* row = sW + (v * P + j + 2) * P + ii;
           const double q0 = row[1];
-          const double h = mc_half_slope(row[0], q0, row[2]);
-          sQx[(v * M + j) * (M + 2) + ii] = q0 - h;
-          sQx[((5 + v) * M + j) * (M + 2) + ii] = q0 + h;
+          const double t = mc_slope_x2(row[0], q0, row[2]);
+          sQx[(v * M + j) * (M + 2) + ii] = fma(-0.25, t, q0);
+          sQx[((5 + v) * M + j) * (M + 2) + ii] = fma(0.25, t, q0);
         }
       } else {
         const int s2 = s - QX;
@@ -162,9 +162,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         for (int v = 0; v < 5; ++v) {
           const double* col = sW + (v * P + jj) * P + i + 2;
           const double q0 = col[P];
-          const double h = mc_half_slope(col[0], q0, col[2 * P]);
-          sQy[(v * (M + 2) + jj) * M + i] = q0 - h;
-          sQy[((5 + v) * (M + 2) + jj) * M + i] = q0 + h;
+          const double t = mc_slope_x2(col[0], q0, col[2 * P]);
+          sQy[(v * (M + 2) + jj) * M + i] = fma(-0.25, t, q0);
+          sQy[((5 + v) * (M + 2) + jj) * M + i] = fma(0.25, t, q0);
         }
       }
     }
@@ -218,7 +218,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double r = fma(-dtx, fx, __ldg(a.Uin + o));
       r = fma(-dty, fy, r);
       if (DIM3) r = fma(-dtz, Fzp[v] - Fzm[v], r);
-      out[v] = a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
+      // combine 2: a = b = 1/2 (second SSP-RK2 stage), one FP64 add
+      out[v] = a.combine == 2 ? half_any(a.Un[o] + r) : a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
       a.Uout[o] = out[v];
     }
     if (a.flux_slot && col_in && (E == 0 || (k >= 0 && k < L.nz))) {
@@ -246,9 +247,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + cj) * N + ci] = Fzp[v];
     }
     if (E == 0 && a.smax_acc) {
-      double W[5];
-      cons_to_prim(out, W, e);
-      smax = fmax(smax, signal_speed(W, e, idx, idy, idz, DIM3));
+      double W[5], ir;
+      cons_to_prim_ir(out, W, e, ir);
+      smax = fmax(smax, signal_speed_ir(W, ir, e, idx, idy, idz, DIM3));
     }
 
     if (DIM3) {

@@ -140,7 +140,7 @@ extern "C" int hydro_step_static(const gbh_params* params, double* U, double dt,
   A.Uout = U;
   A.a = 0.5;
   A.b = 0.5;
-  A.combine = 1;
+  A.combine = 2;   // a = b = 1/2
   if ((e = gbh::launch_stage(A, s)) != cudaSuccess) return cuda_fail(e, "stage 2 launch");
   return GBH_OK;
 }

@@ -283,6 +283,24 @@ int hydro_advance(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, double *d
  * into dt_hist_host (nsteps doubles, may be NULL).  Synchronises the stream. */
 int hydro_advance_host(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist_host, void *stream);
 
+/* One step of a state in HOST memory with the copies overlapped with the
+ * stages (one hydro_step_cfl in effect).  dt_host (HOST, [nproblems]) is in
+ * and out: if dt_host[0] > 0 it is the step's time step (every entry must be
+ * finite and > 0), typically the value the previous call returned;
+ * otherwise the CFL time step of U_host is computed first.  On return U_host
+ * holds the new state (interior; guard cells are overwritten with
+ * unspecified values) and dt_host the CFL time step of the new state.
+ * The state is split into chunks of consecutive blocks: a chunk's first
+ * stage starts as soon as the chunks its face neighbours live in are on the
+ * device, its second stage writes a separate device state, and the chunk is
+ * copied back as soon as that is done, so the copies in both directions
+ * overlap the stages (U_host should be pinned for that).  Two-level
+ * contexts, the telescoping mode and three stages run the same step
+ * unpipelined.  Uses context-owned device buffers (three states, allocated
+ * on first use) and streams; synchronises the stream.  The results equal
+ * hydro_step_cfl's bit for bit. */
+int hydro_step_host(gbh_ctx *ctx, double *U_host, double *dt_host, void *stream);
+
 /* Scan the interior of U: counts cells whose density <= small_rho, pressure
  * <= small_p, or any variable is non-finite.  Synchronises the stream, writes
  * the count to *nbad_host and returns GBH_ERR_UNPHYSICAL if it is non-zero. */

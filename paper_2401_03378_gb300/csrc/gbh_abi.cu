@@ -74,6 +74,18 @@ struct gbh_ctx {
   // adjoint buffers (allocated on first use): per-face adjoint slots, intermediate adjoint
   double* d_adj_lamW = nullptr;
   double* d_adj_tmp = nullptr;
+  // pipelined host-buffer step (hydro_step_host), set up on first use: chunks
+  // of consecutive blocks, the highest chunk any face neighbour of a chunk
+  // lives in, streams (copy in, stage 1, stage 2, copy out) and events
+  std::vector<int> h_face;          // host copy of the face table
+  int pipe_chunks = 0;
+  std::vector<int> pipe_first, pipe_need;
+  cudaStream_t pipe_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> pipe_ev;   // [3][chunks]: copied in, stage 1 done, stage 2 done
+  cudaEvent_t pipe_mark[3] = {nullptr, nullptr, nullptr};
+  int* d_ident = nullptr;           // identity block list
+  double* d_pipe_out = nullptr;     // the new state
+  double* d_pipe_dt = nullptr;      // its CFL dt
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -138,7 +150,7 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
 // many guard cells around the interior, from Uin's own guard cells.
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
                  double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, int ring = 0,
-                 double* flux_reg = nullptr) {
+                 double* flux_reg = nullptr, const int* list = nullptr, int nlist = 0) {
   gbh::StageArgs A{};
   A.Uin = Uin;
   A.Un = Un;
@@ -170,6 +182,10 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
     A.nlist = c->nactive;
     A.flux_slot = c->d_flux_slot;
     A.flux_reg = flux_reg ? flux_reg : c->d_flux_reg;
+  }
+  if (list) {
+    A.block_list = list;
+    A.nlist = nlist;
   }
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
@@ -490,6 +506,7 @@ static int create_common(const gbh_params* p, gbh_ctx** out) {
     return code;
   }
   c->d_smax = c->d_words;
+  c->h_face = std::move(face);
   *out = c;
   return GBH_OK;
 }
@@ -903,6 +920,14 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_smax_own);
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t& st : c->pipe_stream)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : c->pipe_ev) cudaEventDestroy(ev);
+  for (cudaEvent_t& ev : c->pipe_mark)
+    if (ev) cudaEventDestroy(ev);
+  cudaFree(c->d_ident);
+  cudaFree(c->d_pipe_out);
+  cudaFree(c->d_pipe_dt);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
   return GBH_OK;
@@ -1022,6 +1047,156 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
                                         cudaMemcpyDeviceToHost, s), "D2H dt copy")))
     return rc;
   return cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+}
+
+// Buffers, chunks, streams and events of the pipelined host-buffer step.
+static int pipe_setup(gbh_ctx* c) {
+  const size_t bytes = sizeof(double) * state_elems(c->lay);
+  const int NB = c->lay.nblocks;
+  cudaError_t e = cudaSuccess;
+  if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
+  if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double) * c->nproblems);
+  if (e == cudaSuccess && !c->d_pipe_out) {
+    e = cudaMalloc(&c->d_pipe_out, bytes);
+    if (e == cudaSuccess) e = cudaMemset(c->d_pipe_out, 0, bytes);   // guard cells: defined, unspecified values
+  }
+  if (e == cudaSuccess && !c->d_pipe_dt) e = cudaMalloc(&c->d_pipe_dt, sizeof(double) * c->nproblems);
+  if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "host-step buffers: %s", cudaGetErrorString(e));
+  if (c->pipe_chunks) return GBH_OK;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  // chunks of about two resident CTAs per SM, at most 64
+  int K = NB / (2 * (sms > 0 ? sms : 1));
+  K = K < 1 ? 1 : (K > 64 ? 64 : K);
+  c->pipe_first.resize(K + 1);
+  for (int k = 0; k <= K; ++k) c->pipe_first[k] = (int)((long long)NB * k / K);
+  std::vector<int> chunk_of(NB);
+  for (int k = 0; k < K; ++k)
+    for (int b = c->pipe_first[k]; b < c->pipe_first[k + 1]; ++b) chunk_of[b] = k;
+  c->pipe_need.assign(K, 0);
+  for (int k = 0; k < K; ++k) {
+    int m = k;
+    for (int b = c->pipe_first[k]; b < c->pipe_first[k + 1]; ++b)
+      for (int f = 0; f < 6; ++f) {
+        const int nb = c->h_face[6 * (size_t)b + f];
+        if (nb >= 0 && chunk_of[nb] > m) m = chunk_of[nb];
+      }
+    c->pipe_need[k] = m;
+  }
+  std::vector<int> ident(NB);
+  for (int b = 0; b < NB; ++b) ident[b] = b;
+  e = cudaMalloc(&c->d_ident, sizeof(int) * NB);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_ident, ident.data(), sizeof(int) * NB, cudaMemcpyHostToDevice);
+  for (cudaStream_t& st : c->pipe_stream)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  c->pipe_ev.assign(3 * (size_t)K, nullptr);
+  for (cudaEvent_t& ev : c->pipe_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : c->pipe_mark)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return set_err(c, GBH_ERR_CUDA, "host-step setup: %s", cudaGetErrorString(e));
+  c->pipe_chunks = K;
+  return GBH_OK;
+}
+
+int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!U_host || !dt_host) return set_err(c, GBH_ERR_INVAL, "U_host and dt_host must be non-null");
+  const bool given = dt_host[0] > 0.0;
+  for (int p = 0; given && p < c->nproblems; ++p)
+    if ((rc = check_dt(c, dt_host[p]))) return rc;
+  if ((rc = pipe_setup(c))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bstride = sizeof(double) * (size_t)c->lay.bstride;
+  const size_t dtb = sizeof(double) * c->nproblems;
+  double* U = c->d_host_state;
+  cudaError_t e = cudaSuccess;
+  if (c->refined || c->telescoping || c->nstages != 2) {
+    // the other step forms exchange data across the whole state between their
+    // stages: copy in, step, copy out
+    e = cudaMemcpyAsync(U, U_host, bstride * c->lay.nblocks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, s);
+    if ((rc = cuda_err(c, e, "H2D copy"))) return rc;
+    if (!given && (rc = reduce_dt(c, U, c->d_host_dt, nullptr, s))) return rc;
+    if (c->refined) {
+      rc = c->telescoping ? refined_telescoping_step(c, U, c->d_host_dt, 0.0, s)
+                          : refined_step(c, U, c->d_host_dt, 0.0, s);
+      if (!rc) rc = reduce_dt(c, U, c->d_pipe_dt, nullptr, s);
+    } else {
+      rc = uniform_step(c, U, c->d_host_dt, 0.0, true, s);
+      if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
+                             "dt finalize launch");
+    }
+    if (rc) return rc;
+    e = cudaMemcpyAsync(U_host, U, bstride * c->lay.nblocks, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt_host, c->d_pipe_dt, dtb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(c, e, "host step");
+  }
+  // Pipelined SSP-RK2 step: chunk k's stage 1 starts once the chunks up to
+  // need[k] are on the device (copies run in order), its stage 2 once stage 1
+  // is done up to need[k]; stage 2 writes a separate state so that later
+  // stage-1 launches still read U^n; chunk k goes back as soon as its stage 2
+  // is done.  With dt given, copy-in, both stages and copy-out overlap.
+  const int K = c->pipe_chunks;
+  cudaStream_t sin = c->pipe_stream[0], s1 = c->pipe_stream[1], s2 = c->pipe_stream[2], sout = c->pipe_stream[3];
+  cudaEvent_t* ev_in = &c->pipe_ev[0];
+  cudaEvent_t* ev_s1 = &c->pipe_ev[K];
+  cudaEvent_t* ev_s2 = &c->pipe_ev[2 * (size_t)K];
+  e = cudaEventRecord(c->pipe_mark[0], s);
+  for (cudaStream_t st : c->pipe_stream)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->pipe_mark[0], 0);
+  if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, sin);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const size_t off = (size_t)c->pipe_first[k] * c->lay.bstride;
+    const size_t n = bstride * (size_t)(c->pipe_first[k + 1] - c->pipe_first[k]);
+    e = cudaMemcpyAsync(U + off, U_host + off, n, cudaMemcpyHostToDevice, sin);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], sin);
+  }
+  if ((rc = cuda_err(c, e, "H2D copies"))) return rc;
+  if (!given) {
+    if ((rc = cuda_err(c, cudaStreamWaitEvent(s1, ev_in[K - 1], 0), "event wait"))) return rc;
+    if ((rc = reduce_dt(c, U, c->d_host_dt, nullptr, s1))) return rc;
+  }
+  for (int k = 0; k < K; ++k) {
+    const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
+    if ((rc = cuda_err(c, cudaStreamWaitEvent(s1, ev_in[c->pipe_need[k]], 0), "event wait"))) return rc;
+    rc = stage_launch(c, U, nullptr, c->d_scratch, c->d_host_dt, 0.0, 0.0, 1.0, true, false, s1, 0, nullptr,
+                      c->d_ident + first, cnt);
+    if (rc) return rc;
+    if ((rc = cuda_err(c, cudaEventRecord(ev_s1[k], s1), "event record"))) return rc;
+  }
+  for (int k = 0; k < K; ++k) {
+    const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
+    if ((rc = cuda_err(c, cudaStreamWaitEvent(s2, ev_s1[c->pipe_need[k]], 0), "event wait"))) return rc;
+    rc = stage_launch(c, c->d_scratch, U, c->d_pipe_out, c->d_host_dt, 0.0, 0.5, 0.5, true, true, s2, 0, nullptr,
+                      c->d_ident + first, cnt);
+    if (rc) return rc;
+    if ((rc = cuda_err(c, cudaEventRecord(ev_s2[k], s2), "event record"))) return rc;
+  }
+  if ((rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s2, c->nproblems),
+                     "dt finalize launch")))
+    return rc;
+  e = cudaEventRecord(c->pipe_mark[1], s2);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const size_t off = (size_t)c->pipe_first[k] * c->lay.bstride;
+    const size_t n = bstride * (size_t)(c->pipe_first[k + 1] - c->pipe_first[k]);
+    e = cudaStreamWaitEvent(sout, ev_s2[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U_host + off, c->d_pipe_out + off, n, cudaMemcpyDeviceToHost, sout);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, c->pipe_mark[1], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt_host, c->d_pipe_dt, dtb, cudaMemcpyDeviceToHost, sout);
+  if (e == cudaSuccess) e = cudaEventRecord(c->pipe_mark[2], sout);
+  for (cudaStream_t st : {sin, s1}) {
+    // join the remaining streams too, so that the caller's stream orders after all of them
+    if (e != cudaSuccess) break;
+    e = cudaEventRecord(c->pipe_mark[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->pipe_mark[0], 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->pipe_mark[2], 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_err(c, e, "host step");
 }
 
 int hydro_check_state(gbh_ctx* c, const double* U, long long* nbad_host, void* stream) {

@@ -230,8 +230,7 @@ class Hydro:
                                                     self._state(lamW, "lamW"), _stream_handle()))
         return lamW
 
-    def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
-        """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
+    def _host_state(self, U_host) -> int:
         if isinstance(U_host, torch.Tensor):
             if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous():
                 raise TypeError("U_host must be a contiguous float64 CPU tensor")
@@ -242,6 +241,22 @@ class Hydro:
             ptr = U_host.ctypes.data
         if tuple(U_host.shape) != self.shape:
             raise ValueError(f"U_host must have shape {self.shape}")
+        return ptr
+
+    def step_host(self, U_host, dt_host):
+        """One step of a host-resident state with the copies overlapped with the
+        stages.  dt_host: float64 numpy array of nproblems entries, in and out
+        (<= 0 on the first call: computed from U_host); returns U_host."""
+        if not (isinstance(dt_host, np.ndarray) and dt_host.dtype == np.float64 and dt_host.size >= self.nproblems
+                and dt_host.flags.c_contiguous):
+            raise TypeError("dt_host must be a contiguous float64 array with one entry per problem")
+        self._check(self.lib.hydro_step_host(self.ctx, self._host_state(U_host), dt_host.ctypes.data,
+                                             _stream_handle()))
+        return U_host
+
+    def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
+        """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
+        ptr = self._host_state(U_host)
         h = None
         if dt_hist_host is not None:
             h = dt_hist_host.ctypes.data if isinstance(dt_hist_host, np.ndarray) else dt_hist_host.data_ptr()

@@ -237,6 +237,71 @@ def test_repeatable_and_step_variants_agree(gb):
     assert np.array_equal(hist_h, hh)
 
 
+def test_checkpoint_resume_bitwise(gb, tmp_path):
+    """Checkpoint / resume: the state is plain tensors, so torch.save of U and
+    the device dt after 10 steps, a fresh context and a load, then 10 more
+    steps give the same bits as 20 uninterrupted steps (uniform and two-level)."""
+    cases = [(wl.lattice_3d(2, 2, 2, 16, 16, 16, 4), None),
+             (None, wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3)))]
+    for lat, tl in cases:
+        U0 = wl.sedov(lat) if tl is None else wl.sedov_two_level(tl)
+        make = (lambda: gb.Hydro.from_lattice(lat)) if tl is None else (lambda: gb.Hydro.from_two_level(tl))
+        h = make()
+        A = dev(U0)
+        if tl is not None:
+            h.fill_guardcells(A)
+        da = h.compute_dt(A)
+        h.advance(A, 20, da)
+        B = dev(U0)
+        if tl is not None:
+            h.fill_guardcells(B)
+        db = h.compute_dt(B)
+        h.advance(B, 10, db)
+        path = tmp_path / "ckpt.pt"
+        torch.save({"U": B.cpu(), "dt": db.cpu(), "step": 10}, path)
+        h.close()
+        del B, db
+        ck = torch.load(path)
+        h2 = make()
+        C, dc = ck["U"].cuda(), ck["dt"].cuda()
+        h2.advance(C, 20 - ck["step"], dc)
+        assert torch.equal(A, C) and torch.equal(da, dc)
+
+
+@pytest.mark.parametrize("kind", ["3d", "2d_many_chunks", "periodic_z", "batched", "telescoping"])
+def test_step_host_equals_device_steps_bitwise(gb, kind):
+    """hydro_step_host (copies overlapped with the stages, chunked by blocks)
+    gives hydro_step_cfl's bits and dt, call after call."""
+    if kind == "batched":
+        probs = wl.ensemble(count=5, seed=4, choices=(64, 128))
+        lats = [l for l, _ in probs]
+        U0 = np.concatenate([u for _, u in probs])
+        make = lambda: gb.Hydro.from_batch(lats)
+        sl = lats[0].interior_slices()
+    else:
+        lat = {"3d": wl.lattice_3d(16, 8, 8, 8, 8, 8, 4),
+               "2d_many_chunks": wl.lattice_2d(64, 64, 8, 8, 4),
+               "periodic_z": wl.lattice_3d(8, 8, 16, 8, 8, 8, 4, bc=("outflow", "outflow", "periodic")),
+               "telescoping": wl.lattice_3d(8, 8, 16, 8, 8, 8, 4)}[kind]
+        U0 = wl.sedov(lat) if lat.ndim == 3 else wl.sod(lat)
+        make = lambda: gb.Hydro.from_lattice(lat)
+        sl = lat.interior_slices()
+    hd, hh = make(), make()
+    if kind == "telescoping":
+        hd.set_telescoping(True)
+        hh.set_telescoping(True)
+    D = dev(U0)
+    dt = hd.compute_dt(D)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    dth = np.zeros(hh.nproblems)
+    zs, ys, xs = sl
+    for _ in range(3):
+        hd.step_cfl(D, dt)
+        hh.step_host(Uh, dth)
+        assert np.array_equal(host(D)[:, :, zs, ys, xs], Uh.numpy()[:, :, zs, ys, xs])
+        assert np.array_equal(host(dt), dth)
+
+
 def test_periodic_conservation(gb):
     lat = wl.lattice_3d(2, 2, 2, 16, 16, 16, 4, bc="periodic")
     U = wl.random_state(lat, seed=12, rough=True)

@@ -302,6 +302,60 @@ def test_step_host_equals_device_steps_bitwise(gb, kind):
         assert np.array_equal(host(dt), dth)
 
 
+@pytest.mark.parametrize("drift", [4.0, -4.0, 0.0])
+def test_supersonic_faces(gb, drift):
+    """Rough states with velocities drift + U(-3, 3) in every direction (Mach up
+    to ~10): most faces have the whole wave fan on one side, the HLLC branch
+    F = F_L (or F_R) that subsonic data never takes."""
+    lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, 4, bc="periodic")
+    rng = np.random.default_rng(71)
+    shape = (lat.nblocks,) + lat.padded
+    rho, p = rng.uniform(0.5, 2.0, shape), rng.uniform(0.5, 2.0, shape)
+    vel = drift + rng.uniform(-3.0, 3.0, (3,) + shape)
+    U = wl._assemble(lat, rho, vel[0], vel[1], vel[2], p, 1.4)
+    c = np.sqrt(1.4 * p / rho)
+    if drift:
+        assert np.mean(np.abs(vel[0]) > c) > 0.5
+    o = Oracle(lat)
+    dt = o.compute_dt(U)
+    ref = U.copy()
+    hits = o.step(ref, dt)
+    h = gb.Hydro.from_lattice(lat)
+    Ug = dev(U)
+    h.step(Ug, dt)
+    assert np.all(interior_err(host(Ug), ref, lat) <= TOL_TINY)
+    assert h.floor_hits() == hits
+
+
+@pytest.mark.slow
+def test_state_beyond_2_31_elements(gb):
+    """512^3 as 32768 blocks of 16^3 + 4 guards: 2.26e9 doubles per state, so
+    every offset needs 64-bit arithmetic.  An x-only Sod problem must give
+    bit-identical (y, z) rows equal to the 32 x 1 x 1-block lattice's result."""
+    big = wl.lattice_3d(32, 32, 32, 16, 16, 16, 4)
+    import dataclasses
+    small = dataclasses.replace(wl.lattice_3d(32, 1, 1, 16, 16, 16, 4, bc=("outflow", "periodic", "periodic")),
+                                extent=(1.0, 1.0 / 32, 1.0 / 32))
+    assert small.dx == big.dx
+    assert big.nblocks * 5 * np.prod(big.padded) > 2 ** 31
+    Us = dev(wl.sod(small))
+    hs = gb.Hydro.from_lattice(small)
+    Ub = Us.index_select(0, torch.arange(32, device="cuda").repeat(32 * 32))
+    hb = gb.Hydro.from_lattice(big)
+    ds, db = hs.compute_dt(Us), hb.compute_dt(Ub)
+    assert torch.equal(ds, db)
+    hs.advance(Us, 3, ds)
+    hb.advance(Ub, 3, db)
+    assert torch.equal(ds, db)
+    zs, ys, xs = big.interior_slices()
+    got = Ub.view(32 * 32, 32, 5, *big.padded)[:, :, :, zs, ys, xs]
+    ref = Us[:, :, zs, ys, xs]
+    for r in range(0, 32 * 32, 64):
+        assert torch.equal(got[r:r + 64], ref.expand(min(64, 32 * 32 - r), *ref.shape))
+    del Ub, got
+    torch.cuda.empty_cache()
+
+
 def test_periodic_conservation(gb):
     lat = wl.lattice_3d(2, 2, 2, 16, 16, 16, 4, bc="periodic")
     U = wl.random_state(lat, seed=12, rough=True)

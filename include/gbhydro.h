@@ -334,6 +334,20 @@ int gbh_fastmath_selftest(const double *x_dev, double *out_dev, long long n, voi
 /* Number of SMs of the current device (for sizing probes), or a negative error. */
 int gbh_device_sm_count(void);
 
+/* Checked build (libgbhydro_check.so, compiled with -DGBH_CHECK): every
+ * computed global and shared-memory index of the kernels is compared with
+ * its buffer's length; an index outside the buffer is counted and the
+ * access redirected to the buffer's first element, so no access leaves its
+ * buffer (the stand-in for a memory checker, which this build does not
+ * use).  gbh_check_violations synchronises the device, writes the number of
+ * such indices since the previous call to *count_host and clears it.
+ * gbh_check_selftest runs one kernel that computes an index one past a
+ * 4-element buffer and writes the count it produced (1 when the checks work).
+ * In the normal build both return GBH_ERR_UNSUPPORTED with *count_host = 0.
+ * The paper has no counterpart. */
+int gbh_check_violations(long long *count_host);
+int gbh_check_selftest(long long *count_host);
+
 #ifdef __cplusplus
 }
 #endif

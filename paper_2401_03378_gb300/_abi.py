@@ -83,10 +83,14 @@ SIGNATURES = {
     "gbh_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "gbh_fastmath_selftest": (C.c_int, [_dp, _dp, C.c_longlong, _vp]),
     "gbh_device_sm_count": (C.c_int, []),
+    "gbh_check_violations": (C.c_int, [C.POINTER(C.c_longlong)]),
+    "gbh_check_selftest": (C.c_int, [C.POINTER(C.c_longlong)]),
 }
 
+LIB_PATH_CHECK = os.path.join(HERE, "libgbhydro_check.so")
+
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 class GbhError(RuntimeError):
@@ -95,13 +99,13 @@ class GbhError(RuntimeError):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
 
 
-def load(path: str | None = None):
-    """Load libgbhydro.so (built in-tree).  Raises if it is missing: there is
+def load(path: str | None = None, checked: bool = False):
+    """Load libgbhydro.so (or, checked=True, the checked build
+    libgbhydro_check.so), built in-tree.  Raises if it is missing: there is
     no fallback implementation."""
-    global _lib
+    p = path or (LIB_PATH_CHECK if checked else LIB_PATH)
     with _lock:
-        if _lib is None:
-            p = path or LIB_PATH
+        if p not in _libs:
             if not os.path.exists(p):
                 raise RuntimeError(
                     f"{p} is missing: build it with `python -m paper_2401_03378_gb300.build` "
@@ -111,5 +115,5 @@ def load(path: str | None = None):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[p] = lib
+        return _libs[p]

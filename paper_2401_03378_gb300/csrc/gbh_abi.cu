@@ -182,6 +182,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
     A.nlist = c->nactive;
     A.flux_slot = c->d_flux_slot;
     A.flux_reg = flux_reg ? flux_reg : c->d_flux_reg;
+    A.flux_reg_len = (long long)c->flux_reg_doubles;
   }
   if (list) {
     A.block_list = list;
@@ -656,6 +657,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.cf_faces = c->d_cf_faces;
   A.ncf_faces = (int)cf_faces.size();
   A.flux_reg = c->d_flux_reg;
+  A.flux_reg_len = (long long)c->flux_reg_doubles;
   A.inv_dx = c->d_inv_dx;
   *out = c;
   return GBH_OK;
@@ -1266,6 +1268,39 @@ int gbh_fastmath_selftest(const double* x_dev, double* out_dev, long long n, voi
   cudaError_t e = gbh::launch_fastmath_selftest(x_dev, out_dev, n, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "self-test launch: %s", cudaGetErrorString(e));
   return GBH_OK;
+}
+
+int gbh_check_violations(long long* count_host) {
+  if (!count_host) return set_err(nullptr, GBH_ERR_INVAL, "count_host is NULL");
+#ifdef GBH_CHECK
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "cudaDeviceSynchronize: %s", cudaGetErrorString(e));
+  const long long parts[4] = {gbh::check_take_stage(), gbh::check_take_aux(), gbh::check_take_amr(),
+                              gbh::check_take_adjoint()};
+  long long total = 0;
+  for (long long v : parts) {
+    if (v < 0) return set_err(nullptr, GBH_ERR_CUDA, "reading the check counters failed");
+    total += v;
+  }
+  *count_host = total;
+  return GBH_OK;
+#else
+  *count_host = 0;
+  return set_err(nullptr, GBH_ERR_UNSUPPORTED, "not a checked build (compile with -DGBH_CHECK)");
+#endif
+}
+
+int gbh_check_selftest(long long* count_host) {
+  if (!count_host) return set_err(nullptr, GBH_ERR_INVAL, "count_host is NULL");
+#ifdef GBH_CHECK
+  const long long n = gbh::check_selftest();
+  if (n < 0) return set_err(nullptr, GBH_ERR_CUDA, "check self-test failed");
+  *count_host = n;
+  return GBH_OK;
+#else
+  *count_host = 0;
+  return set_err(nullptr, GBH_ERR_UNSUPPORTED, "not a checked build (compile with -DGBH_CHECK)");
+#endif
 }
 
 int gbh_device_sm_count(void) {

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gbh_check.cuh"
 #include "gbh_device.cuh"
 #include "gbh_gather.cuh"
 #include "gbh_internal.h"
@@ -228,14 +229,15 @@ __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos&
 // (s = position - (k-2)); the cell pass sums the slots that refer to a cell.
 
 struct FaceGeom {
+  long long total;     // doubles in the slot buffer (checked build)
   long long base[3];   // offset of each dimension's slots in the buffer
   int n[3];            // pencil length per dimension
   int n1[3], n2[3];    // transverse extents per dimension
 };
 
-__device__ __host__ __forceinline__ long long slot_index(const FaceGeom& G, int d, int b, int pen, int k, int s) {
+__device__ __forceinline__ long long slot_index(const FaceGeom& G, int d, int b, int pen, int k, int s) {
   const long long npen = (long long)G.n1[d] * G.n2[d];
-  return G.base[d] + ((((long long)b * npen + pen) * (G.n[d] + 1) + k) * 4 + s) * 5;
+  return GBH_IX(G.base[d] + ((((long long)b * npen + pen) * (G.n[d] + 1) + k) * 4 + s) * 5, G.total - 4);
 }
 
 __device__ __forceinline__ void pencil_to_cell(int d, int pos, int p1, int p2, int& i, int& j, int& k) {
@@ -245,7 +247,8 @@ __device__ __forceinline__ void pencil_to_cell(int d, int pos, int p1, int p2, i
 }
 
 __device__ __forceinline__ long long own_offset(const Layout& L, int b, int i, int j, int k) {
-  return (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+  return GBH_IX((long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g),
+                (long long)L.nblocks * L.bstride - 4 * L.vstride);
 }
 
 template <int N, int d>
@@ -452,10 +455,13 @@ FaceGeom face_geom(const Layout& L) {
     G.base[d] = off;
     if (d < L.ndim) off += (long long)L.nblocks * G.n1[d] * G.n2[d] * (n[d] + 1) * 20;
   }
+  G.total = off;
   return G;
 }
 
 }  // namespace
+
+GBH_CHECK_TAKE(check_take_adjoint)
 
 size_t stage_vjp_scratch_doubles(const Layout& L) {
   long long total = 0;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gbh_check.cuh"
 #include "gbh_device.cuh"
 #include "gbh_internal.h"
 
@@ -33,7 +34,8 @@ int grid_for(long long work) {
 }
 
 __device__ __forceinline__ long long at(const Layout& L, int b, int v, int i, int j, int k) {
-  return (long long)b * L.bstride + v * L.vstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+  return GBH_IX((long long)b * L.bstride + v * L.vstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g),
+                (long long)L.nblocks * L.bstride);
 }
 
 // Restriction: one thread per (covered block, interior cell); 5 variables.
@@ -85,7 +87,8 @@ __device__ __forceinline__ long long coarse_offset(const AmrArgs& a, int parent,
       for (int d = 0; d < 3; ++d) c[d] = c[d] < 0 ? 0 : (c[d] >= n[d] ? n[d] - 1 : c[d]);
     }
   }
-  return (long long)blk * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g);
+  return GBH_IX((long long)blk * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g),
+                (long long)L.nblocks * L.bstride - 4 * L.vstride);
 }
 
 __device__ __forceinline__ int floor_div2(int x) { return x >= 0 ? x / 2 : -((1 - x) / 2); }
@@ -241,9 +244,11 @@ __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, 
       double fsum = 0.0;
       for (int b2 = 0; b2 < (L.ndim == 3 ? 2 : 1); ++b2)
         for (int b1 = 0; b1 < 2; ++b1)
-          fsum = __dadd_rn(fsum, Ff[((long long)v * n2 + f2 + b2) * N + f1 + b1]);
+          fsum = __dadd_rn(fsum, Ff[GBH_IX((long long)fs * sstride + ((long long)v * n2 + f2 + b2) * N + f1 + b1,
+                                           a.flux_reg_len) - (long long)fs * sstride]);
       const double fmean = __dmul_rn(fsum, nfine);
-      const double fc = Fc[((long long)v * n2 + (L.ndim == 3 ? t2 : 0)) * N + t1];
+      const double fc = Fc[GBH_IX((long long)en.coarse_slot * sstride + ((long long)v * n2 + (L.ndim == 3 ? t2 : 0)) * N + t1,
+                                  a.flux_reg_len) - (long long)en.coarse_slot * sstride];
       const double corr = side ? __dsub_rn(fc, fmean) : __dsub_rn(fmean, fc);
       const long long o = at(L, en.block, v, x[0], x[1], x[2]);
       U[o] = __dadd_rn(U[o], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
@@ -252,6 +257,8 @@ __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, 
 }
 
 }  // namespace
+
+GBH_CHECK_TAKE(check_take_amr)
 
 cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s) {
   if (a.ncovered == 0) return cudaSuccess;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gbh_check.cuh"
 #include "gbh_device.cuh"
 #include "gbh_internal.h"
 
@@ -59,9 +60,10 @@ __global__ void fill_kernel(const FillArgs a) {
       if (src < 0) continue;
       for (int d = 0; d < 3; ++d) c[d] -= o[d] * n[d];
     }
-    const long long so =
-        (long long)src * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g);
-    const long long dof = (long long)b * L.bstride + ((long long)kk * L.nyp + jj) * L.nxp + ii;
+    const long long lim = (long long)L.nblocks * L.bstride - 4 * L.vstride;
+    const long long so = GBH_IX(
+        (long long)src * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g), lim);
+    const long long dof = GBH_IX((long long)b * L.bstride + ((long long)kk * L.nyp + jj) * L.nxp + ii, lim);
 #pragma unroll
     for (int v = 0; v < 5; ++v) a.U[dof + v * L.vstride] = a.U[so + v * L.vstride];
   }
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
     r /= L.nx;
     const int j = (int)(r % L.ny);
     const int k = (int)(r / L.ny);
-    const long long o = (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+    const long long o = GBH_IX((long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g),
+                               (long long)L.nblocks * L.bstride - 4 * L.vstride);
     double U[5], W[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
@@ -162,7 +165,8 @@ __global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const 
     r /= L.nx;
     const int j = (int)(r % L.ny);
     const int k = (int)(r / L.ny);
-    const long long o = (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+    const long long o = GBH_IX((long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g),
+                               (long long)L.nblocks * L.bstride - 4 * L.vstride);
     double u[5];
     bool finite = true;
     for (int v = 0; v < 5; ++v) {
@@ -204,6 +208,15 @@ __global__ void fastmath_selftest_kernel(const double* x, double* out, long long
   }
 }
 
+#ifdef GBH_CHECK
+// One index past a 4-element buffer: the check counts it and redirects the
+// store to element 0 (the access stays inside the buffer).
+__global__ void check_selftest_kernel(double* buf) {
+  const long long i = 4;
+  buf[GBH_IX(i, 4)] = 1.0;
+}
+#endif
+
 int grid_for(long long work, int threads) {
   long long g = (work + threads - 1) / threads;
   if (g > 152LL * 16) g = 152LL * 16;
@@ -212,6 +225,23 @@ int grid_for(long long work, int threads) {
 }
 
 }  // namespace
+
+GBH_CHECK_TAKE(check_take_aux)
+
+long long check_selftest() {
+#ifdef GBH_CHECK
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 4 * sizeof(double)) != cudaSuccess) return -1;
+  const long long before = check_take_aux();
+  check_selftest_kernel<<<1, 1>>>(buf);
+  const cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(buf);
+  if (e != cudaSuccess || before < 0) return -1;
+  return check_take_aux();
+#else
+  return -1;
+#endif
+}
 
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
   const long long work = (long long)a.lay.nblocks * a.lay.nzp * a.lay.nyp * a.lay.nxp;

@@ -10,6 +10,7 @@
 
 #include <cuda_runtime.h>
 
+#include "gbh_check.cuh"
 #include "gbh_device.cuh"
 #include "gbh_internal.h"
 
@@ -61,7 +62,8 @@ __device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int 
 
     }
   }
-  return (long long)blk * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+  const long long o = (long long)blk * L.bstride + ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+  return GBH_IX(o, (long long)L.nblocks * L.bstride - 4 * L.vstride);   // o + v*vstride, v < 5, in the state
 }
 
 template <int N>

@@ -51,6 +51,7 @@ struct StageArgs {
   int nlist;                        // entries of block_list
   const int* flux_slot;             // [nblocks][6] flux-register slot of a face, or -1
   double* flux_reg;                 // [slots][5][n_t2][N] face fluxes (t1 fastest)
+  long long flux_reg_len;           // doubles in flux_reg (checked build)
 };
 
 // One coarse face on the boundary of the fine region: the coarse block, its
@@ -75,6 +76,7 @@ struct AmrArgs {
   const RefluxEntry* reflux;
   int nreflux;
   double* flux_reg;
+  long long flux_reg_len;  // doubles in flux_reg (checked build)
   const double* inv_dx;
 };
 
@@ -131,6 +133,16 @@ cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, 
 cudaError_t launch_prim_to_cons(const Layout& L, const Eos& e, const double* W, double* U, const double* lamU,
                                 double* lamW, cudaStream_t s);
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);
+
+// Checked build (-DGBH_CHECK, gbh_check.cuh): per translation unit, read and
+// clear the count of out-of-range indices (0 in the normal build, -1 if the
+// read failed); the self-test plants one index past a 4-element buffer and
+// returns the count it produced (checked build only).
+long long check_take_stage();
+long long check_take_aux();
+long long check_take_amr();
+long long check_take_adjoint();
+long long check_selftest();
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, double* out, cudaStream_t s);
 
 }  // namespace gbh

@@ -127,7 +127,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     // (A) primitives of plane k and its 2-deep x/y rims -> shared memory
     //     (i, j: tile positions)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sW[(v * P + ty + 2) * P + tx + 2] = W0[v];
+    for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + ty + 2) * P + tx + 2, 5 * P * P)] = W0[v];
     for (int r = tid; r < 8 * M; r += NT) {
       const int q = r / (2 * M), t = r - q * 2 * M;
       const int depth = t / M, pos = t - depth * M;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double W[5];
       load_prim<N>(a, b, i - E, j - E, k, W);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sW[(v * P + j + 2) * P + i + 2] = W[v];
+      for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + j + 2) * P + i + 2, 5 * P * P)] = W[v];
     }
     __syncthreads();
 
@@ -152,8 +152,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
           const double* row = sW + (v * P + j + 2) * P + ii;
           const double q0 = row[1];
           const double t = mc_slope_x2(row[0], q0, row[2]);
-          sQx[(v * M + j) * (M + 2) + ii] = fma(-0.25, t, q0);
-          sQx[((5 + v) * M + j) * (M + 2) + ii] = fma(0.25, t, q0);
+          sQx[GBH_IX((v * M + j) * (M + 2) + ii, 10 * QX)] = fma(-0.25, t, q0);
+          sQx[GBH_IX(((5 + v) * M + j) * (M + 2) + ii, 10 * QX)] = fma(0.25, t, q0);
         }
       } else {
         const int s2 = s - QX;
@@ -163,8 +163,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
           const double* col = sW + (v * P + jj) * P + i + 2;
           const double q0 = col[P];
           const double t = mc_slope_x2(col[0], q0, col[2 * P]);
-          sQy[(v * (M + 2) + jj) * M + i] = fma(-0.25, t, q0);
-          sQy[((5 + v) * (M + 2) + jj) * M + i] = fma(0.25, t, q0);
+          sQy[GBH_IX((v * (M + 2) + jj) * M + i, 10 * QX)] = fma(-0.25, t, q0);
+          sQy[GBH_IX(((5 + v) * (M + 2) + jj) * M + i, 10 * QX)] = fma(0.25, t, q0);
         }
       }
     }
@@ -196,10 +196,10 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double F[5];
       hllc_flux(wl, wr, e, F);
       if (xf) {
-        double* o = sFx + j * (M + 1) + i;
+        double* o = sFx + GBH_IX(j * (M + 1) + i, FX);
         o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
       } else {
-        double* o = sFy + j * M + i;
+        double* o = sFy + GBH_IX(j * M + i, FX);
         o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
       }
     }
@@ -212,9 +212,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     double out[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double fx = sFx[(v * M + ty) * (M + 1) + tx + 1] - sFx[(v * M + ty) * (M + 1) + tx];
-      const double fy = sFy[(v * (M + 1) + ty + 1) * M + tx] - sFy[(v * (M + 1) + ty) * M + tx];
-      const long long o = base + v * L.vstride;
+      const double fx = sFx[GBH_IX((v * M + ty) * (M + 1) + tx + 1, 5 * FX)] - sFx[(v * M + ty) * (M + 1) + tx];
+      const double fy = sFy[GBH_IX((v * (M + 1) + ty + 1) * M + tx, 5 * FX)] - sFy[(v * (M + 1) + ty) * M + tx];
+      const long long o = GBH_IX(base + v * L.vstride, (long long)L.nblocks * L.bstride);
       double r = fma(-dtx, fx, __ldg(a.Uin + o));
       r = fma(-dty, fy, r);
       if (DIM3) r = fma(-dtz, Fzp[v] - Fzm[v], r);
@@ -231,20 +231,20 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       const int t2k = DIM3 ? k : 0;
       if (ci == 0 && fsl[FACE_XM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_XM] * ss + (v * n2 + t2k) * N + cj] = sFx[(v * M + ty) * (M + 1) + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_XM] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * M + ty) * (M + 1) + tx];
       if (ci == N - 1 && fsl[FACE_XP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_XP] * ss + (v * n2 + t2k) * N + cj] = sFx[(v * M + ty) * (M + 1) + tx + 1];
+          a.flux_reg[GBH_IX(fsl[FACE_XP] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * M + ty) * (M + 1) + tx + 1];
       if (cj == 0 && fsl[FACE_YM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_YM] * ss + (v * n2 + t2k) * N + ci] = sFy[(v * (M + 1) + ty) * M + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_YM] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (M + 1) + ty) * M + tx];
       if (cj == N - 1 && fsl[FACE_YP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[fsl[FACE_YP] * ss + (v * n2 + t2k) * N + ci] = sFy[(v * (M + 1) + ty + 1) * M + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_YP] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (M + 1) + ty + 1) * M + tx];
       if (DIM3 && k == 0 && fsl[FACE_ZM] >= 0)
-        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZM] * ss + (v * n2 + cj) * N + ci] = Fzm[v];
+        for (int v = 0; v < 5; ++v) a.flux_reg[GBH_IX(fsl[FACE_ZM] * ss + (v * n2 + cj) * N + ci, a.flux_reg_len)] = Fzm[v];
       if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
-        for (int v = 0; v < 5; ++v) a.flux_reg[fsl[FACE_ZP] * ss + (v * n2 + cj) * N + ci] = Fzp[v];
+        for (int v = 0; v < 5; ++v) a.flux_reg[GBH_IX(fsl[FACE_ZP] * ss + (v * n2 + cj) * N + ci, a.flux_reg_len)] = Fzp[v];
     }
     if (E == 0 && a.smax_acc) {
       double W[5], ir;
@@ -333,6 +333,8 @@ cudaError_t launch_e(const StageArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+GBH_CHECK_TAKE(check_take_stage)
 
 size_t stage_smem_bytes(int nx) {
   switch (nx) {

@@ -36,8 +36,8 @@ class Hydro:
                  dx: Optional[np.ndarray] = None, gamma: float = 1.4, cfl: float = 0.8,
                  small_rho: float = 1e-12, small_p: float = 1e-14,
                  parent: Optional[np.ndarray] = None, children: Optional[np.ndarray] = None,
-                 problem: Optional[np.ndarray] = None, nproblems: int = 1):
-        self.lib = _abi.load()
+                 problem: Optional[np.ndarray] = None, nproblems: int = 1, checked: bool = False):
+        self.lib = _abi.load(checked=checked)
         self.ndim = int(ndim)
         nx, ny, nz = (int(n[0]), int(n[1]), int(n[2]) if ndim == 3 else 1)
         if nbr is None:

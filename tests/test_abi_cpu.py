@@ -32,14 +32,23 @@ def test_header_lists_the_abi():
         assert required in names
 
 
-def test_every_declared_symbol_is_exported(lib):
+@pytest.mark.parametrize("checked", [False, True])
+def test_every_declared_symbol_is_exported(lib, checked):
     from paper_2401_03378_gb300 import _abi
-    out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True,
+    path = _abi.LIB_PATH_CHECK if checked else _abi.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
                          check=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
     for name in declared_functions():
         assert name in exported, name
         assert name in _abi.SIGNATURES, f"binding lacks {name}"
+
+
+def test_normal_build_has_no_index_checks(lib):
+    n = C.c_longlong(-1)
+    assert lib.gbh_check_violations(C.byref(n)) == -5 and n.value == 0
+    assert lib.gbh_check_selftest(C.byref(n)) == -5 and n.value == 0
+    assert lib.gbh_check_violations(None) == -1
 
 
 def _params(**over):

@@ -70,9 +70,7 @@ __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp)
 // normal numbers; a subnormal |dm| or |dp| would compare as if it were about
 // 2^-1020, which moves the result by less than that), saving the FP64
 // multiply by 1/4.
-__device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
-  const double dm = q0 - qm;
-  const double dp = qp - q0;
+__device__ __forceinline__ double mc_slope_x2_d(double dm, double dp) {
   const double sum = dm + dp;
   const long long bm = dbits(dm), bp = dbits(dp);
   const unsigned long long mask = 0x7fffffffffffffffULL;
@@ -82,6 +80,11 @@ __device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
   m = as < m ? as : m;
   const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
   return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+}
+
+// The same from the cell values (dm = q0 - qm, dp = qp - q0).
+__device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
+  return mc_slope_x2_d(q0 - qm, qp - q0);
 }
 
 // x / 2 for a positive normal x >= 2^-1021 (one off the exponent field)

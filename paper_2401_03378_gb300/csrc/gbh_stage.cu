@@ -77,6 +77,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   int hits = 0;
   double smax = 0.0;
   double W0[5], Wp1[5], qpz[5], Fzm[5];     // column state carried along z
+  double dz1[5];                            // Wp1 - W0 (the next z slope's left difference)
 
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
@@ -89,7 +90,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       qpm1[v] = fma(0.25, mc_slope_x2(Wm2[v], Wm1[v], W0[v]), Wm1[v]);
-      const double t = mc_slope_x2(Wm1[v], W0[v], Wp1[v]);
+      dz1[v] = Wp1[v] - W0[v];
+      const double t = mc_slope_x2_d(W0[v] - Wm1[v], dz1[v]);
       qm0[v] = fma(-0.25, t, W0[v]);
       qpz[v] = fma(0.25, t, W0[v]);
     }
@@ -113,7 +115,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double qmz[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double t = mc_slope_x2(W0[v], Wp1[v], Wn[v]);
+        const double dn = Wn[v] - Wp1[v];
+        const double t = mc_slope_x2_d(dz1[v], dn);
+        dz1[v] = dn;
         qmz[v] = fma(-0.25, t, Wp1[v]);
         qpn[v] = fma(0.25, t, Wp1[v]);
       }
@@ -143,28 +147,40 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
     __syncthreads();
 
-    // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M]
-    for (int s = tid; s < 2 * QX; s += NT) {
-      if (s < QX) {
-        const int ii = s % (M + 2), j = s / (M + 2);   // slope cell i = ii - 1
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const double* row = sW + (v * P + j + 2) * P + ii;
-          const double q0 = row[1];
-          const double t = mc_slope_x2(row[0], q0, row[2]);
-          sQx[GBH_IX((v * M + j) * (M + 2) + ii, 10 * QX)] = fma(-0.25, t, q0);
-          sQx[GBH_IX(((5 + v) * M + j) * (M + 2) + ii, 10 * QX)] = fma(0.25, t, q0);
+    // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M],
+    //     three consecutive cells per work item, so the two inner differences
+    //     are formed once for two slopes (the last triple of a row may be
+    //     partial: its reads are clamped to the row and its extra slopes not
+    //     stored)
+    constexpr int TR = (M + 2 + 2) / 3;               // triples per row
+    for (int s = tid; s < 2 * TR * M; s += NT) {
+      const bool xs = s < TR * M;
+      const int s2 = xs ? s : s - TR * M;
+      const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // row (x) or column (y); first slope cell + 1
+      const int step = xs ? 1 : P;
+      const int first = xs ? (line + 2) * P + c0 : c0 * P + line + 2;
+      const int last = M + 3 - c0;                    // positions c0 .. M + 3 exist
+      const int k3 = 3 < last ? 3 : last, k4 = 4 < last ? 4 : last;
+      const bool two = c0 + 1 < M + 2, three = c0 + 2 < M + 2;
+#pragma unroll 1
+      for (int v = 0; v < 5; ++v) {
+        const double* q = sW + v * P * P + first;
+        const double q1 = q[step], q2 = q[2 * step], q3 = q[k3 * step];
+        const double d0 = q1 - q[0], d1 = q2 - q1, d2 = q3 - q2, d3 = q[k4 * step] - q3;
+        const double t0 = mc_slope_x2_d(d0, d1), t1 = mc_slope_x2_d(d1, d2), t2 = mc_slope_x2_d(d2, d3);
+        double* qm = xs ? sQx + GBH_IX((v * M + line) * (M + 2) + c0, 10 * QX)
+                        : sQy + GBH_IX((v * (M + 2) + c0) * M + line, 10 * QX);
+        const int os = xs ? 1 : M;                    // next slope cell
+        const int op = 5 * QX;                        // plus states follow the minus states
+        qm[0] = fma(-0.25, t0, q1);
+        qm[op] = fma(0.25, t0, q1);
+        if (two) {
+          qm[os] = fma(-0.25, t1, q2);
+          qm[os + op] = fma(0.25, t1, q2);
         }
-      } else {
-        const int s2 = s - QX;
-        const int i = s2 % M, jj = s2 / M;             // slope cell j = jj - 1
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const double* col = sW + (v * P + jj) * P + i + 2;
-          const double q0 = col[P];
-          const double t = mc_slope_x2(col[0], q0, col[2 * P]);
-          sQy[GBH_IX((v * (M + 2) + jj) * M + i, 10 * QX)] = fma(-0.25, t, q0);
-          sQy[GBH_IX(((5 + v) * (M + 2) + jj) * M + i, 10 * QX)] = fma(0.25, t, q0);
+        if (three) {
+          qm[2 * os] = fma(-0.25, t2, q3);
+          qm[2 * os + op] = fma(0.25, t2, q3);
         }
       }
     }

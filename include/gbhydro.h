@@ -203,6 +203,13 @@ int hydro_stage_vjp(gbh_ctx *ctx, const double *U, const double *M, double scale
                     const double *B, double cB, double *out, void *stream);
 int hydro_step_adjoint(gbh_ctx *ctx, const double *Un, double dt, const double *lam_next, double *lam_prev,
                        void *stream);
+
+/* The same with the first-stage state U1 = Un + dt L(Un) of that step given
+ * (DEVICE, e.g. kept while recomputing a checkpointed segment with
+ * hydro_stage), which saves the stage the call would otherwise recompute.
+ * U1 is read only; lam_prev must not overlap Un or U1. */
+int hydro_step_adjoint_stored(gbh_ctx *ctx, const double *Un, const double *U1, double dt, const double *lam_next,
+                              double *lam_prev, void *stream);
 int hydro_prim_to_cons(gbh_ctx *ctx, const double *W, double *U, void *stream);
 int hydro_prim_to_cons_vjp(gbh_ctx *ctx, const double *W, const double *lamU, double *lamW, void *stream);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "hydro_stage_vjp": (C.c_int, [_vp, _dp, _dp, C.c_double, _dp, C.c_double, _dp, C.c_double, _dp, _vp]),
     "hydro_step_adjoint": (C.c_int, [_vp, _dp, C.c_double, _dp, _dp, _vp]),
+    "hydro_step_adjoint_stored": (C.c_int, [_vp, _dp, _dp, C.c_double, _dp, _dp, _vp]),
     "hydro_prim_to_cons": (C.c_int, [_vp, _dp, _dp, _vp]),
     "hydro_prim_to_cons_vjp": (C.c_int, [_vp, _dp, _dp, _dp, _vp]),
     "gbh_destroy": (C.c_int, [_vp]),

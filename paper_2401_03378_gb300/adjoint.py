@@ -2,9 +2,10 @@
 
 The forward run advances nsteps SSP-RK2 steps with the CFL dt on the device,
 keeping a copy of the state every `every` steps (checkpoints) and the dt of
-every step.  The reverse sweep recomputes each segment's states from its
-checkpoint (hydro_step with the recorded dt, bitwise the forward states) and
-applies hydro_step_adjoint backwards.  dt is held fixed (its dependence on the
+every step.  The reverse sweep recomputes each segment from its checkpoint
+stage by stage (hydro_stage with the recorded dt: the same launches as
+hydro_step, so bitwise the forward states), keeping every step's state and
+first-stage state, and applies hydro_step_adjoint_stored backwards.  dt is held fixed (its dependence on the
 state is not differentiated) and every branch keeps its forward decision.
 All arithmetic runs in libgbhydro's kernels; this module only schedules them.
 """
@@ -43,13 +44,18 @@ class CheckpointedRun:
         lam = lam_final.clone().contiguous()
         for start in reversed(range(0, self.nsteps, self.every)):
             end = min(start + self.every, self.nsteps)
-            states = [self.checkpoints[start].clone()]
-            for s in range(start, end - 1):
-                X = states[-1].clone()
-                self.h.step(X, self.dts[s])
-                states.append(X)
+            states, firsts = [self.checkpoints[start].clone()], []
+            for s in range(start, end):
+                X, dt = states[-1], self.dts[s]
+                U1 = torch.empty_like(X)
+                self.h.stage(X, None, U1, dt, 0.0, 1.0)
+                firsts.append(U1)
+                if s < end - 1:
+                    Xn = X.clone()
+                    self.h.stage(U1, X, Xn, dt, 0.5, 0.5)
+                    states.append(Xn)
             for s in reversed(range(start, end)):
-                self.h.step_adjoint(states[s - start], self.dts[s], lam, lam)
+                self.h.step_adjoint(states[s - start], self.dts[s], lam, lam, U1=firsts[s - start])
         return lam
 
 

@@ -74,6 +74,7 @@ struct gbh_ctx {
   // adjoint buffers (allocated on first use): per-face adjoint slots, intermediate adjoint
   double* d_adj_lamW = nullptr;
   double* d_adj_tmp = nullptr;
+  double* d_adj_prim = nullptr;     // primitives of the state a VJP linearises about
   // pipelined host-buffer step (hydro_step_host), set up on first use: chunks
   // of consecutive blocks, the highest chunk any face neighbour of a chunk
   // lives in, streams (copy in, stage 1, stage 2, copy out) and events
@@ -336,6 +337,7 @@ int ensure_adjoint_buffers(gbh_ctx* c) {
   cudaError_t e = cudaSuccess;
   if (!c->d_adj_lamW) e = cudaMalloc(&c->d_adj_lamW, sizeof(double) * gbh::stage_vjp_scratch_doubles(c->lay));
   if (e == cudaSuccess && !c->d_adj_tmp) e = cudaMalloc(&c->d_adj_tmp, bytes);
+  if (e == cudaSuccess && !c->d_adj_prim) e = cudaMalloc(&c->d_adj_prim, bytes);
   if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
   return GBH_OK;
 }
@@ -848,32 +850,48 @@ int hydro_stage_vjp(gbh_ctx* c, const double* U, const double* M, double scale, 
   if ((out < U + n && U < out + n) || (out < M + n && M < out + n))
     return set_err(c, GBH_ERR_INVAL, "out must not overlap U or M");
   if ((rc = ensure_adjoint_buffers(c))) return rc;
-  return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, U), M, scale, A, cA, B, cB, c->d_adj_lamW, out,
+  return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, U), M, scale, A, cA, B, cB, c->d_adj_lamW, c->d_adj_prim, out,
                                            (cudaStream_t)stream), "stage VJP launch");
 }
 
-int hydro_step_adjoint(gbh_ctx* c, const double* Un, double dt, const double* lam_next, double* lam_prev,
-                       void* stream) {
+static int step_adjoint_common(gbh_ctx* c, const double* Un, const double* U1, double dt, const double* lam_next,
+                               double* lam_prev, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if ((rc = adjoint_supported(c))) return rc;
   if ((rc = check_dt(c, dt))) return rc;
-  if (!Un || !lam_next || !lam_prev || !aligned8(Un) || !aligned8(lam_next) || !aligned8(lam_prev))
+  if (!Un || !lam_next || !lam_prev || !aligned8(Un) || !aligned8(lam_next) || !aligned8(lam_prev) ||
+      (U1 && !aligned8(U1)))
     return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
   const long long n = state_elems(c->lay);
   if (lam_prev < Un + n && Un < lam_prev + n) return set_err(c, GBH_ERR_INVAL, "lam_prev must not overlap Un");
+  if (U1 && lam_prev < U1 + n && U1 < lam_prev + n) return set_err(c, GBH_ERR_INVAL, "lam_prev must not overlap U1");
   if ((rc = ensure_adjoint_buffers(c))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  // U1 = Un + dt L(Un) (recomputed forward stage)
-  rc = stage_launch(c, Un, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
-  if (rc) return rc;
+  if (!U1) {
+    // U1 = Un + dt L(Un) (recomputed forward stage)
+    rc = stage_launch(c, Un, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
+    if (rc) return rc;
+    U1 = c->d_scratch;
+  }
   // U^{n+1} = 1/2 Un + 1/2 (U1 + dt L(U1)):  lam_U1 = 1/2 lam + J_L(U1)^T (dt/2 lam)
-  rc = cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, c->d_scratch), lam_next, 0.5 * dt, lam_next, 0.5, nullptr, 0.0,
-                                         c->d_adj_lamW, c->d_adj_tmp, s), "stage VJP launch");
+  rc = cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, U1), lam_next, 0.5 * dt, lam_next, 0.5, nullptr, 0.0,
+                                         c->d_adj_lamW, c->d_adj_prim, c->d_adj_tmp, s), "stage VJP launch");
   if (rc) return rc;
   // lam_n = 1/2 lam + lam_U1 + J_L(Un)^T (dt lam_U1)
   return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, Un), c->d_adj_tmp, dt, lam_next, 0.5, c->d_adj_tmp, 1.0,
-                                           c->d_adj_lamW, lam_prev, s), "stage VJP launch");
+                                           c->d_adj_lamW, c->d_adj_prim, lam_prev, s), "stage VJP launch");
+}
+
+int hydro_step_adjoint(gbh_ctx* c, const double* Un, double dt, const double* lam_next, double* lam_prev,
+                       void* stream) {
+  return step_adjoint_common(c, Un, nullptr, dt, lam_next, lam_prev, stream);
+}
+
+int hydro_step_adjoint_stored(gbh_ctx* c, const double* Un, const double* U1, double dt, const double* lam_next,
+                              double* lam_prev, void* stream) {
+  if (!U1) return set_err(c, GBH_ERR_INVAL, "U1 is NULL");
+  return step_adjoint_common(c, Un, U1, dt, lam_next, lam_prev, stream);
 }
 
 int hydro_prim_to_cons(gbh_ctx* c, const double* W, double* U, void* stream) {
@@ -919,6 +937,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_problem);
   cudaFree(c->d_adj_lamW);
   cudaFree(c->d_adj_tmp);
+  cudaFree(c->d_adj_prim);
   cudaFree(c->d_smax_own);
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

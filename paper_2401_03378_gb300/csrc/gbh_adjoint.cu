@@ -107,7 +107,8 @@ __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos&
   const double hL = fma(0.5 * rL, kL, e.g_gm1 * pL);
   const double hR = fma(0.5 * rR, kR, e.g_gm1 * pR);
   const double zL = e.gamma * pL * iL, zR = e.gamma * pR * iR;
-  const double cL = sqrt_nr(zL), cR = sqrt_nr(zR);
+  const double qL = rsqrt_nr(zL), qR = rsqrt_nr(zR);   // 1/c (kept for the reverse)
+  const double cL = zL * qL, cR = zR * qR;
   const double w = rcp_nr(sL + sR);
   const double wl = sL * w, wr = sR * w;
   const double ut = fma(wl, uL, wr * uR);
@@ -117,7 +118,8 @@ __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos&
   const double Ht = T * w;
   const double kt = fma(wt, wt, fma(vt, vt, ut * ut));
   const double zc = e.gm1 * fma(-0.5, kt, Ht);
-  const double ct = sqrt_nr(zc);
+  const double qc = rsqrt_nr(zc);
+  const double ct = zc * qc;
   const double l1 = uL - cL, l2 = ut - ct, r1 = uR + cR, r2 = ut + ct;
   const bool selL1 = !(order_key(l2) < order_key(l1));   // SL = l1
   const bool selR1 = !(order_key(r1) < order_key(r2));   // SR = r1
@@ -182,7 +184,7 @@ __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos&
   double but = 0, bct = 0, bcL = 0, bcR = 0;
   if (selL1) { buL += bSL; bcL -= bSL; } else { but += bSL; bct -= bSL; }
   if (selR1) { buR += bSR; bcR += bSR; } else { but += bSR; bct += bSR; }
-  const double bzc = bct * 0.5 * rcp_nr(ct);
+  const double bzc = bct * 0.5 * qc;
   const double bHt = bzc * e.gm1, bkt = -0.5 * bzc * e.gm1;
   but += 2.0 * ut * bkt;
   const double bvt = 2.0 * vt * bkt, bwt = 2.0 * wt * bkt;
@@ -200,7 +202,7 @@ __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos&
   const double bss = -bw * w * w;
   bsL += bss;
   bsR += bss;
-  const double bzL = bcL * 0.5 * rcp_nr(cL), bzR = bcR * 0.5 * rcp_nr(cR);
+  const double bzL = bcL * 0.5 * qL, bzR = bcR * 0.5 * qR;
   bpL += bzL * e.gamma * iL;
   bpR += bzR * e.gamma * iR;
   const double biL = bzL * e.gamma * pL, biR = bzR * e.gamma * pR;
@@ -252,8 +254,9 @@ __device__ __forceinline__ long long own_offset(const Layout& L, int b, int i, i
 }
 
 template <int N, int d>
-__device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G, const double* __restrict__ M,
-                                          double scale, double* __restrict__ C, long long t) {
+__device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G, const double* __restrict__ Wp,
+                                          const double* __restrict__ M, double scale, double* __restrict__ C,
+                                          long long t) {
   const Layout& L = a.lay;
   const int nf = G.n[d] + 1;
   const int k = (int)(t % nf);
@@ -270,8 +273,11 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   double W[4][5];
   int ci, cj, ck;
   for (int s = 0; s < 4; ++s) {
+    // primitives of the stencil position (the halo gathered as in the stage kernel)
     pencil_to_cell(d, k - 2 + s, p1, p2, ci, cj, ck);
-    load_prim<N>(a, b, ci, cj, ck, W[s]);
+    const long long o = cell_offset<N>(a, b, ci, cj, ck);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) W[s][v] = __ldg(Wp + o + v * L.vstride);
   }
   double h0[5], h1[5];
   int b0[5], b1[5];
@@ -322,19 +328,44 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) vjp_face_kernel(const StageArgs a, const FaceGeom G, const double* __restrict__ M,
+__global__ void __launch_bounds__(128) vjp_face_kernel(const StageArgs a, const FaceGeom G,
+                                                      const double* __restrict__ Wp, const double* __restrict__ M,
                                                       double scale, double* __restrict__ C) {
   const Layout& L = a.lay;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   for (int d = 0; d < L.ndim; ++d) {
     const long long count = (long long)L.nblocks * G.n1[d] * G.n2[d] * (G.n[d] + 1);
     if (t < count) {
-      if (d == 0) face_work<N, 0>(a, G, M, scale, C, t);
-      else if (d == 1) face_work<N, 1>(a, G, M, scale, C, t);
-      else face_work<N, 2>(a, G, M, scale, C, t);
+      if (d == 0) face_work<N, 0>(a, G, Wp, M, scale, C, t);
+      else if (d == 1) face_work<N, 1>(a, G, Wp, M, scale, C, t);
+      else face_work<N, 2>(a, G, Wp, M, scale, C, t);
       return;
     }
     t -= count;
+  }
+}
+
+// Primitives of every interior cell of Uin (cons_to_prim, floors as in the
+// stage kernel) into Wp, state layout; the face pass gathers them.
+__global__ void vjp_prim_kernel(const StageArgs a, double* __restrict__ Wp) {
+  const Layout& L = a.lay;
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * L.nblocks;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    long long r = t % per;
+    const int i = (int)(r % L.nx);
+    r /= L.nx;
+    const int j = (int)(r % L.ny);
+    const int k = (int)(r / L.ny);
+    const long long o = own_offset(L, b, i, j, k);
+    double U[5], W[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
+    cons_to_prim(U, W, a.eos);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Wp[o + v * L.vstride] = W[v];
   }
 }
 
@@ -474,19 +505,22 @@ size_t stage_vjp_scratch_doubles(const Layout& L) {
 }
 
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,
-                             const double* B, double cB, double* C, double* out, cudaStream_t s) {
+                             const double* B, double cB, double* C, double* Wp, double* out, cudaStream_t s) {
   const Layout& L = a.lay;
   const FaceGeom G = face_geom(L);
+  vjp_prim_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(a, Wp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   long long faces = 0;
   for (int d = 0; d < L.ndim; ++d) faces += (long long)L.nblocks * G.n1[d] * G.n2[d] * (G.n[d] + 1);
   const unsigned grid = (unsigned)((faces + 127) / 128);
   switch (L.nx) {
-    case 4: vjp_face_kernel<4><<<grid, 128, 0, s>>>(a, G, M, scale, C); break;
-    case 8: vjp_face_kernel<8><<<grid, 128, 0, s>>>(a, G, M, scale, C); break;
-    case 16: vjp_face_kernel<16><<<grid, 128, 0, s>>>(a, G, M, scale, C); break;
+    case 4: vjp_face_kernel<4><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 8: vjp_face_kernel<8><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 16: vjp_face_kernel<16><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vjp_cell_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(a, G, C, A, cA, B, cB, out);
   return cudaGetLastError();

@@ -129,7 +129,7 @@ cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long lon
 
 size_t stage_vjp_scratch_doubles(const Layout& L);   // face-slot buffer of launch_stage_vjp
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,
-                             const double* B, double cB, double* C, double* out, cudaStream_t s);
+                             const double* B, double cB, double* C, double* Wp, double* out, cudaStream_t s);
 cudaError_t launch_prim_to_cons(const Layout& L, const Eos& e, const double* W, double* U, const double* lamU,
                                 double* lamW, cudaStream_t s);
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);

@@ -198,13 +198,20 @@ class Hydro:
         self._check(self.lib.gbh_set_rk_stages(self.ctx, int(nstages)))
 
     # -- adjoint ------------------------------------------------------------
-    def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None):
-        """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen)."""
+    def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None, U1=None):
+        """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen).
+        U1: that step's first-stage state if the caller kept it (saves a stage)."""
         if lam_prev is None:
             lam_prev = torch.zeros_like(lam_next)
-        self._check(self.lib.hydro_step_adjoint(self.ctx, self._state(Un, "Un"), float(dt),
-                                                self._state(lam_next, "lam_next"), self._state(lam_prev, "lam_prev"),
-                                                _stream_handle()))
+        if U1 is None:
+            rc = self.lib.hydro_step_adjoint(self.ctx, self._state(Un, "Un"), float(dt),
+                                             self._state(lam_next, "lam_next"), self._state(lam_prev, "lam_prev"),
+                                             _stream_handle())
+        else:
+            rc = self.lib.hydro_step_adjoint_stored(self.ctx, self._state(Un, "Un"), self._state(U1, "U1"), float(dt),
+                                                    self._state(lam_next, "lam_next"),
+                                                    self._state(lam_prev, "lam_prev"), _stream_handle())
+        self._check(rc)
         return lam_prev
 
     def stage_vjp(self, U, M, scale: float, A=None, cA: float = 0.0, B=None, cB: float = 0.0, out=None):

@@ -130,10 +130,18 @@ class ClockSampler:
 
 
 def source_hash():
+    """Hash of what the stage kernel compiles from: its sources, the headers it
+    includes and the definitions of Layout, Eos and StageArgs."""
     h = hashlib.sha256()
-    for rel in ("gbh_stage.cu", "gbh_device.cuh", "gbh_gather.cuh", "gbh_internal.h"):
-        with open(os.path.join(ROOT, "paper_2401_03378_gb300", "csrc", rel), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_2401_03378_gb300", "csrc")
+    for rel in ("gbh_stage.cu", "gbh_device.cuh", "gbh_fastmath.cuh", "gbh_gather.cuh", "gbh_check.cuh"):
+        with open(os.path.join(csrc, rel), "rb") as f:
             h.update(f.read())
+    with open(os.path.join(csrc, "gbh_internal.h")) as f:
+        text = f.read()
+    a = text.index("struct Layout {")
+    b = text.index("};", text.index("struct StageArgs {")) + 2
+    h.update(text[a:b].encode())
     return h.hexdigest()[:16]
 
 

@@ -194,6 +194,33 @@ def test_sedov_3d_256_50_steps_sampled(gb):
     assert h.floor_hits() == 0
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("ng,stages,tele", [(4, 2, True), (4, 3, False), (6, 3, True)])
+def test_sedov_3d_256_variants_sampled(gb, ng, stages, tele):
+    """The stepper variants bench.py times at 256^3 (telescoping two-stage,
+    three-stage, telescoping three-stage on 6 guard cells), in that launch
+    configuration: 19 steps with the device dt, then step 20 against the
+    oracle's step of the same variant from the GPU's state."""
+    lat = wl.lattice_3d(16, 16, 16, 16, 16, 16, ng)
+    U0 = wl.sedov(lat)
+    h = gb.Hydro.from_lattice(lat)
+    h.set_rk_stages(stages)
+    h.set_telescoping(tele)
+    Ug = dev(U0)
+    dt = h.compute_dt(Ug)
+    h.advance(Ug, 19, dt)
+    snap = host(Ug)
+    o = Oracle(lat)
+    dt_o = o.compute_dt(snap)
+    assert abs(float(host(dt)[0]) / dt_o - 1) <= TOL_DT
+    ref = snap.copy()
+    o.step(ref, dt_o, telescoping=tele, stages=stages)
+    h.step(Ug, dt_o)
+    assert np.all(interior_err(host(Ug), ref, lat) <= TOL_TINY)
+    assert h.floor_hits() == 0
+    h.close()
+
+
 def test_poisoned_guards_have_no_effect(gb):
     lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, 4)
     U = wl.random_state(lat, seed=9)

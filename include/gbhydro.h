@@ -308,6 +308,11 @@ int hydro_advance_host(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist
  * hydro_step_cfl's bit for bit. */
 int hydro_step_host(gbh_ctx *ctx, double *U_host, double *dt_host, void *stream);
 
+/* Number of block chunks hydro_step_host pipelines (1..64); 0 (the default)
+ * picks the fewest chunks of at most two resident CTAs per SM, one wave of the
+ * stage kernel each.  GBH_ERR_INVAL outside [0, 64]. */
+int gbh_set_host_pipeline(gbh_ctx *ctx, int chunks);
+
 /* Scan the interior of U: counts cells whose density <= small_rho, pressure
  * <= small_p, or any variable is non-finite.  Synchronises the stream, writes
  * the count to *nbad_host and returns GBH_ERR_UNPHYSICAL if it is non-zero. */

@@ -80,6 +80,7 @@ struct gbh_ctx {
   // lives in, streams (copy in, stage 1, stage 2, copy out) and events
   std::vector<int> h_face;          // host copy of the face table
   int pipe_chunks = 0;
+  int pipe_chunks_wanted = 0;       // gbh_set_host_pipeline (0: about two CTAs per SM per chunk)
   std::vector<int> pipe_first, pipe_need;
   cudaStream_t pipe_stream[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> pipe_ev;   // [3][chunks]: copied in, stage 1 done, stage 2 done
@@ -770,6 +771,17 @@ static int ensure_step_buffers(gbh_ctx* c, bool telescoping, int nstages) {
   return GBH_OK;
 }
 
+int gbh_set_host_pipeline(gbh_ctx* c, int chunks) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (chunks < 0 || chunks > 64) return set_err(c, GBH_ERR_INVAL, "chunks must be in [0, 64] (got %d)", chunks);
+  for (cudaEvent_t ev : c->pipe_ev) cudaEventDestroy(ev);
+  c->pipe_ev.clear();
+  c->pipe_chunks = 0;          // chunks and events are set up again on the next hydro_step_host
+  c->pipe_chunks_wanted = chunks;
+  return GBH_OK;
+}
+
 int gbh_set_telescoping(gbh_ctx* c, int enable) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -1086,9 +1098,12 @@ static int pipe_setup(gbh_ctx* c) {
   if (c->pipe_chunks) return GBH_OK;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  // chunks of about two resident CTAs per SM, at most 64
-  int K = NB / (2 * (sms > 0 ? sms : 1));
-  K = K < 1 ? 1 : (K > 64 ? 64 : K);
+  // chunks of at most two resident CTAs per SM (one wave of the stage kernel; a
+  // chunk a few CTAs larger would leave a nearly empty second wave), at most 64
+  // chunks (or the count set)
+  const int wave = 2 * (sms > 0 ? sms : 1);
+  int K = c->pipe_chunks_wanted > 0 ? c->pipe_chunks_wanted : (NB + wave - 1) / wave;
+  K = K < 1 ? 1 : (K > 64 ? 64 : (K > NB ? NB : K));
   c->pipe_first.resize(K + 1);
   for (int k = 0; k <= K; ++k) c->pipe_first[k] = (int)((long long)NB * k / K);
   std::vector<int> chunk_of(NB);
@@ -1104,17 +1119,19 @@ static int pipe_setup(gbh_ctx* c) {
       }
     c->pipe_need[k] = m;
   }
-  std::vector<int> ident(NB);
-  for (int b = 0; b < NB; ++b) ident[b] = b;
-  e = cudaMalloc(&c->d_ident, sizeof(int) * NB);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_ident, ident.data(), sizeof(int) * NB, cudaMemcpyHostToDevice);
+  if (!c->d_ident) {
+    std::vector<int> ident(NB);
+    for (int b = 0; b < NB; ++b) ident[b] = b;
+    e = cudaMalloc(&c->d_ident, sizeof(int) * NB);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_ident, ident.data(), sizeof(int) * NB, cudaMemcpyHostToDevice);
+  }
   for (cudaStream_t& st : c->pipe_stream)
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !st) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   c->pipe_ev.assign(3 * (size_t)K, nullptr);
   for (cudaEvent_t& ev : c->pipe_ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   for (cudaEvent_t& ev : c->pipe_mark)
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) return set_err(c, GBH_ERR_CUDA, "host-step setup: %s", cudaGetErrorString(e));
   c->pipe_chunks = K;
   return GBH_OK;

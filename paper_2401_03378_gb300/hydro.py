@@ -261,6 +261,10 @@ class Hydro:
                                              _stream_handle()))
         return U_host
 
+    def set_host_pipeline(self, chunks: int = 0):
+        """Block chunks of step_host (0: the fewest chunks of one stage-kernel wave each)."""
+        self._check(self.lib.gbh_set_host_pipeline(self.ctx, int(chunks)))
+
     def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
         """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
         ptr = self._host_state(U_host)

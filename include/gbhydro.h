@@ -171,8 +171,9 @@ int gbh_set_telescoping(gbh_ctx *ctx, int enable);
  * b) and level-by-level telescoping (correction weights 1/6, 1/6, 2/3).
  * Allocates a second scratch state (and flux registers) on first use.
  * Errors: GBH_ERR_INVAL for other values or too few guard cells for the
- * telescoping mode; GBH_ERR_NOMEM.  The adjoint is of the two-stage step
- * (GBH_ERR_UNSUPPORTED otherwise).  Drops a captured graph. */
+ * telescoping mode; GBH_ERR_NOMEM.  hydro_step_adjoint follows the stage
+ * count; hydro_step_adjoint_stored is of the two-stage step only.  Drops a
+ * captured graph. */
 int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
 
 /* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
@@ -194,9 +195,12 @@ int hydro_advance_graph(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, voi
  *   flux-difference operator evaluated at U (guard data gathered from the
  *   neighbours as in hydro_stage).  A and B may be NULL; out may equal A or B
  *   but must not overlap U or M.
- * hydro_step_adjoint: given lam_next = dJ/dU^{n+1} of one hydro_step(Un, dt),
- *   writes lam_prev = dJ/dU^n (recomputes the intermediate stage; lam_prev
- *   may equal lam_next, must not overlap Un).
+ * hydro_step_adjoint: given lam_next = dJ/dU^{n+1} of one hydro_step(Un, dt)
+ *   with the context's stage count (2 or 3; the non-telescoping step),
+ *   writes lam_prev = dJ/dU^n: the Shu-Osher recursion run backwards,
+ *   lam_{s-1} = b_s lam_s + J_L(U(s-1))^T (b_s dt lam_s), with U^n also
+ *   collecting a_s lam_s from every stage (recomputes the intermediate
+ *   stages; lam_prev may equal lam_next, must not overlap Un).
  * hydro_prim_to_cons: U = conserved(W) on interior cells, W = (rho, u, v, w, p)
  *   in the state layout; hydro_prim_to_cons_vjp: lamW = (dU/dW)^T lamU. */
 int hydro_stage_vjp(gbh_ctx *ctx, const double *U, const double *M, double scale, const double *A, double cA,
@@ -207,7 +211,8 @@ int hydro_step_adjoint(gbh_ctx *ctx, const double *Un, double dt, const double *
 /* The same with the first-stage state U1 = Un + dt L(Un) of that step given
  * (DEVICE, e.g. kept while recomputing a checkpointed segment with
  * hydro_stage), which saves the stage the call would otherwise recompute.
- * U1 is read only; lam_prev must not overlap Un or U1. */
+ * U1 is read only; lam_prev must not overlap Un or U1.  Two-stage contexts
+ * only (GBH_ERR_UNSUPPORTED otherwise). */
 int hydro_step_adjoint_stored(gbh_ctx *ctx, const double *Un, const double *U1, double dt, const double *lam_next,
                               double *lam_prev, void *stream);
 int hydro_prim_to_cons(gbh_ctx *ctx, const double *W, double *U, void *stream);

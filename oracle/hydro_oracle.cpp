@@ -961,34 +961,47 @@ void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale,
       }
 }
 
-/* dJ/dU^n of one SSP-RK2 step (dt held fixed) from dJ/dU^{n+1}. */
-void step_adjoint(const OrcGrid& G, const double* Un, double dt, const double* lam, double* lam_prev) {
+/* dJ/dU^n of one SSP-RK step of S stages (dt held fixed) from dJ/dU^{n+1}:
+ * the Shu-Osher recursion U(s) = a_s U^n + b_s (U(s-1) + dt L(U(s-1))) run
+ * backwards.  With lam_S = lam the adjoint of U(S) = U^{n+1},
+ *   lam_{s-1} = b_s lam_s + J_L(U(s-1))^T (b_s dt lam_s),
+ * and U^n collects lam_0 plus a_s lam_s from every stage. */
+void step_adjoint(const OrcGrid& G, const double* Un, double dt, const double* lam, double* lam_prev,
+                  int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
   const Geo geo(G);
   const ll total = geo.nblocks() * 5 * geo.cells;
-  std::vector<double> U0(Un, Un + total), U1(total), tmp(total, 0.0), j1(total, 0.0), j0(total, 0.0);
-  fill_guardcells(G, U0.data());
-  std::memcpy(U1.data(), U0.data(), total * sizeof(double));
-  stage(G, U0.data(), nullptr, U1.data(), dt, 0.0, 1.0, nullptr, 0);
-  fill_guardcells(G, U1.data());
-  /* lam_U1 = 1/2 lam + J_L(U1)^T (dt/2 lam) */
-  stage_vjp(G, U1.data(), lam, 0.5 * dt, j1.data());
+  /* forward: X[s] = U(s) with filled guard cells, s = 0 .. S-1 */
+  std::vector<std::vector<double>> X(r.S);
+  X[0].assign(Un, Un + total);
+  fill_guardcells(G, X[0].data());
+  for (int st = 1; st < r.S; ++st) {
+    X[st] = X[st - 1];
+    stage(G, X[st - 1].data(), X[0].data(), X[st].data(), dt, r.a[st - 1], r.b[st - 1], nullptr, 0);
+    fill_guardcells(G, X[st].data());
+  }
+  std::vector<double> cur(lam, lam + total), acc(total, 0.0), jt(total, 0.0);
+  for (int st = r.S - 1; st >= 0; --st) {
+    /* stage st maps U(st) to U(st+1) with (a, b) = (r.a[st], r.b[st]) */
+    std::fill(jt.begin(), jt.end(), 0.0);
+    stage_vjp(G, X[st].data(), cur.data(), r.b[st] * dt, jt.data());
+    for (ll b = 0; b < geo.nblocks(); ++b)
+      for (int v = 0; v < 5; ++v)
+        for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+          for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+            for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+              const ll o = geo.at(b, v, k, j, i);
+              acc[o] = acc[o] + r.a[st] * cur[o];
+              cur[o] = r.b[st] * cur[o] + jt[o];
+            }
+  }
   for (ll b = 0; b < geo.nblocks(); ++b)
     for (int v = 0; v < 5; ++v)
       for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
         for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
           for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
             const ll o = geo.at(b, v, k, j, i);
-            tmp[o] = 0.5 * lam[o] + j1[o];
-          }
-  /* lam_n = 1/2 lam + lam_U1 + J_L(U^n)^T (dt lam_U1) */
-  stage_vjp(G, U0.data(), tmp.data(), dt, j0.data());
-  for (ll b = 0; b < geo.nblocks(); ++b)
-    for (int v = 0; v < 5; ++v)
-      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
-        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
-          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
-            const ll o = geo.at(b, v, k, j, i);
-            lam_prev[o] = 0.5 * lam[o] + tmp[o] + j0[o];
+            lam_prev[o] = acc[o] + cur[o];
           }
 }
 
@@ -1149,6 +1162,14 @@ void orc_stage_vjp(const OrcGrid* G, const double* U, const double* M, double sc
 
 void orc_step_adjoint(const OrcGrid* G, const double* Un, double dt, const double* lam_next, double* lam_prev) {
   step_adjoint(*G, Un, dt, lam_next, lam_prev);
+}
+
+/* The same for nstages (2 or 3) stages; -1 if nstages is invalid. */
+int orc_step_adjoint_rk(const OrcGrid* G, const double* Un, double dt, const double* lam_next, double* lam_prev,
+                        int nstages) {
+  if (nstages != 2 && nstages != 3) return -1;
+  step_adjoint(*G, Un, dt, lam_next, lam_prev, nstages);
+  return 0;
 }
 
 }  // extern "C"

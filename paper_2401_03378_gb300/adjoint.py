@@ -42,6 +42,8 @@ class CheckpointedRun:
 
     def backward(self, lam_final: torch.Tensor) -> torch.Tensor:
         lam = lam_final.clone().contiguous()
+        if self.h.nstages != 2:
+            return self._backward_recompute(lam)
         for start in reversed(range(0, self.nsteps, self.every)):
             end = min(start + self.every, self.nsteps)
             states, firsts = [self.checkpoints[start].clone()], []
@@ -56,6 +58,20 @@ class CheckpointedRun:
                     states.append(Xn)
             for s in reversed(range(start, end)):
                 self.h.step_adjoint(states[s - start], self.dts[s], lam, lam, U1=firsts[s - start])
+        return lam
+
+    def _backward_recompute(self, lam: torch.Tensor) -> torch.Tensor:
+        """Three-stage contexts: the segment's states by hydro_step, each step's
+        adjoint recomputing its intermediate stages."""
+        for start in reversed(range(0, self.nsteps, self.every)):
+            end = min(start + self.every, self.nsteps)
+            states = [self.checkpoints[start].clone()]
+            for s in range(start, end - 1):
+                X = states[-1].clone()
+                self.h.step(X, self.dts[s])
+                states.append(X)
+            for s in reversed(range(start, end)):
+                self.h.step_adjoint(states[s - start], self.dts[s], lam, lam)
         return lam
 
 

@@ -75,6 +75,7 @@ struct gbh_ctx {
   double* d_adj_lamW = nullptr;
   double* d_adj_tmp = nullptr;
   double* d_adj_prim = nullptr;     // primitives of the state a VJP linearises about
+  double* d_adj_tmp2 = nullptr;     // second intermediate adjoint (three stages)
   // pipelined host-buffer step (hydro_step_host), set up on first use: chunks
   // of consecutive blocks, the highest chunk any face neighbour of a chunk
   // lives in, streams (copy in, stage 1, stage 2, copy out) and events
@@ -339,6 +340,7 @@ int ensure_adjoint_buffers(gbh_ctx* c) {
   if (!c->d_adj_lamW) e = cudaMalloc(&c->d_adj_lamW, sizeof(double) * gbh::stage_vjp_scratch_doubles(c->lay));
   if (e == cudaSuccess && !c->d_adj_tmp) e = cudaMalloc(&c->d_adj_tmp, bytes);
   if (e == cudaSuccess && !c->d_adj_prim) e = cudaMalloc(&c->d_adj_prim, bytes);
+  if (e == cudaSuccess && c->nstages == 3 && !c->d_adj_tmp2) e = cudaMalloc(&c->d_adj_tmp2, bytes);
   if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
   return GBH_OK;
 }
@@ -355,8 +357,7 @@ gbh::StageArgs vjp_args(gbh_ctx* c, const double* U) {
 
 int adjoint_supported(gbh_ctx* c) {
   if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is not implemented on two-level contexts");
-  if (c->telescoping || c->nstages != 2)
-    return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping two-stage step");
+  if (c->telescoping) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping step");
   if (c->nproblems > 1) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint takes one dt: not on batched contexts");
   return GBH_OK;
 }
@@ -880,6 +881,30 @@ static int step_adjoint_common(gbh_ctx* c, const double* Un, const double* U1, d
   if (U1 && lam_prev < U1 + n && U1 < lam_prev + n) return set_err(c, GBH_ERR_INVAL, "lam_prev must not overlap U1");
   if ((rc = ensure_adjoint_buffers(c))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->nstages == 3) {
+    if (U1) return set_err(c, GBH_ERR_UNSUPPORTED, "the stored-state adjoint is of the two-stage step");
+    // forward: U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
+    rc = stage_launch(c, Un, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
+    if (!rc) rc = stage_launch(c, c->d_scratch, Un, c->d_scratch2, nullptr, dt, 0.75, 0.25, true, false, s);
+    if (rc) return rc;
+    // U^{n+1} = 1/3 Un + 2/3 (U2 + dt L(U2)):  lam_U2 = 2/3 lam + J_L(U2)^T (2/3 dt lam)
+    rc = cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, c->d_scratch2), lam_next, 2.0 / 3.0 * dt, lam_next, 2.0 / 3.0,
+                                           nullptr, 0.0, c->d_adj_lamW, c->d_adj_prim, c->d_adj_tmp2, s),
+                  "stage VJP launch");
+    if (rc) return rc;
+    // lam_U1 = 1/4 lam_U2 + J_L(U1)^T (1/4 dt lam_U2)
+    rc = cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, c->d_scratch), c->d_adj_tmp2, 0.25 * dt, c->d_adj_tmp2, 0.25,
+                                           nullptr, 0.0, c->d_adj_lamW, c->d_adj_prim, c->d_adj_tmp, s),
+                  "stage VJP launch");
+    if (rc) return rc;
+    // Un's direct terms 1/3 lam + 3/4 lam_U2, then lam_n = those + lam_U1 + J_L(Un)^T (dt lam_U1)
+    rc = cuda_err(c, gbh::launch_axpby(c->lay, 0.75, c->d_adj_tmp2, 1.0 / 3.0, lam_next, c->d_adj_tmp2, s),
+                  "axpby launch");
+    if (rc) return rc;
+    return cuda_err(c, gbh::launch_stage_vjp(vjp_args(c, Un), c->d_adj_tmp, dt, c->d_adj_tmp, 1.0, c->d_adj_tmp2, 1.0,
+                                             c->d_adj_lamW, c->d_adj_prim, lam_prev, s),
+                    "stage VJP launch");
+  }
   if (!U1) {
     // U1 = Un + dt L(Un) (recomputed forward stage)
     rc = stage_launch(c, Un, nullptr, c->d_scratch, nullptr, dt, 0.0, 1.0, true, false, s);
@@ -950,6 +975,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_adj_lamW);
   cudaFree(c->d_adj_tmp);
   cudaFree(c->d_adj_prim);
+  cudaFree(c->d_adj_tmp2);
   cudaFree(c->d_smax_own);
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -433,6 +433,27 @@ __global__ void vjp_cell_kernel(const StageArgs a, const FaceGeom G, const doubl
   }
 }
 
+// out = a X + b Y on interior cells (state layout; out may alias X or Y).
+__global__ void axpby_kernel(const Layout L, double a, const double* X, double b, const double* Y, double* out) {
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * L.nblocks;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int bk = (int)(t / per);
+    long long r = t % per;
+    const int i = (int)(r % L.nx);
+    r /= L.nx;
+    const int j = (int)(r % L.ny);
+    const int k = (int)(r / L.ny);
+    const long long o = own_offset(L, bk, i, j, k);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const long long ov = o + v * L.vstride;
+      out[ov] = fma(a, X[ov], b * Y[ov]);
+    }
+  }
+}
+
 // W (primitive, state layout) -> U on interior cells, and its adjoint.
 __global__ void prim_to_cons_kernel(const Layout L, const Eos e, const double* W, double* U, const double* lamU,
                                     double* lamW) {
@@ -523,6 +544,12 @@ cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vjp_cell_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(a, G, C, A, cA, B, cB, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(const Layout& L, double a, const double* X, double b, const double* Y, double* out,
+                         cudaStream_t s) {
+  axpby_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(L, a, X, b, Y, out);
   return cudaGetLastError();
 }
 

@@ -130,6 +130,8 @@ cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long lon
 size_t stage_vjp_scratch_doubles(const Layout& L);   // face-slot buffer of launch_stage_vjp
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,
                              const double* B, double cB, double* C, double* Wp, double* out, cudaStream_t s);
+cudaError_t launch_axpby(const Layout& L, double a, const double* X, double b, const double* Y, double* out,
+                         cudaStream_t s);   // out = a X + b Y on interior cells
 cudaError_t launch_prim_to_cons(const Layout& L, const Eos& e, const double* W, double* U, const double* lamU,
                                 double* lamW, cudaStream_t s);
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);

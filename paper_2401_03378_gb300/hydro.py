@@ -80,6 +80,7 @@ class Hydro:
             raise _abi.GbhError(rc, self.lib.gbh_last_error(None).decode())
         self.ctx = ctx
         self.device = torch.cuda.current_device()
+        self.nstages = 2
 
     @classmethod
     def from_lattice(cls, lat, **kw):
@@ -196,6 +197,7 @@ class Hydro:
     def set_rk_stages(self, nstages: int):
         """2 (SSP-RK2, the default) or 3 (SSP-RK3) Shu-Osher stages per step."""
         self._check(self.lib.gbh_set_rk_stages(self.ctx, int(nstages)))
+        self.nstages = int(nstages)
 
     # -- adjoint ------------------------------------------------------------
     def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None, U1=None):

@@ -77,6 +77,42 @@ def test_step_adjoint_matches_oracle(gb, lat):
     assert np.all(err(host(out), ref, lat) <= 1e-10)
 
 
+@pytest.mark.parametrize("lat", LATS[:4])
+def test_three_stage_step_adjoint_matches_oracle(gb, lat):
+    U = wl.random_state(lat, seed=23, rough=False)
+    rng = np.random.default_rng(24)
+    lam = rng.normal(size=U.shape) * mask(lat)
+    o = Oracle(lat)
+    dt = o.compute_dt(U)
+    ref = o.step_adjoint(U, dt, lam, stages=3)
+    h = gb.Hydro.from_lattice(lat)
+    h.set_rk_stages(3)
+    out = h.step_adjoint(dev(U), dt, dev(lam))
+    assert np.all(err(host(out), ref, lat) <= 1e-10)
+
+
+def test_three_stage_checkpointed_gradient(gb):
+    from paper_2401_03378_gb300.adjoint import CheckpointedRun
+    lat = wl.lattice_2d(4, 4, 16, 16, 4)
+    U0 = wl.sod_smooth(lat)
+    lamF = np.random.default_rng(25).normal(size=U0.shape) * mask(lat)
+    h = gb.Hydro.from_lattice(lat)
+    h.set_rk_stages(3)
+    run = CheckpointedRun(h, 6, every=4)
+    run.forward(dev(U0))
+    g = host(run.backward(dev(lamF)))
+    o = Oracle(lat)
+    ost = [U0.copy()]
+    for s in range(6):
+        X = ost[-1].copy()
+        o.step(X, run.dts[s], stages=3)
+        ost.append(X)
+    lo = lamF.copy()
+    for s in reversed(range(6)):
+        lo = o.step_adjoint(ost[s], run.dts[s], lo, stages=3)
+    assert np.all(err(g, lo, lat) <= 1e-9)
+
+
 def test_checkpointed_gradient_equals_unsegmented_and_oracle_chain(gb):
     from paper_2401_03378_gb300.adjoint import CheckpointedRun
     lat = wl.lattice_2d(4, 4, 16, 16, 4)

@@ -170,7 +170,8 @@ def test_errors(gb):
     with pytest.raises(GbhError):
         h.set_telescoping(True)
     U = dev(wl.random_state(lat, seed=2))
-    with pytest.raises(GbhError):
-        h.step_adjoint(U, 1e-4, torch.zeros_like(U))
+    h.step_adjoint(U, 1e-4, torch.zeros_like(U))          # the three-stage adjoint
+    with pytest.raises(GbhError):                          # the stored-state form is two-stage only
+        h.step_adjoint(U, 1e-4, torch.zeros_like(U), U1=U.clone())
     h.set_rk_stages(2)
-    h.step_adjoint(U, 1e-4, torch.zeros_like(U))
+    h.step_adjoint(U, 1e-4, torch.zeros_like(U), U1=U.clone())

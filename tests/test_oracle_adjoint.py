@@ -93,3 +93,39 @@ def test_step_adjoint_linear_in_the_cotangent():
     lhs = o.step_adjoint(U, dt, 2.0 * a - 3.0 * b)
     rhs = 2.0 * o.step_adjoint(U, dt, a) - 3.0 * o.step_adjoint(U, dt, b)
     assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+
+
+@pytest.mark.parametrize("lat", LATS[:2])
+def test_three_stage_step_adjoint_matches_finite_differences(lat):
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=14, rough=False)
+    rng = np.random.default_rng(15)
+    w = rng.normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+
+    def G(V):
+        X = V.copy()
+        o.step(X, dt, stages=3)
+        return float(np.sum(w * X * interior_mask(lat)))
+
+    grad = o.step_adjoint(U, dt, w, stages=3)
+    scale = np.max(np.abs(grad))
+    for c in pick(lat, 12, 16):
+        h = 1e-6 * max(1.0, abs(U[c]))
+        Up, Um = U.copy(), U.copy()
+        Up[c] += h
+        Um[c] -= h
+        fd = (G(Up) - G(Um)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+def test_three_stage_adjoint_differs_from_two_stage():
+    """The stage count enters the adjoint: the three-stage adjoint is not the
+    two-stage one (a planted stage count would be caught)."""
+    lat = LATS[0]
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=17, rough=False)
+    w = np.random.default_rng(18).normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+    a, b = o.step_adjoint(U, dt, w, stages=3), o.step_adjoint(U, dt, w, stages=2)
+    assert np.max(np.abs(a - b)) > 1e-6 * np.max(np.abs(a))

@@ -96,14 +96,9 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
                                   __ldg(a.inv_dx + 3 * b + 2), d3);
     smax = fmax(smax, s);
   }
-  __shared__ double red[kThreads];
-  red[threadIdx.x] = smax;
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(red[0]));
+  __shared__ double red[kThreads / 32];
+  const double m = block_max<kThreads>(smax, red);
+  if (threadIdx.x == 0) atomicMax(a.smax_acc, (unsigned long long)__double_as_longlong(m));
 }
 
 // dt = cfl / smax per problem; also records it and clears the accumulator for
@@ -124,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
   const Layout& L = a.lay;
   const int per = L.nx * L.ny * L.nz;
   const bool d3 = L.ndim == 3;
-  __shared__ double red[kThreads];
+  __shared__ double red[kThreads / 32];
   const int nb = a.block_list ? a.nlist : L.nblocks;
   for (int s = blockIdx.x; s < nb; s += gridDim.x) {
     const int b = a.block_list ? __ldg(a.block_list + s) : s;
@@ -141,13 +136,8 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
       smax = fmax(smax, signal_speed_ir(W, ir, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
                                      __ldg(a.inv_dx + 3 * b + 2), d3));
     }
-    red[threadIdx.x] = smax;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicMax(a.smax_acc + __ldg(problem + b), (unsigned long long)__double_as_longlong(red[0]));
+    const double m = block_max<kThreads>(smax, red);
+    if (threadIdx.x == 0) atomicMax(a.smax_acc + __ldg(problem + b), (unsigned long long)__double_as_longlong(m));
     __syncthreads();
   }
 }

@@ -99,6 +99,30 @@ __device__ __forceinline__ double half_any(double x) {
   return bitsd(mag >= (2LL << 52) ? b - (1LL << 52) : ((b ^ mag) | (mag >> 1)));
 }
 
+// Maximum over the NT threads of a CTA (NT a power of two) of non-negative
+// values: xor shuffles within each warp (over the lanes the CTA has), then
+// the warps' maxima through s_warp[NT/32] and one more warp of shuffles.  The
+// result is valid in thread 0; every thread of the CTA must call it.
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* s_warp) {
+  constexpr int WL = NT < 32 ? NT : 32;
+  constexpr unsigned mask = WL == 32 ? 0xffffffffu : ((1u << WL) - 1u);
+#pragma unroll
+  for (int o = WL / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
+  if constexpr (NT > 32) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      v = lane < NW ? s_warp[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+  }
+  return v;
+}
+
 // Signal-speed sum of one cell for the CFL rule; W from cons_to_prim and
 // ir = 1 / W[0] (cons_to_prim_ir returns it).
 __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, const Eos& e, double idx,

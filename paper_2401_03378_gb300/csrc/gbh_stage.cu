@@ -281,14 +281,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 
   if (hits) atomicAdd(a.floor_count, (unsigned long long)hits);
   if (E == 0 && a.smax_acc) {
-    s_red[tid] = smax;
-    __syncthreads();
-#pragma unroll
-    for (int w = NT / 2; w > 0; w >>= 1) {
-      if (tid < w) s_red[tid] = fmax(s_red[tid], s_red[tid + w]);
-      __syncthreads();
-    }
-    if (tid == 0) atomicMax(a.smax_acc + prob, (unsigned long long)__double_as_longlong(s_red[0]));
+    const double m = block_max<NT>(smax, s_red);   // warp shuffles, then across warps
+    if (tid == 0) atomicMax(a.smax_acc + prob, (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -298,7 +292,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 template <int N, bool DIM3, int E>
 __global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E)) stage_kernel(const StageArgs a) {
   extern __shared__ double smem[];
-  __shared__ double s_red[E == 0 ? N * N : 1];
+  __shared__ double s_red[E == 0 && N * N > 32 ? N * N / 32 : 1];
   const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
   const int first = blockIdx.x * a.items_per_cta;
   const int last = min(nitems, first + a.items_per_cta);

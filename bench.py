@@ -277,6 +277,9 @@ def run_gpu(args):
     ensemble = None
     if args.ensemble_steps > 0:
         ensemble = run_ensemble(args, gb, torch, barrier)
+    tl_ensemble = None
+    if args.tl_ensemble_steps > 0:
+        tl_ensemble = run_two_level_ensemble(args, gb, torch, barrier)
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = run_adjoint(args, gb, torch, barrier)
@@ -331,6 +334,7 @@ def run_gpu(args):
         "e2e": e2e,
         "two_level": two_level,
         "ensemble": ensemble,
+        "two_level_ensemble": tl_ensemble,
         "adjoint": adjoint,
         "variants": variants,
         "unphysical_cells": nbad,
@@ -502,6 +506,69 @@ def run_ensemble(args, gb, torch, barrier):
             "speedup": separate / batched}
 
 
+def run_two_level_ensemble(args, gb, torch, barrier):
+    """Batched two-level ensemble: 12 independent 3-D two-level Sedov problems of
+    uneven sizes (coarse 4^3, 6^3 or 8^3 blocks of 16^3 cells drawn with seed 0,
+    the central half refined), each with its own dt, advanced together as one
+    CUDA graph of batched launches over both levels of all problems -- against
+    a two-level context per problem."""
+    import numpy as np
+    import workloads as wl
+    probs = wl.two_level_ensemble(count=12, seed=0)
+    tls = [t for t, _ in probs]
+    zones = sum(t.leaf_cells for t in tls)
+    n = args.tl_ensemble_steps
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    h = gb.Hydro.from_two_level_batch(tls)
+    U0 = np.concatenate([u for _, u in probs])
+    U = torch.from_numpy(U0).cuda()
+    h.fill_guardcells(U)
+    dt = h.compute_dt(U)
+    h.advance_graph(U, n, dt)          # capture + warm-up run
+    U.copy_(torch.from_numpy(U0))
+    h.fill_guardcells(U)
+    h.compute_dt(U, dt)
+    batched = timed(lambda: h.advance_graph(U, n, dt))
+    nbad = h.check_state(U)
+    h.close()
+    del U
+    torch.cuda.empty_cache()
+    ctxs = [(gb.Hydro.from_two_level(t), torch.from_numpy(u).cuda()) for t, u in probs]
+    dts = []
+    for c, u in ctxs:
+        c.fill_guardcells(u)
+        dts.append(c.compute_dt(u))
+    for (c, u), d in zip(ctxs, dts):
+        c.step_cfl(u, d)
+    def loop():
+        for _ in range(n):
+            for (c, u), d in zip(ctxs, dts):
+                c.step_cfl(u, d)
+    separate = timed(loop)
+    for c, _ in ctxs:
+        c.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    return {"workload": "12 independent 3-D two-level Sedov problems, coarse 4^3/6^3/8^3 blocks (seed 0) of "
+                        "16^3 cells + 4 guards, central half refined, own CFL dt each, FP64",
+            "zones": zones, "blocks": sum(t.nblocks for t in tls), "steps": n,
+            "batched_graph": {"value": zones * n / batched, "unit": UNIT, "ms_per_step": 1e3 * batched / n,
+                              "launches_per_step": 11, "graph_launches": 1, "unphysical_cells": nbad},
+            "one_context_per_problem": {"value": zones * n / separate, "unit": UNIT,
+                                        "ms_per_step": 1e3 * separate / n, "launches_per_step": 11 * len(tls)},
+            "speedup": separate / batched}
+
+
 def run_adjoint(args, gb, torch, barrier):
     """Gradient workload: 2-D Sod-like 256^2 in 16^2 blocks, 50 steps, checkpoint
     every 10; forward (with checkpoints) and adjoint sweep timed separately."""
@@ -603,6 +670,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--two-level-steps", type=int, default=20)
     ap.add_argument("--ensemble-steps", type=int, default=100)
+    ap.add_argument("--tl-ensemble-steps", type=int, default=10)
     ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)

@@ -125,6 +125,18 @@ int gbh_create_refined(const gbh_params *params, const gbh_refinement *refinemen
  * host dt to all problems.  The paper has no batched mode. */
 int gbh_create_batched(const gbh_params *params, const int32_t *problem, int nproblems, gbh_ctx **out);
 
+/* Batched two-level ensembles: independent two-level composite grids (each
+ * with the tables gbh_create_refined takes, block ids offset so that they
+ * index the concatenated arrays) in one context, advanced together with one
+ * launch per kernel for all problems and all levels.  problem[b] is as for
+ * gbh_create_batched; neither a neighbour entry nor a parent may connect
+ * blocks of different problems (GBH_ERR_INVAL).  The time-step rules of
+ * gbh_create_batched apply (dt_dev[nproblems]); the flux correction at each
+ * problem's fine-coarse faces uses that problem's dt.  Everything else is as
+ * for gbh_create_refined.  The paper has no batched mode. */
+int gbh_create_refined_batched(const gbh_params *params, const gbh_refinement *refinement, const int32_t *problem,
+                               int nproblems, gbh_ctx **out);
+
 /* Work decomposition of the stage kernel: kchunk = z planes per work item
  * (3-D; 0 or nzb = the whole block) and items_per_cta = consecutive work
  * items one CTA processes (1 = a CTA per item; a grid of about two CTAs per

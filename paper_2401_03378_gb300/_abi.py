@@ -54,6 +54,8 @@ SIGNATURES = {
     "gbh_create": (C.c_int, [C.POINTER(GbhParams), C.POINTER(_vp)]),
     "gbh_create_refined": (C.c_int, [C.POINTER(GbhParams), C.POINTER(GbhRefinement), C.POINTER(_vp)]),
     "gbh_create_batched": (C.c_int, [C.POINTER(GbhParams), C.POINTER(C.c_int32), C.c_int, C.POINTER(_vp)]),
+    "gbh_create_refined_batched": (C.c_int, [C.POINTER(GbhParams), C.POINTER(GbhRefinement), C.POINTER(C.c_int32),
+                                             C.c_int, C.POINTER(_vp)]),
     "gbh_autotune": (C.c_int, [_vp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int), _vp]),
     "gbh_set_decomposition": (C.c_int, [_vp, C.c_int, C.c_int]),
     "gbh_set_telescoping": (C.c_int, [_vp, C.c_int]),

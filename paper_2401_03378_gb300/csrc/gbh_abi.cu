@@ -527,6 +527,67 @@ int gbh_create(const gbh_params* p, gbh_ctx** out) {
   return create_common(p, out);
 }
 
+// Problem ids of a batched context: in range, and no neighbour (or, on two
+// levels, parent or child) in another problem.
+static int check_problems(const gbh_params* p, const int32_t* problem, int nproblems, const gbh_refinement* r) {
+  if (!problem || nproblems < 1) return set_err(nullptr, GBH_ERR_INVAL, "problem table and nproblems >= 1 are required");
+  const int nn = p->ndim == 3 ? 27 : 9;
+  for (long long b = 0; b < p->nblocks; ++b) {
+    const int pb = problem[b];
+    if (pb < 0 || pb >= nproblems) return set_err(nullptr, GBH_ERR_INVAL, "problem[%lld] = %d out of range", b, pb);
+  }
+  for (long long b = 0; b < p->nblocks; ++b) {
+    const int pb = problem[b];
+    for (int e = 0; e < nn; ++e) {
+      const int v = p->nbr[b * nn + e];
+      if (v >= 0 && problem[v] != pb)
+        return set_err(nullptr, GBH_ERR_INVAL, "block %lld and its neighbour %d belong to different problems", b, v);
+    }
+    if (r) {
+      const int P = r->parent[4 * b];
+      if (P >= 0 && P < p->nblocks && problem[P] != pb)
+        return set_err(nullptr, GBH_ERR_INVAL, "block %lld and its parent %d belong to different problems", b, P);
+    }
+  }
+  return GBH_OK;
+}
+
+// Per-block problem ids and per-problem CFL accumulators on a new context.
+static int attach_problems(gbh_ctx* c, const gbh_params* p, const int32_t* problem, int nproblems) {
+  cudaError_t e = cudaMalloc(&c->d_problem, sizeof(int) * (size_t)p->nblocks);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_problem, problem, sizeof(int) * (size_t)p->nblocks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_smax_own, sizeof(unsigned long long) * nproblems);
+  if (e == cudaSuccess) e = cudaMemset(c->d_smax_own, 0, sizeof(unsigned long long) * nproblems);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
+    return set_err(nullptr, code, "problem tables: %s", cudaGetErrorString(e));
+  }
+  c->d_smax = c->d_smax_own;
+  c->nproblems = nproblems;
+  c->amr.problem = c->d_problem;
+  return GBH_OK;
+}
+
+int gbh_create_refined_batched(const gbh_params* p, const gbh_refinement* r, const int32_t* problem, int nproblems,
+                               gbh_ctx** out) {
+  if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_params(p, true);
+  if (rc) return rc;
+  if (!r || !r->parent || !r->children) return set_err(nullptr, GBH_ERR_INVAL, "refinement tables are required");
+  for (long long b = 0; b < p->nblocks; ++b)
+    if (r->parent[4 * b] >= p->nblocks) return set_err(nullptr, GBH_ERR_INVAL, "parent[%lld] out of range", b);
+  if ((rc = check_problems(p, problem, nproblems, r))) return rc;
+  gbh_ctx* c = nullptr;
+  if ((rc = gbh_create_refined(p, r, &c))) return rc;
+  if ((rc = attach_problems(c, p, problem, nproblems))) {
+    gbh_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return GBH_OK;
+}
+
 int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** out) {
   if (!out) return set_err(nullptr, GBH_ERR_INVAL, "out is NULL");
   *out = nullptr;
@@ -672,31 +733,13 @@ int gbh_create_batched(const gbh_params* p, const int32_t* problem, int nproblem
   *out = nullptr;
   int rc = validate_params(p, false);
   if (rc) return rc;
-  if (!problem || nproblems < 1) return set_err(nullptr, GBH_ERR_INVAL, "problem table and nproblems >= 1 are required");
-  const int nn = p->ndim == 3 ? 27 : 9;
-  for (long long b = 0; b < p->nblocks; ++b) {
-    const int pb = problem[b];
-    if (pb < 0 || pb >= nproblems) return set_err(nullptr, GBH_ERR_INVAL, "problem[%lld] = %d out of range", b, pb);
-    for (int e = 0; e < nn; ++e) {
-      const int v = p->nbr[b * nn + e];
-      if (v >= 0 && problem[v] != pb)
-        return set_err(nullptr, GBH_ERR_INVAL, "block %lld and its neighbour %d belong to different problems", b, v);
-    }
-  }
+  if ((rc = check_problems(p, problem, nproblems, nullptr))) return rc;
   gbh_ctx* c = nullptr;
   if ((rc = create_common(p, &c))) return rc;
-  cudaError_t e = cudaMalloc(&c->d_problem, sizeof(int) * (size_t)p->nblocks);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_problem, problem, sizeof(int) * (size_t)p->nblocks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_smax_own, sizeof(unsigned long long) * nproblems);
-  if (e == cudaSuccess) e = cudaMemset(c->d_smax_own, 0, sizeof(unsigned long long) * nproblems);
-  if (e != cudaSuccess) {
-    const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
-    set_err(nullptr, code, "gbh_create_batched: %s", cudaGetErrorString(e));
+  if ((rc = attach_problems(c, p, problem, nproblems))) {
     gbh_destroy(c);
-    return code;
+    return rc;
   }
-  c->d_smax = c->d_smax_own;
-  c->nproblems = nproblems;
   *out = c;
   return GBH_OK;
 }

@@ -219,11 +219,12 @@ __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, 
   const int half = N / 2;
   const long long per = (long long)N * n2;
   const long long total = per * a.nreflux;
-  const double dt = dt_dev ? *dt_dev : dt_val;
   const long long sstride = 5LL * N * n2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const RefluxEntry en = a.reflux[t / per];
+    // the time step of the block's problem (one entry unless batched)
+    const double dt = dt_dev ? dt_dev[a.problem ? __ldg(a.problem + en.block) : 0] : dt_val;
     const int r = (int)(t % per);
     const int t1 = r % N, t2 = r / N;
     const int d = en.face >> 1, side = en.face & 1;

@@ -78,6 +78,7 @@ struct AmrArgs {
   double* flux_reg;
   long long flux_reg_len;  // doubles in flux_reg (checked build)
   const double* inv_dx;
+  const int* problem;      // [nblocks] problem of each block (batched two-level ensembles), or null
 };
 
 cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s);

@@ -84,6 +84,32 @@ def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
     return nbr, dx, parent, children
 
 
+def batched_two_level_tables(grids):
+    """Tables of independent two-level composite grids in one state array.
+
+    grids: sequence of (ndim, nb0, n, lo, hi, periodic, dx0), the arguments of
+    two_level_tables (same block shape).  The blocks of grid i (its coarse
+    blocks, then its fine blocks) follow those of grid i-1.  Returns
+    (nbr, dx, parent, children, problem) for gbh_create_refined_batched.
+    """
+    nbrs, dxs, pars, chls, ids = [], [], [], [], []
+    off = 0
+    for i, g in enumerate(grids):
+        nbr, dx, parent, children = two_level_tables(*g)
+        nbr = nbr.astype(np.int64)
+        nbrs.append(np.where(nbr >= 0, nbr + off, nbr).astype(np.int32))
+        dxs.append(dx)
+        parent = parent.astype(np.int64)
+        parent[:, 0] = np.where(parent[:, 0] >= 0, parent[:, 0] + off, parent[:, 0])
+        pars.append(parent.astype(np.int32))
+        children = children.astype(np.int64)
+        chls.append(np.where(children >= 0, children + off, children).astype(np.int32))
+        ids.append(np.full(nbr.shape[0], i, dtype=np.int32))
+        off += nbr.shape[0]
+    return (np.concatenate(nbrs), np.concatenate(dxs), np.concatenate(pars), np.concatenate(chls),
+            np.concatenate(ids))
+
+
 def batched_tables(problems):
     """Tables of independent problems in one state array.
 

@@ -63,16 +63,20 @@ class Hydro:
         ctx = C.c_void_p()
         self.refined = parent is not None
         self.nproblems = int(nproblems) if problem is not None else 1
-        if problem is not None:
-            self.problem = np.ascontiguousarray(problem, dtype=np.int32)
-            rc = self.lib.gbh_create_batched(C.byref(p), self.problem.ctypes.data_as(C.POINTER(C.c_int32)),
-                                             self.nproblems, C.byref(ctx))
-        elif self.refined:
+        if self.refined:
             self.parent = np.ascontiguousarray(parent, dtype=np.int32)
             self.children = np.ascontiguousarray(children, dtype=np.int32)
             r = _abi.GbhRefinement()
             r.parent = self.parent.ctypes.data_as(C.POINTER(C.c_int32))
             r.children = self.children.ctypes.data_as(C.POINTER(C.c_int32))
+        if problem is not None:
+            self.problem = np.ascontiguousarray(problem, dtype=np.int32)
+            pp = self.problem.ctypes.data_as(C.POINTER(C.c_int32))
+            if self.refined:
+                rc = self.lib.gbh_create_refined_batched(C.byref(p), C.byref(r), pp, self.nproblems, C.byref(ctx))
+            else:
+                rc = self.lib.gbh_create_batched(C.byref(p), pp, self.nproblems, C.byref(ctx))
+        elif self.refined:
             rc = self.lib.gbh_create_refined(C.byref(p), C.byref(r), C.byref(ctx))
         else:
             rc = self.lib.gbh_create(C.byref(p), C.byref(ctx))
@@ -97,6 +101,21 @@ class Hydro:
         nbr, dx, parent, children = two_level_tables(
             c.ndim, c.nb, c.n, tl.lo, tl.hi, tuple(b == "periodic" for b in c.bc), c.dx)
         return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children, **kw)
+
+    @classmethod
+    def from_two_level_batch(cls, grids, **kw):
+        """Independent two-level composite grids (objects like those
+        from_two_level takes, with equal block shapes and guard widths) in one
+        context; the state array holds their blocks one problem after another,
+        each problem's coarse blocks before its fine blocks."""
+        from .grid import batched_two_level_tables
+        tls = list(grids)
+        c = tls[0].coarse
+        nbr, dx, parent, children, problem = batched_two_level_tables(
+            [(t.coarse.ndim, t.coarse.nb, t.coarse.n, t.lo, t.hi,
+              tuple(b == "periodic" for b in t.coarse.bc), t.coarse.dx) for t in tls])
+        return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children,
+                   problem=problem, nproblems=len(tls), **kw)
 
     @classmethod
     def from_batch(cls, lattices, **kw):
@@ -132,10 +151,17 @@ class Hydro:
             raise ValueError(f"{name} must be contiguous with shape {self.shape}, got {tuple(U.shape)}")
         return U.data_ptr()
 
-    def _scalar(self, t: torch.Tensor, name="dt") -> int:
-        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or t.numel() < 1:
-            raise TypeError(f"{name} must be a float64 CUDA tensor")
+    def _scalar(self, t: torch.Tensor, name="dt", n: int = 1) -> int:
+        """Device pointer of a contiguous float64 CUDA tensor of at least n values."""
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} values, {n} are needed")
         return t.data_ptr()
+
+    def _dt(self, t: torch.Tensor, name="dt_dev") -> int:
+        """One time step per problem (nproblems values)."""
+        return self._scalar(t, name, self.nproblems)
 
     def empty_state(self) -> torch.Tensor:
         return torch.empty(self.shape, dtype=torch.float64, device="cuda")
@@ -148,7 +174,7 @@ class Hydro:
     def compute_dt(self, U, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(self.nproblems, dtype=torch.float64, device="cuda")
-        self._check(self.lib.hydro_compute_dt(self.ctx, self._state(U), self._scalar(out), _stream_handle()))
+        self._check(self.lib.hydro_compute_dt(self.ctx, self._state(U), self._dt(out, "out"), _stream_handle()))
         return out
 
     def stage(self, Uin, Un, Uout, dt: float, a: float, b: float, guarded: bool = False):
@@ -163,22 +189,20 @@ class Hydro:
         return U
 
     def step_cfl(self, U, dt_dev: torch.Tensor):
-        self._check(self.lib.hydro_step_cfl(self.ctx, self._state(U), self._scalar(dt_dev), _stream_handle()))
+        self._check(self.lib.hydro_step_cfl(self.ctx, self._state(U), self._dt(dt_dev), _stream_handle()))
         return U
 
     def advance(self, U, nsteps: int, dt_dev: torch.Tensor, dt_hist: Optional[torch.Tensor] = None):
         h = None
         if dt_hist is not None:
-            if dt_hist.numel() < nsteps:
-                raise ValueError("dt_hist is too short")
-            h = self._scalar(dt_hist, "dt_hist")
-        self._check(self.lib.hydro_advance(self.ctx, self._state(U), int(nsteps), self._scalar(dt_dev), h,
+            h = self._scalar(dt_hist, "dt_hist", int(nsteps) * self.nproblems)
+        self._check(self.lib.hydro_advance(self.ctx, self._state(U), int(nsteps), self._dt(dt_dev), h,
                                            _stream_handle()))
         return U
 
     def advance_graph(self, U, nsteps: int, dt_dev: torch.Tensor):
         """nsteps of step_cfl as one CUDA graph (captured on first use)."""
-        self._check(self.lib.hydro_advance_graph(self.ctx, self._state(U), int(nsteps), self._scalar(dt_dev),
+        self._check(self.lib.hydro_advance_graph(self.ctx, self._state(U), int(nsteps), self._dt(dt_dev),
                                                  _stream_handle()))
         return U
 
@@ -272,7 +296,16 @@ class Hydro:
         ptr = self._host_state(U_host)
         h = None
         if dt_hist_host is not None:
-            h = dt_hist_host.ctypes.data if isinstance(dt_hist_host, np.ndarray) else dt_hist_host.data_ptr()
+            need = int(nsteps) * self.nproblems
+            if isinstance(dt_hist_host, np.ndarray):
+                if dt_hist_host.dtype != np.float64 or not dt_hist_host.flags.c_contiguous or dt_hist_host.size < need:
+                    raise ValueError(f"dt_hist_host must be a contiguous float64 array of >= {need} values")
+                h = dt_hist_host.ctypes.data
+            else:
+                if (dt_hist_host.is_cuda or dt_hist_host.dtype != torch.float64 or not dt_hist_host.is_contiguous()
+                        or dt_hist_host.numel() < need):
+                    raise ValueError(f"dt_hist_host must be a contiguous float64 CPU tensor of >= {need} values")
+                h = dt_hist_host.data_ptr()
         self._check(self.lib.hydro_advance_host(self.ctx, ptr, int(nsteps), h, _stream_handle()))
         return U_host
 

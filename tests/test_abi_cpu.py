@@ -217,3 +217,45 @@ def test_create_batched_rejects_cross_problem_neighbours_without_gpu(lib):
     ctx = C.c_void_p()
     rc = lib.gbh_create_batched(C.byref(p), keep[2].ctypes.data_as(C.POINTER(C.c_int32)), 2, C.byref(ctx))
     assert rc == -1 and b"different problems" in lib.gbh_last_error(None)
+
+
+def test_batched_two_level_tables_and_checks_without_gpu(lib):
+    from paper_2401_03378_gb300 import _abi
+    from paper_2401_03378_gb300.grid import batched_two_level_tables, two_level_tables
+    grids = [(2, (4, 4, 1), (8, 8, 1), (1, 1), (3, 3), (True, True, False), (1 / 32, 1 / 32, 1.0)),
+             (2, (5, 4, 1), (8, 8, 1), (1, 1), (4, 3), (False, False, False), (1 / 40, 1 / 32, 1.0))]
+    nbr, dx, parent, children, prob = batched_two_level_tables(grids)
+    one = [two_level_tables(*g) for g in grids]
+    n = [t[0].shape[0] for t in one]
+    assert nbr.shape == (sum(n), 9) and list(prob) == [0] * n[0] + [1] * n[1]
+    # the second grid's tables, shifted by the first grid's block count
+    nb2, dx2, par2, ch2 = one[1]
+    assert np.array_equal(nbr[n[0]:], np.where(nb2 >= 0, nb2 + n[0], nb2))
+    assert np.array_equal(dx[n[0]:], dx2)
+    assert np.array_equal(parent[n[0]:, 0], np.where(par2[:, 0] >= 0, par2[:, 0] + n[0], -1))
+    assert np.array_equal(parent[n[0]:, 1:], par2[:, 1:])
+    assert np.array_equal(children[n[0]:], np.where(ch2 >= 0, ch2 + n[0], -1))
+    assert np.array_equal(nbr[:n[0]], one[0][0]) and np.array_equal(children[:n[0]], one[0][3])
+
+    def attempt(prob_, parent_=parent, nproblems=2):
+        keep = [np.ascontiguousarray(x) for x in (nbr, dx, parent_, children, prob_)]
+        p = _abi.GbhParams()
+        p.ndim, p.nxb, p.nyb, p.nzb, p.nguard, p.nblocks = 2, 8, 8, 1, 4, keep[0].shape[0]
+        p.gamma, p.cfl, p.small_rho, p.small_p = 1.4, 0.8, 1e-12, 1e-14
+        p.nbr = keep[0].ctypes.data_as(C.POINTER(C.c_int32))
+        p.dx = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+        r = _abi.GbhRefinement()
+        r.parent = keep[2].ctypes.data_as(C.POINTER(C.c_int32))
+        r.children = keep[3].ctypes.data_as(C.POINTER(C.c_int32))
+        ctx = C.c_void_p()
+        return lib.gbh_create_refined_batched(C.byref(p), C.byref(r), keep[4].ctypes.data_as(C.POINTER(C.c_int32)),
+                                              nproblems, C.byref(ctx))
+    # a fine block of grid 0 whose own same-level neighbours stay in problem 0 but
+    # whose parent is then in another problem: move its whole fine lattice
+    bad = prob.copy()
+    f0 = 16
+    bad[f0:n[0]] = 1
+    assert attempt(bad) == -1 and b"different problems" in lib.gbh_last_error(None)
+    bad = prob.copy(); bad[3] = 2
+    assert attempt(bad) == -1 and b"out of range" in lib.gbh_last_error(None)
+    assert attempt(prob, nproblems=0) == -1

@@ -400,3 +400,19 @@ def ensemble(count: int = 96, seed: int = 0, nxb: int = 16, ng: int = 4, choices
         U = sod_periodic(lat, seed=1000 + i) if i % 2 == 0 else kelvin_helmholtz(lat, seed=1000 + i)
         out.append((lat, U))
     return out
+
+
+def two_level_ensemble(count: int = 8, seed: int = 0, ndim: int = 3, nxb: int = 16, ng: int = 4,
+                       choices=(4, 6, 8)):
+    """Ensemble of independent two-level Sedov problems of uneven sizes: problem
+    i has a coarse lattice of c^ndim blocks (c drawn from `choices` with seed
+    `seed`, outflow boundaries) refined over its central c/2 blocks per
+    dimension, with the Sedov blast of sedov_two_level in the fine region.
+    Returns a list of (TwoLevel, U)."""
+    out = []
+    for c in ensemble_sizes(count, seed, choices):
+        lat = lattice_3d(c, c, c, nxb, nxb, nxb, ng) if ndim == 3 else lattice_2d(c, c, nxb, nxb, ng)
+        lo, hi = (c // 4,) * ndim, (c - c // 4,) * ndim
+        tl = two_level(lat, lo, hi)
+        out.append((tl, sedov_two_level(tl)))
+    return out

@@ -234,6 +234,18 @@ def run_gpu(args):
     clocks = clk.summary()
     tmax, units = aggregate(secs, float(zones) * args.steps, world)
     value = units / tmax
+    # the same loop repeated (5 x 10 steps, CUDA events each): spread and median
+    reps = []
+    for _ in range(5 if args.repeats else 0):
+        barrier()
+        e0.record(stream)
+        for _ in range(10):
+            h.step_cfl(U, dt)
+        e1.record(stream)
+        barrier()
+        reps.append(e0.elapsed_time(e1) / 10)
+    repeats = ({"ms_per_step": reps, "median_ms_per_step": float(np.median(reps)), "steps_each": 10}
+               if reps else None)
     nbad = h.check_state(U)
 
     # end to end through the host-buffer C-ABI call: every step copies the
@@ -330,6 +342,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
+        "repeats": repeats,
         "roofline": roof,
         "e2e": e2e,
         "two_level": two_level,
@@ -674,6 +687,8 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-repeats", dest="repeats", action="store_false",
+                    help="skip the 5 x 10-step repeats after the timed loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -431,6 +431,7 @@ void layout_from_params(const gbh_params* p, Layout* L, Eos* e) {
   e->g_gm1 = p->gamma / (p->gamma - 1.0);
   e->small_rho = p->small_rho;
   e->small_p = p->small_p;
+  e->hgm1 = 0.5 * (p->gamma - 1.0);
 }
 
 void face_table_from_params(const gbh_params* p, long long b, int face[6], double inv_dx[3]) {

@@ -44,16 +44,13 @@ __device__ __forceinline__ double mc_half_slope_br(double qm, double q0, double 
   const double dm = q0 - qm;
   const double dp = qp - q0;
   const double s4 = 0.25 * (dm + dp);
-  const long long bm = dbits(dm), bp = dbits(dp);
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long am = (unsigned long long)bm & mask, ap = (unsigned long long)bp & mask;
-  const unsigned long long as = (unsigned long long)dbits(s4) & mask;
+  const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(s4);
   const unsigned long long m1 = am < ap ? am : ap;
   const bool central = as < m1;
   const unsigned long long m = central ? as : m1;
-  const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
+  const bool same = ((dbits(dm) ^ dbits(dp)) >= 0) && am != 0 && ap != 0;
   br = !same ? 0 : (central ? 1 : (am < ap ? 2 : 3));
-  return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+  return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
 }
 
 __device__ __forceinline__ void mc_half_slope_vjp(int br, double bh, double& bqm, double& bq0, double& bqp) {
@@ -92,8 +89,10 @@ __device__ __forceinline__ void prim_vjp(const double W[5], bool fr, bool fp, co
   bU[0] = fr ? 0.0 : bW[0] - ir * (u * bW[1] + v * bW[2] + w * bW[3]) + bp * 0.5 * (u * u + v * v + w * w);
 }
 
-// Reverse of hllc_flux (gbh_device.cuh): recomputes the forward
-// intermediates with the same formulas, then accumulates (dF/dW)^T bF.
+// Reverse of the HLLC flux of hllc_flux (gbh_device.cuh).  The forward
+// intermediates are recomputed in Toro's form (Roe-averaged H~ and transverse
+// velocities, both sides' E + p), which equals hllc_flux's arrangement
+// algebraically, then (dF/dW)^T bF is accumulated.
 __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos& e, const double bF[5],
                               double bWL[5], double bWR[5]) {
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];

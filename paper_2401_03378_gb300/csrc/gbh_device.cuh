@@ -45,22 +45,30 @@ __device__ __forceinline__ int cons_to_prim(const double U[5], double W[5], cons
   return cons_to_prim_ir(U, W, e, ir);
 }
 
+// Magnitudes and signs of doubles on the integer pipe.  The magnitude key is
+// the bit pattern shifted left by one (the sign bit drops out): magnitudes of
+// doubles order like these unsigned integers.  Masking the sign bit off with
+// an AND would say the same, but the compiler turns that pattern into an FP64
+// absolute-value operation (a DADD on the FP64 pipe, the resource this kernel
+// is bound by), and it does not do so for the shift.
+__device__ __forceinline__ unsigned long long mag_key(double x) { return (unsigned long long)dbits(x) << 1; }
+__device__ __forceinline__ unsigned long long sign_bit(double x) {
+  return ((unsigned long long)dbits(x) >> 63) << 63;
+}
+
 // calcLims role: half of the MC-limited slope at q0,
 //   sigma/2 = sign(dp) * min(|dm+dp|/4, |dm|, |dp|) if dm, dp have the same strict sign, else 0,
 // so that the face values are q0 -/+ sigma/2.  Sign test and minimum on bit
-// patterns (magnitudes of doubles order like unsigned integers).
+// patterns.
 __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp) {
   const double dm = q0 - qm;
   const double dp = qp - q0;
   const double s4 = 0.25 * (dm + dp);
-  const long long bm = dbits(dm), bp = dbits(dp);
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long am = (unsigned long long)bm & mask, ap = (unsigned long long)bp & mask;
-  const unsigned long long as = (unsigned long long)dbits(s4) & mask;
+  const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(s4);
   unsigned long long m = am < ap ? am : ap;
   m = as < m ? as : m;
-  const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
-  return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+  const bool same = ((dbits(dm) ^ dbits(dp)) >= 0) && am != 0 && ap != 0;
+  return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
 }
 
 // Twice the MC-limited slope, 2 sigma = sign(dp) * min(|dm+dp|, 4|dm|, 4|dp|)
@@ -69,17 +77,14 @@ __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp)
 // mc_half_slope.  The factors 4 are added to the exponent fields (exact for
 // normal numbers; a subnormal |dm| or |dp| would compare as if it were about
 // 2^-1020, which moves the result by less than that), saving the FP64
-// multiply by 1/4.
+// multiply by 1/4.  One FP64 operation (the sum).
 __device__ __forceinline__ double mc_slope_x2_d(double dm, double dp) {
   const double sum = dm + dp;
-  const long long bm = dbits(dm), bp = dbits(dp);
-  const unsigned long long mask = 0x7fffffffffffffffULL;
-  const unsigned long long am = (unsigned long long)bm & mask, ap = (unsigned long long)bp & mask;
-  const unsigned long long as = (unsigned long long)dbits(sum) & mask;
-  unsigned long long m = (am < ap ? am : ap) + (2ULL << 52);   // min(4|dm|, 4|dp|)
+  const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(sum);
+  unsigned long long m = (am < ap ? am : ap) + (4ULL << 52);   // min(4|dm|, 4|dp|): exponent + 2 in key form
   m = as < m ? as : m;
-  const bool same = (bm ^ bp) >= 0 && am != 0 && ap != 0;
-  return bitsd(same ? (long long)(m | ((unsigned long long)bp & ~mask)) : 0LL);
+  const bool same = ((dbits(dm) ^ dbits(dp)) >= 0) && am != 0 && ap != 0;
+  return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
 }
 
 // The same from the cell values (dm = q0 - qm, dp = qp - q0).
@@ -94,9 +99,8 @@ __device__ __forceinline__ double half_pos(double x) { return bitsd(dbits(x) - (
 // |x| >= 2^-1021, else the magnitude bits shifted right (exact except that
 // the last bit of a subnormal result is truncated)
 __device__ __forceinline__ double half_any(double x) {
-  const long long b = dbits(x);
-  const long long mag = b & 0x7fffffffffffffffLL;
-  return bitsd(mag >= (2LL << 52) ? b - (1LL << 52) : ((b ^ mag) | (mag >> 1)));
+  const unsigned long long m2 = mag_key(x);
+  return bitsd(m2 >= (4ULL << 52) ? dbits(x) - (1LL << 52) : (long long)(sign_bit(x) | (m2 >> 2)));
 }
 
 // Maximum over the NT threads of a CTA (NT a power of two) of non-negative
@@ -154,35 +158,37 @@ __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, 
 // Side K = L when S* >= 0, else R.  With delta = (S* - u_K) / (S_K - S*),
 // Toro's star state satisfies
 //   U*_K - U_K = delta [rho_K, rho_K S_K, rho_K v_K, rho_K w_K, h_K + m_K S*]
-// (h = E + p), so F = F_K + S_K (U*_K - U_K) becomes, with g = S_K delta,
-//   F0 = rho_K u_K + g rho_K,  F1 = rho_K u_K^2 + p_K + g rho_K S_K,
-//   F2 = v_K F0,  F3 = w_K F0,  F4 = u_K h_K + g (h_K + m_K S*).
+// (h = E + p), so F = F_K + S_K (U*_K - U_K) becomes, with g = S_K delta and
+// t = u_K + g,
+//   F0 = rho_K t,  F1 = F0 u_K + p_K + g m_K,  F2 = v_K F0,  F3 = w_K F0,
+//   F4 = h_K t + g m_K S*.
 // When the whole fan lies on one side (S_L >= 0, or S_R <= 0) g = 0 and
 // F = F_K.
+//
+// The Roe averages are evaluated in an algebraically equal form with fewer
+// FP64 operations: the weights are w_L = 1 / (1 + r), w_R = r w_L with
+// r = sqrt(rho_R / rho_L), and, because H_K = c_K^2 / (gamma-1) + |u_K|^2 / 2
+// and w_L + w_R = 1,
+//   c~^2 = (gamma-1) (H~ - |u~|^2 / 2) = w_L c_L^2 + w_R c_R^2
+//          + (gamma-1)/2 w_L w_R |u_L - u_R|^2,
+// a sum of non-negative terms (no cancellation at high Mach number), so the
+// transverse Roe velocities and H~ are not formed.  h_K is formed for the
+// chosen side only.  86 FP64 operations per face.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
 
-  const double aL = rsqrt_nr(rL), aR = rsqrt_nr(rR);    // 1/sqrt(rho)
-  const double sL = rL * aL, sR = rR * aR;              // sqrt(rho)
-  const double iL = aL * aL, iR = aR * aR;              // 1/rho
+  const double iL = rcp_nr(rL), iR = rcp_nr(rR);                 // 1/rho
+  const double cL2 = e.gamma * pL * iL, cR2 = e.gamma * pR * iR;   // c^2
+  const double cL = sqrt_nr(cL2), cR = sqrt_nr(cR2);
 
-  const double kL = fma(wL, wL, fma(vL, vL, uL * uL));
-  const double kR = fma(wR, wR, fma(vR, vR, uR * uR));
-  const double hL = fma(half_pos(rL), kL, e.g_gm1 * pL);    // E + p (rho >= small_rho, normal)
-  const double hR = fma(half_pos(rR), kR, e.g_gm1 * pR);
-  const double cL = sqrt_nr(e.gamma * pL * iL);
-  const double cR = sqrt_nr(e.gamma * pR * iR);
-
-  const double w = rcp_nr(sL + sR);
-  const double wl = sL * w, wr = sR * w;
+  const double r = sqrt_nr(rR * iL);                  // sqrt(rho_R / rho_L)
+  const double wl = rcp_nr(1.0 + r), wr = r * wl;     // Roe weights
   const double ut = fma(wl, uL, wr * uR);
-  const double vt = fma(wl, vL, wr * vR);
-  const double wt = fma(wl, wL, wr * wR);
-  const double Ht = fma(hL, aL, hR * aR) * w;           // sqrt(rho) H = h / sqrt(rho)
-  const double kt = fma(wt, wt, fma(vt, vt, ut * ut));
-  const double ct = sqrt_nr(e.gm1 * fma(-0.5, kt, Ht));
+  const double du = uL - uR, dv = vL - vR, dw = wL - wR;
+  const double du2 = fma(dw, dw, fma(dv, dv, du * du));
+  const double ct = sqrt_nr(fma(e.hgm1 * (wl * wr), du2, fma(wl, cL2, wr * cR2)));
 
   const double SL = min_d(uL - cL, ut - ct);
   const double SR = max_d(uR + cR, ut + ct);
@@ -192,18 +198,21 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
 
   const bool left = ge0(Ss);
   const double rK = sel(left, rL, rR), uK = sel(left, uL, uR), vK = sel(left, vL, vR);
-  const double wK = sel(left, wL, wR), pK = sel(left, pL, pR), hK = sel(left, hL, hR);
+  const double wK = sel(left, wL, wR), pK = sel(left, pL, pR);
   const double SK = sel(left, SL, SR), mK = sel(left, mL, mR);
   const bool fan = left ? lt0(SL) : gt0(SR);
 
   const double delta = (Ss - uK) * rcp_nr(SK - Ss);
   const double g = sel(fan, SK, 0.0) * delta;
-  const double mass = rK * uK;
-  F[0] = fma(g, rK, mass);
-  F[1] = fma(g, rK * SK, fma(mass, uK, pK));
+  // E + p of the chosen side (rho >= small_rho, a normal number)
+  const double hK = fma(half_pos(rK), fma(wK, wK, fma(vK, vK, uK * uK)), e.g_gm1 * pK);
+  const double t = uK + g;
+  const double gm = g * mK;
+  F[0] = rK * t;
+  F[1] = fma(F[0], uK, pK) + gm;
   F[2] = vK * F[0];
   F[3] = wK * F[0];
-  F[4] = fma(g, fma(mK, Ss, hK), uK * hK);
+  F[4] = fma(hK, t, gm * Ss);
 }
 
 }  // namespace gbh

@@ -24,6 +24,7 @@ struct Layout {
 
 struct Eos {
   double gamma, gm1, inv_gm1, g_gm1, small_rho, small_p;  // g_gm1 = gamma / (gamma - 1)
+  double hgm1;                                            // (gamma - 1) / 2
 };
 
 // Arguments of one RK-stage launch: Uout = a*Un + b*(Uin + dt*L(Uin)).

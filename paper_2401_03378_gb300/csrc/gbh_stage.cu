@@ -147,13 +147,19 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
     __syncthreads();
 
+    // Work-list rotation: the item -> thread map of (B) and (C) is shifted by
+    // 32 * rot threads, rot = (k + CTA) mod 4, so the leftover warp passes of
+    // these lists (6 and 17 warp passes at N = 16) do not always fall to the
+    // same warps; the items and their arithmetic are unchanged.
+    const int rtid = NT % 128 == 0 ? (tid + 32 * ((k + (int)blockIdx.x) & 3)) % NT : tid;
+
     // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M],
     //     three consecutive cells per work item, so the two inner differences
     //     are formed once for two slopes (the last triple of a row may be
     //     partial: its reads are clamped to the row and its extra slopes not
     //     stored)
     constexpr int TR = (M + 2 + 2) / 3;               // triples per row
-    for (int s = tid; s < 2 * TR * M; s += NT) {
+    for (int s = rtid; s < 2 * TR * M; s += NT) {
       const bool xs = s < TR * M;
       const int s2 = xs ? s : s - TR * M;
       const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // row (x) or column (y); first slope cell + 1
@@ -187,7 +193,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     __syncthreads();
 
     // (C) HLLC on the x faces (i - 1/2, i in [0, M]) and y faces (j - 1/2, j in [0, M])
-    for (int f = tid; f < 2 * FX; f += NT) {
+    for (int f = rtid; f < 2 * FX; f += NT) {
       const bool xf = f < FX;
       int i, j;
       const double *ql, *qr;       // minus/plus state arrays, var stride vs

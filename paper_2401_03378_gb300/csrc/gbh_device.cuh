@@ -163,28 +163,31 @@ __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, 
 //   F0 = rho_K t,  F1 = F0 u_K + p_K + g m_K,  F2 = v_K F0,  F3 = w_K F0,
 //   F4 = h_K t + g m_K S*.
 // When the whole fan lies on one side (S_L >= 0, or S_R <= 0) g = 0 and
-// F = F_K.
+// F = F_K; otherwise t = u_K + g = S* (S_K - u_K) / (S_K - S*).
 //
 // The Roe averages are evaluated in an algebraically equal form with fewer
-// FP64 operations: the weights are w_L = 1 / (1 + r), w_R = r w_L with
-// r = sqrt(rho_R / rho_L), and, because H_K = c_K^2 / (gamma-1) + |u_K|^2 / 2
-// and w_L + w_R = 1,
+// FP64 operations.  One reciprocal square root q = 1/sqrt(rho_L rho_R) gives
+// 1/rho_L = rho_R q^2, 1/rho_R = rho_L q^2 and r = sqrt(rho_R / rho_L) =
+// rho_R q; the weights are w_L = 1 / (1 + r), w_R = r w_L; and, because
+// H_K = c_K^2 / (gamma-1) + |u_K|^2 / 2 and w_L + w_R = 1,
 //   c~^2 = (gamma-1) (H~ - |u~|^2 / 2) = w_L c_L^2 + w_R c_R^2
 //          + (gamma-1)/2 w_L w_R |u_L - u_R|^2,
 // a sum of non-negative terms (no cancellation at high Mach number), so the
 // transverse Roe velocities and H~ are not formed.  h_K is formed for the
-// chosen side only.  86 FP64 operations per face.
+// chosen side only.  83 FP64 operations per face.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
 
-  const double iL = rcp_nr(rL), iR = rcp_nr(rR);                 // 1/rho
+  const double q = rsqrt_nr(rL * rR);                 // 1/sqrt(rho_L rho_R)
+  const double q2 = q * q;
+  const double iL = rR * q2, iR = rL * q2;              // 1/rho
   const double cL2 = e.gamma * pL * iL, cR2 = e.gamma * pR * iR;   // c^2
   const double cL = sqrt_nr(cL2), cR = sqrt_nr(cR2);
 
-  const double r = sqrt_nr(rR * iL);                  // sqrt(rho_R / rho_L)
-  const double wl = rcp_nr(1.0 + r), wr = r * wl;     // Roe weights
+  const double r = rR * q;                              // sqrt(rho_R / rho_L)
+  const double wl = rcp_nr(1.0 + r), wr = r * wl;       // Roe weights
   const double ut = fma(wl, uL, wr * uR);
   const double du = uL - uR, dv = vL - vR, dw = wL - wR;
   const double du2 = fma(dw, dw, fma(dv, dv, du * du));
@@ -192,21 +195,21 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
 
   const double SL = min_d(uL - cL, ut - ct);
   const double SR = max_d(uR + cR, ut + ct);
-  const double mL = rL * (SL - uL);
-  const double mR = rR * (SR - uR);
+  const double dL = SL - uL, dR = SR - uR;
+  const double mL = rL * dL, mR = rR * dR;
   const double Ss = fma(-mR, uR, fma(mL, uL, pR - pL)) * rcp_nr(mL - mR);
 
   const bool left = ge0(Ss);
   const double rK = sel(left, rL, rR), uK = sel(left, uL, uR), vK = sel(left, vL, vR);
   const double wK = sel(left, wL, wR), pK = sel(left, pL, pR);
-  const double SK = sel(left, SL, SR), mK = sel(left, mL, mR);
+  const double SK = sel(left, SL, SR), mK = sel(left, mL, mR), dK = sel(left, dL, dR);
   const bool fan = left ? lt0(SL) : gt0(SR);
 
-  const double delta = (Ss - uK) * rcp_nr(SK - Ss);
-  const double g = sel(fan, SK, 0.0) * delta;
+  // t = u_K + g; S_K - S* != 0 inside the fan, and t = u_K (g = 0) outside it
+  const double t = sel(fan, Ss * (dK * rcp_nr(SK - Ss)), uK);
+  const double g = t - uK;
   // E + p of the chosen side (rho >= small_rho, a normal number)
   const double hK = fma(half_pos(rK), fma(wK, wK, fma(vK, vK, uK * uK)), e.g_gm1 * pK);
-  const double t = uK + g;
   const double gm = g * mK;
   F[0] = rK * t;
   F[1] = fma(F[0], uK, pK) + gm;

@@ -78,8 +78,13 @@ __device__ __forceinline__ double min_d(double a, double b) { return order_key(b
 __device__ __forceinline__ double max_d(double a, double b) { return order_key(a) < order_key(b) ? b : a; }
 __device__ __forceinline__ bool less_d(double a, double b) { return order_key(a) < order_key(b) && ((dbits(a) | dbits(b)) << 1) != 0; }
 
-// x >= 0 (true for +0 and -0), x < 0, x > 0
-__device__ __forceinline__ bool ge0(double x) { const long long b = dbits(x); return b >= 0 || (b << 1) == 0; }
+// x >= 0 (true for +0 and -0), x < 0, x > 0.  (-0 is tested by its exact bit
+// pattern: a test of the bits below the sign against zero is turned into an
+// FP64 compare by the compiler.)
+__device__ __forceinline__ bool ge0(double x) {
+  const long long b = dbits(x);
+  return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
 __device__ __forceinline__ bool lt0(double x) { return !ge0(x); }
 __device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
 

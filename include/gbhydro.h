@@ -348,10 +348,15 @@ int gbh_stage_kernel_time(gbh_ctx *ctx, double *ms_host, long long *launches_hos
 
 /* FP64 throughput probe (not part of the method): launches blocks x threads
  * threads; in every warp the first `lanes` (1..32) lanes run 8 independent
- * chains of iters fused multiply-adds, the others none.  Writes one double
- * per thread to out_dev (blocks*threads doubles).  FP64 flops executed =
- * 16 * iters * blocks * (threads/32) * lanes for threads a multiple of 32. */
-int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, double *out_dev, void *stream);
+ * chains of iters FP64 operations, the others none.  form selects the
+ * operation: 0 = fused multiply-add with two compile-time constant operands,
+ * 1 = fused multiply-add with all three operands in per-thread registers,
+ * 2 = add, 3 = multiply (operands in per-thread registers), 4 = fused
+ * multiply-add with two warp-uniform register operands.  Writes one double per thread to
+ * out_dev (blocks*threads doubles).  FP64 operations executed =
+ * 8 * iters * blocks * (threads/32) * lanes for threads a multiple of 32
+ * (x2 flops for forms 0, 1 and 4).  GBH_ERR_INVAL for out-of-range arguments. */
+int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double *out_dev, void *stream);
 
 /* Self-test of the FP64 reciprocal / reciprocal-square-root / square-root
  * building blocks the kernels use (hardware seed + one refinement step):

@@ -432,6 +432,9 @@ void layout_from_params(const gbh_params* p, Layout* L, Eos* e) {
   e->small_rho = p->small_rho;
   e->small_p = p->small_p;
   e->hgm1 = 0.5 * (p->gamma - 1.0);
+  e->k.one = 1.0;
+  e->k.nz = -0.0;
+  e->opaque = 0;
 }
 
 void face_table_from_params(const gbh_params* p, long long b, int face[6], double inv_dx[3]) {
@@ -1361,10 +1364,11 @@ int gbh_stage_kernel_time(gbh_ctx* c, double* ms_host, long long* launches_host,
   return GBH_OK;
 }
 
-int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, double* out_dev, void* stream) {
-  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || lanes < 1 || lanes > 32 || !out_dev)
+int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double* out_dev, void* stream) {
+  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || lanes < 1 || lanes > 32 || form < 0 ||
+      form > 4 || !out_dev)
     return set_err(nullptr, GBH_ERR_INVAL, "invalid probe arguments");
-  cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, lanes, out_dev, (cudaStream_t)stream);
+  cudaError_t e = gbh::launch_fp64_probe(blocks, threads, iters, lanes, form, out_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "probe launch: %s", cudaGetErrorString(e));
   return GBH_OK;
 }

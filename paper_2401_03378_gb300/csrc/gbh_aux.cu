@@ -172,16 +172,31 @@ __global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const 
 // 8 independent FMA chains per thread; the multiplier and addend keep the
 // values bounded (fixed point 1.0).  Only the first `lanes` lanes of each
 // warp run the chains (to measure how the FP64 pipe charges partial warps).
-__global__ void fp64_probe_kernel(int iters, int lanes, double* out) {
-  const double m = 0.999999999, c = 1e-9;
-  double x0 = 1.0 + 1e-3 * threadIdx.x, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
-  double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+// FP64 pipe probe: 8 independent chains per thread, run by the first `lanes`
+// lanes of each warp.  FORM 0: x = fma(x, m, c) with m, c compile-time
+// constants (constant-bank operands); 1: the same with m, c in per-thread
+// registers (their bit patterns OR-ed with a run-time zero that depends on the
+// thread index, so the compiler can neither fold them into constants nor keep
+// them in warp-uniform registers); 2: x = x + c (DADD); 3: x = x * m (DMUL),
+// c and m in per-thread registers; 4: as 1 with m, c warp-uniform (OR-ed with
+// the run-time zero alone).
+template <int FORM>
+__global__ void fp64_probe_kernel(int iters, int lanes, long long zero, double* out) {
+  const long long z = FORM == 4 ? zero : (zero & (long long)threadIdx.x);
+  const double m = FORM == 0 ? 0.999999999 : __longlong_as_double(__double_as_longlong(0.999999999) | z);
+  const double c = FORM == 0 ? 1e-9 : __longlong_as_double(__double_as_longlong(1e-9) | z);
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * threadIdx.x + 0.1 * k;
   const int n = (int)(threadIdx.x & 31) < lanes ? iters : 0;
   for (int i = 0; i < n; ++i) {
-    x0 = fma(x0, m, c); x1 = fma(x1, m, c); x2 = fma(x2, m, c); x3 = fma(x3, m, c);
-    x4 = fma(x4, m, c); x5 = fma(x5, m, c); x6 = fma(x6, m, c); x7 = fma(x7, m, c);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = FORM == 2 ? x[k] + c : FORM == 3 ? x[k] * m : fma(x[k], m, c);
   }
-  out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += x[k];
+  out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = sum;
 }
 
 // Self-test of the refined reciprocal / square roots: out[6][n] =
@@ -269,8 +284,15 @@ cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, double* out, cudaStream_t s) {
-  fp64_probe_kernel<<<blocks, threads, 0, s>>>(iters, lanes, out);
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double* out, cudaStream_t s) {
+  switch (form) {
+    case 0: fp64_probe_kernel<0><<<blocks, threads, 0, s>>>(iters, lanes, 0, out); break;
+    case 1: fp64_probe_kernel<1><<<blocks, threads, 0, s>>>(iters, lanes, 0, out); break;
+    case 2: fp64_probe_kernel<2><<<blocks, threads, 0, s>>>(iters, lanes, 0, out); break;
+    case 3: fp64_probe_kernel<3><<<blocks, threads, 0, s>>>(iters, lanes, 0, out); break;
+    case 4: fp64_probe_kernel<4><<<blocks, threads, 0, s>>>(iters, lanes, 0, out); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

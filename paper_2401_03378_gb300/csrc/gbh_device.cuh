@@ -28,13 +28,14 @@ namespace gbh {
 // p = (gamma-1) (E - (mx u + my v + mz w)/2).  Floors rho at small_rho and p
 // at small_p; returns 1 when a floor applied.
 __device__ __forceinline__ int cons_to_prim_ir(const double U[5], double W[5], const Eos& e, double& ir) {
+  const Rk& k = e.k;
   int hit = 0;
   double rho = U[0];
   if (less_d(rho, e.small_rho)) { rho = e.small_rho; hit = 1; }
-  ir = rcp_nr(rho);
-  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-  const double m2 = fma(U[3], w, fma(U[2], v, U[1] * u));
-  double p = e.gm1 * fma(-0.5, m2, U[4]);
+  ir = rcp_nr(rho, k);
+  const double u = mul(U[1], ir, k), v = mul(U[2], ir, k), w = mul(U[3], ir, k);
+  const double m2 = fma(U[3], w, fma(U[2], v, mul(U[1], u, k)));   // >= 0
+  double p = mul(e.gm1, fma(-half_any(m2), k.one, U[4]), k);       // (gamma-1) (E - m2/2)
   if (less_d(p, e.small_p)) { p = e.small_p; hit = 1; }
   W[0] = rho; W[1] = u; W[2] = v; W[3] = w; W[4] = p;
   return hit;
@@ -43,17 +44,6 @@ __device__ __forceinline__ int cons_to_prim_ir(const double U[5], double W[5], c
 __device__ __forceinline__ int cons_to_prim(const double U[5], double W[5], const Eos& e) {
   double ir;
   return cons_to_prim_ir(U, W, e, ir);
-}
-
-// Magnitudes and signs of doubles on the integer pipe.  The magnitude key is
-// the bit pattern shifted left by one (the sign bit drops out): magnitudes of
-// doubles order like these unsigned integers.  Masking the sign bit off with
-// an AND would say the same, but the compiler turns that pattern into an FP64
-// absolute-value operation (a DADD on the FP64 pipe, the resource this kernel
-// is bound by), and it does not do so for the shift.
-__device__ __forceinline__ unsigned long long mag_key(double x) { return (unsigned long long)dbits(x) << 1; }
-__device__ __forceinline__ unsigned long long sign_bit(double x) {
-  return ((unsigned long long)dbits(x) >> 63) << 63;
 }
 
 // calcLims role: half of the MC-limited slope at q0,
@@ -92,16 +82,25 @@ __device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
   return mc_slope_x2_d(q0 - qm, qp - q0);
 }
 
+// Half the MC-limited slope from the differences, sigma/2 = (2 sigma) / 4,
+// with 2 sigma as in mc_slope_x2_d and the division by 4 taken off the
+// exponent field on the integer pipe (exact for results >= 2^-1020; below,
+// the bit pattern is shifted, which moves the result by less than 2^-1020).
+// The face values are then q0 -/+ sigma/2 as register FMAs.  One FP64
+// operation (the sum).
+__device__ __forceinline__ double mc_half_slope_d(double dm, double dp, const Rk& k) {
+  const double sum = add(dm, dp, k);
+  const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(sum);
+  unsigned long long m = (am < ap ? am : ap) + (4ULL << 52);   // min(4|dm|, 4|dp|): exponent + 2 in key form
+  m = as < m ? as : m;
+  m >>= 1;                                                       // magnitude bits of 2 sigma
+  m = m >= (3ULL << 52) ? m - (2ULL << 52) : m >> 2;            // / 4
+  const bool same = ((dbits(dm) ^ dbits(dp)) >= 0) && am != 0 && ap != 0;
+  return bitsd(same ? (long long)(m | sign_bit(dp)) : 0LL);
+}
+
 // x / 2 for a positive normal x >= 2^-1021 (one off the exponent field)
 __device__ __forceinline__ double half_pos(double x) { return bitsd(dbits(x) - (1LL << 52)); }
-
-// x / 2 for any finite x on the integer pipe: one off the exponent field when
-// |x| >= 2^-1021, else the magnitude bits shifted right (exact except that
-// the last bit of a subnormal result is truncated)
-__device__ __forceinline__ double half_any(double x) {
-  const unsigned long long m2 = mag_key(x);
-  return bitsd(m2 >= (4ULL << 52) ? dbits(x) - (1LL << 52) : (long long)(sign_bit(x) | (m2 >> 2)));
-}
 
 // Maximum over the NT threads of a CTA (NT a power of two) of non-negative
 // values: xor shuffles within each warp (over the lanes the CTA has), then
@@ -131,21 +130,18 @@ __device__ __forceinline__ double block_max(double v, double* s_warp) {
 // ir = 1 / W[0] (cons_to_prim_ir returns it).
 __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, const Eos& e, double idx,
                                                   double idy, double idz, bool dim3) {
-  const double c = sqrt_nr(e.gamma * W[4] * ir);
-  double s = (fabs(W[1]) + c) * idx;
-  s = fma(fabs(W[2]) + c, idy, s);
-  if (dim3) s = fma(fabs(W[3]) + c, idz, s);
+  const Rk& k = e.k;
+  const double c = sqrt_nr(mul(mul(e.gamma, W[4], k), ir, k), k);
+  double s = mul(add(fabs(W[1]), c, k), idx, k);
+  s = fma(add(fabs(W[2]), c, k), idy, s);
+  if (dim3) s = fma(add(fabs(W[3]), c, k), idz, s);
   return s;
 }
 
 // Signal-speed sum of one cell for the CFL rule (W from cons_to_prim).
 __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, double idx,
                                                double idy, double idz, bool dim3) {
-  const double c = sqrt_nr(e.gamma * W[4] * rcp_nr(W[0]));
-  double s = (fabs(W[1]) + c) * idx;
-  s = fma(fabs(W[2]) + c, idy, s);
-  if (dim3) s = fma(fabs(W[3]) + c, idz, s);
-  return s;
+  return signal_speed_ir(W, rcp_nr(W[0], e.k), e, idx, idy, idz, dim3);
 }
 
 // calcFlux role: HLLC flux through a face whose normal is the first velocity
@@ -177,27 +173,28 @@ __device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, 
 // chosen side only.  83 FP64 operations per face.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
+  const Rk& k = e.k;
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
 
-  const double q = rsqrt_nr(rL * rR);                 // 1/sqrt(rho_L rho_R)
-  const double q2 = q * q;
-  const double iL = rR * q2, iR = rL * q2;              // 1/rho
-  const double cL2 = e.gamma * pL * iL, cR2 = e.gamma * pR * iR;   // c^2
-  const double cL = sqrt_nr(cL2), cR = sqrt_nr(cR2);
+  const double q = rsqrt_nr(mul(rL, rR, k), k);          // 1/sqrt(rho_L rho_R)
+  const double q2 = mul(q, q, k);
+  const double iL = mul(rR, q2, k), iR = mul(rL, q2, k);   // 1/rho
+  const double cL2 = mul(mul(e.gamma, pL, k), iL, k), cR2 = mul(mul(e.gamma, pR, k), iR, k);   // c^2
+  const double cL = sqrt_nr(cL2, k), cR = sqrt_nr(cR2, k);
 
-  const double r = rR * q;                              // sqrt(rho_R / rho_L)
-  const double wl = rcp_nr(1.0 + r), wr = r * wl;       // Roe weights
-  const double ut = fma(wl, uL, wr * uR);
-  const double du = uL - uR, dv = vL - vR, dw = wL - wR;
-  const double du2 = fma(dw, dw, fma(dv, dv, du * du));
-  const double ct = sqrt_nr(fma(e.hgm1 * (wl * wr), du2, fma(wl, cL2, wr * cR2)));
+  const double r = mul(rR, q, k);                          // sqrt(rho_R / rho_L)
+  const double wl = rcp_nr(add(r, k.one, k), k), wr = mul(r, wl, k);   // Roe weights
+  const double ut = fma(wl, uL, mul(wr, uR, k));
+  const double du = sub(uL, uR, k), dv = sub(vL, vR, k), dw = sub(wL, wR, k);
+  const double du2 = fma(dw, dw, fma(dv, dv, mul(du, du, k)));
+  const double ct = sqrt_nr(fma(mul(e.hgm1, mul(wl, wr, k), k), du2, fma(wl, cL2, mul(wr, cR2, k))), k);
 
-  const double SL = min_d(uL - cL, ut - ct);
-  const double SR = max_d(uR + cR, ut + ct);
-  const double dL = SL - uL, dR = SR - uR;
-  const double mL = rL * dL, mR = rR * dR;
-  const double Ss = fma(-mR, uR, fma(mL, uL, pR - pL)) * rcp_nr(mL - mR);
+  const double SL = min_d(sub(uL, cL, k), sub(ut, ct, k));
+  const double SR = max_d(add(uR, cR, k), add(ut, ct, k));
+  const double dL = sub(SL, uL, k), dR = sub(SR, uR, k);
+  const double mL = mul(rL, dL, k), mR = mul(rR, dR, k);
+  const double Ss = mul(fma(-mR, uR, fma(mL, uL, sub(pR, pL, k))), rcp_nr(sub(mL, mR, k), k), k);
 
   const bool left = ge0(Ss);
   const double rK = sel(left, rL, rR), uK = sel(left, uL, uR), vK = sel(left, vL, vR);
@@ -206,16 +203,16 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
   const bool fan = left ? lt0(SL) : gt0(SR);
 
   // t = u_K + g; S_K - S* != 0 inside the fan, and t = u_K (g = 0) outside it
-  const double t = sel(fan, Ss * (dK * rcp_nr(SK - Ss)), uK);
-  const double g = t - uK;
+  const double t = sel(fan, mul(Ss, mul(dK, rcp_nr(sub(SK, Ss, k), k), k), k), uK);
+  const double g = sub(t, uK, k);
   // E + p of the chosen side (rho >= small_rho, a normal number)
-  const double hK = fma(half_pos(rK), fma(wK, wK, fma(vK, vK, uK * uK)), e.g_gm1 * pK);
-  const double gm = g * mK;
-  F[0] = rK * t;
-  F[1] = fma(F[0], uK, pK) + gm;
-  F[2] = vK * F[0];
-  F[3] = wK * F[0];
-  F[4] = fma(hK, t, gm * Ss);
+  const double hK = fma(half_pos(rK), fma(wK, wK, fma(vK, vK, mul(uK, uK, k))), mul(e.g_gm1, pK, k));
+  const double gm = mul(g, mK, k);
+  F[0] = mul(rK, t, k);
+  F[1] = add(fma(F[0], uK, pK), gm, k);
+  F[2] = mul(vK, F[0], k);
+  F[3] = mul(wK, F[0], k);
+  F[4] = fma(hK, t, mul(gm, Ss, k));
 }
 
 }  // namespace gbh

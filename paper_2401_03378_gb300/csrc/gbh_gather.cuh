@@ -66,13 +66,15 @@ __device__ __forceinline__ long long cell_offset(const StageArgs& a, int b, int 
   return GBH_IX(o, (long long)L.nblocks * L.bstride - 4 * L.vstride);   // o + v*vstride, v < 5, in the state
 }
 
+// Primitives of a cell (cell_offset's addressing); e: a.eos, or its
+// register copy (reg_eos).
 template <int N>
-__device__ __forceinline__ int load_prim(const StageArgs& a, int b, int i, int j, int k, double W[5]) {
+__device__ __forceinline__ int load_prim(const StageArgs& a, const Eos& e, int b, int i, int j, int k, double W[5]) {
   const long long o = cell_offset<N>(a, b, i, j, k);
   double U[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * a.lay.vstride);
-  return cons_to_prim(U, W, a.eos);
+  return cons_to_prim(U, W, e);
 }
 
 

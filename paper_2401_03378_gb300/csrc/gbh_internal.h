@@ -22,9 +22,18 @@ struct Layout {
   long long bstride;     // 5*vstride
 };
 
+// The FP64 constants 1 and -0: a + b = fma(a, one, b), a - b = fma(-b, one, a)
+// and a * b = fma(a, b, nz) give exactly the results of the plain operations
+// (gbh_fastmath.cuh).
+struct Rk {
+  double one, nz;
+};
+
 struct Eos {
   double gamma, gm1, inv_gm1, g_gm1, small_rho, small_p;  // g_gm1 = gamma / (gamma - 1)
   double hgm1;                                            // (gamma - 1) / 2
+  Rk k;                                                   // {1, -0}
+  long long opaque;                                       // 0 (see reg_eos)
 };
 
 // Arguments of one RK-stage launch: Uout = a*Un + b*(Uin + dt*L(Uin)).
@@ -147,6 +156,6 @@ long long check_take_aux();
 long long check_take_amr();
 long long check_take_adjoint();
 long long check_selftest();
-cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, double* out, cudaStream_t s);
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double* out, cudaStream_t s);
 
 }  // namespace gbh

@@ -71,8 +71,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   const double dt = a.dt_dev ? a.dt_dev[prob] : a.dt;
   const double idx = __ldg(a.inv_dx + 3 * b), idy = __ldg(a.inv_dx + 3 * b + 1);
   const double idz = DIM3 ? __ldg(a.inv_dx + 3 * b + 2) : 0.0;
-  const double dtx = dt * idx, dty = dt * idy, dtz = dt * idz;
-  const Eos& e = a.eos;
+  // FP64 constants in per-thread registers (gbh_fastmath.cuh)
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);
+  const Rk& rk = e.k;
+  const double dtx = reg_const(dt * idx, zt), dty = reg_const(dt * idy, zt), dtz = reg_const(dt * idz, zt);
 
   int hits = 0;
   double smax = 0.0;
@@ -81,19 +84,20 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
-    load_prim<N>(a, b, ci, cj, k0 - 2, Wm2);
-    load_prim<N>(a, b, ci, cj, k0 - 1, Wm1);
-    const int h0 = load_prim<N>(a, b, ci, cj, k0, W0);
+    load_prim<N>(a, e, b, ci, cj, k0 - 2, Wm2);
+    load_prim<N>(a, e, b, ci, cj, k0 - 1, Wm1);
+    const int h0 = load_prim<N>(a, e, b, ci, cj, k0, W0);
     if (counted(k0)) hits += h0;
-    const int h1 = load_prim<N>(a, b, ci, cj, k0 + 1, Wp1);
+    const int h1 = load_prim<N>(a, e, b, ci, cj, k0 + 1, Wp1);
     if (counted(k0 + 1)) hits += h1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      qpm1[v] = fma(0.25, mc_slope_x2(Wm2[v], Wm1[v], W0[v]), Wm1[v]);
-      dz1[v] = Wp1[v] - W0[v];
-      const double t = mc_slope_x2_d(W0[v] - Wm1[v], dz1[v]);
-      qm0[v] = fma(-0.25, t, W0[v]);
-      qpz[v] = fma(0.25, t, W0[v]);
+      const double d0 = sub(W0[v], Wm1[v], rk);
+      qpm1[v] = add(Wm1[v], mc_half_slope_d(sub(Wm1[v], Wm2[v], rk), d0, rk), rk);
+      dz1[v] = sub(Wp1[v], W0[v], rk);
+      const double t = mc_half_slope_d(d0, dz1[v], rk);
+      qm0[v] = sub(W0[v], t, rk);
+      qpz[v] = add(W0[v], t, rk);
     }
     // z face k0 - 1/2; rotated order (rho, w, u, v, p)
     double wl[5] = {qpm1[0], qpm1[3], qpm1[1], qpm1[2], qpm1[4]};
@@ -102,7 +106,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     hllc_flux(wl, wr, e, f);
     Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
   } else {
-    const int h0 = load_prim<N>(a, b, ci, cj, 0, W0);
+    const int h0 = load_prim<N>(a, e, b, ci, cj, 0, W0);
     if (col_in) hits += h0;
   }
 
@@ -110,16 +114,16 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     double Fzp[5], Wn[5], qpn[5];
     if (DIM3) {
       // own column: primitives at k+2, face states of k+1, z flux at k + 1/2
-      const int hn = load_prim<N>(a, b, ci, cj, k + 2, Wn);
+      const int hn = load_prim<N>(a, e, b, ci, cj, k + 2, Wn);
       if (counted(k + 2)) hits += hn;
       double qmz[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double dn = Wn[v] - Wp1[v];
-        const double t = mc_slope_x2_d(dz1[v], dn);
+        const double dn = sub(Wn[v], Wp1[v], rk);
+        const double t = mc_half_slope_d(dz1[v], dn, rk);
         dz1[v] = dn;
-        qmz[v] = fma(-0.25, t, Wp1[v]);
-        qpn[v] = fma(0.25, t, Wp1[v]);
+        qmz[v] = sub(Wp1[v], t, rk);
+        qpn[v] = add(Wp1[v], t, rk);
       }
       double wl[5] = {qpz[0], qpz[3], qpz[1], qpz[2], qpz[4]};
       double wr[5] = {qmz[0], qmz[3], qmz[1], qmz[2], qmz[4]};
@@ -141,7 +145,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       else if (q == 2) { i = pos; j = -1 - depth; }
       else { i = pos; j = M + depth; }
       double W[5];
-      load_prim<N>(a, b, i - E, j - E, k, W);
+      load_prim<N>(a, e, b, i - E, j - E, k, W);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + j + 2) * P + i + 2, 5 * P * P)] = W[v];
     }
@@ -172,21 +176,23 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       for (int v = 0; v < 5; ++v) {
         const double* q = sW + v * P * P + first;
         const double q1 = q[step], q2 = q[2 * step], q3 = q[k3 * step];
-        const double d0 = q1 - q[0], d1 = q2 - q1, d2 = q3 - q2, d3 = q[k4 * step] - q3;
-        const double t0 = mc_slope_x2_d(d0, d1), t1 = mc_slope_x2_d(d1, d2), t2 = mc_slope_x2_d(d2, d3);
+        const double d0 = sub(q1, q[0], rk), d1 = sub(q2, q1, rk), d2 = sub(q3, q2, rk);
+        const double d3 = sub(q[k4 * step], q3, rk);
+        const double t0 = mc_half_slope_d(d0, d1, rk), t1 = mc_half_slope_d(d1, d2, rk);
+        const double t2 = mc_half_slope_d(d2, d3, rk);
         double* qm = xs ? sQx + GBH_IX((v * M + line) * (M + 2) + c0, 10 * QX)
                         : sQy + GBH_IX((v * (M + 2) + c0) * M + line, 10 * QX);
         const int os = xs ? 1 : M;                    // next slope cell
         const int op = 5 * QX;                        // plus states follow the minus states
-        qm[0] = fma(-0.25, t0, q1);
-        qm[op] = fma(0.25, t0, q1);
+        qm[0] = sub(q1, t0, rk);
+        qm[op] = add(q1, t0, rk);
         if (two) {
-          qm[os] = fma(-0.25, t1, q2);
-          qm[os + op] = fma(0.25, t1, q2);
+          qm[os] = sub(q2, t1, rk);
+          qm[os + op] = add(q2, t1, rk);
         }
         if (three) {
-          qm[2 * os] = fma(-0.25, t2, q3);
-          qm[2 * os + op] = fma(0.25, t2, q3);
+          qm[2 * os] = sub(q3, t2, rk);
+          qm[2 * os + op] = add(q3, t2, rk);
         }
       }
     }
@@ -234,14 +240,15 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     double out[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double fx = sFx[GBH_IX((v * M + ty) * (M + 1) + tx + 1, 5 * FX)] - sFx[(v * M + ty) * (M + 1) + tx];
-      const double fy = sFy[GBH_IX((v * (M + 1) + ty + 1) * M + tx, 5 * FX)] - sFy[(v * (M + 1) + ty) * M + tx];
+      const double fx = sub(sFx[GBH_IX((v * M + ty) * (M + 1) + tx + 1, 5 * FX)], sFx[(v * M + ty) * (M + 1) + tx], rk);
+      const double fy = sub(sFy[GBH_IX((v * (M + 1) + ty + 1) * M + tx, 5 * FX)], sFy[(v * (M + 1) + ty) * M + tx], rk);
       const long long o = GBH_IX(base + v * L.vstride, (long long)L.nblocks * L.bstride);
       double r = fma(-dtx, fx, __ldg(a.Uin + o));
       r = fma(-dty, fy, r);
-      if (DIM3) r = fma(-dtz, Fzp[v] - Fzm[v], r);
+      if (DIM3) r = fma(-dtz, sub(Fzp[v], Fzm[v], rk), r);
       // combine 2: a = b = 1/2 (second SSP-RK2 stage), one FP64 add
-      out[v] = a.combine == 2 ? half_any(a.Un[o] + r) : a.combine ? fma(a.a, a.Un[o], a.b * r) : r;
+      out[v] = a.combine == 2 ? half_any(add(a.Un[o], r, rk))
+               : a.combine ? fma(reg_const(a.a, zt), a.Un[o], mul(reg_const(a.b, zt), r, rk)) : r;
       a.Uout[o] = out[v];
     }
     if (a.flux_slot && col_in && (E == 0 || (k >= 0 && k < L.nz))) {
@@ -271,7 +278,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     if (E == 0 && a.smax_acc) {
       double W[5], ir;
       cons_to_prim_ir(out, W, e, ir);
-      smax = fmax(smax, signal_speed_ir(W, ir, e, idx, idy, idz, DIM3));
+      smax = fmax(smax, signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3));
     }
 
     if (DIM3) {

@@ -330,9 +330,13 @@ class Hydro:
         return float(ms.value), int(n.value)
 
 
-def fp64_probe(blocks: int, threads: int, iters: int, out: torch.Tensor, lanes: int = 32):
+def fp64_probe(blocks: int, threads: int, iters: int, out: torch.Tensor, lanes: int = 32, form: int = 1):
+    """FP64 throughput probe (gbh_fp64_probe): form 0 = FMA with constant
+    operands, 1 = FMA with per-thread register operands, 2 = add, 3 = multiply,
+    4 = FMA with warp-uniform register operands."""
     lib = _abi.load()
-    rc = lib.gbh_fp64_probe(int(blocks), int(threads), int(iters), int(lanes), out.data_ptr(), _stream_handle())
+    rc = lib.gbh_fp64_probe(int(blocks), int(threads), int(iters), int(lanes), int(form), out.data_ptr(),
+                            _stream_handle())
     if rc != 0:
         raise _abi.GbhError(rc, lib.gbh_last_error(None).decode())
 

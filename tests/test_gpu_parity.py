@@ -423,8 +423,12 @@ def test_errors_and_floors(gb):
 
 def test_fp64_probe_runs(gb):
     out = torch.zeros(152 * 4 * 256, dtype=torch.float64, device="cuda")
-    gb.fp64_probe(152 * 4, 256, 1000, out)
-    assert torch.isfinite(out).all()
+    for form in range(5):
+        out.zero_()
+        gb.fp64_probe(152 * 4, 256, 1000, out, 32, form)
+        assert torch.isfinite(out).all() and bool((out != 0).all())
+    with pytest.raises(Exception):
+        gb.fp64_probe(152 * 4, 256, 1000, out, 32, 5)
 
 
 def test_refined_reciprocal_and_roots_within_two_ulp(gb):

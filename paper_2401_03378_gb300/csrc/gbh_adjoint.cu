@@ -39,11 +39,16 @@ namespace {
 
 // ---- reverse of the pointwise pieces ---------------------------------------
 
+// Every add and multiply below is a register FMA (a + b = fma(a, 1, b),
+// a - b = fma(-b, 1, a), a * b = fma(a, b, -0); gbh_fastmath.cuh), with the
+// constants of reg_eos in per-thread registers: the same results as the plain
+// operations at the FP64 pipe's full issue rate.
+
 // mc_half_slope with the branch it takes: 0 zero, 1 central, 2 |dm|, 3 |dp|.
-__device__ __forceinline__ double mc_half_slope_br(double qm, double q0, double qp, int& br) {
-  const double dm = q0 - qm;
-  const double dp = qp - q0;
-  const double s4 = 0.25 * (dm + dp);
+__device__ __forceinline__ double mc_half_slope_br(double qm, double q0, double qp, int& br, const Rk& k) {
+  const double dm = sub(q0, qm, k);
+  const double dp = sub(qp, q0, k);
+  const double s4 = quarter_any(add(dm, dp, k));
   const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(s4);
   const unsigned long long m1 = am < ap ? am : ap;
   const bool central = as < m1;
@@ -53,24 +58,37 @@ __device__ __forceinline__ double mc_half_slope_br(double qm, double q0, double 
   return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
 }
 
-__device__ __forceinline__ void mc_half_slope_vjp(int br, double bh, double& bqm, double& bq0, double& bqp) {
-  const double bdm = br == 1 ? 0.25 * bh : (br == 2 ? bh : 0.0);
-  const double bdp = br == 1 ? 0.25 * bh : (br == 3 ? bh : 0.0);
-  bqm -= bdm;
-  bq0 += bdm - bdp;
-  bqp += bdp;
+// Adjoint of mc_half_slope_br's result scaled by SIGN (+1 or -1): the
+// cotangent is SIGN * bh (the sign is applied by the choice of FMA forms, so
+// no negated value has to be formed).
+template <int SIGN>
+__device__ __forceinline__ void mc_half_slope_vjp(int br, double bh, double& bqm, double& bq0, double& bqp,
+                                                  const Rk& k) {
+  const double bq = quarter_any(bh);
+  const double bdm = br == 1 ? bq : (br == 2 ? bh : 0.0);
+  const double bdp = br == 1 ? bq : (br == 3 ? bh : 0.0);
+  if (SIGN > 0) {
+    bqm = sub(bqm, bdm, k);
+    bq0 = add(bq0, sub(bdm, bdp, k), k);
+    bqp = add(bqp, bdp, k);
+  } else {
+    bqm = add(bqm, bdm, k);
+    bq0 = add(bq0, sub(bdp, bdm, k), k);
+    bqp = sub(bqp, bdp, k);
+  }
 }
 
 // cons_to_prim reporting which floors applied.
 __device__ __forceinline__ void cons_to_prim_flags(const double U[5], double W[5], const Eos& e, bool& fr,
                                                    bool& fp) {
+  const Rk& k = e.k;
   double rho = U[0];
   fr = less_d(rho, e.small_rho);
   if (fr) rho = e.small_rho;
-  const double ir = rcp_nr(rho);
-  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-  const double m2 = fma(U[3], w, fma(U[2], v, U[1] * u));
-  double p = e.gm1 * fma(-0.5, m2, U[4]);
+  const double ir = rcp_nr(rho, k);
+  const double u = mul(U[1], ir, k), v = mul(U[2], ir, k), w = mul(U[3], ir, k);
+  const double m2 = fma(U[3], w, fma(U[2], v, mul(U[1], u, k)));
+  double p = mul(e.gm1, fma(-half_any(m2), k.one, U[4]), k);
   fp = less_d(p, e.small_p);
   if (fp) p = e.small_p;
   W[0] = rho; W[1] = u; W[2] = v; W[3] = w; W[4] = p;
@@ -79,145 +97,181 @@ __device__ __forceinline__ void cons_to_prim_flags(const double U[5], double W[5
 // bU = (dW/dU)^T bW for W = cons_to_prim(U); floored components are constants.
 __device__ __forceinline__ void prim_vjp(const double W[5], bool fr, bool fp, const Eos& e, const double bW[5],
                                          double bU[5]) {
-  const double ir = rcp_nr(W[0]);
+  const Rk& k = e.k;
+  const double ir = rcp_nr(W[0], k);
   const double u = W[1], v = W[2], w = W[3];
-  const double bp = fp ? 0.0 : bW[4] * e.gm1;
+  const double bp = fp ? 0.0 : mul(bW[4], e.gm1, k);
   bU[4] = bp;
-  bU[1] = ir * bW[1] - bp * u;
-  bU[2] = ir * bW[2] - bp * v;
-  bU[3] = ir * bW[3] - bp * w;
-  bU[0] = fr ? 0.0 : bW[0] - ir * (u * bW[1] + v * bW[2] + w * bW[3]) + bp * 0.5 * (u * u + v * v + w * w);
+  bU[1] = fma(ir, bW[1], -mul(bp, u, k));
+  bU[2] = fma(ir, bW[2], -mul(bp, v, k));
+  bU[3] = fma(ir, bW[3], -mul(bp, w, k));
+  const double uw = fma(w, bW[3], fma(v, bW[2], mul(u, bW[1], k)));
+  const double k2 = fma(w, w, fma(v, v, mul(u, u, k)));
+  bU[0] = fr ? 0.0 : fma(half_any(bp), k2, fma(-ir, uw, bW[0]));
 }
 
-// Reverse of the HLLC flux of hllc_flux (gbh_device.cuh).  The forward
-// intermediates are recomputed in Toro's form (Roe-averaged H~ and transverse
-// velocities, both sides' E + p), which equals hllc_flux's arrangement
-// algebraically, then (dF/dW)^T bF is accumulated.
+// Reverse of hllc_flux (gbh_device.cuh): the forward is recomputed in the same
+// arrangement (one reciprocal square root of rho_L rho_R, the Roe sound speed
+// from w_L c_L^2 + w_R c_R^2 + (gamma-1)/2 w_L w_R |u_L - u_R|^2, the star
+// state through t = u_K + g), then (dF/dW)^T bF is accumulated step by step
+// in reverse.  Branches (the min / max of the wave-speed bounds, the side K,
+// the fan) keep the forward's decisions and are taken by selects.
 __device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos& e, const double bF[5],
                               double bWL[5], double bWR[5]) {
+  const Rk& k = e.k;
+  auto A = [&](double x, double y) { return fma(x, k.one, y); };    // x + y
+  auto S = [&](double x, double y) { return fma(-y, k.one, x); };   // x - y
+  auto M = [&](double x, double y) { return fma(x, y, k.nz); };     // x * y
   const double rL = WL[0], uL = WL[1], vL = WL[2], wL = WL[3], pL = WL[4];
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
-  // ---- forward (as hllc_flux) ----
-  const double aL = rsqrt_nr(rL), aR = rsqrt_nr(rR);
-  const double sL = rL * aL, sR = rR * aR;
-  const double iL = aL * aL, iR = aR * aR;
-  const double kL = fma(wL, wL, fma(vL, vL, uL * uL));
-  const double kR = fma(wR, wR, fma(vR, vR, uR * uR));
-  const double hL = fma(0.5 * rL, kL, e.g_gm1 * pL);
-  const double hR = fma(0.5 * rR, kR, e.g_gm1 * pR);
-  const double zL = e.gamma * pL * iL, zR = e.gamma * pR * iR;
-  const double qL = rsqrt_nr(zL), qR = rsqrt_nr(zR);   // 1/c (kept for the reverse)
-  const double cL = zL * qL, cR = zR * qR;
-  const double w = rcp_nr(sL + sR);
-  const double wl = sL * w, wr = sR * w;
-  const double ut = fma(wl, uL, wr * uR);
-  const double vt = fma(wl, vL, wr * vR);
-  const double wt = fma(wl, wL, wr * wR);
-  const double T = fma(hL, aL, hR * aR);
-  const double Ht = T * w;
-  const double kt = fma(wt, wt, fma(vt, vt, ut * ut));
-  const double zc = e.gm1 * fma(-0.5, kt, Ht);
-  const double qc = rsqrt_nr(zc);
-  const double ct = zc * qc;
-  const double l1 = uL - cL, l2 = ut - ct, r1 = uR + cR, r2 = ut + ct;
-  const bool selL1 = !(order_key(l2) < order_key(l1));   // SL = l1
-  const bool selR1 = !(order_key(r1) < order_key(r2));   // SR = r1
+  // ---- forward ----
+  const double q = rsqrt_nr(M(rL, rR), k);                 // 1/sqrt(rho_L rho_R)
+  const double q2 = M(q, q);
+  const double iL = M(rR, q2), iR = M(rL, q2);             // 1/rho
+  const double gpL = M(e.gamma, pL), gpR = M(e.gamma, pR);
+  const double cL2 = M(gpL, iL), cR2 = M(gpR, iR);         // c^2
+  const double qL = rsqrt_nr(cL2, k), qR = rsqrt_nr(cR2, k);   // 1/c
+  const double cL = M(cL2, qL), cR = M(cR2, qR);
+  const double r = M(rR, q);                               // sqrt(rho_R / rho_L)
+  const double wl = rcp_nr(A(r, k.one), k), wr = M(r, wl);
+  const double ut = fma(wl, uL, M(wr, uR));
+  const double du = S(uL, uR), dv = S(vL, vR), dw = S(wL, wR);
+  const double du2 = fma(dw, dw, fma(dv, dv, M(du, du)));
+  const double Bw = M(e.hgm1, M(wl, wr));
+  const double ct2 = fma(Bw, du2, fma(wl, cL2, M(wr, cR2)));
+  const double qc = rsqrt_nr(ct2, k);
+  const double ct = M(ct2, qc);
+  const double l1 = S(uL, cL), l2 = S(ut, ct), r1 = A(uR, cR), r2 = A(ut, ct);
+  const bool selL1 = !(order_key(l2) < order_key(l1));     // S_L = l1
+  const bool selR1 = !(order_key(r1) < order_key(r2));     // S_R = r1
   const double SL = selL1 ? l1 : l2, SR = selR1 ? r1 : r2;
-  const double mL = rL * (SL - uL), mR = rR * (SR - uR);
-  const double rd = rcp_nr(mL - mR);
-  const double Ss = fma(-mR, uR, fma(mL, uL, pR - pL)) * rd;
+  const double dL = S(SL, uL), dR = S(SR, uR);
+  const double mL = M(rL, dL), mR = M(rR, dR);
+  const double rd = rcp_nr(S(mL, mR), k);
+  const double Ss = M(fma(-mR, uR, fma(mL, uL, S(pR, pL))), rd);
   const bool left = ge0(Ss);
   const double rK = sel(left, rL, rR), uK = sel(left, uL, uR), vK = sel(left, vL, vR);
-  const double wK = sel(left, wL, wR), pK = sel(left, pL, pR), hK = sel(left, hL, hR);
-  const double SK = sel(left, SL, SR), mK = sel(left, mL, mR);
+  const double wK = sel(left, wL, wR), pK = sel(left, pL, pR);
+  const double SK = sel(left, SL, SR), mK = sel(left, mL, mR), dK = sel(left, dL, dR);
   const bool fan = left ? lt0(SL) : gt0(SR);
-  const double rr = rcp_nr(SK - Ss);
-  const double delta = (Ss - uK) * rr;
-  const double g = sel(fan, SK, 0.0) * delta;
-  const double mass = rK * uK;
-  const double F0 = fma(g, rK, mass);
+  const double R = rcp_nr(S(SK, Ss), k);                   // used inside the fan only
+  const double dKR = M(dK, R);
+  const double t = sel(fan, M(Ss, dKR), uK);
+  const double g = S(t, uK);
+  const double kK = fma(wK, wK, fma(vK, vK, M(uK, uK)));
+  const double hK = fma(half_pos(rK), kK, M(e.g_gm1, pK));
+  const double gm = M(g, mK);
+  const double F0 = M(rK, t);
   // ---- reverse ----
-  const double bF0 = bF[0] + bF[2] * vK + bF[3] * wK;
-  const double bvK = bF[2] * F0, bwK = bF[3] * F0;
-  double buK = bF[4] * hK;
-  double bhK = bF[4] * (uK + g);
-  double bg = bF[4] * fma(mK, Ss, hK);
-  const double bmK = bF[4] * g * Ss;
-  double bSs = bF[4] * g * mK;
-  double bmass = bF[1] * uK;
-  buK += bF[1] * mass;
-  const double bpK = bF[1];
-  bg += bF[1] * rK * SK;
-  double brK = bF[1] * g * SK;
-  double bSK = bF[1] * g * rK;
-  bmass += bF0;
-  bg += bF0 * rK;
-  brK += bF0 * g;
-  brK += bmass * uK;
-  buK += bmass * rK;
-  const double bdelta = fan ? bg * SK : 0.0;
-  if (fan) bSK += bg * delta;
-  bSs += bdelta * (SK - uK) * rr * rr;
-  buK -= bdelta * rr;
-  bSK -= bdelta * delta * rr;
-  double brL = 0, buL = 0, bvL = 0, bwL = 0, bpL = 0, bhL = 0, bSL = 0, bmL = 0;
-  double brR = 0, buR = 0, bvR = 0, bwR = 0, bpR = 0, bhR = 0, bSR = 0, bmR = 0;
-  if (left) {
-    brL = brK; buL = buK; bvL = bvK; bwL = bwK; bpL = bpK; bhL = bhK; bSL = bSK; bmL = bmK;
-  } else {
-    brR = brK; buR = buK; bvR = bvK; bwR = bwK; bpR = bpK; bhR = bhK; bSR = bSK; bmR = bmK;
-  }
-  const double bnum = bSs * rd, bden = -bSs * Ss * rd;
-  bpR += bnum;
-  bpL -= bnum;
-  bmL += bnum * uL + bden;
-  buL += bnum * mL;
-  bmR -= bnum * uR + bden;
-  buR -= bnum * mR;
-  brL += bmL * (SL - uL);
-  bSL += bmL * rL;
-  buL -= bmL * rL;
-  brR += bmR * (SR - uR);
-  bSR += bmR * rR;
-  buR -= bmR * rR;
-  double but = 0, bct = 0, bcL = 0, bcR = 0;
-  if (selL1) { buL += bSL; bcL -= bSL; } else { but += bSL; bct -= bSL; }
-  if (selR1) { buR += bSR; bcR += bSR; } else { but += bSR; bct += bSR; }
-  const double bzc = bct * 0.5 * qc;
-  const double bHt = bzc * e.gm1, bkt = -0.5 * bzc * e.gm1;
-  but += 2.0 * ut * bkt;
-  const double bvt = 2.0 * vt * bkt, bwt = 2.0 * wt * bkt;
-  const double bT = bHt * w;
-  double bw = bHt * T;
-  bhL += bT * aL;
-  bhR += bT * aR;
-  double baL = bT * hL, baR = bT * hR;
-  const double bwl = but * uL + bvt * vL + bwt * wL;
-  const double bwr = but * uR + bvt * vR + bwt * wR;
-  buL += but * wl; bvL += bvt * wl; bwL += bwt * wl;
-  buR += but * wr; bvR += bvt * wr; bwR += bwt * wr;
-  double bsL = bwl * w, bsR = bwr * w;
-  bw += bwl * sL + bwr * sR;
-  const double bss = -bw * w * w;
-  bsL += bss;
-  bsR += bss;
-  const double bzL = bcL * 0.5 * qL, bzR = bcR * 0.5 * qR;
-  bpL += bzL * e.gamma * iL;
-  bpR += bzR * e.gamma * iR;
-  const double biL = bzL * e.gamma * pL, biR = bzR * e.gamma * pR;
-  brL += bhL * 0.5 * kL;
-  brR += bhR * 0.5 * kR;
-  const double bkL = bhL * 0.5 * rL, bkR = bhR * 0.5 * rR;
-  bpL += bhL * e.g_gm1;
-  bpR += bhR * e.g_gm1;
-  buL += 2.0 * uL * bkL; bvL += 2.0 * vL * bkL; bwL += 2.0 * wL * bkL;
-  buR += 2.0 * uR * bkR; bvR += 2.0 * vR * bkR; bwR += 2.0 * wR * bkR;
-  baL += 2.0 * aL * biL + bsL * rL;
-  baR += 2.0 * aR * biR + bsR * rR;
-  brL += bsL * aL;
-  brR += bsR * aR;
-  brL += baL * (-0.5 * aL * iL);
-  brR += baR * (-0.5 * aR * iR);
+  // F2 = vK F0, F3 = wK F0
+  const double bF0 = fma(bF[3], wK, fma(bF[2], vK, bF[0]));
+  double bvK = M(bF[2], F0), bwK = M(bF[3], F0);
+  // F4 = hK t + gm Ss
+  const double bhK = M(bF[4], t);
+  double bt = M(bF[4], hK);
+  double bgm = A(M(bF[4], Ss), bF[1]);                     // with F1's direct term
+  double bSs = M(bF[4], gm);
+  // F1 = F0 uK + pK + gm
+  const double bF0t = fma(bF[1], uK, bF0);
+  double buK = M(bF[1], F0);
+  double bpK = bF[1];
+  // F0 = rK t
+  double brK = M(bF0t, t);
+  bt = fma(bF0t, rK, bt);
+  // gm = g mK
+  const double bg = M(bgm, mK);
+  const double bmK = M(bgm, g);
+  // hK = rK kK / 2 + g_gm1 pK, kK = |u_K|^2
+  brK = fma(half_any(kK), bhK, brK);
+  const double bkK2 = M(bhK, rK);                          // 2 * (rK / 2) * bhK
+  bpK = fma(bhK, e.g_gm1, bpK);
+  buK = fma(bkK2, uK, buK);
+  bvK = fma(bkK2, vK, bvK);
+  bwK = fma(bkK2, wK, bwK);
+  // g = t - uK
+  bt = A(bt, bg);
+  buK = S(buK, bg);
+  // t = Ss dK R in the fan, R = 1 / (SK - Ss); t = uK outside it
+  const double btS = M(bt, Ss);
+  const double nbX = M(M(btS, dK), M(R, R));               // -(adjoint of SK - Ss)
+  bSs = sel(fan, A(fma(bt, dKR, bSs), nbX), bSs);
+  const double bdK = sel(fan, M(btS, R), 0.0);
+  const double nbSK = sel(fan, nbX, 0.0);                  // -(adjoint of SK)
+  buK = sel(fan, buK, A(buK, bt));
+  // the chosen side
+  double brL = sel(left, brK, 0.0), buL = sel(left, buK, 0.0), bvL = sel(left, bvK, 0.0);
+  double bwL = sel(left, bwK, 0.0), bpL = sel(left, bpK, 0.0);
+  double bmL = sel(left, bmK, 0.0), bdL = sel(left, bdK, 0.0);
+  double brR = sel(left, 0.0, brK), buR = sel(left, 0.0, buK), bvR = sel(left, 0.0, bvK);
+  double bwR = sel(left, 0.0, bwK), bpR = sel(left, 0.0, bpK);
+  double bmR = sel(left, 0.0, bmK), bdR = sel(left, 0.0, bdK);
+  const double nbSL = sel(left, nbSK, 0.0), nbSR = sel(left, 0.0, nbSK);
+  // Ss = N rd, N = pR - pL + mL uL - mR uR, rd = 1 / (mL - mR)
+  const double bN = M(bSs, rd);
+  const double nbD = M(bN, Ss);                            // -(adjoint of mL - mR)
+  bpR = A(bpR, bN);
+  bpL = S(bpL, bN);
+  bmL = S(fma(bN, uL, bmL), nbD);
+  buL = fma(bN, mL, buL);
+  bmR = A(fma(-bN, uR, bmR), nbD);
+  buR = fma(-bN, mR, buR);
+  // mL = rL dL, mR = rR dR; dL = SL - uL, dR = SR - uR
+  brL = fma(bmL, dL, brL);
+  bdL = fma(bmL, rL, bdL);
+  brR = fma(bmR, dR, brR);
+  bdR = fma(bmR, rR, bdR);
+  const double bSL = S(bdL, nbSL);
+  buL = S(buL, bdL);
+  const double bSR = S(bdR, nbSR);
+  buR = S(buR, bdR);
+  // SL = min(uL - cL, ut - ct), SR = max(uR + cR, ut + ct)
+  const double sLl = sel(selL1, bSL, 0.0), sLt = sel(selL1, 0.0, bSL);
+  const double sRr = sel(selR1, bSR, 0.0), sRt = sel(selR1, 0.0, bSR);
+  buL = A(buL, sLl);
+  buR = A(buR, sRr);
+  const double but = A(sLt, sRt);
+  const double bct = S(sRt, sLt);
+  // ct = sqrt(ct2): d ct / d ct2 = qc / 2
+  const double bct2 = M(half_any(bct), qc);
+  // ct2 = Bw du2 + wl cL2 + wr cR2, Bw = hgm1 wl wr
+  const double bBh = M(M(bct2, du2), e.hgm1);
+  const double b2 = M(A(bct2, bct2), Bw);                  // 2 * adjoint of du2
+  double bwl = fma(bct2, cL2, M(bBh, wr));
+  double bwr = fma(bct2, cR2, M(bBh, wl));
+  double bcL2 = M(bct2, wl), bcR2 = M(bct2, wr);
+  // du2 = du^2 + dv^2 + dw^2
+  const double bdu = M(b2, du), bdv = M(b2, dv), bdw = M(b2, dw);
+  buL = A(buL, bdu);
+  buR = S(buR, bdu);
+  bvL = A(bvL, bdv);
+  bvR = S(bvR, bdv);
+  bwL = A(bwL, bdw);
+  bwR = S(bwR, bdw);
+  // ut = wl uL + wr uR
+  bwl = fma(but, uL, bwl);
+  buL = fma(but, wl, buL);
+  bwr = fma(but, uR, bwr);
+  buR = fma(but, wr, buR);
+  // wr = r wl, wl = 1 / (1 + r)
+  bwl = fma(bwr, r, bwl);
+  const double br = fma(-bwl, M(wl, wl), M(bwr, wl));
+  // cL = sqrt(cL2) = cL2 qL, cR likewise; bcL = -sLl, bcR = sRr
+  bcL2 = fma(-half_any(sLl), qL, bcL2);
+  bcR2 = fma(half_any(sRr), qR, bcR2);
+  // cL2 = gamma pL iL, cR2 = gamma pR iR
+  bpL = fma(M(bcL2, iL), e.gamma, bpL);
+  bpR = fma(M(bcR2, iR), e.gamma, bpR);
+  const double biL = M(bcL2, gpL), biR = M(bcR2, gpR);
+  // iL = rR q2, iR = rL q2, r = rR q, q2 = q q
+  brR = fma(biL, q2, brR);
+  brL = fma(biR, q2, brL);
+  const double bq2 = fma(biL, rR, M(biR, rL));
+  brR = fma(br, q, brR);
+  const double bq = fma(br, rR, M(A(bq2, bq2), q));
+  // q = (rL rR)^(-1/2): d q / d(rL rR) = -q^3 / 2
+  const double nbP = M(M(half_any(bq), q), q2);
+  brL = fma(-nbP, rR, brL);
+  brR = fma(-nbP, rL, brR);
   bWL[0] = brL; bWL[1] = buL; bWL[2] = bvL; bWL[3] = bwL; bWL[4] = bpL;
   bWR[0] = brR; bWR[1] = buR; bWR[2] = bvR; bWR[3] = bwR; bWR[4] = bpR;
 }
@@ -265,12 +319,15 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   const int b = (int)(r / npen);
   const int p1 = pen % G.n1[d], p2 = pen / G.n1[d];
   const int nd = G.n[d];
-  const Eos& e = a.eos;
-  const double sc = scale * __ldg(a.inv_dx + 3 * b + d);
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers
+  const Rk& kr = e.k;
+  const double sc = reg_const(scale * __ldg(a.inv_dx + 3 * b + d), zt);
   const int rot[5] = {0, 1 + d, d == 0 ? 2 : 1, d == 2 ? 2 : 3, 4};
 
   double W[4][5];
   int ci, cj, ck;
+#pragma unroll
   for (int s = 0; s < 4; ++s) {
     // primitives of the stencil position (the halo gathered as in the stage kernel)
     pencil_to_cell(d, k - 2 + s, p1, p2, ci, cj, ck);
@@ -282,8 +339,8 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   int b0[5], b1[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    h0[v] = mc_half_slope_br(W[0][v], W[1][v], W[2][v], b0[v]);   // slope of position k-1
-    h1[v] = mc_half_slope_br(W[1][v], W[2][v], W[3][v], b1[v]);   // slope of position k
+    h0[v] = mc_half_slope_br(W[0][v], W[1][v], W[2][v], b0[v], kr);   // slope of position k-1
+    h1[v] = mc_half_slope_br(W[1][v], W[2][v], W[3][v], b1[v], kr);   // slope of position k
   }
   double bF[5];
   {
@@ -298,13 +355,13 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
       const long long o = own_offset(L, b, ci, cj, ck);
       for (int v = 0; v < 5; ++v) mk1[v] = __ldg(M + o + v * L.vstride);
     }
-    for (int v = 0; v < 5; ++v) bF[v] = sc * (mk[v] - mk1[v]);
+    for (int v = 0; v < 5; ++v) bF[v] = mul(sc, sub(mk[v], mk1[v], kr), kr);
   }
   double wl[5], wr[5], bFr[5], bwl[5], bwr[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    wl[q] = W[1][rot[q]] + h0[rot[q]];
-    wr[q] = W[2][rot[q]] - h1[rot[q]];
+    wl[q] = add(W[1][rot[q]], h0[rot[q]], kr);
+    wr[q] = sub(W[2][rot[q]], h1[rot[q]], kr);
     bFr[q] = bF[rot[q]];
   }
   hllc_flux_vjp(wl, wr, e, bFr, bwl, bwr);
@@ -314,10 +371,10 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const int v = rot[q];
-    Cs[1][v] += bwl[q];
-    Cs[2][v] += bwr[q];
-    mc_half_slope_vjp(b0[v], bwl[q], Cs[0][v], Cs[1][v], Cs[2][v]);
-    mc_half_slope_vjp(b1[v], -bwr[q], Cs[1][v], Cs[2][v], Cs[3][v]);
+    Cs[1][v] = add(Cs[1][v], bwl[q], kr);
+    Cs[2][v] = add(Cs[2][v], bwr[q], kr);
+    mc_half_slope_vjp<1>(b0[v], bwl[q], Cs[0][v], Cs[1][v], Cs[2][v], kr);
+    mc_half_slope_vjp<-1>(b1[v], bwr[q], Cs[1][v], Cs[2][v], Cs[3][v], kr);   // wr = W2 - h1
   }
   double* out = C + slot_index(G, d, b, pen, k, 0);
 #pragma unroll
@@ -348,6 +405,7 @@ __global__ void __launch_bounds__(128) vjp_face_kernel(const StageArgs a, const 
 // stage kernel) into Wp, state layout; the face pass gathers them.
 __global__ void vjp_prim_kernel(const StageArgs a, double* __restrict__ Wp) {
   const Layout& L = a.lay;
+  const Eos e = reg_eos(a.eos, thread_zero(a.eos));
   const long long per = (long long)L.nx * L.ny * L.nz;
   const long long total = per * L.nblocks;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -362,7 +420,7 @@ __global__ void vjp_prim_kernel(const StageArgs a, double* __restrict__ Wp) {
     double U[5], W[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
-    cons_to_prim(U, W, a.eos);
+    cons_to_prim(U, W, e);
 #pragma unroll
     for (int v = 0; v < 5; ++v) Wp[o + v * L.vstride] = W[v];
   }
@@ -371,12 +429,12 @@ __global__ void vjp_prim_kernel(const StageArgs a, double* __restrict__ Wp) {
 // Sum of the slots of block b, dimension d, pencil pen that refer to the
 // halo-extended position q (-2..n_d+1), in increasing face order.
 __device__ __forceinline__ void add_position(const FaceGeom& G, const double* __restrict__ C, int d, int b, int pen,
-                                             int q, double acc[5]) {
+                                             int q, double acc[5], const Rk& kr) {
   const int nd = G.n[d];
   for (int k = q - 1; k <= q + 2; ++k) {
     if (k < 0 || k > nd) continue;
     const double* c = C + slot_index(G, d, b, pen, k, q + 2 - k);
-    for (int v = 0; v < 5; ++v) acc[v] += c[v];
+    for (int v = 0; v < 5; ++v) acc[v] = add(acc[v], c[v], kr);
   }
 }
 
@@ -385,6 +443,10 @@ __device__ __forceinline__ void add_position(const FaceGeom& G, const double* __
 __global__ void vjp_cell_kernel(const StageArgs a, const FaceGeom G, const double* __restrict__ C, const double* A,
                                 double cA, const double* B, double cB, double* out) {
   const Layout& L = a.lay;
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers
+  const Rk& kr = e.k;
+  const double rcA = reg_const(cA, zt), rcB = reg_const(cB, zt);
   const long long per = (long long)L.nx * L.ny * L.nz;
   const long long total = per * L.nblocks;
   const int n[3] = {L.nx, L.ny, L.nz};
@@ -402,17 +464,17 @@ __global__ void vjp_cell_kernel(const StageArgs a, const FaceGeom G, const doubl
       const int pos = c[d];
       const int p1 = d == 0 ? j : i, p2 = d == 2 ? j : k;
       const int pen = p1 + G.n1[d] * p2;
-      add_position(G, C, d, b, pen, pos, bW);
+      add_position(G, C, d, b, pen, pos, bW, kr);
       // adjoint of the fused halo gather along d
       for (int side = 0; side < 2; ++side) {
         const bool near = side ? pos >= n[d] - 2 : pos < 2;
         if (!near) continue;
         const int nb = __ldg(a.face_nbr + 6 * b + 2 * d + side);
         if (nb >= 0) {
-          add_position(G, C, d, nb, pen, side ? pos - n[d] : pos + n[d], bW);
+          add_position(G, C, d, nb, pen, side ? pos - n[d] : pos + n[d], bW, kr);
         } else if (nb == GBH_BC_OUTFLOW && pos == (side ? n[d] - 1 : 0)) {
-          add_position(G, C, d, b, pen, side ? n[d] : -1, bW);
-          add_position(G, C, d, b, pen, side ? n[d] + 1 : -2, bW);
+          add_position(G, C, d, b, pen, side ? n[d] : -1, bW, kr);
+          add_position(G, C, d, b, pen, side ? n[d] + 1 : -2, bW, kr);
         }
       }
     }
@@ -420,13 +482,13 @@ __global__ void vjp_cell_kernel(const StageArgs a, const FaceGeom G, const doubl
     double U[5], W[5], bU[5];
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
     bool fr, fp;
-    cons_to_prim_flags(U, W, a.eos, fr, fp);
-    prim_vjp(W, fr, fp, a.eos, bW, bU);
+    cons_to_prim_flags(U, W, e, fr, fp);
+    prim_vjp(W, fr, fp, e, bW, bU);
     for (int v = 0; v < 5; ++v) {
       const long long ov = o + v * L.vstride;
       double x = bU[v];
-      if (A) x = fma(cA, A[ov], x);
-      if (B) x = fma(cB, B[ov], x);
+      if (A) x = fma(rcA, A[ov], x);
+      if (B) x = fma(rcB, B[ov], x);
       out[ov] = x;
     }
   }

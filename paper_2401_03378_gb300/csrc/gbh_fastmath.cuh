@@ -85,6 +85,14 @@ __device__ __forceinline__ double half_any(double x) {
   return bitsd(m2 >= (4ULL << 52) ? dbits(x) - (1LL << 52) : (long long)(sign_bit(x) | (m2 >> 2)));
 }
 
+// x / 4 for any finite x on the integer pipe: two off the exponent field when
+// |x| >= 2^-1020, else the magnitude bits shifted right by two (which moves
+// the result by less than 2^-1022)
+__device__ __forceinline__ double quarter_any(double x) {
+  const unsigned long long m2 = mag_key(x);
+  return bitsd(m2 >= (6ULL << 52) ? dbits(x) - (2LL << 52) : (long long)(sign_bit(x) | (m2 >> 3)));
+}
+
 __device__ __forceinline__ double rcp_approx(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));

@@ -151,19 +151,46 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
     __syncthreads();
 
-    // Work-list rotation: the item -> thread map of (B) and (C) is shifted by
-    // 32 * rot threads, rot = (k + CTA) mod 4, so the leftover warp passes of
-    // these lists (6 and 17 warp passes at N = 16) do not always fall to the
-    // same warps; the items and their arithmetic are unchanged.
+    // Work-list rotation: the item -> thread map of (B) is shifted by
+    // 32 * rot threads, rot = (k + CTA) mod 4, so the warps left without an
+    // item (7 warp passes for 8 warps at N = 16) are not always the same ones;
+    // the items and their arithmetic are unchanged.
     const int rtid = NT % 128 == 0 ? (tid + 32 * ((k + (int)blockIdx.x) & 3)) % NT : tid;
 
     // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M],
     //     three consecutive cells per work item, so the two inner differences
     //     are formed once for two slopes (the last triple of a row may be
     //     partial: its reads are clamped to the row and its extra slopes not
-    //     stored)
+    //     stored).  The list ends with the 2 M block-boundary faces x = M - 1/2
+    //     and y = M - 1/2, each forming the two face states it needs from the
+    //     primitives (the same arithmetic as the slope items): so (C) is
+    //     exactly 2 M^2 faces, two full passes of the CTA, with no ragged pass.
     constexpr int TR = (M + 2 + 2) / 3;               // triples per row
-    for (int s = rtid; s < 2 * TR * M; s += NT) {
+    for (int s = rtid; s < 2 * TR * M + 2 * M; s += NT) {
+      if (s >= 2 * TR * M) {
+        const int f = s - 2 * TR * M;
+        const bool xf = f < M;
+        const int line = xf ? f : f - M;                        // row j (x face) or column i (y face)
+        const int step = xf ? 1 : P;
+        const int first = xf ? (line + 2) * P + M : M * P + line + 2;   // position M - 2 along the normal
+        double ql[5], qr[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double* q = sW + GBH_IX(v * P * P + first, 5 * P * P - 3 * step);
+          const double a0 = q[0], a1 = q[step], a2 = q[2 * step], a3 = q[3 * step];
+          const double d0 = sub(a1, a0, rk), d1 = sub(a2, a1, rk), d2 = sub(a3, a2, rk);
+          ql[v] = add(a1, mc_half_slope_d(d0, d1, rk), rk);   // plus state of cell M - 1
+          qr[v] = sub(a2, mc_half_slope_d(d1, d2, rk), rk);   // minus state of cell M
+        }
+        const int vn = xf ? 1 : 2, vt = xf ? 2 : 1;
+        double wl[5] = {ql[0], ql[vn], ql[vt], ql[3], ql[4]};
+        double wr[5] = {qr[0], qr[vn], qr[vt], qr[3], qr[4]};
+        double F[5];
+        hllc_flux(wl, wr, e, F);
+        double* o = xf ? sFx + GBH_IX(line * (M + 1) + M, FX) : sFy + GBH_IX(M * M + line, FX);
+        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+        continue;
+      }
       const bool xs = s < TR * M;
       const int s2 = xs ? s : s - TR * M;
       const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // row (x) or column (y); first slope cell + 1
@@ -198,20 +225,21 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
     __syncthreads();
 
-    // (C) HLLC on the x faces (i - 1/2, i in [0, M]) and y faces (j - 1/2, j in [0, M])
-    for (int f = rtid; f < 2 * FX; f += NT) {
-      const bool xf = f < FX;
+    // (C) HLLC on the x faces (i - 1/2, i in [0, M - 1]) and y faces (j - 1/2,
+    //     j in [0, M - 1]); the faces at M - 1/2 came with (B)
+    for (int f = tid; f < 2 * M * M; f += NT) {
+      const bool xf = f < M * M;
       int i, j;
       const double *ql, *qr;       // minus/plus state arrays, var stride vs
       int vs, ol, orr;
       if (xf) {
-        i = f % (M + 1); j = f / (M + 1);
+        i = f % M; j = f / M;
         vs = M * (M + 2);
         ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
         orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
-        const int f2 = f - FX;
+        const int f2 = f - M * M;
         i = f2 % M; j = f2 / M;
         vs = (M + 2) * M;
         ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
@@ -303,7 +331,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 // `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
 // grid makes the kernel persistent).  No CTA waits on another.
 template <int N, bool DIM3, int E>
-__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E)) stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E), E == 0 ? 2 : 1) stage_kernel(const StageArgs a) {
   extern __shared__ double smem[];
   __shared__ double s_red[E == 0 && N * N > 32 ? N * N / 32 : 1];
   const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;

@@ -1179,6 +1179,11 @@ static int pipe_setup(gbh_ctx* c) {
   K = K < 1 ? 1 : (K > 64 ? 64 : (K > NB ? NB : K));
   c->pipe_first.resize(K + 1);
   for (int k = 0; k <= K; ++k) c->pipe_first[k] = (int)((long long)NB * k / K);
+  if (c->pipe_chunks_wanted == 0 && (long long)wave * (K - 1) < NB && (K - 1) * wave > 0) {
+    // whole waves, the remainder last
+    for (int k = 0; k < K; ++k) c->pipe_first[k] = k * wave;
+    c->pipe_first[K] = NB;
+  }
   std::vector<int> chunk_of(NB);
   for (int k = 0; k < K; ++k)
     for (int b = c->pipe_first[k]; b < c->pipe_first[k + 1]; ++b) chunk_of[b] = k;

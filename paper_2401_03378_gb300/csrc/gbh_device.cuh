@@ -61,33 +61,14 @@ __device__ __forceinline__ double mc_half_slope(double qm, double q0, double qp)
   return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
 }
 
-// Twice the MC-limited slope, 2 sigma = sign(dp) * min(|dm+dp|, 4|dm|, 4|dp|)
-// if dm, dp have the same strict sign, else 0; the face values q0 -/+ sigma/2
-// are then fma(-/+0.25, 2 sigma, q0), bit for bit the values of
-// mc_half_slope.  The factors 4 are added to the exponent fields (exact for
-// normal numbers; a subnormal |dm| or |dp| would compare as if it were about
-// 2^-1020, which moves the result by less than that), saving the FP64
-// multiply by 1/4.  One FP64 operation (the sum).
-__device__ __forceinline__ double mc_slope_x2_d(double dm, double dp) {
-  const double sum = dm + dp;
-  const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(sum);
-  unsigned long long m = (am < ap ? am : ap) + (4ULL << 52);   // min(4|dm|, 4|dp|): exponent + 2 in key form
-  m = as < m ? as : m;
-  const bool same = ((dbits(dm) ^ dbits(dp)) >= 0) && am != 0 && ap != 0;
-  return bitsd(same ? (long long)((m >> 1) | sign_bit(dp)) : 0LL);
-}
-
-// The same from the cell values (dm = q0 - qm, dp = qp - q0).
-__device__ __forceinline__ double mc_slope_x2(double qm, double q0, double qp) {
-  return mc_slope_x2_d(q0 - qm, qp - q0);
-}
-
-// Half the MC-limited slope from the differences, sigma/2 = (2 sigma) / 4,
-// with 2 sigma as in mc_slope_x2_d and the division by 4 taken off the
-// exponent field on the integer pipe (exact for results >= 2^-1020; below,
-// the bit pattern is shifted, which moves the result by less than 2^-1020).
-// The face values are then q0 -/+ sigma/2 as register FMAs.  One FP64
-// operation (the sum).
+// Half the MC-limited slope from the differences dm = q0 - qm, dp = qp - q0:
+//   sigma/2 = sign(dp) * min(|dm+dp|, 4|dm|, 4|dp|) / 4
+// if dm, dp have the same strict sign, else 0, so the face values are
+// q0 -/+ sigma/2 (register FMAs).  The factors 4 are added to the exponent
+// fields of |dm|, |dp| and the division by 4 taken off the exponent of the
+// minimum, on the integer pipe: exact for normal numbers (a subnormal |dm| or
+// |dp|, or a minimum below 2^-1020, is scaled by shifting the bit pattern,
+// which moves the result by less than 2^-1020).  One FP64 operation (the sum).
 __device__ __forceinline__ double mc_half_slope_d(double dm, double dp, const Rk& k) {
   const double sum = add(dm, dp, k);
   const unsigned long long am = mag_key(dm), ap = mag_key(dp), as = mag_key(sum);
@@ -136,12 +117,6 @@ __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, 
   s = fma(add(fabs(W[2]), c, k), idy, s);
   if (dim3) s = fma(add(fabs(W[3]), c, k), idz, s);
   return s;
-}
-
-// Signal-speed sum of one cell for the CFL rule (W from cons_to_prim).
-__device__ __forceinline__ double signal_speed(const double W[5], const Eos& e, double idx,
-                                               double idy, double idz, bool dim3) {
-  return signal_speed_ir(W, rcp_nr(W[0], e.k), e, idx, idy, idz, dim3);
 }
 
 // calcFlux role: HLLC flux through a face whose normal is the first velocity

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
   const long long per = (long long)L.nx * L.ny * L.nz;
   const long long total = per * (a.block_list ? a.nlist : L.nblocks);
   const bool d3 = L.ndim == 3;
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers (gbh_fastmath.cuh)
   double smax = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -91,9 +93,10 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
     double ir;
-    cons_to_prim_ir(U, W, a.eos, ir);
-    const double s = signal_speed_ir(W, ir, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
-                                  __ldg(a.inv_dx + 3 * b + 2), d3);
+    cons_to_prim_ir(U, W, e, ir);
+    const double s = signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * b), zt),
+                                     reg_const(__ldg(a.inv_dx + 3 * b + 1), zt),
+                                     reg_const(__ldg(a.inv_dx + 3 * b + 2), zt), d3);
     smax = fmax(smax, s);
   }
   __shared__ double red[kThreads / 32];
@@ -119,6 +122,8 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
   const Layout& L = a.lay;
   const int per = L.nx * L.ny * L.nz;
   const bool d3 = L.ndim == 3;
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers (gbh_fastmath.cuh)
   __shared__ double red[kThreads / 32];
   const int nb = a.block_list ? a.nlist : L.nblocks;
   for (int s = blockIdx.x; s < nb; s += gridDim.x) {
@@ -132,9 +137,10 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
 #pragma unroll
       for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
       double ir;
-      cons_to_prim_ir(U, W, a.eos, ir);
-      smax = fmax(smax, signal_speed_ir(W, ir, a.eos, __ldg(a.inv_dx + 3 * b), __ldg(a.inv_dx + 3 * b + 1),
-                                     __ldg(a.inv_dx + 3 * b + 2), d3));
+      cons_to_prim_ir(U, W, e, ir);
+      smax = fmax(smax, signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * b), zt),
+                                        reg_const(__ldg(a.inv_dx + 3 * b + 1), zt),
+                                        reg_const(__ldg(a.inv_dx + 3 * b + 2), zt), d3));
     }
     const double m = block_max<kThreads>(smax, red);
     if (threadIdx.x == 0) atomicMax(a.smax_acc + __ldg(problem + b), (unsigned long long)__double_as_longlong(m));

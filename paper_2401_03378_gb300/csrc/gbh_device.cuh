@@ -145,7 +145,7 @@ __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, 
 //          + (gamma-1)/2 w_L w_R |u_L - u_R|^2,
 // a sum of non-negative terms (no cancellation at high Mach number), so the
 // transverse Roe velocities and H~ are not formed.  h_K is formed for the
-// chosen side only.  83 FP64 operations per face.
+// chosen side only, and u~ = u_L - w_R (u_L - u_R).  82 FP64 operations per face.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
   const Rk& k = e.k;
@@ -160,8 +160,8 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
 
   const double r = mul(rR, q, k);                          // sqrt(rho_R / rho_L)
   const double wl = rcp_nr(add(r, k.one, k), k), wr = mul(r, wl, k);   // Roe weights
-  const double ut = fma(wl, uL, mul(wr, uR, k));
   const double du = sub(uL, uR, k), dv = sub(vL, vR, k), dw = sub(wL, wR, k);
+  const double ut = fma(-wr, du, uL);                      // w_L u_L + w_R u_R
   const double du2 = fma(dw, dw, fma(dv, dv, mul(du, du, k)));
   const double ct = sqrt_nr(fma(mul(e.hgm1, mul(wl, wr, k), k), du2, fma(wl, cL2, mul(wr, cR2, k))), k);
 

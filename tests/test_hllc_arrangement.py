@@ -2,11 +2,11 @@
 
 The oracle computes the HLLC flux with Einfeldt / Roe wave-speed bounds in the
 textbook form (Roe-averaged H and transverse velocities, Toro's star state).
-The stage kernel and its adjoint evaluate an algebraically equal arrangement
-with fewer FP64 operations:
+The stage kernel evaluates an algebraically equal arrangement with fewer FP64
+operations (its adjoint the same one, with u~ = w_L u_L + w_R u_R):
 - one reciprocal square root q = 1/sqrt(rho_L rho_R) gives 1/rho_L = rho_R q^2,
   1/rho_R = rho_L q^2 and the Roe ratio r = sqrt(rho_R/rho_L) = rho_R q;
-- Roe weights w_L = 1/(1 + r), w_R = r w_L;
+- Roe weights w_L = 1/(1 + r), w_R = r w_L, and u~ = u_L - w_R (u_L - u_R);
 - the Roe sound speed as w_L c_L^2 + w_R c_R^2 + (gamma-1)/2 w_L w_R |u_L - u_R|^2,
   equal to (gamma-1)(H~ - |u~|^2/2) because H_K = c_K^2/(gamma-1) + |u_K|^2/2 and
   w_L + w_R = 1;
@@ -40,7 +40,7 @@ def arranged_hllc(WL, WR, gamma=G):
     r = rR * q
     wl = 1.0 / (1.0 + r)
     wr = r * wl
-    ut = wl * uL + wr * uR
+    ut = uL - wr * (uL - uR)
     du2 = (uL - uR) ** 2 + (vL - vR) ** 2 + (wL - wR) ** 2
     ct = math.sqrt(0.5 * (gamma - 1.0) * wl * wr * du2 + wl * cL2 + wr * cR2)
     SL = min(uL - cL, ut - ct)

@@ -116,7 +116,7 @@ __device__ __forceinline__ void prim_vjp(const double W[5], bool fr, bool fp, co
 // state through t = u_K + g), then (dF/dW)^T bF is accumulated step by step
 // in reverse.  Branches (the min / max of the wave-speed bounds, the side K,
 // the fan) keep the forward's decisions and are taken by selects.
-__device__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos& e, const double bF[5],
+__device__ __forceinline__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos& e, const double bF[5],
                               double bWL[5], double bWR[5]) {
   const Rk& k = e.k;
   auto A = [&](double x, double y) { return fma(x, k.one, y); };    // x + y
@@ -384,7 +384,7 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) vjp_face_kernel(const StageArgs a, const FaceGeom G,
+__global__ void __launch_bounds__(128, 4) vjp_face_kernel(const StageArgs a, const FaceGeom G,
                                                       const double* __restrict__ Wp, const double* __restrict__ M,
                                                       double scale, double* __restrict__ C) {
   const Layout& L = a.lay;

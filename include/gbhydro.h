@@ -68,7 +68,7 @@ typedef struct gbh_params {
   int nblocks;            /* >= 1 */
   double gamma;           /* ratio of specific heats, > 1 */
   double cfl;             /* Courant number for hydro_compute_dt / hydro_step_cfl, in (0, 1] */
-  double small_rho;       /* density floor used when converting conserved -> primitive (e.g. 1e-12), >= 1e-300 */
+  double small_rho;       /* density floor used when converting conserved -> primitive (e.g. 1e-12), >= 1e-150 */
   double small_p;         /* pressure floor, same use (e.g. 1e-14) */
   const int32_t *nbr;     /* HOST [nblocks][3^ndim]: block id (>= 0) of the neighbour at lattice offset
                              (ox, oy[, oz]) in {-1,0,1}^ndim, entry index (oz+1)*9 + (oy+1)*3 + (ox+1)

@@ -388,8 +388,9 @@ int validate_params(const gbh_params* p, bool allow_coarser) {
   if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return set_err(nullptr, GBH_ERR_INVAL, "gamma must be > 1");
   if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return set_err(nullptr, GBH_ERR_INVAL, "cfl must be in (0, 1]");
   if (!(p->small_rho > 0.0) || !(p->small_p > 0.0)) return set_err(nullptr, GBH_ERR_INVAL, "floors must be > 0");
-  if (!(p->small_rho >= 1e-300))
-    return set_err(nullptr, GBH_ERR_INVAL, "small_rho must be >= 1e-300 (densities are kept normal numbers)");
+  if (!(p->small_rho >= 1e-150))
+    return set_err(nullptr, GBH_ERR_INVAL,
+                   "small_rho must be >= 1e-150 (the HLLC flux takes 1/sqrt(rho_L rho_R), which must stay a normal number)");
   if (!p->nbr || !p->dx) return set_err(nullptr, GBH_ERR_INVAL, "nbr and dx tables are required");
   const int nn = p->ndim == 3 ? 27 : 9;
   const int centre = p->ndim == 3 ? 13 : 4;

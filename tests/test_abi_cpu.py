@@ -80,6 +80,7 @@ def _params(**over):
     (dict(nzb=1), -1),
     (dict(nxb=12, nyb=12), -5),
     (dict(nxb=16, nyb=8, nguard=4), -5),
+    (dict(small_rho=1e-200), -1),   # 1/sqrt(rho_L rho_R) in the HLLC flux must stay normal
 ])
 def test_create_rejects_invalid_params_without_gpu(lib, over, code):
     p, keep = _params(**over)

@@ -365,6 +365,14 @@ int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, int form, doub
  * IEEE 1/sqrt(x) | refined sqrt(x) | IEEE sqrt(x)].  Not part of the method. */
 int gbh_fastmath_selftest(const double *x_dev, double *out_dev, long long n, void *stream);
 
+/* Self-test of the integer-pipe helpers of the stage kernel (not part of the
+ * method): for n finite DEVICE doubles x_dev, y_dev writes 6*n DEVICE doubles
+ * out_dev = [x/2 | x/4 (both from the exponent field, exact for normal
+ * results) | half the MC-limited slope from the differences x, y (dm, dp) |
+ * 1 if x >= 0 (also -0) else 0 | min(x, y) | max(x, y) (bit-pattern order)].
+ * GBH_ERR_INVAL for null pointers or n < 1. */
+int gbh_bits_selftest(const double *x_dev, const double *y_dev, double *out_dev, long long n, void *stream);
+
 /* Number of SMs of the current device (for sizing probes), or a negative error. */
 int gbh_device_sm_count(void);
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "gbh_stage_kernel_time": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _vp]),
     "gbh_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "gbh_fastmath_selftest": (C.c_int, [_dp, _dp, C.c_longlong, _vp]),
+    "gbh_bits_selftest": (C.c_int, [_dp, _dp, _dp, C.c_longlong, _vp]),
     "gbh_device_sm_count": (C.c_int, []),
     "gbh_check_violations": (C.c_int, [C.POINTER(C.c_longlong)]),
     "gbh_check_selftest": (C.c_int, [C.POINTER(C.c_longlong)]),

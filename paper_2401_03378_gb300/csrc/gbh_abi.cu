@@ -1386,6 +1386,13 @@ int gbh_fastmath_selftest(const double* x_dev, double* out_dev, long long n, voi
   return GBH_OK;
 }
 
+int gbh_bits_selftest(const double* x_dev, const double* y_dev, double* out_dev, long long n, void* stream) {
+  if (!x_dev || !y_dev || !out_dev || n < 1) return set_err(nullptr, GBH_ERR_INVAL, "invalid self-test arguments");
+  cudaError_t e = gbh::launch_bits_selftest(x_dev, y_dev, out_dev, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "self-test launch: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
 int gbh_check_violations(long long* count_host) {
   if (!count_host) return set_err(nullptr, GBH_ERR_INVAL, "count_host is NULL");
 #ifdef GBH_CHECK

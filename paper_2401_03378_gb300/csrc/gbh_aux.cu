@@ -219,6 +219,23 @@ __global__ void fastmath_selftest_kernel(const double* x, double* out, long long
   }
 }
 
+// Self-test of the integer-pipe helpers the stage kernel relies on:
+// out[6][n] = half_any(x), quarter_any(x), mc_half_slope_d(x, y) with the
+// constants in per-thread registers, ge0(x) (1 or 0), min_d(x, y), max_d(x, y).
+__global__ void bits_selftest_kernel(const double* x, const double* y, double* out, long long n, long long zero) {
+  const long long z = zero & (long long)threadIdx.x;
+  const Rk k{reg_const(1.0, z), reg_const(-0.0, z)};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = x[i], b = y[i];
+    out[i] = half_any(a);
+    out[n + i] = quarter_any(a);
+    out[2 * n + i] = mc_half_slope_d(a, b, k);
+    out[3 * n + i] = ge0(a) ? 1.0 : 0.0;
+    out[4 * n + i] = min_d(a, b);
+    out[5 * n + i] = max_d(a, b);
+  }
+}
+
 #ifdef GBH_CHECK
 // One index past a 4-element buffer: the check counts it and redirects the
 // store to element 0 (the access stays inside the buffer).
@@ -282,6 +299,11 @@ cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long lon
                          cudaStream_t s) {
   const long long work = (long long)lay.nblocks * lay.nx * lay.ny * lay.nz;
   check_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(U, lay, eos, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bits_selftest(const double* x, const double* y, double* out, long long n, cudaStream_t s) {
+  bits_selftest_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(x, y, out, n, 0);
   return cudaGetLastError();
 }
 

@@ -146,6 +146,7 @@ cudaError_t launch_axpby(const Layout& L, double a, const double* X, double b, c
 cudaError_t launch_prim_to_cons(const Layout& L, const Eos& e, const double* W, double* U, const double* lamU,
                                 double* lamW, cudaStream_t s);
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s);
+cudaError_t launch_bits_selftest(const double* x, const double* y, double* out, long long n, cudaStream_t s);
 
 // Checked build (-DGBH_CHECK, gbh_check.cuh): per translation unit, read and
 // clear the count of out-of-range indices (0 in the normal build, -1 if the

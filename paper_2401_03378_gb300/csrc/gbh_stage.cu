@@ -17,8 +17,11 @@
 //    is reconstructed and solved exactly once;
 //  - per plane, the primitives of the plane plus its 2-deep x/y rims go to
 //    shared memory; MC face states of the (N+2)*N x-slope cells and
-//    N*(N+2) y-slope cells, then the (N+1)*N x faces and N*(N+1) y faces are
-//    processed as flat work lists over all threads (full warps);
+//    N*(N+2) y-slope cells (with the 2N faces on the block's upper x and y
+//    boundaries, which form their own face states), then the remaining N*N x
+//    faces and N*N y faces are processed as flat work lists over all threads
+//    (full warps, two passes of the CTA for the faces);
+//  - all FP64 arithmetic is register FMAs (gbh_fastmath.cuh);
 //  - the update of the plane reads its x/y fluxes from shared memory and its
 //    z fluxes from registers and writes Uout.
 // Optional epilogue (second RK stage): max over the CTA of the CFL signal

@@ -135,11 +135,21 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       Fzp[0] = f[0]; Fzp[1] = f[2]; Fzp[2] = f[3]; Fzp[3] = f[1]; Fzp[4] = f[4];
     }
 
+    // Ring stages (E > 0): the next stage reads this stage's output only in
+    // its own box (ring width E - 2) and in 2-deep slabs across its faces.
+    // So in the outer z planes, outside that box, only the columns of the box
+    // are read: the window [2, M - 2) of the tile.  There the x/y work (rims,
+    // slopes, faces, update) is done on the window alone; its slopes need no
+    // rims.  Elsewhere the window is the whole tile (ow = 0, Mw = M).
+    const bool outer = E > 0 && (k < 2 - E || k >= L.nz + E - 2);
+    const int ow = outer ? 2 : 0;             // window offset in tile positions
+    const int Mw = M - 2 * ow;                // window width
+
     // (A) primitives of plane k and its 2-deep x/y rims -> shared memory
     //     (i, j: tile positions)
 #pragma unroll
     for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + ty + 2) * P + tx + 2, 5 * P * P)] = W0[v];
-    for (int r = tid; r < 8 * M; r += NT) {
+    for (int r = tid; r < (outer ? 0 : 8 * M); r += NT) {
       const int q = r / (2 * M), t = r - q * 2 * M;
       const int depth = t / M, pos = t - depth * M;
       int i, j;
@@ -168,14 +178,16 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     //     and y = M - 1/2, each forming the two face states it needs from the
     //     primitives (the same arithmetic as the slope items): so (C) is
     //     exactly 2 M^2 faces, two full passes of the CTA, with no ragged pass.
-    constexpr int TR = (M + 2 + 2) / 3;               // triples per row
-    for (int s = rtid; s < 2 * TR * M + 2 * M; s += NT) {
-      if (s >= 2 * TR * M) {
-        const int f = s - 2 * TR * M;
-        const bool xf = f < M;
-        const int line = xf ? f : f - M;                        // row j (x face) or column i (y face)
+    //     Positions below are in window coordinates (tile position minus ow).
+    const int TR = (Mw + 2 + 2) / 3;                  // triples per row
+    for (int s = rtid; s < 2 * TR * Mw + 2 * Mw; s += NT) {
+      if (s >= 2 * TR * Mw) {
+        const int f = s - 2 * TR * Mw;
+        const bool xf = f < Mw;
+        const int line = xf ? f : f - Mw;                       // row j (x face) or column i (y face)
         const int step = xf ? 1 : P;
-        const int first = xf ? (line + 2) * P + M : M * P + line + 2;   // position M - 2 along the normal
+        // position Mw - 2 along the normal
+        const int first = xf ? (line + ow + 2) * P + Mw + ow : (Mw + ow) * P + line + ow + 2;
         double ql[5], qr[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -190,18 +202,19 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         double wr[5] = {qr[0], qr[vn], qr[vt], qr[3], qr[4]};
         double F[5];
         hllc_flux(wl, wr, e, F);
-        double* o = xf ? sFx + GBH_IX(line * (M + 1) + M, FX) : sFy + GBH_IX(M * M + line, FX);
+        double* o = xf ? sFx + GBH_IX((line + ow) * (M + 1) + Mw + ow, FX)
+                       : sFy + GBH_IX((Mw + ow) * M + line + ow, FX);
         o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
         continue;
       }
-      const bool xs = s < TR * M;
-      const int s2 = xs ? s : s - TR * M;
+      const bool xs = s < TR * Mw;
+      const int s2 = xs ? s : s - TR * Mw;
       const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // row (x) or column (y); first slope cell + 1
       const int step = xs ? 1 : P;
-      const int first = xs ? (line + 2) * P + c0 : c0 * P + line + 2;
-      const int last = M + 3 - c0;                    // positions c0 .. M + 3 exist
+      const int first = xs ? (line + ow + 2) * P + c0 + ow : (c0 + ow) * P + line + ow + 2;
+      const int last = Mw + 3 - c0;                   // positions c0 .. Mw + 3 exist
       const int k3 = 3 < last ? 3 : last, k4 = 4 < last ? 4 : last;
-      const bool two = c0 + 1 < M + 2, three = c0 + 2 < M + 2;
+      const bool two = c0 + 1 < Mw + 2, three = c0 + 2 < Mw + 2;
 #pragma unroll 1
       for (int v = 0; v < 5; ++v) {
         const double* q = sW + v * P * P + first;
@@ -210,8 +223,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         const double d3 = sub(q[k4 * step], q3, rk);
         const double t0 = mc_half_slope_d(d0, d1, rk), t1 = mc_half_slope_d(d1, d2, rk);
         const double t2 = mc_half_slope_d(d2, d3, rk);
-        double* qm = xs ? sQx + GBH_IX((v * M + line) * (M + 2) + c0, 10 * QX)
-                        : sQy + GBH_IX((v * (M + 2) + c0) * M + line, 10 * QX);
+        double* qm = xs ? sQx + GBH_IX((v * M + line + ow) * (M + 2) + c0 + ow, 10 * QX)
+                        : sQy + GBH_IX((v * (M + 2) + c0 + ow) * M + line + ow, 10 * QX);
         const int os = xs ? 1 : M;                    // next slope cell
         const int op = 5 * QX;                        // plus states follow the minus states
         qm[0] = sub(q1, t0, rk);
@@ -230,20 +243,20 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 
     // (C) HLLC on the x faces (i - 1/2, i in [0, M - 1]) and y faces (j - 1/2,
     //     j in [0, M - 1]); the faces at M - 1/2 came with (B)
-    for (int f = tid; f < 2 * M * M; f += NT) {
-      const bool xf = f < M * M;
-      int i, j;
+    for (int f = tid; f < 2 * Mw * Mw; f += NT) {
+      const bool xf = f < Mw * Mw;
+      int i, j;                    // tile positions
       const double *ql, *qr;       // minus/plus state arrays, var stride vs
       int vs, ol, orr;
       if (xf) {
-        i = f % M; j = f / M;
+        i = f % Mw + ow; j = f / Mw + ow;
         vs = M * (M + 2);
         ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
         orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
-        const int f2 = f - M * M;
-        i = f2 % M; j = f2 / M;
+        const int f2 = f - Mw * Mw;
+        i = f2 % Mw + ow; j = f2 / Mw + ow;
         vs = (M + 2) * M;
         ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
         orr = (j + 1) * M + i;                // minus state of cell j (slot j+1)
@@ -268,9 +281,12 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     //     Uin + dt L = Uin - dt/dx dFx - dt/dy dFy - dt/dz dFz
     const long long base =
         (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (cj + L.g)) * L.nxp + (ci + L.g);
+    // in an outer plane of a ring stage only the window's cells are updated
+    // (the others are never read again and their fluxes were not formed)
+    const bool upd = !outer || (tx >= 2 && tx < M - 2 && ty >= 2 && ty < M - 2);
     double out[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < 5 && upd; ++v) {
       const double fx = sub(sFx[GBH_IX((v * M + ty) * (M + 1) + tx + 1, 5 * FX)], sFx[(v * M + ty) * (M + 1) + tx], rk);
       const double fy = sub(sFy[GBH_IX((v * (M + 1) + ty + 1) * M + tx, 5 * FX)], sFy[(v * (M + 1) + ty) * M + tx], rk);
       const long long o = GBH_IX(base + v * L.vstride, (long long)L.nblocks * L.bstride);

@@ -663,6 +663,15 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   }
   for (long long b = 0; b < NB; ++b) {
     if (par[4 * b] >= 0 || chl[8 * b] >= 0) continue;
+    // reflux_kernel corrects each cell next to a coarse-fine face from one
+    // thread per face cell: a block bordering the fine region through two faces
+    // would have its edge cells corrected by two threads at once
+    int cf = 0;
+    for (int f = 0; f < 2 * nd; ++f) cf += face[6 * b + f] >= 0 && chl[8 * face[6 * b + f]] >= 0;
+    if (cf > 1)
+      return set_err(nullptr, GBH_ERR_UNSUPPORTED,
+                     "coarse block %lld borders the refined region through %d faces; the flux correction "
+                     "supports one (refine a box, or boxes at least two coarse blocks apart)", b, cf);
     for (int f = 0; f < 2 * nd; ++f) {
       const int nb = face[6 * b + f];
       if (nb < 0 || chl[8 * nb] < 0) continue;

@@ -260,3 +260,80 @@ def test_batched_two_level_tables_and_checks_without_gpu(lib):
     bad = prob.copy(); bad[3] = 2
     assert attempt(bad) == -1 and b"out of range" in lib.gbh_last_error(None)
     assert attempt(prob, nproblems=0) == -1
+
+
+def refined_tables(ndim, nb0, n, refined, dx0):
+    """Two-level tables for any set of refined coarse blocks (coarse lattice
+    coordinates), non-periodic: fine blocks in lexicographic order of the fine
+    lattice, GBH_NBR_COARSER where a fine block's neighbour lies on the coarse
+    level.  For a box this is two_level_tables' layout."""
+    from paper_2401_03378_gb300.grid import GBH_BC_OUTFLOW, GBH_NBR_COARSER, neighbour_table
+    nd = ndim
+    nb0 = tuple(nb0) + (1,) * (3 - len(nb0))
+    ref = {tuple(c) + (0,) * (3 - len(c)) for c in refined}
+    n0 = nb0[0] * nb0[1] * nb0[2]
+    fdim = tuple(2 * nb0[d] if d < nd else 1 for d in range(3))
+    fine = [(fx, fy, fz) for fz in range(fdim[2]) for fy in range(fdim[1]) for fx in range(fdim[0])
+            if tuple(c // 2 if d < nd else 0 for d, c in enumerate((fx, fy, fz))) in ref]
+    fid = {fc: n0 + i for i, fc in enumerate(fine)}
+    offs = [(ox, oy, oz) for oz in ((-1, 0, 1) if nd == 3 else (0,)) for oy in (-1, 0, 1) for ox in (-1, 0, 1)]
+    nbr = np.concatenate([neighbour_table(nd, nb0, (False,) * 3),
+                          np.empty((len(fine), len(offs)), dtype=np.int32)])
+    parent = np.zeros((n0 + len(fine), 4), dtype=np.int32)
+    parent[:n0, 0] = -1
+    children = np.full((n0 + len(fine), 8), -1, dtype=np.int32)
+    for i, fc in enumerate(fine):
+        for e, o in enumerate(offs):
+            q = tuple(fc[d] + o[d] for d in range(3))
+            inside = all(0 <= q[d] < fdim[d] for d in range(3))
+            nbr[n0 + i, e] = fid.get(q, GBH_NBR_COARSER if inside else GBH_BC_OUTFLOW)
+        pc = tuple(fc[d] // 2 if d < nd else 0 for d in range(3))
+        pid = pc[0] + nb0[0] * (pc[1] + nb0[1] * pc[2])
+        parent[n0 + i] = (pid, *((fc[d] % 2) * (n[d] // 2) if d < nd else 0 for d in range(3)))
+        children[pid, sum((fc[d] % 2) << d for d in range(nd))] = n0 + i
+    dx = np.empty((n0 + len(fine), 3))
+    dx[:n0] = dx0
+    dx[n0:] = np.asarray(dx0) * 0.5
+    return nbr, dx, parent, children
+
+
+def test_create_refined_rejects_a_coarse_block_on_two_refined_faces_without_gpu(lib):
+    """The flux correction runs one thread per coarse face cell, so a coarse
+    block next to the refined region through two faces (the inner corner of an
+    L-shaped region) is refused before anything touches the GPU; a box is not."""
+    from paper_2401_03378_gb300 import _abi
+    from paper_2401_03378_gb300.grid import two_level_tables
+    dx0 = (1 / 32, 1 / 32, 1.0)
+    box = [(x, y) for y in (1, 2) for x in (1, 2)]
+    mine = refined_tables(2, (4, 4), (8, 8), box, dx0)
+    ref = two_level_tables(2, (4, 4, 1), (8, 8, 1), (1, 1), (3, 3), (False, False, False), dx0)
+    for a, b in zip(mine, ref):
+        assert np.array_equal(a, b)
+
+    def attempt(tables):
+        keep = [np.ascontiguousarray(x) for x in tables]
+        p = _abi.GbhParams()
+        p.ndim, p.nxb, p.nyb, p.nzb, p.nguard, p.nblocks = 2, 8, 8, 1, 4, keep[0].shape[0]
+        p.gamma, p.cfl, p.small_rho, p.small_p = 1.4, 0.8, 1e-12, 1e-14
+        p.nbr = keep[0].ctypes.data_as(C.POINTER(C.c_int32))
+        p.dx = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+        r = _abi.GbhRefinement()
+        r.parent = keep[2].ctypes.data_as(C.POINTER(C.c_int32))
+        r.children = keep[3].ctypes.data_as(C.POINTER(C.c_int32))
+        ctx = C.c_void_p()
+        rc = lib.gbh_create_refined(C.byref(p), C.byref(r), C.byref(ctx))
+        if rc == 0:
+            lib.gbh_destroy(ctx)
+        return rc, lib.gbh_last_error(None)
+
+    # L shape: coarse block (2, 2) borders (2, 1) across -y and (1, 2) across -x
+    rc, msg = attempt(refined_tables(2, (4, 4), (8, 8), [(1, 1), (2, 1), (1, 2)], dx0))
+    assert rc == -5 and b"coarse block 10 borders the refined region through 2 faces" in msg
+    # two boxes one coarse block apart in a 5 x 4 lattice: block (2, 1) sits between them
+    rc, msg = attempt(refined_tables(2, (5, 4), (8, 8), [(1, 1), (1, 2), (3, 1), (3, 2)], (1 / 40, 1 / 32, 1.0)))
+    assert rc == -5 and b"through 2 faces" in msg
+    # the box, and two boxes two coarse blocks apart, pass the table checks (without a GPU
+    # the context allocation then fails)
+    for tables in (mine, refined_tables(2, (8, 4), (8, 8), [(1, 1), (1, 2), (4, 1), (4, 2)], (1 / 64, 1 / 32, 1.0))):
+        rc, msg = attempt(tables)
+        assert rc in (0, -2, -4) and b"faces" not in msg, msg

@@ -204,16 +204,19 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
 // covered coarse blocks of Uin, prolong into the fine guard slabs that face
 // the coarser level, update the leaf blocks (writing the boundary fluxes to
 // the flux registers), and correct the coarse side of the fine-region
-// boundary.  Uin's covered blocks and fine guard cells are rewritten.
+// boundary.  Uin's covered blocks and fine guard cells are rewritten.  With
+// dt_epilogue (the last stage) the stage kernel and the correction also leave
+// the CFL signal-speed max of the leaf cells of Uout in the accumulator.
 int refined_stage(gbh_ctx* c, double* Uin, const double* Un, double* Uout, const double* dt_dev, double dt,
-                  double a, double b, cudaStream_t s) {
+                  double a, double b, bool dt_epilogue, cudaStream_t s) {
   int rc = cuda_err(c, gbh::launch_restrict(Uin, c->amr, s), "restrict launch");
   if (rc) return rc;
   rc = cuda_err(c, gbh::launch_prolong(Uin, c->amr, 2, true, s), "prolong launch");
   if (rc) return rc;
-  rc = stage_launch(c, Uin, Un, Uout, dt_dev, dt, a, b, true, false, s);
+  rc = stage_launch(c, Uin, Un, Uout, dt_dev, dt, a, b, true, dt_epilogue, s);
   if (rc) return rc;
-  return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, s), "reflux launch");
+  return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, dt_epilogue ? c->d_smax : nullptr, s),
+                  "reflux launch");
 }
 
 // Shu-Osher coefficients of the SSP-RK stages: U(s) = a_s U^n + b_s (U(s-1) +
@@ -246,13 +249,15 @@ double* flux_regs(gbh_ctx* c, int s) { return s == 0 ? c->d_flux_reg : s == 1 ? 
 
 // One SSP-RK step on a two-level grid, all-levels non-telescoping; ends with
 // the restriction of the new state so that covered coarse cells hold the
-// mean of their children.
-int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
+// mean of their children.  dt_epilogue: the CFL max of the new leaf cells goes
+// into the accumulator (the restriction changes covered blocks only).
+int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
   const RkCoef r = rk_coef(c->nstages);
   double* in = U;
   for (int st = 0; st < r.S; ++st) {
     double* out = stage_out(c, st, U);
-    int rc = refined_stage(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], s);
+    int rc = refined_stage(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st],
+                           dt_epilogue && st == r.S - 1, s);
     if (rc) return rc;
     in = out;
   }
@@ -292,7 +297,10 @@ int uniform_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt
 // correction with each stage's weight in U^{n+1}, restriction.  The two
 // levels need no data from each other inside the step, so both go through
 // the same launches; the paper's finest-first level loop orders nothing here.
-int refined_telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, cudaStream_t s) {
+// dt_epilogue: the CFL max of the new leaf cells goes into the accumulator
+// (the last stage's epilogue, and the last correction for the cells it changes).
+int refined_telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue,
+                             cudaStream_t s) {
   const RkCoef r = rk_coef(c->nstages);
   int rc = cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
   if (rc) return rc;
@@ -302,15 +310,17 @@ int refined_telescoping_step(gbh_ctx* c, double* U, const double* dt_dev, double
   const double* in = U;
   for (int st = 0; st < r.S; ++st) {
     double* out = stage_out(c, st, U);
-    rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], false, false, s,
-                      2 * (r.S - 1 - st), flux_regs(c, st));
+    rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], false,
+                      dt_epilogue && st == r.S - 1, s, 2 * (r.S - 1 - st), flux_regs(c, st));
     if (rc) return rc;
     in = out;
   }
   for (int st = 0; st < r.S; ++st) {
     gbh::AmrArgs A = c->amr;
     A.flux_reg = flux_regs(c, st);
-    if ((rc = cuda_err(c, gbh::launch_reflux(U, A, dt_dev, dt, rk_weight(r, st), s), "reflux launch"))) return rc;
+    unsigned long long* acc = dt_epilogue && st == r.S - 1 ? c->d_smax : nullptr;
+    if ((rc = cuda_err(c, gbh::launch_reflux(U, A, dt_dev, dt, rk_weight(r, st), acc, s), "reflux launch")))
+      return rc;
   }
   return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
 }
@@ -471,13 +481,9 @@ static int create_common(const gbh_params* p, gbh_ctx** out);
 extern "C" int gbh_destroy(gbh_ctx* c);
 
 static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
-  if (c->refined) {
-    // the CFL speed must see the flux-corrected state: separate reduction
-    int rc = c->telescoping ? refined_telescoping_step(c, U, dt_dev, 0.0, s) : refined_step(c, U, dt_dev, 0.0, s);
-    if (rc) return rc;
-    return reduce_dt(c, U, dt_dev, nullptr, s);
-  }
-  int rc = uniform_step(c, U, dt_dev, 0.0, true, s);
+  int rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, dt_dev, 0.0, true, s)
+                                        : refined_step(c, U, dt_dev, 0.0, true, s))
+                      : uniform_step(c, U, dt_dev, 0.0, true, s);
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
                   "dt finalize launch");
@@ -738,6 +744,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.flux_reg = c->d_flux_reg;
   A.flux_reg_len = (long long)c->flux_reg_doubles;
   A.inv_dx = c->d_inv_dx;
+  A.eos = c->eos;
   *out = c;
   return GBH_OK;
 }
@@ -1105,7 +1112,9 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if ((rc = check_dt(c, dt))) return rc;
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  if (c->refined) return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, s) : refined_step(c, U, nullptr, dt, s);
+  if (c->refined)
+    return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, false, s)
+                          : refined_step(c, U, nullptr, dt, false, s);
   return uniform_step(c, U, nullptr, dt, false, s);
 }
 
@@ -1245,15 +1254,11 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, s);
     if ((rc = cuda_err(c, e, "H2D copy"))) return rc;
     if (!given && (rc = reduce_dt(c, U, c->d_host_dt, nullptr, s))) return rc;
-    if (c->refined) {
-      rc = c->telescoping ? refined_telescoping_step(c, U, c->d_host_dt, 0.0, s)
-                          : refined_step(c, U, c->d_host_dt, 0.0, s);
-      if (!rc) rc = reduce_dt(c, U, c->d_pipe_dt, nullptr, s);
-    } else {
-      rc = uniform_step(c, U, c->d_host_dt, 0.0, true, s);
-      if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
-                             "dt finalize launch");
-    }
+    rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, c->d_host_dt, 0.0, true, s)
+                                      : refined_step(c, U, c->d_host_dt, 0.0, true, s))
+                    : uniform_step(c, U, c->d_host_dt, 0.0, true, s);
+    if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
+                           "dt finalize launch");
     if (rc) return rc;
     e = cudaMemcpyAsync(U_host, U, bstride * c->lay.nblocks, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt_host, c->d_pipe_dt, dtb, cudaMemcpyDeviceToHost, s);

@@ -211,9 +211,17 @@ __global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
 }
 
 // Flux correction on the coarse side of the fine-region boundary.  One
-// thread per (interface face, face cell).
-__global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, double dt_val, double coef) {
+// thread per (interface face, face cell); each corrected cell has a single
+// entry (gbh_create_refined refuses a coarse block bordering the refined
+// region through two faces).  With smax_acc (the last correction of a step),
+// the thread also forms the corrected cell's CFL signal-speed sum, which the
+// stage kernel's epilogue left out, and adds it to the step's max.
+__global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrArgs a, const double* dt_dev,
+                                                          double dt_val, double coef, unsigned long long* smax_acc) {
   const Layout& L = a.lay;
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers (gbh_fastmath.cuh)
+  double smax = 0.0;
   const int N = L.nx;
   const int n2 = L.ndim == 3 ? N : 1;
   const int half = N / 2;
@@ -241,6 +249,7 @@ __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, 
     const double* Ff = a.flux_reg + (long long)fs * sstride;
     const double idx = __ldg(a.inv_dx + 3 * en.block + d);
     const double nfine = L.ndim == 3 ? 0.25 : 0.5;
+    double Uc[5];
     for (int v = 0; v < 5; ++v) {
       double fsum = 0.0;
       for (int b2 = 0; b2 < (L.ndim == 3 ? 2 : 1); ++b2)
@@ -252,8 +261,25 @@ __global__ void reflux_kernel(double* U, const AmrArgs a, const double* dt_dev, 
                                   a.flux_reg_len) - (long long)en.coarse_slot * sstride];
       const double corr = side ? __dsub_rn(fc, fmean) : __dsub_rn(fmean, fc);
       const long long o = at(L, en.block, v, x[0], x[1], x[2]);
-      U[o] = __dadd_rn(U[o], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
+      U[o] = Uc[v] = __dadd_rn(U[o], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
     }
+    if (smax_acc) {
+      double W[5], ir;
+      cons_to_prim_ir(Uc, W, e, ir);
+      const double sp = signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * en.block), zt),
+                                        reg_const(__ldg(a.inv_dx + 3 * en.block + 1), zt),
+                                        reg_const(__ldg(a.inv_dx + 3 * en.block + 2), zt), L.ndim == 3);
+      if (a.problem)
+        atomicMax(smax_acc + __ldg(a.problem + en.block), (unsigned long long)__double_as_longlong(sp));
+      else
+        smax = fmax(smax, sp);
+    }
+  }
+  if (smax_acc && !a.problem) {
+    // one accumulator: warp max, one atomic per warp (every lane of the warp
+    // reaches this point: the block size is a multiple of 32)
+    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(smax_acc, (unsigned long long)__double_as_longlong(smax));
   }
 }
 
@@ -281,10 +307,10 @@ cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_on
 }
 
 cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, double dt, double coef,
-                          cudaStream_t s) {
+                          unsigned long long* smax_acc, cudaStream_t s) {
   if (a.nreflux == 0) return cudaSuccess;
   const long long per = (long long)a.lay.nx * (a.lay.ndim == 3 ? a.lay.nx : 1);
-  reflux_kernel<<<grid_for(per * a.nreflux), kThreads, 0, s>>>(U, a, dt_dev, dt, coef);
+  reflux_kernel<<<grid_for(per * a.nreflux), kThreads, 0, s>>>(U, a, dt_dev, dt, coef, smax_acc);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,8 @@
 //    z fluxes from registers and writes Uout.
 // Optional epilogue (second RK stage): max over the CTA of the CFL signal
 // speed of Uout, one 64-bit atomicMax per CTA on the bit pattern of the
-// non-negative double.
+// non-negative double (on two-level grids without the cells the flux
+// correction changes afterwards).
 //
 // Telescoping mode (Sec. 4.2): the earlier stages also update a ring of E
 // guard cells around the interior (E = 2 (S - s) for stage s of S), from the
@@ -42,6 +43,21 @@
 
 namespace gbh {
 namespace {
+
+// Two-level grids: a cell that the flux correction changes after this stage,
+// next to a face of a coarse block whose face neighbour is refined (a
+// flux-register slot and a block neighbour; the slotted faces of a fine block
+// face the coarser level instead).  The correction adds the CFL speed of these
+// cells itself.
+template <int N, bool DIM3>
+__device__ __forceinline__ bool corrected_cell(const StageArgs& a, int b, int i, int j, int k, int nz) {
+  if (!a.flux_slot) return false;
+  const int* fs = a.flux_slot + 6 * b;
+  const int* fn = a.face_nbr + 6 * b;
+  auto on = [&](int f) { return __ldg(fs + f) >= 0 && __ldg(fn + f) >= 0; };
+  return (i == 0 && on(FACE_XM)) || (i == N - 1 && on(FACE_XP)) || (j == 0 && on(FACE_YM)) ||
+         (j == N - 1 && on(FACE_YP)) || (DIM3 && k == 0 && on(FACE_ZM)) || (DIM3 && k == nz - 1 && on(FACE_ZP));
+}
 
 // One work item: block `b` of the list (or of the lattice) and z-chunk
 // `chunk`.  Uses the caller's shared memory; ends with the per-item atomics.
@@ -325,7 +341,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     if (E == 0 && a.smax_acc) {
       double W[5], ir;
       cons_to_prim_ir(out, W, e, ir);
-      smax = fmax(smax, signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3));
+      const double sp = signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3);
+      if (!corrected_cell<N, DIM3>(a, b, ci, cj, k, L.nz)) smax = fmax(smax, sp);
     }
 
     if (DIM3) {

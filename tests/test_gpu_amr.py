@@ -162,3 +162,77 @@ def test_refined_sedov_4096_plus_4096_sampled(gb):
     h.step(Ug, dt_o)
     assert np.all(leaf_err(host(Ug), ref, tl) <= 1e-13)
     assert h.floor_hits() == 0
+
+
+def banded(tl, side, seed):
+    """The smooth state with the pressure raised 30-fold in one layer of cells
+    along the fine region's boundary, so that the largest CFL speeds sit there:
+    side "coarse": the coarse cells just outside the box's faces (the cells the
+    flux correction changes); "beside": the next coarse layer out (same
+    blocks, not corrected); "fine": the first fine layer inside the box."""
+    c = tl.coarse
+    nd = c.ndim
+    blk = [c.n[d] * c.dx[d] for d in range(nd)]
+    lo = [tl.lo[d] * blk[d] for d in range(nd)]
+    hi = [tl.hi[d] * blk[d] for d in range(nd)]
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0, 2 * np.pi, 8)
+
+    def fn(X, Y, Z):
+        P = (X, Y, Z)
+        s = np.sin(2 * np.pi * X + ph[0]) * np.cos(2 * np.pi * Y + ph[1])
+        rho = 1 + 0.4 * s
+        u = 0.5 * np.sin(2 * np.pi * Y + ph[3]) + 0 * X
+        v = 0.4 * np.cos(2 * np.pi * X + ph[4])
+        w = 0.3 * np.sin(2 * np.pi * X + ph[5]) if nd == 3 else 0 * X
+        p = 1 + 0.3 * s
+        od = [np.maximum(np.maximum(lo[d] - P[d], P[d] - hi[d]), 0) for d in range(nd)]
+        one = np.sum([o > 0 for o in od], axis=0) == 1          # outside across one face only
+        out = np.max(od, axis=0)
+        inn = np.min([np.minimum(P[d] - lo[d], hi[d] - P[d]) for d in range(nd)], axis=0)
+        if side == "coarse":
+            band = one & (out < c.dx[0])
+        elif side == "beside":
+            band = one & (out > c.dx[0]) & (out < 2 * c.dx[0])
+        else:
+            band = (inn > 0) & (inn < 0.5 * c.dx[0])
+        return rho, u, v, w, np.where(band, 30.0 * p, p)
+    return wl.two_level_state(tl, fn)
+
+
+@pytest.mark.parametrize("tl", [GRIDS[0], GRIDS[1], GRIDS[4]])
+@pytest.mark.parametrize("side", ["coarse", "beside", "fine"])
+@pytest.mark.parametrize("mode", ["all-levels", "level-by-level", "three-stage"])
+def test_refined_step_dt_equals_a_separate_reduction(gb, tl, side, mode):
+    """The CFL dt of a two-level step comes from the last stage's epilogue over
+    the leaf cells the flux correction leaves alone and from the correction
+    kernel over the cells it changes.  It must equal, bit for bit, a separate
+    reduction over the final state, with the fastest cells on either side of
+    the coarse-fine boundary."""
+    U = banded(tl, side, 4)
+    h = gb.Hydro.from_two_level(tl)
+    if mode == "level-by-level":
+        h.set_telescoping(True)
+    if mode == "three-stage":
+        h.set_rk_stages(3)
+    Ug = dev(U)
+    h.fill_guardcells(Ug)
+    dt = h.compute_dt(Ug)
+    for _ in range(4):
+        h.step_cfl(Ug, dt)
+        ref = h.compute_dt(Ug)
+        assert host(dt)[0] == host(ref)[0]
+    zs, ys, xs = tl.coarse.interior_slices()
+    assert np.all(np.isfinite(host(Ug)[:, :, zs, ys, xs]))
+
+
+def test_refined_batched_step_dt_equals_a_separate_reduction(gb):
+    tls = [GRIDS[0], GRIDS[1]]
+    parts = [banded(tls[0], "coarse", 5), banded(tls[1], "fine", 6)]
+    h = gb.Hydro.from_two_level_batch(tls)
+    Ug = dev(np.concatenate(parts))
+    h.fill_guardcells(Ug)
+    dt = h.compute_dt(Ug)
+    for _ in range(3):
+        h.step_cfl(Ug, dt)
+        assert np.array_equal(host(dt), host(h.compute_dt(Ug)))

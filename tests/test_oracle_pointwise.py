@@ -177,6 +177,40 @@ def test_hllc_sod_face_star_pressure_bracketed():
     assert d["SR"] >= math.sqrt(1.4 * 0.1 / 0.125) - 1e-15
 
 
+def test_hllc_sod_face_in_50_digit_arithmetic():
+    """The initial Sod face worked through in 50-digit decimal arithmetic, step
+    by step from the definitions (Roe averages with sqrt(rho) weights, Einfeldt
+    bounds, Toro's contact speed and left star state; the fan straddles the
+    face with S* > 0, so F = F_L + S_L (U*_L - U_L)).  The oracle's double
+    result agrees to rounding: a check of its evaluation order and constants
+    at one stated face, beside the structural pins above."""
+    from decimal import Decimal as D, getcontext
+    getcontext().prec = 50
+    g = D("1.4")
+    rL, pL, rR, pR = D(1), D(1), D("0.125"), D("0.1")
+    EL, ER = pL / (g - 1), pR / (g - 1)                 # at rest: E = p / (gamma - 1)
+    cL, cR = (g * pL / rL).sqrt(), (g * pR / rR).sqrt()
+    r = rR.sqrt() / rL.sqrt()
+    ut = D(0)                                          # (u_L + r u_R) / (1 + r) with u = 0
+    HL, HR = (EL + pL) / rL, (ER + pR) / rR            # 3.5 and 2.8
+    Ht = (HL + r * HR) / (1 + r)
+    ct = ((g - 1) * (Ht - ut * ut / 2)).sqrt()
+    SL, SR = min(-cL, ut - ct), max(cR, ut + ct)
+    Ss = (pR - pL) / (rL * SL - rR * SR)               # Toro's contact speed with u_L = u_R = 0
+    assert Ss > 0 and SL < 0
+    k = rL * SL / (SL - Ss)                            # rho_L (S_L - u_L) / (S_L - S*)
+    Ustar = [k, k * Ss, D(0), D(0), k * (EL / rL + Ss * (Ss + pL / (rL * SL)))]
+    UL = [rL, D(0), D(0), D(0), EL]
+    FL = [D(0), pL, D(0), D(0), D(0)]
+    F = [FL[i] + SL * (Ustar[i] - UL[i]) for i in range(5)]
+    Fo, d = orc.hllc(np.array([1.0, 0, 0, 0, 1.0]), np.array([0.125, 0, 0, 0, 0.1]), detail=True)
+    scale = max(abs(float(x)) for x in F)
+    assert max(abs(Fo[i] - float(F[i])) for i in range(5)) <= 1e-15 * scale
+    for key, ref in (("SL", SL), ("SR", SR), ("Ss", Ss)):
+        assert abs(d[key] - float(ref)) <= 1e-15 * abs(float(ref))
+    assert Fo[2] == 0.0 and Fo[3] == 0.0
+
+
 def test_euler_flux_entry_point():
     for W in random_states(50, 9):
         assert rel(orc.euler_flux(W), euler_flux_by_definition(W)) < 1e-15

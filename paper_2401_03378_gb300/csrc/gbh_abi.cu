@@ -138,8 +138,11 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
   if (!c->timing) return GBH_OK;
   if (c->ev_used + 2 > c->ev.size()) {
     cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    if (cudaEventCreate(&a) != cudaSuccess) return set_err(c, GBH_ERR_CUDA, "cudaEventCreate failed");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
       return set_err(c, GBH_ERR_CUDA, "cudaEventCreate failed");
+    }
     c->ev.push_back(a);
     c->ev.push_back(b);
   }

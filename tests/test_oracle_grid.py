@@ -111,10 +111,13 @@ def test_sedov_radius_symmetry_energy():
     E0 = U[:, 4, zs, ys, xs].sum()
     M0 = U[:, 0, zs, ys, xs].sum()
     t = 0.0
+    peaks = []
     for n in range(1, 61):
         dt = o.compute_dt(U)
         assert o.step(U, dt) == 0
         t += dt
+        if n in (20, 40, 60):
+            peaks.append(U[:, 0, zs, ys, xs].max())
         if n in (40, 60):
             rho = U[:, 0, zs, ys, xs].ravel()
             prof = np.bincount(bins, rho) / np.maximum(np.bincount(bins), 1)
@@ -122,6 +125,9 @@ def test_sedov_radius_symmetry_energy():
             Rs = sedov.shock_radius(t)
             assert Rs * N >= 8
             assert abs(rpk / Rs - 1) < 0.05, (n, rpk, Rs)
+    # the peak density climbs toward the strong-shock compression (gamma+1)/(gamma-1) = 6
+    # as the shell spreads over more cells, and stays below it
+    assert peaks[0] < peaks[1] < peaks[2] < 6.0 and peaks[0] > 1.5, peaks
     assert abs(U[:, 4, zs, ys, xs].sum() / E0 - 1) < 1e-13
     assert abs(U[:, 0, zs, ys, xs].sum() / M0 - 1) < 1e-13
     Gl = to_global(U, lat)

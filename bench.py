@@ -160,6 +160,33 @@ def measured_traffic(zones: int):
     return per_zone * zones
 
 
+def measured_fp64_inst(zones: int):
+    """FP64 thread instructions per stage-kernel launch (mean of the two stages)
+    from the committed ncu record, if it was taken on the current kernel source
+    (else None)."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash() or "fp64_inst_per_zone_stage1" not in rec:
+        return None
+    return 0.5 * (rec["fp64_inst_per_zone_stage1"] + rec["fp64_inst_per_zone_stage2"]) * zones
+
+
+def fp64_issue(inst_per_launch, ms_per_launch: float, sm_mhz, sms: int):
+    """FP64 lanes issued per SM clock (2 is the unit's peak) over a launch."""
+    if not inst_per_launch or not ms_per_launch or not sms:
+        return None
+    mhz = sm_mhz if sm_mhz else 2070.0
+    lanes = inst_per_launch / (ms_per_launch / 1e3 * mhz * 1e6 * sms)
+    return {"fp64_inst_per_launch": inst_per_launch, "lanes_per_sm_clock": lanes, "of_peak_lanes": lanes / 2.0,
+            "sm_mhz": mhz, "sm_mhz_source": "sampled median" if sm_mhz else "nominal (no clock samples)",
+            "note": "FP64 thread instructions per zone from the ncu record of the same kernel source, "
+                    "times zones, over the CUDA-event launch time"}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -328,6 +355,7 @@ def run_gpu(args):
         "traffic": traffic,
         "algorithmic_bytes_per_launch": ALG_BYTES_PER_ZONE / 2 * zones,
         "hbm_frac": (ALG_BYTES_PER_ZONE / 2 * zones / (ms_per_launch / 1e3)) / (hbm * 1e9) if hbm else None,
+        "fp64_issue": fp64_issue(measured_fp64_inst(zones), ms_per_launch, clocks.get("sm_mhz"), gb.sm_count()),
     }
     out = {
         "metric": METRIC,

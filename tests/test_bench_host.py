@@ -74,3 +74,23 @@ def test_clock_sampler_summary(tmp_path):
     out = s.summary()
     assert out["sm_mhz"] == 2070 and out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+
+
+def test_fp64_issue_rate_and_ncu_record():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 401.6 instructions per zone over 16.8 M zones in 11.01 ms at 2070 MHz on 152 SMs
+    r = bench.fp64_issue(401.6 * 256 ** 3, 11.01, 2070.0, 152)
+    assert abs(r["lanes_per_sm_clock"] - 401.6 * 256 ** 3 / (11.01e-3 * 2070e6 * 152)) < 1e-12
+    assert abs(r["of_peak_lanes"] - r["lanes_per_sm_clock"] / 2) < 1e-15
+    assert bench.fp64_issue(1e9, 1.0, None, 152)["sm_mhz_source"].startswith("nominal")
+    assert bench.fp64_issue(None, 1.0, 2070.0, 152) is None
+    # the committed ncu record counts only while it belongs to the current kernel source
+    rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
+    z = 256 ** 3
+    if rec["source_hash"] == bench.source_hash():
+        assert bench.measured_fp64_inst(z) == 0.5 * (rec["fp64_inst_per_zone_stage1"]
+                                                     + rec["fp64_inst_per_zone_stage2"]) * z
+        assert bench.measured_traffic(z) == rec["dram_bytes_per_launch"] / rec["zones"] * z
+    else:
+        assert bench.measured_fp64_inst(z) is None and bench.measured_traffic(z) is None

@@ -77,10 +77,11 @@ typedef struct gbh_params {
   const double *dx;       /* HOST [nblocks][3]: cell widths of each block (dz ignored in 2-D), > 0.  Copied. */
 } gbh_params;
 
-/* Create a context: validates params (GBH_ERR_INVAL, GBH_ERR_UNSUPPORTED),
- * copies the tables to the current CUDA device and allocates the stage
- * scratch (one state-sized buffer) and a few device words.  Synchronous.
- * *out is set to NULL on failure. */
+/* Create a context for one block-structured grid of equal blocks with guard
+ * cells (Sec. 2.2 of the paper): validates params (GBH_ERR_INVAL,
+ * GBH_ERR_UNSUPPORTED), copies the tables to the current CUDA device and
+ * allocates the stage scratch (one state-sized buffer) and a few device
+ * words.  Synchronous.  *out is set to NULL on failure. */
 int gbh_create(const gbh_params *params, gbh_ctx **out);
 
 /* Two-level composite grids (refinement ratio 2, one dt for all levels).
@@ -140,7 +141,8 @@ int gbh_create_batched(const gbh_params *params, const int32_t *problem, int npr
 int gbh_create_refined_batched(const gbh_params *params, const gbh_refinement *refinement, const int32_t *problem,
                                int nproblems, gbh_ctx **out);
 
-/* Work decomposition of the stage kernel: kchunk = z planes per work item
+/* Work decomposition of the stage kernel (how the concurrent-data pattern of
+ * Sec. 3.2 maps blocks onto CTAs; not a choice the paper makes): kchunk = z planes per work item
  * (3-D; 0 or nzb = the whole block) and items_per_cta = consecutive work
  * items one CTA processes (1 = a CTA per item; a grid of about two CTAs per
  * SM makes the kernel persistent).  Results do not depend on it (bitwise).
@@ -191,7 +193,8 @@ int gbh_set_telescoping(gbh_ctx *ctx, int enable);
  * captured graph. */
 int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
 
-/* nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
+/* (No counterpart in the paper: launch batching.)
+ * nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
  * private stream; re-captured when U, dt_dev or nsteps change, or the
  * decomposition changes) and launched on `stream` as one graph.  Kernel
  * timing must be off.  The first call captures: make it outside any capture
@@ -230,6 +233,12 @@ int hydro_step_adjoint(gbh_ctx *ctx, const double *Un, double dt, const double *
  * only (GBH_ERR_UNSUPPORTED otherwise). */
 int hydro_step_adjoint_stored(gbh_ctx *ctx, const double *Un, const double *U1, double dt, const double *lam_next,
                               double *lam_prev, void *stream);
+/* Conserved variables from primitive ones, the inverse of the calcEos
+ * conversion (Alg. "Intra stage calculations for Spark"): U = (rho, rho u,
+ * rho v, rho w, p/(gamma-1) + rho |u|^2 / 2) from W = (rho, u, v, w, p), on
+ * interior cells of DEVICE state arrays; and its VJP, lamW = (dU/dW)^T lamU
+ * on interior cells (overwritten; the paper has no adjoint).  GBH_ERR_INVAL
+ * for null or misaligned pointers. */
 int hydro_prim_to_cons(gbh_ctx *ctx, const double *W, double *U, void *stream);
 int hydro_prim_to_cons_vjp(gbh_ctx *ctx, const double *W, const double *lamU, double *lamW, void *stream);
 
@@ -249,15 +258,18 @@ long long gbh_state_bytes(const gbh_ctx *ctx);
  * edge and corner guards are defined too).  Reads interior cells only. */
 int hydro_fill_guardcells(gbh_ctx *ctx, double *U, void *stream);
 
-/* CFL time step of the state U (interior cells of all blocks):
- * *dt_dev = cfl / max sum_d (|u_d| + c) / dx_d, written to the DEVICE double
- * dt_dev.  No synchronisation. */
+/* CFL time step of the state U (interior cells of all blocks; leaf cells on
+ * two-level grids): *dt_dev = cfl / max sum_d (|u_d| + c) / dx_d, written to
+ * the DEVICE double dt_dev (one per problem on batched contexts).  The paper
+ * gives no time-step rule; this unsplit-sum CFL form is the library's reading.
+ * No synchronisation. */
 int hydro_compute_dt(gbh_ctx *ctx, const double *U, double *dt_dev, void *stream);
 
-/* One RK stage in Shu-Osher form on the interior of every block:
+/* One RK stage in Shu-Osher form on the interior of every block (a stage of
+ * the paper's multistage SSP-RK stepper, Sec. 4.2):
  *     Uout = a * Un + b * (Uin + dt * L(Uin)),
  * L = the flux-difference operator of the intra-stage calculations (calcLims,
- * calcFlux, updSoln).  With a == 0 and b == 1 this is Uin + dt L(Uin) and Un
+ * calcFlux, updSoln; Alg. "Intra stage calculations for Spark").  With a == 0 and b == 1 this is Uin + dt L(Uin) and Un
  * is not read (may be NULL).  Guard data of Uin are gathered from the
  * neighbour blocks' interiors through the neighbour table (Uin's own guard
  * cells are not read).  Uout may equal Un but must not overlap Uin.
@@ -270,9 +282,11 @@ int hydro_stage(gbh_ctx *ctx, const double *Uin, const double *Un, double *Uout,
 int hydro_stage_guarded(gbh_ctx *ctx, const double *Uin, const double *Un, double *Uout, double dt,
                         double a, double b, void *stream);
 
-/* One full SSP-RK2 step in place with a host-given dt:
+/* One full SSP-RK2 step in place with a host-given dt (the paper's
+ * non-telescoping stepper, Sec. 4.2, with two Shu-Osher stages):
  *     U1 = U + dt L(U);   U <- 1/2 U + 1/2 (U1 + dt L(U1)).
- * U1 lives in the context's scratch buffer. */
+ * U1 lives in the context's scratch buffer.  GBH_ERR_INVAL for dt <= 0 or
+ * non-finite, or a null / misaligned U. */
 int hydro_step(gbh_ctx *ctx, double *U, double dt, void *stream);
 
 /* One SSP-RK2 step in place, as hydro_step, for callers that cannot
@@ -303,7 +317,9 @@ int hydro_step_cfl(gbh_ctx *ctx, double *U, double *dt_dev, void *stream);
  * dt used by each step (DEVICE array of nsteps doubles). */
 int hydro_advance(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, double *dt_hist_dev, void *stream);
 
-/* Host-buffer variant for callers whose state lives in host memory:
+/* Host-buffer variant for callers whose state lives in host memory (the
+ * paper's heterogeneous case, where host-device movement adds to the cost of
+ * every exchange, Sec. 4.2; the entry point itself has no counterpart there):
  * copies U_host (pinned or pageable, one state array) to a context-owned
  * device buffer (allocated on first use), computes dt, advances nsteps, and
  * copies the interior-updated state back into U_host and the dt of each step
@@ -333,7 +349,8 @@ int hydro_step_host(gbh_ctx *ctx, double *U_host, double *dt_host, void *stream)
  * stage kernel each.  GBH_ERR_INVAL outside [0, 64]. */
 int gbh_set_host_pipeline(gbh_ctx *ctx, int chunks);
 
-/* Scan the interior of U: counts cells whose density <= small_rho, pressure
+/* Failure check for the floors of the calcEos conversion (no counterpart in
+ * the paper).  Scan the interior of U: counts cells whose density <= small_rho, pressure
  * <= small_p, or any variable is non-finite.  Synchronises the stream, writes
  * the count to *nbad_host and returns GBH_ERR_UNPHYSICAL if it is non-zero. */
 int hydro_check_state(gbh_ctx *ctx, const double *U, long long *nbad_host, void *stream);

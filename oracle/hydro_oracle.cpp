@@ -859,14 +859,17 @@ template <int K> bool operator==(const Dual<K>& a, const Dual<K>& b) { return a.
 
 using D20 = Dual<20>;
 
-/* J_L(U)^T (scale M) on the interior of every block; U must have its guard
- * cells filled.  out is written on interior cells. */
-void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale, double* out) {
+/* The transposed face loop of one stage on the box of width `ring` around
+ * the interior (ring = 0: the interior; ring > 0: a stage of the telescoping
+ * mode, which reads U's own cells 2 beyond the box): for the cotangent M on
+ * the box's cells, J_L(U)^T (scale M) is added into adj at every padded cell
+ * the face stencils read. */
+void stage_vjp_local(const OrcGrid& G, const double* U, const double* M, double scale, double* adj, int ring) {
   const Geo geo(G);
   const ll nbk = geo.nblocks();
   const ll cells = geo.cells;
   const int nd = geo.ndim;
-  std::vector<double> ext(nbk * 5 * cells, 0.0);   /* adjoint of the conserved stencil inputs */
+  const Box R(geo, ring);
   const ll stride[3] = {1, geo.p[0], (ll)geo.p[0] * geo.p[1]};
 #pragma omp parallel for schedule(dynamic, 1)
   for (ll b = 0; b < nbk; ++b) {
@@ -878,17 +881,17 @@ void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale,
         for (int j = 0; j < geo.p[1]; ++j)
           for (int i = 0; i < geo.p[0]; ++i) {
             const int x[3] = {i, j, k};
-            bool ok = x[d] >= geo.g[d] && x[d] <= geo.g[d] + geo.n[d];
+            bool ok = x[d] >= R.lo[d] && x[d] <= R.hi[d];
             for (int e = 0; e < 3; ++e)
-              if (e != d && !inside(geo, e, x[e])) ok = false;
+              if (e != d && !R.in(e, x[e])) ok = false;
             if (!ok) continue;
             const ll c = geo.cell(k, j, i);
             /* flux adjoint from this block's own cells c - e_d and c */
             double lamF[5];
             for (int v = 0; v < 5; ++v) {
-              const double mc = inside(geo, d, x[d]) ? M[geo.at(b, v, k, j, i) ] : 0.0;
+              const double mc = R.in(d, x[d]) ? M[geo.at(b, v, k, j, i) ] : 0.0;
               const int xm = x[d] - 1;
-              const double mm = inside(geo, d, xm) ? M[geo.at(b, v, k, j, i) - stride[d]] : 0.0;
+              const double mm = R.in(d, xm) ? M[geo.at(b, v, k, j, i) - stride[d]] : 0.0;
               lamF[v] = scale * idx * (mc - mm);
             }
             /* the 4 stencil cells c-2e, c-e, c, c+e as dual inputs (20 slots) */
@@ -916,12 +919,23 @@ void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale,
               for (int v = 0; v < 5; ++v) {
                 double acc = 0.0;
                 for (int q = 0; q < 5; ++q) acc += lamF[vmap[q]] * F[q].d[5 * s + v];
-                ext[b * 5 * cells + v * cells + cs] += acc;
+                adj[b * 5 * cells + v * cells + cs] += acc;
               }
             }
           }
     }
   }
+}
+
+/* J_L(U)^T (scale M) on the interior of every block; U must have its guard
+ * cells filled.  out is written on interior cells. */
+void stage_vjp(const OrcGrid& G, const double* U, const double* M, double scale, double* out) {
+  const Geo geo(G);
+  const ll nbk = geo.nblocks();
+  const ll cells = geo.cells;
+  const int nd = geo.ndim;
+  std::vector<double> ext(nbk * 5 * cells, 0.0);   /* adjoint of the conserved stencil inputs */
+  stage_vjp_local(G, U, M, scale, ext.data(), 0);
   /* adjoint of the guard fill (face slabs only: the stencil reads no
    * corners): a guard position hands its adjoint to the interior cell it was
    * copied from -- the neighbour's, or the block's own boundary cell at an
@@ -1002,6 +1016,91 @@ void step_adjoint(const OrcGrid& G, const double* Un, double dt, const double* l
           for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
             const ll o = geo.at(b, v, k, j, i);
             lam_prev[o] = acc[o] + cur[o];
+          }
+}
+
+/* dJ/dU^n of one telescoping SSP-RK step (step_telescoping, dt held fixed)
+ * from dJ/dU^{n+1} on interior cells.  Forward: Uf = fill(U^n) (all guard
+ * layers), X_0 = Uf, stage s writes X_{s+1} = a_s Uf + b_s (X_s + dt L(X_s))
+ * on the box of width ring_s = 2 (S-1-s) from X_s's own cells, and keeps Uf's
+ * values elsewhere.  Backwards, with lam_S the cotangent of X_S:
+ *   on box_s:   Uf gets a_s lam_{s+1};  lam_s = b_s lam_{s+1} + J_L(X_s)^T (b_s dt lam_{s+1}),
+ *   elsewhere:  Uf gets lam_{s+1} (X_{s+1} holds Uf's values there),
+ * X_0 = Uf gets lam_0, and the fill is reversed: every guard cell's adjoint
+ * goes to the interior cell its value was copied from.  That source map is
+ * read off by filling an array that holds each interior cell's own index
+ * (the fill only copies values). */
+void step_adjoint_telescoping(const OrcGrid& G, const double* Un, double dt, const double* lam, double* lam_prev,
+                              int nstages = 2) {
+  const Rk r = rk_scheme(nstages);
+  const Geo geo(G);
+  const ll nbk = geo.nblocks();
+  const ll total = nbk * 5 * geo.cells;
+  std::vector<double> Uf(Un, Un + total);
+  fill_guardcells(G, Uf.data());
+  std::vector<std::vector<double>> X(r.S);
+  X[0] = Uf;
+  for (int st = 0; st + 1 < r.S; ++st) {
+    X[st + 1] = Uf;
+    stage(G, X[st].data(), st ? Uf.data() : nullptr, X[st + 1].data(), dt, r.a[st], r.b[st], nullptr, 0,
+          2 * (r.S - 1 - st));
+  }
+  /* lam_S: the cotangent on interior cells */
+  std::vector<double> cur(total, 0.0), accU(total, 0.0), jt(total, 0.0);
+  for (ll b = 0; b < nbk; ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) cur[geo.at(b, v, k, j, i)] = lam[geo.at(b, v, k, j, i)];
+  for (int st = r.S - 1; st >= 0; --st) {
+    const int ring = 2 * (r.S - 1 - st);
+    const Box R(geo, ring);
+    std::fill(jt.begin(), jt.end(), 0.0);
+    /* the cotangent of the box cells only: the stage writes nothing else */
+    std::vector<double> M(total, 0.0);
+    for (ll b = 0; b < nbk; ++b)
+      for (int v = 0; v < 5; ++v)
+        for (int k = 0; k < geo.p[2]; ++k)
+          for (int j = 0; j < geo.p[1]; ++j)
+            for (int i = 0; i < geo.p[0]; ++i)
+              if (R.in(0, i) && R.in(1, j) && R.in(2, k)) M[geo.at(b, v, k, j, i)] = cur[geo.at(b, v, k, j, i)];
+    stage_vjp_local(G, X[st].data(), M.data(), r.b[st] * dt, jt.data(), ring);
+    for (ll b = 0; b < nbk; ++b)
+      for (int v = 0; v < 5; ++v)
+        for (int k = 0; k < geo.p[2]; ++k)
+          for (int j = 0; j < geo.p[1]; ++j)
+            for (int i = 0; i < geo.p[0]; ++i) {
+              const ll o = geo.at(b, v, k, j, i);
+              if (R.in(0, i) && R.in(1, j) && R.in(2, k)) {
+                accU[o] = accU[o] + r.a[st] * cur[o];
+                cur[o] = r.b[st] * cur[o] + jt[o];
+              } else {
+                accU[o] = accU[o] + cur[o];
+                cur[o] = jt[o];
+              }
+            }
+  }
+  for (ll o = 0; o < total; ++o) accU[o] = accU[o] + cur[o];
+  /* reverse of the fill */
+  std::vector<double> src(total, -1.0);
+  for (ll b = 0; b < nbk; ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) src[geo.at(b, v, k, j, i)] = (double)geo.at(b, v, k, j, i);
+  fill_guardcells(G, src.data());
+  std::vector<double> out(total, 0.0);
+  for (ll o = 0; o < total; ++o) {
+    const ll from = (ll)src[o];
+    if (from >= 0) out[from] += accU[o];
+  }
+  for (ll b = 0; b < nbk; ++b)
+    for (int v = 0; v < 5; ++v)
+      for (int k = geo.g[2]; k < geo.g[2] + geo.n[2]; ++k)
+        for (int j = geo.g[1]; j < geo.g[1] + geo.n[1]; ++j)
+          for (int i = geo.g[0]; i < geo.g[0] + geo.n[0]; ++i) {
+            const ll o = geo.at(b, v, k, j, i);
+            lam_prev[o] = out[o];
           }
 }
 
@@ -1169,6 +1268,15 @@ int orc_step_adjoint_rk(const OrcGrid* G, const double* Un, double dt, const dou
                         int nstages) {
   if (nstages != 2 && nstages != 3) return -1;
   step_adjoint(*G, Un, dt, lam_next, lam_prev, nstages);
+  return 0;
+}
+
+/* Adjoint of the telescoping step of nstages (2 or 3) stages; -1 if nstages is
+ * invalid or the guard width is below 2 * nstages. */
+int orc_step_adjoint_telescoping(const OrcGrid* G, const double* Un, double dt, const double* lam_next,
+                                 double* lam_prev, int nstages) {
+  if ((nstages != 2 && nstages != 3) || G->ng < 2 * nstages) return -1;
+  step_adjoint_telescoping(*G, Un, dt, lam_next, lam_prev, nstages);
   return 0;
 }
 

@@ -78,6 +78,8 @@ def lib():
             L.orc_step_adjoint.restype = None
             L.orc_step_adjoint_rk.argtypes = [gp, dp, C.c_double, dp, dp, C.c_int]
             L.orc_step_adjoint_rk.restype = C.c_int
+            L.orc_step_adjoint_telescoping.argtypes = [gp, dp, C.c_double, dp, dp, C.c_int]
+            L.orc_step_adjoint_telescoping.restype = C.c_int
             ap = C.POINTER(OrcAmr2)
             L.orc2_restrict.argtypes = [gp, ap, dp]
             L.orc2_restrict.restype = None
@@ -188,12 +190,17 @@ class Oracle:
         self.L.orc_stage_vjp(C.byref(self.g), _dp(U), _dp(M), float(scale), _dp(out))
         return out
 
-    def step_adjoint(self, Un, dt, lam_next, stages=2):
-        """dJ/dU^n of one step(Un, dt, stages=stages) from dJ/dU^{n+1} (interior cells)."""
+    def step_adjoint(self, Un, dt, lam_next, stages=2, telescoping=False):
+        """dJ/dU^n of one step(Un, dt, stages=stages, telescoping=telescoping)
+        from dJ/dU^{n+1} (interior cells)."""
         _check(Un, self.lat)
         _check(lam_next, self.lat)
         out = np.zeros_like(Un)
-        if stages == 2:
+        if telescoping:
+            if self.L.orc_step_adjoint_telescoping(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out),
+                                                   int(stages)) != 0:
+                raise ValueError("stages must be 2 or 3, with at least 2 * stages guard cells")
+        elif stages == 2:
             self.L.orc_step_adjoint(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out))
         elif self.L.orc_step_adjoint_rk(C.byref(self.g), _dp(Un), float(dt), _dp(lam_next), _dp(out),
                                         int(stages)) != 0:

@@ -129,3 +129,84 @@ def test_three_stage_adjoint_differs_from_two_stage():
     dt = o.compute_dt(U)
     a, b = o.step_adjoint(U, dt, w, stages=3), o.step_adjoint(U, dt, w, stages=2)
     assert np.max(np.abs(a - b)) > 1e-6 * np.max(np.abs(a))
+
+
+TELE_LATS = [wl.lattice_2d(2, 2, 8, 8, 4), wl.lattice_3d(2, 2, 2, 4, 4, 4, 4, bc="periodic"),
+             wl.lattice_2d(3, 2, 8, 8, 4, bc=("periodic", "outflow"))]
+
+
+@pytest.mark.parametrize("lat", TELE_LATS)
+def test_telescoping_step_adjoint_matches_finite_differences(lat):
+    """The adjoint of the telescoping step (one fill of all guard layers, the
+    first stage on the interior widened by 2 from the block's own cells)
+    against central differences of the oracle's telescoping step."""
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=21, rough=False)
+    w = np.random.default_rng(22).normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+
+    def G(V):
+        X = V.copy()
+        o.step(X, dt, telescoping=True)
+        return float(np.sum(w * X * interior_mask(lat)))
+
+    grad = o.step_adjoint(U, dt, w, telescoping=True)
+    scale = np.max(np.abs(grad))
+    # cells next to block and domain edges, where the ring and the fill matter, and random ones
+    cells = pick(lat, 10, 23)
+    zs, ys, xs = lat.interior_slices()
+    cells += [(0, 0, zs.start, ys.start, xs.start), (1, 1, zs.stop - 1, ys.start, xs.stop - 1),
+              (lat.nblocks - 1, 4, zs.stop - 1, ys.stop - 2, xs.start + 1)]
+    for c in cells:
+        h = 1e-6 * max(1.0, abs(U[c]))
+        Up, Um = U.copy(), U.copy()
+        Up[c] += h
+        Um[c] -= h
+        fd = (G(Up) - G(Um)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+def test_telescoping_three_stage_adjoint_matches_finite_differences():
+    lat = wl.lattice_2d(2, 2, 8, 8, 6)
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=24, rough=False)
+    w = np.random.default_rng(25).normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+
+    def G(V):
+        X = V.copy()
+        o.step(X, dt, telescoping=True, stages=3)
+        return float(np.sum(w * X * interior_mask(lat)))
+
+    grad = o.step_adjoint(U, dt, w, stages=3, telescoping=True)
+    scale = np.max(np.abs(grad))
+    for c in pick(lat, 12, 26):
+        h = 1e-6 * max(1.0, abs(U[c]))
+        Up, Um = U.copy(), U.copy()
+        Up[c] += h
+        Um[c] -= h
+        fd = (G(Up) - G(Um)) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+@pytest.mark.parametrize("stages,ng", [(2, 4), (3, 6)])
+def test_telescoping_adjoint_equals_plain_adjoint_on_periodic_lattices(stages, ng):
+    """On a periodic lattice the telescoping step is the plain step bit for bit,
+    so the two adjoints agree to rounding; at an outflow edge they differ (the
+    first stage evolves the zero-gradient copies there)."""
+    lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, ng, bc="periodic")
+    o = Oracle(lat)
+    U = wl.random_state(lat, seed=27, rough=True)
+    w = np.random.default_rng(28).normal(size=U.shape) * interior_mask(lat)
+    dt = o.compute_dt(U)
+    a = o.step_adjoint(U, dt, w, stages=stages, telescoping=True)
+    b = o.step_adjoint(U, dt, w, stages=stages)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    lat2 = wl.lattice_2d(2, 2, 8, 8, ng)
+    o2 = Oracle(lat2)
+    U2 = wl.random_state(lat2, seed=29, rough=True)
+    w2 = np.random.default_rng(30).normal(size=U2.shape) * interior_mask(lat2)
+    dt2 = o2.compute_dt(U2)
+    a2 = o2.step_adjoint(U2, dt2, w2, stages=stages, telescoping=True)
+    b2 = o2.step_adjoint(U2, dt2, w2, stages=stages)
+    assert np.max(np.abs(a2 - b2)) > 1e-8 * np.max(np.abs(b2))

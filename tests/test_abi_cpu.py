@@ -337,3 +337,20 @@ def test_create_refined_rejects_a_coarse_block_on_two_refined_faces_without_gpu(
     for tables in (mine, refined_tables(2, (8, 4), (8, 8), [(1, 1), (1, 2), (4, 1), (4, 2)], (1 / 64, 1 / 32, 1.0))):
         rc, msg = attempt(tables)
         assert rc in (0, -2, -4) and b"faces" not in msg, msg
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: loading a library that is not there raises, and a
+    context cannot be created without a CUDA device (the error names CUDA)."""
+    from paper_2401_03378_gb300 import _abi
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _abi.load(str(tmp_path / "libgbhydro.so"))
+
+
+def test_hydro_binding_without_a_device_raises(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2401_03378_gb300 import Hydro, _abi
+    with pytest.raises(_abi.GbhError):
+        Hydro(3, (8, 8, 8), 4, nb=(2, 2, 2))

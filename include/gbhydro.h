@@ -293,17 +293,19 @@ int hydro_step(gbh_ctx *ctx, double *U, double dt, void *stream);
  * allocate device memory (a host whose memory manager owns the device pool,
  * a plug-in in a process that forbids cudaMalloc/cudaFree after start-up):
  * no context is created and nothing is allocated.  The intermediate stage,
- * the face-neighbour table, the inverse cell widths and a counter live in one
- * fixed file-scope device array of 40 MiB + 385 KiB that every GPU loading
- * the library holds until the process exits.  params is read as in
- * gbh_create (HOST tables); U is the caller's DEVICE state.  Rejected with
+ * the face-neighbour table and the inverse cell widths live in one fixed
+ * file-scope device array of 40 MiB + 385 KiB that every GPU loading the
+ * library holds until the process exits.  params is read as in gbh_create
+ * (HOST tables); U is the caller's DEVICE state.  Rejected with
  * GBH_ERR_INVAL: a state larger than 40 MiB (41,943,040 bytes) or more than
- * 8192 blocks.  The first call on a device (with it current) looks up the
- * array's address and sets a kernel attribute, so it should come before any
- * stream capture.  All calls share the array and leave their data in it:
- * calls that may overlap on the GPU race and must be serialised by the
- * caller.  The paper has no counterpart of this entry point.  Errors are
- * reported through gbh_last_error(NULL). */
+ * 8192 blocks.  Every call looks up the array's device address for the
+ * current device; the first call on a device also loads the library's
+ * kernels there, so it should come before any stream capture.  All calls
+ * share the array and leave their data in it: calls that may overlap on the
+ * GPU race and must be serialised by the caller.  The floors are applied as
+ * in hydro_step but not counted (no floor hits are reported).  The paper has
+ * no counterpart of this entry point.  Errors are reported through
+ * gbh_last_error(NULL). */
 int hydro_step_static(const gbh_params *params, double *U, double dt, void *stream);
 
 /* One SSP-RK2 step in place whose dt is read from the DEVICE double *dt_dev

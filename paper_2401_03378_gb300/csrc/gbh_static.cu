@@ -1,15 +1,14 @@
 // gbh_static.cu -- hydro_step_static: one SSP-RK2 step that allocates nothing.
 //
 // Some callers cannot allocate device memory: a host application whose
-// memory manager owns the whole device pool, a plug-in loaded into a process
-// that forbids cudaMalloc/cudaFree after start-up (allocation there would
-// synchronise the device or fragment the pool), or code running inside a
-// captured region that must not change the allocation state.  For them this
+// memory manager owns the whole device pool, or a plug-in loaded into a
+// process that forbids cudaMalloc/cudaFree after start-up (an allocation
+// there would synchronise the device or fragment the pool).  For them this
 // entry point keeps everything the step needs beyond the caller's state --
 // the intermediate stage U1, the face-neighbour table, the inverse cell
-// widths and a counter -- in ONE file-scope __device__ array of fixed size.
-// The array exists on every GPU that loads the library, for the life of the
-// process.
+// widths and a discard word for the stage kernel's floor counter -- in ONE
+// file-scope __device__ array of fixed size.  The array exists on every GPU
+// that loads the library, for the life of the process.
 //
 // Limits: the state array (all blocks, guard cells included) must fit the
 // U1 region (kU1Bytes = 40 MiB, e.g. a 2-D 128^2 problem of 64 blocks of
@@ -18,13 +17,21 @@
 // GBH_ERR_INVAL.  Every call shares the array and leaves its contents in it,
 // so calls that can overlap on the GPU (different streams without ordering,
 // or different host threads) race and must not be issued concurrently.
+// Nothing in the array has to start at zero: U1 and the tables are written
+// in full before they are read, and the floor counter is never read, so
+// this entry point reports no floor hits (the floors are still applied).
 //
-// Set-up: the first call on a device (with that device current) looks up
-// the array's device address with cudaGetSymbolAddress and sets the stage
-// kernel's shared-memory attribute; that first call should therefore come
-// before any stream capture.  Later calls only copy the tables (from host
-// memory, staged synchronously by the runtime) and launch the two stage
-// kernels.
+// Device address: in host code g_static_scratch names a host-side stand-in,
+// not device memory, so every call looks the array's device address up with
+// cudaGetSymbolAddress, with the caller's device current, and sets the stage
+// kernel's shared-memory attribute.  Both are host-side calls that allocate
+// nothing; doing them on every call (instead of caching them per device
+// index) keeps the address right when the caller's context changes, e.g.
+// after cudaDeviceReset or under a non-primary context.  The first call on a
+// device loads the library's kernels and the array there, so that first call
+// should come before any stream capture.  Each call then copies the tables
+// (from host memory, staged by the runtime before cudaMemcpyAsync returns)
+// and launches the two stage kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,15 +48,12 @@ constexpr size_t kU1Bytes = 40ull << 20;                 // intermediate stage U
 constexpr int kMaxBlocks = 8192;
 constexpr size_t kFaceOffset = kU1Bytes;                  // int [kMaxBlocks][6]
 constexpr size_t kInvDxOffset = kFaceOffset + sizeof(int) * 6 * kMaxBlocks;      // double [kMaxBlocks][3]
-constexpr size_t kWordsOffset = kInvDxOffset + sizeof(double) * 3 * kMaxBlocks;  // unsigned long long [4]
+constexpr size_t kWordsOffset = kInvDxOffset + sizeof(double) * 3 * kMaxBlocks;  // unsigned long long (discard)
 constexpr size_t kStaticBytes = kWordsOffset + 256;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char* g_base[kMaxDevices] = {nullptr};   // device address of g_static_scratch per device
-unsigned g_prepared[kMaxDevices] = {0};           // bit per (nx, ndim) stage kernel attribute set
+std::mutex g_mutex;   // guards the host staging buffers below
 
 // host staging of the per-call tables (copied with cudaMemcpyAsync from
 // pageable memory, which the runtime stages before returning)
@@ -85,26 +89,14 @@ extern "C" int hydro_step_static(const gbh_params* params, double* U, double dt,
   if (params->nblocks > kMaxBlocks)
     return fail(GBH_ERR_INVAL, "nblocks %lld exceeds the static limit of %lld", params->nblocks, kMaxBlocks);
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(GBH_ERR_UNSUPPORTED, "device index %lld out of range", dev);
   cudaStream_t s = (cudaStream_t)stream;
-
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_base[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-    g_base[dev] = (unsigned char*)ptr;
-  }
-  const unsigned bit = 1u << ((L.nx == 4 ? 0 : L.nx == 8 ? 1 : 2) * 2 + (L.ndim == 3 ? 1 : 0));
-  if (!(g_prepared[dev] & bit)) {
-    e = gbh::stage_prepare(L.nx, L.ndim);
-    if (e != cudaSuccess) return cuda_fail(e, "stage kernel attribute");
-    g_prepared[dev] |= bit;
-  }
-  unsigned char* base = g_base[dev];
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+  e = gbh::stage_prepare(L.nx, L.ndim);
+  if (e != cudaSuccess) return cuda_fail(e, "stage kernel attribute");
+  unsigned char* base = (unsigned char*)ptr;
   double* U1 = (double*)base;
   int* face = (int*)(base + kFaceOffset);
   double* inv = (double*)(base + kInvDxOffset);
@@ -115,7 +107,6 @@ extern "C" int hydro_step_static(const gbh_params* params, double* U, double dt,
   e = cudaMemcpyAsync(face, g_face_host, sizeof(int) * 6 * params->nblocks, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(inv, g_inv_host, sizeof(double) * 3 * params->nblocks, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, sizeof(unsigned long long) * 4, s);   // floor counter
   if (e != cudaSuccess) return cuda_fail(e, "table upload");
 
   gbh::StageArgs A{};
@@ -124,7 +115,7 @@ extern "C" int hydro_step_static(const gbh_params* params, double* U, double dt,
   A.inv_dx = inv;
   A.dt = dt;
   A.gather = 1;
-  A.floor_count = words + 1;
+  A.floor_count = words;   // discard word: this entry point reports no floor hits
   A.smax_acc = nullptr;
   // stage 1: U1 = U + dt L(U)
   A.Uin = U;

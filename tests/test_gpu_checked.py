@@ -183,7 +183,7 @@ def test_static_step(gb):
     for checked in (False, True):
         lib = gb.load(checked=checked)
         keep = []
-        p = _params(None, lat, keep)
+        p = _params(lat, keep)
         U = dev(U0)
         for _ in range(2):
             assert lib.hydro_step_static(C.byref(p), U.data_ptr(), 1e-4, torch.cuda.current_stream().cuda_stream) == 0

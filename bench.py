@@ -195,6 +195,34 @@ def load_peaks():
         return {}
 
 
+def bench_config(lat):
+    """The workload object both arms print (identical for the same --nb)."""
+    workload = WORKLOAD if lat.nb[0] == 16 else f"{WORKLOAD} (at {lat.global_cells[0]}^3)"
+    return {"workload": workload, "zones": lat.interior_cells, "blocks": lat.nblocks,
+            "l2": "state %.2f GB per array > 129 MB L2: no flush needed" % (
+                8 * lat.nblocks * 5 * lat.padded[0] * lat.padded[1] * lat.padded[2] / 1e9)}
+
+
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def make_problem(nb: int):
     import workloads as wl
     lat = wl.lattice_3d(nb, nb, nb, 16, 16, 16, 4)
@@ -370,9 +398,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded Sedov initial condition)",
-        "config": {"workload": WORKLOAD, "zones": zones, "blocks": lat.nblocks,
-                   "l2": "state 2.26 GB per array > 129 MB L2: no flush needed",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(lat),
+        "parallelism": f"replicas x{world}",
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "repeats": repeats,
@@ -669,7 +696,7 @@ def cpu_baseline(args, U0, lat):
     rate1, _, secs1 = oracle_step_rate(lat1, wl.sedov(lat1), 1, threads=1)
     from oracle import oracle as orc
     orc.set_threads(0)
-    return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+    return {"value": rate, "unit": UNIT, "cores": used, "cpu_model": host_cpu_model(), "kind": "oracle",
             "sample": f"{args.cpu_steps} oracle SSP-RK2 step(s) of the full 256^3 workload "
                       f"({secs:.1f} s, OpenMP over blocks, {used} threads)",
             "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
@@ -699,9 +726,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Sedov initial condition)",
-        "config": {"workload": WORKLOAD if args.nb == 16 else f"{WORKLOAD} (sampled at {lat.global_cells[0]}^3)",
-                   "zones": lat.interior_cells},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "config": bench_config(lat),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "cpu_model": host_cpu_model(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

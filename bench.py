@@ -223,6 +223,28 @@ def host_cpu_model():
     return platform.processor() or platform.machine()
 
 
+def autotuned(h, U, rings, time_default):
+    """Run the library's autotuner on U and describe its choice; when that is
+    not the default decomposition (whole block per work item, one item per
+    CTA, unsplit tiles), time_default() is timed with the default restored
+    before the choice is set back."""
+    kc, ipc = h.autotune(U)
+    splits = {r: h.tile_split(r) for r in rings}
+    full = h.n[2] if h.ndim == 3 else 1
+    choice = {"kchunk": kc, "items_per_cta": ipc, "ysplit": {str(r): s for r, s in splits.items()}}
+    is_default = kc == full and ipc == 1 and all(s == 1 for s in splits.values())
+    out = {"chosen": choice, "chosen_is_default": is_default, "default_ms_per_step": None}
+    if not is_default:
+        h.set_decomposition(0, 1)
+        for r in rings:
+            h.set_tile_split(r, 1)
+        out["default_ms_per_step"] = time_default()
+        h.set_decomposition(kc if h.ndim == 3 else 0, ipc)
+        for r, sp in splits.items():
+            h.set_tile_split(r, sp)
+    return out
+
+
 def make_problem(nb: int):
     import workloads as wl
     lat = wl.lattice_3d(nb, nb, nb, 16, 16, 16, 4)
@@ -263,16 +285,34 @@ def run_gpu(args):
     zones = lat.interior_cells
     h = gb.Hydro.from_lattice(lat)
     U = torch.from_numpy(U0).cuda()
-    dt = h.compute_dt(U)
-    for _ in range(args.warmup):
-        h.step_cfl(U, dt)
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
+
+    def ms_per_step(n=10):
+        V = torch.from_numpy(U0).cuda()
+        d = h.compute_dt(V)
+        for _ in range(3):
+            h.step_cfl(V, d)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        for _ in range(n):
+            h.step_cfl(V, d)
+        e1.record()
+        barrier()
+        return e0.elapsed_time(e1) / n
+
+    # the decomposition the library's autotuner picks on this workload (the
+    # timed loop below runs with it)
+    tuning = autotuned(h, U, (0,), ms_per_step)
+    dt = h.compute_dt(U)
+    for _ in range(args.warmup):
+        h.step_cfl(U, dt)
+    torch.cuda.synchronize()
 
     h.set_kernel_timing(True)
     h.stage_kernel_time()  # clear
@@ -401,6 +441,7 @@ def run_gpu(args):
         "config": bench_config(lat),
         "parallelism": f"replicas x{world}",
         "gpu_launches": 3 * args.steps,
+        "autotune": tuning,
         "clocks": clocks,
         "repeats": repeats,
         "roofline": roof,
@@ -436,7 +477,25 @@ def run_variants(args, gb, torch, barrier, ms_headline):
         h = gb.Hydro.from_lattice(lat)
         h.set_rk_stages(stages)
         h.set_telescoping(tele)
-        U = torch.from_numpy(wl.sedov(lat)).cuda()
+        U0 = wl.sedov(lat)
+        U = torch.from_numpy(U0).cuda()
+
+        def ms_per_step(n=5):
+            V = torch.from_numpy(U0).cuda()
+            d = h.compute_dt(V)
+            h.step_cfl(V, d)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record()
+            for _ in range(n):
+                h.step_cfl(V, d)
+            e1.record()
+            barrier()
+            del V
+            return e0.elapsed_time(e1) / n
+
+        rings = (0,) + ((2,) if tele else ()) + ((4,) if tele and stages == 3 else ())
+        tuning = autotuned(h, U, rings, ms_per_step)
         dt = h.compute_dt(U)
         for _ in range(args.warmup):
             h.step_cfl(U, dt)
@@ -463,7 +522,8 @@ def run_variants(args, gb, torch, barrier, ms_headline):
                      "steps": args.variant_steps, "ms_per_step": ms,
                      "stage_kernels_ms_per_step": stage_ms / args.variant_steps,
                      "over_headline_step": ms / ms_headline,
-                     "launches_per_step": stages + 1 + (1 if tele else 0), "unphysical_cells": nbad}
+                     "launches_per_step": stages + 1 + (1 if tele else 0), "unphysical_cells": nbad,
+                     "autotune": tuning}
     out["workload"] = f"{WORKLOAD} -- stepper variants (nguard as listed)"
     return out
 
@@ -546,7 +606,17 @@ def run_ensemble(args, gb, torch, barrier):
     h = gb.Hydro.from_batch(lats)
     U0 = np.concatenate([u for _, u in probs])
     U = torch.from_numpy(U0).cuda()
-    kc, ipc = h.autotune(U)
+
+    def default_ms():
+        V = torch.from_numpy(U0).cuda()
+        d = h.compute_dt(V)
+        h.advance(V, 3, d)
+        ms = timed(lambda: h.advance(V, 10, d)) * 1e3 / 10
+        del V
+        return ms
+
+    tuning = autotuned(h, U, (0,), default_ms)
+    kc, ipc = tuning["chosen"]["kchunk"], tuning["chosen"]["items_per_cta"]
     dt = h.compute_dt(U)
     h.advance_graph(U, n, dt)          # capture + warm-up run
     U.copy_(torch.from_numpy(U0))
@@ -573,7 +643,8 @@ def run_ensemble(args, gb, torch, barrier):
                         "noise (sigma 0.1, seeds 1000+i), own CFL dt each, FP64",
             "zones": zones, "blocks": sum(l.nblocks for l in lats), "steps": n,
             "batched_graph": {"value": zones * n / batched, "unit": UNIT, "ms_per_step": 1e3 * batched / n,
-                              "launches_per_step": 3, "graph_launches": 1, "kchunk": kc, "items_per_cta": ipc},
+                              "launches_per_step": 3, "graph_launches": 1, "kchunk": kc, "items_per_cta": ipc,
+                              "autotune": tuning},
             "one_launch_per_problem": {"value": zones * n / separate, "unit": UNIT,
                                        "ms_per_step": 1e3 * separate / n, "launches_per_step": 3 * len(lats)},
             "speedup": separate / batched}

@@ -145,13 +145,26 @@ int gbh_create_refined_batched(const gbh_params *params, const gbh_refinement *r
  * Sec. 3.2 maps blocks onto CTAs; not a choice the paper makes): kchunk = z planes per work item
  * (3-D; 0 or nzb = the whole block) and items_per_cta = consecutive work
  * items one CTA processes (1 = a CTA per item; a grid of about two CTAs per
- * SM makes the kernel persistent).  Results do not depend on it (bitwise).
- * gbh_autotune times the candidates on U (stage launches into the context's
- * scratch; U is not modified; synchronises the stream; clears the floor
- * counter) and keeps the fastest; gbh_set_decomposition sets one directly.
- * The chosen values are written to *kchunk_out / *items_out if not NULL. */
+ * SM makes the kernel persistent).  A third choice is the tile: the plane
+ * tile of a work item (the nxb x nyb block plane, widened by the ring in the
+ * telescoping mode) can be cut into ysplit row bands, one CTA each, so a CTA
+ * has 1/ysplit of the threads and shared memory (twice as many CTAs fit on
+ * an SM) at the cost of the halo rows and faces both bands form at the cut;
+ * gbh_set_tile_split(ctx, ring, ysplit) sets it per ring width (0: the
+ * interior stage; 2, 4: the ring stages of the telescoping mode), ysplit 1,
+ * or 2 for blocks of at least 8 cells per side.  Results do not depend on
+ * any of these (bitwise).  gbh_autotune times the candidates on U (stage
+ * launches into the context's scratch; U is not modified; synchronises the
+ * stream; clears the floor counter) and keeps the fastest: kchunk x
+ * items_per_cta x ysplit for the interior stage, and, in the telescoping
+ * mode, ysplit for each ring stage.  gbh_set_decomposition sets kchunk and
+ * items_per_cta directly.  The chosen kchunk and items_per_cta are written to
+ * *kchunk_out / *items_out if not NULL; gbh_get_tile_split reads a split.
+ * GBH_ERR_INVAL: a ring other than 0, 2, 4 or an unsupported ysplit. */
 int gbh_autotune(gbh_ctx *ctx, const double *U, int *kchunk_out, int *items_out, void *stream);
 int gbh_set_decomposition(gbh_ctx *ctx, int kchunk, int items_per_cta);
+int gbh_set_tile_split(gbh_ctx *ctx, int ring, int ysplit);
+int gbh_get_tile_split(gbh_ctx *ctx, int ring, int *ysplit);
 
 /* Time-stepping mode (Sec. 4.2, the telescoping variant of the SSP-RK
  * stepper).  enable = 0 (the default): non-telescoping, the guard cells are

@@ -58,6 +58,8 @@ SIGNATURES = {
                                              C.c_int, C.POINTER(_vp)]),
     "gbh_autotune": (C.c_int, [_vp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int), _vp]),
     "gbh_set_decomposition": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "gbh_set_tile_split": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "gbh_get_tile_split": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "gbh_set_telescoping": (C.c_int, [_vp, C.c_int]),
     "gbh_set_rk_stages": (C.c_int, [_vp, C.c_int]),
     "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),

@@ -63,6 +63,7 @@ struct gbh_ctx {
   // stage-kernel work decomposition (gbh_autotune)
   int kchunk = 0;                   // z planes per work item (3-D); 0 = the whole block
   int items_per_cta = 1;
+  int ysplit[3] = {1, 1, 1};        // row bands of the plane tile for ring widths 0, 2, 4
   // CUDA graph of hydro_advance_graph
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -183,6 +184,7 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
     A.nchunks = (c->lay.nz + c->kchunk - 1) / c->kchunk;
   }
   A.items_per_cta = c->items_per_cta;
+  A.ysplit = (ring == 0 || ring == 2 || ring == 4) ? c->ysplit[ring / 2] : 1;
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
@@ -472,6 +474,7 @@ void stage_args_common(StageArgs* A, const Layout& L, const Eos& e) {
   A->kchunk = L.ndim == 3 ? L.nz : 1;   // one work item per block
   A->nchunks = 1;
   A->items_per_cta = 1;
+  A->ysplit = 1;
 }
 
 int set_create_error(int code, const char* msg) { return set_err(nullptr, code, "%s", msg); }
@@ -768,6 +771,21 @@ int gbh_create_batched(const gbh_params* p, const int32_t* problem, int nproblem
   return GBH_OK;
 }
 
+// Mean time of `reps` stage launches (after one untimed launch) into the
+// context's scratch state, with the decomposition the context holds.
+static int time_stage(gbh_ctx* c, const double* U, int ring, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t s,
+                      float* ms) {
+  int rc = GBH_OK;
+  for (int rep = 0; rep < 3 && rc == GBH_OK; ++rep) {
+    if (rep == 1) rc = cuda_err(c, cudaEventRecord(e0, s), "cudaEventRecord");
+    if (!rc) rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, 1e-300, 0.0, 1.0, ring == 0, false, s, ring);
+  }
+  if (!rc) rc = cuda_err(c, cudaEventRecord(e1, s), "cudaEventRecord");
+  if (!rc) rc = cuda_err(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+  if (!rc) rc = cuda_err(c, cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+  return rc;
+}
+
 int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -781,46 +799,89 @@ int gbh_autotune(gbh_ctx* c, const double* U, int* kchunk_out, int* items_out, v
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   std::vector<int> kcs = {0};
   if (c->lay.ndim == 3 && c->lay.nz >= 8 && c->lay.nz % 2 == 0) kcs.push_back(c->lay.nz / 2);
+  std::vector<int> splits = {1};
+  if (c->lay.nx >= 8) splits.push_back(2);
   const long long nlist = c->refined ? c->nactive : c->lay.nblocks;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_err(c, GBH_ERR_CUDA, "cudaEventCreate failed");
+  // the interior stage: z-chunk x CTAs' items x row bands (an unsplit tile
+  // keeps two CTAs per SM resident, a band four)
   float best = 1e30f;
-  int best_kc = 0, best_ipc = 1;
-  for (int kc : kcs) {
-    const long long nitems = nlist * (kc > 0 ? (c->lay.nz + kc - 1) / kc : 1);
-    const long long persistent = (nitems + 2LL * sms - 1) / (2LL * sms);
-    std::vector<int> ipcs = {1, 2, 4};
-    if (persistent > 4) ipcs.push_back((int)persistent);
-    for (int ipc : ipcs) {
-      c->kchunk = kc;
-      c->items_per_cta = ipc;
-      float ms = 0.f;
-      for (int rep = 0; rep < 3 && rc == GBH_OK; ++rep) {
-        if (rep == 1) rc = cuda_err(c, cudaEventRecord(e0, s), "cudaEventRecord");
-        if (!rc) rc = stage_launch(c, U, nullptr, c->d_scratch, nullptr, 1e-300, 0.0, 1.0, true, false, s);
+  int best_kc = 0, best_ipc = 1, best_split = 1;
+  for (int split : splits) {
+    for (int kc : kcs) {
+      const long long nitems = nlist * (kc > 0 ? (c->lay.nz + kc - 1) / kc : 1) * split;
+      const long long resident = 2LL * split * sms;
+      const long long persistent = (nitems + resident - 1) / resident;
+      std::vector<int> ipcs = {1, 2, 4};
+      if (persistent > 4) ipcs.push_back((int)persistent);
+      for (int ipc : ipcs) {
+        c->kchunk = kc;
+        c->items_per_cta = ipc;
+        c->ysplit[0] = split;
+        float ms = 0.f;
+        if ((rc = time_stage(c, U, 0, e0, e1, s, &ms))) break;
+        if (ms < best) {
+          best = ms;
+          best_kc = kc;
+          best_ipc = ipc;
+          best_split = split;
+        }
       }
-      if (!rc) rc = cuda_err(c, cudaEventRecord(e1, s), "cudaEventRecord");
-      if (!rc) rc = cuda_err(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
-      if (!rc) rc = cuda_err(c, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
       if (rc) break;
-      if (ms < best) {
-        best = ms;
-        best_kc = kc;
-        best_ipc = ipc;
-      }
     }
     if (rc) break;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   c->kchunk = best_kc;
   c->items_per_cta = best_ipc;
+  c->ysplit[0] = best_split;
+  // the ring stages of the telescoping mode (ring 2; and 4 with three
+  // stages): row bands with the decomposition chosen above, on U's own guard
+  // cells as they are (the time does not depend on their values)
+  if (!rc && c->telescoping) {
+    for (int ring = 2; ring <= 2 * (c->nstages - 1) && !rc; ring += 2) {
+      if (c->lay.g < ring + 2) continue;
+      float best_r = 1e30f;
+      int pick = 1;
+      for (int split : splits) {
+        c->ysplit[ring / 2] = split;
+        float ms = 0.f;
+        if ((rc = time_stage(c, U, ring, e0, e1, s, &ms))) break;
+        if (ms < best_r) {
+          best_r = ms;
+          pick = split;
+        }
+      }
+      c->ysplit[ring / 2] = pick;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   c->timing = timing;
   cudaMemsetAsync(c->d_words + 1, 0, sizeof(unsigned long long), s);   // trial launches may count floors
   if (rc) return rc;
   if (kchunk_out) *kchunk_out = best_kc > 0 ? best_kc : c->lay.nz;
   if (items_out) *items_out = best_ipc;
+  return GBH_OK;
+}
+
+int gbh_set_tile_split(gbh_ctx* c, int ring, int ysplit) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  if (ring != 0 && ring != 2 && ring != 4) return set_err(c, GBH_ERR_INVAL, "ring must be 0, 2 or 4 (got %d)", ring);
+  if (ysplit != 1 && !(ysplit == 2 && c->lay.nx >= 8))
+    return set_err(c, GBH_ERR_INVAL, "ysplit must be 1, or 2 for blocks of at least 8 cells per side (got %d)",
+                   ysplit);
+  drop_graph(c);
+  c->ysplit[ring / 2] = ysplit;
+  return GBH_OK;
+}
+
+int gbh_get_tile_split(gbh_ctx* c, int ring, int* ysplit) {
+  if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
+  if (ring != 0 && ring != 2 && ring != 4) return set_err(c, GBH_ERR_INVAL, "ring must be 0, 2 or 4 (got %d)", ring);
+  if (!ysplit) return set_err(c, GBH_ERR_INVAL, "null output pointer");
+  *ysplit = c->ysplit[ring / 2];
   return GBH_OK;
 }
 

@@ -50,6 +50,7 @@ struct StageArgs {
   int gather;            // 1: halo from neighbour interiors; 0: from Uin's own guard cells
   int kchunk, nchunks;   // z planes per work item (3-D), work items per block
   int items_per_cta;     // consecutive work items processed by one CTA (>= 1)
+  int ysplit;            // row bands per plane tile, one CTA each (1, or 2 for nx >= 8)
   const int* problem;    // [nblocks] problem of each block (batched ensembles), or null
                          // (then dt_dev and smax_acc have one entry)
   Layout lay;

@@ -59,27 +59,36 @@ __device__ __forceinline__ bool corrected_cell(const StageArgs& a, int b, int i,
          (j == N - 1 && on(FACE_YP)) || (DIM3 && k == 0 && on(FACE_ZM)) || (DIM3 && k == nz - 1 && on(FACE_ZP));
 }
 
-// One work item: block `b` of the list (or of the lattice) and z-chunk
-// `chunk`.  Uses the caller's shared memory; ends with the per-item atomics.
-template <int N, bool DIM3, int E>
+// One work item: block `b` of the list (or of the lattice), z-chunk `chunk`
+// and row band `band` of the plane tile.  The (N+2E)-wide plane tile is cut
+// into S bands of MY = (N+2E)/S rows; a CTA of M*MY threads updates one band
+// (S = 1: the whole tile).  Uses the caller's shared memory; ends with the
+// per-item atomics.
+template <int N, bool DIM3, int E, int S>
 __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red) {
-  constexpr int M = N + 2 * E;              // plane tile (the interior when E = 0)
-  constexpr int NT = M * M;
-  constexpr int P = M + 4;                  // tile with 2-deep x/y rims
-  constexpr int QX = M * (M + 2);           // x-slope cells of a plane
-  constexpr int FX = M * (M + 1);           // x faces of a plane
-  double* sW = smem;                        // [5][P][P] primitives of the plane
-  double* sQx = sW + 5 * P * P;             // [2][5][M][M+2] x face states (minus, plus)
-  double* sQy = sQx + 2 * 5 * QX;           // [2][5][M+2][M] y face states
-  double* sFx = sQy + 2 * 5 * QX;           // [5][M][M+1] x fluxes
-  double* sFy = sFx + 5 * FX;               // [5][M+1][M] y fluxes
+  constexpr int M = N + 2 * E;              // plane tile width (the interior when E = 0)
+  constexpr int MY = M / S;                 // rows of one band
+  constexpr int NT = M * MY;
+  constexpr int PX = M + 4, PY = MY + 4;    // band with 2-deep x/y rims
+  constexpr int QXS = MY * (M + 2);         // x face states of a band, per variable and side
+  constexpr int QYS = (MY + 2) * M;         // y face states
+  constexpr int FXS = MY * (M + 1);         // x fluxes per variable
+  constexpr int FYS = (MY + 1) * M;         // y fluxes per variable
+  double* sW = smem;                        // [5][PY][PX] primitives of the band
+  double* sQx = sW + 5 * PY * PX;           // [2][5][MY][M+2] x face states (minus, plus)
+  double* sQy = sQx + 2 * 5 * QXS;          // [2][5][MY+2][M] y face states
+  double* sFx = sQy + 2 * 5 * QYS;          // [5][MY][M+1] x fluxes
+  double* sFy = sFx + 5 * FXS;              // [5][MY+1][M] y fluxes
 
   const Layout& L = a.lay;
   const int tid = threadIdx.x;
-  const int tx = tid % M, ty = tid / M;     // tile position; cell (tx - E, ty - E)
-  const int ci = tx - E, cj = ty - E;
-  const int slot_idx = item / a.nchunks;
-  const int chunk = item - slot_idx * a.nchunks;
+  const int band = S == 1 ? 0 : item % S;
+  const int rest = S == 1 ? item : item / S;
+  const int y0 = band * MY;                 // first tile row of the band
+  const int tx = tid % M, ty = tid / M;     // band position; cell (tx - E, y0 + ty - E)
+  const int ci = tx - E, cj = y0 + ty - E;
+  const int slot_idx = rest / a.nchunks;
+  const int chunk = rest - slot_idx * a.nchunks;
   const int b = a.block_list ? __ldg(a.block_list + slot_idx) : slot_idx;
   const int prob = a.problem ? __ldg(a.problem + b) : 0;
   const int k0 = DIM3 ? chunk * a.kchunk - E : 0;
@@ -154,29 +163,45 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     // Ring stages (E > 0): the next stage reads this stage's output only in
     // its own box (ring width E - 2) and in 2-deep slabs across its faces.
     // So in the outer z planes, outside that box, only the columns of the box
-    // are read: the window [2, M - 2) of the tile.  There the x/y work (rims,
-    // slopes, faces, update) is done on the window alone; its slopes need no
-    // rims.  Elsewhere the window is the whole tile (ow = 0, Mw = M).
+    // are read: the window [2, M - 2)^2 of the tile.  There the x/y work
+    // (slopes, faces, update) is done on the window alone, and rims are read
+    // only where the window's slopes reach beyond the band (at a cut between
+    // bands).  Elsewhere the window is the whole band.  Window bounds are in
+    // band positions: columns [wx0, wx1), rows [wy0, wy1).
     const bool outer = E > 0 && (k < 2 - E || k >= L.nz + E - 2);
-    const int ow = outer ? 2 : 0;             // window offset in tile positions
-    const int Mw = M - 2 * ow;                // window width
+    const int ow = outer ? 2 : 0;
+    const int wx0 = ow, wx1 = M - ow;
+    const int wy0 = max(ow - y0, 0), wy1 = min(M - ow - y0, MY);
+    const int Wx = wx1 - wx0, Wy = wy1 - wy0;
+    // slope cells reach one position beyond the window, their stencils two
+    const bool rim_xlo = wx0 <= 1, rim_xhi = wx1 >= M - 1, rim_ylo = wy0 <= 1, rim_yhi = wy1 >= MY - 1;
 
-    // (A) primitives of plane k and its 2-deep x/y rims -> shared memory
-    //     (i, j: tile positions)
+    // (A) primitives of plane k in the band and its 2-deep x/y rims -> shared
+    //     memory (i, j: band positions)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + ty + 2) * P + tx + 2, 5 * P * P)] = W0[v];
-    for (int r = tid; r < (outer ? 0 : 8 * M); r += NT) {
-      const int q = r / (2 * M), t = r - q * 2 * M;
-      const int depth = t / M, pos = t - depth * M;
+    for (int v = 0; v < 5; ++v) sW[GBH_IX((v * PY + ty + 2) * PX + tx + 2, 5 * PY * PX)] = W0[v];
+    for (int r = tid; r < 4 * MY + 4 * M; r += NT) {
       int i, j;
-      if (q == 0) { i = -1 - depth; j = pos; }
-      else if (q == 1) { i = M + depth; j = pos; }
-      else if (q == 2) { i = pos; j = -1 - depth; }
-      else { i = pos; j = M + depth; }
+      bool need;
+      if (r < 4 * MY) {
+        const int side = r / (2 * MY), t = r - side * 2 * MY;
+        const int depth = t / MY, pos = t - depth * MY;
+        i = side == 0 ? -1 - depth : M + depth;
+        j = pos;
+        need = side == 0 ? rim_xlo : rim_xhi;
+      } else {
+        const int r2 = r - 4 * MY;
+        const int side = r2 / (2 * M), t = r2 - side * 2 * M;
+        const int depth = t / M, pos = t - depth * M;
+        i = pos;
+        j = side == 0 ? -1 - depth : MY + depth;
+        need = side == 0 ? rim_ylo : rim_yhi;
+      }
+      if (!need) continue;
       double W[5];
-      load_prim<N>(a, e, b, i - E, j - E, k, W);
+      load_prim<N>(a, e, b, i - E, y0 + j - E, k, W);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sW[GBH_IX((v * P + j + 2) * P + i + 2, 5 * P * P)] = W[v];
+      for (int v = 0; v < 5; ++v) sW[GBH_IX((v * PY + j + 2) * PX + i + 2, 5 * PY * PX)] = W[v];
     }
     __syncthreads();
 
@@ -186,63 +211,67 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     // the items and their arithmetic are unchanged.
     const int rtid = NT % 128 == 0 ? (tid + 32 * ((k + (int)blockIdx.x) & 3)) % NT : tid;
 
-    // (B) MC face states: x-slope cells i in [-1, M], y-slope cells j in [-1, M],
-    //     three consecutive cells per work item, so the two inner differences
-    //     are formed once for two slopes (the last triple of a row may be
-    //     partial: its reads are clamped to the row and its extra slopes not
-    //     stored).  The list ends with the 2 M block-boundary faces x = M - 1/2
-    //     and y = M - 1/2, each forming the two face states it needs from the
-    //     primitives (the same arithmetic as the slope items): so (C) is
-    //     exactly 2 M^2 faces, two full passes of the CTA, with no ragged pass.
-    //     Positions below are in window coordinates (tile position minus ow).
-    const int TR = (Mw + 2 + 2) / 3;                  // triples per row
-    for (int s = rtid; s < 2 * TR * Mw + 2 * Mw; s += NT) {
-      if (s >= 2 * TR * Mw) {
-        const int f = s - 2 * TR * Mw;
-        const bool xf = f < Mw;
-        const int line = xf ? f : f - Mw;                       // row j (x face) or column i (y face)
-        const int step = xf ? 1 : P;
-        // position Mw - 2 along the normal
-        const int first = xf ? (line + ow + 2) * P + Mw + ow : (Mw + ow) * P + line + ow + 2;
+    // (B) MC face states: x-slope cells i in [wx0 - 1, wx1] of the window's
+    //     rows, y-slope cells j in [wy0 - 1, wy1] of its columns, three
+    //     consecutive cells per work item, so the two inner differences are
+    //     formed once for two slopes (the last triple of a line may be
+    //     partial: its reads are clamped to the line and its extra slopes not
+    //     stored).  The list ends with the window's upper boundary faces x =
+    //     wx1 - 1/2 and y = wy1 - 1/2, each forming the two face states it
+    //     needs from the primitives (the same arithmetic as the slope items):
+    //     so (C) is exactly 2 Wx Wy faces (two full passes of an unsplit CTA).
+    const int TRX = (Wx + 4) / 3, TRY = (Wy + 4) / 3;   // triples per line (W + 2 slope cells)
+    const int NSX = TRX * Wy, NSY = TRY * Wx;
+    for (int s = rtid; s < NSX + NSY + Wy + Wx; s += NT) {
+      if (s >= NSX + NSY) {
+        const int f = s - NSX - NSY;
+        const bool xf = f < Wy;
+        const int line = xf ? f : f - Wy;                       // window row (x face) or column (y face)
+        const int step = xf ? 1 : PX;
+        // positions wx1 - 2 .. wx1 + 1 along x (or wy1 - 2 .. wy1 + 1 along y)
+        const int first = xf ? (wy0 + line + 2) * PX + wx1 : wy1 * PX + wx0 + line + 2;
         double ql[5], qr[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const double* q = sW + GBH_IX(v * P * P + first, 5 * P * P - 3 * step);
+          const double* q = sW + GBH_IX(v * PY * PX + first, 5 * PY * PX - 3 * step);
           const double a0 = q[0], a1 = q[step], a2 = q[2 * step], a3 = q[3 * step];
           const double d0 = sub(a1, a0, rk), d1 = sub(a2, a1, rk), d2 = sub(a3, a2, rk);
-          ql[v] = add(a1, mc_half_slope_d(d0, d1, rk), rk);   // plus state of cell M - 1
-          qr[v] = sub(a2, mc_half_slope_d(d1, d2, rk), rk);   // minus state of cell M
+          ql[v] = add(a1, mc_half_slope_d(d0, d1, rk), rk);   // plus state of the last window cell
+          qr[v] = sub(a2, mc_half_slope_d(d1, d2, rk), rk);   // minus state of the next cell
         }
         const int vn = xf ? 1 : 2, vt = xf ? 2 : 1;
         double wl[5] = {ql[0], ql[vn], ql[vt], ql[3], ql[4]};
         double wr[5] = {qr[0], qr[vn], qr[vt], qr[3], qr[4]};
         double F[5];
         hllc_flux(wl, wr, e, F);
-        double* o = xf ? sFx + GBH_IX((line + ow) * (M + 1) + Mw + ow, FX)
-                       : sFy + GBH_IX((Mw + ow) * M + line + ow, FX);
-        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+        const int fs = xf ? FXS : FYS;
+        double* o = xf ? sFx + GBH_IX((wy0 + line) * (M + 1) + wx1, FXS)
+                       : sFy + GBH_IX(wy1 * M + wx0 + line, FYS);
+        o[0] = F[0]; o[vn * fs] = F[1]; o[vt * fs] = F[2]; o[3 * fs] = F[3]; o[4 * fs] = F[4];
         continue;
       }
-      const bool xs = s < TR * Mw;
-      const int s2 = xs ? s : s - TR * Mw;
-      const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // row (x) or column (y); first slope cell + 1
-      const int step = xs ? 1 : P;
-      const int first = xs ? (line + ow + 2) * P + c0 + ow : (c0 + ow) * P + line + ow + 2;
-      const int last = Mw + 3 - c0;                   // positions c0 .. Mw + 3 exist
+      const bool xs = s < NSX;
+      const int s2 = xs ? s : s - NSX;
+      const int TR = xs ? TRX : TRY, Wl = xs ? Wx : Wy;
+      const int line = s2 / TR, c0 = 3 * (s2 - line * TR);   // window row (x) or column (y); first slope cell + 1
+      const int step = xs ? 1 : PX;
+      const int first = xs ? (wy0 + line + 2) * PX + wx0 + c0 : (wy0 + c0) * PX + wx0 + line + 2;
+      const int last = Wl + 3 - c0;                   // positions c0 .. Wl + 3 exist
       const int k3 = 3 < last ? 3 : last, k4 = 4 < last ? 4 : last;
-      const bool two = c0 + 1 < Mw + 2, three = c0 + 2 < Mw + 2;
+      const bool two = c0 + 1 < Wl + 2, three = c0 + 2 < Wl + 2;
+      const int os = xs ? 1 : M;                      // next slope cell
+      const int op = xs ? 5 * QXS : 5 * QYS;          // plus states follow the minus states
 #pragma unroll 1
       for (int v = 0; v < 5; ++v) {
-        const double* q = sW + v * P * P + first;
+        const double* q = sW + v * PY * PX + first;
         const double q1 = q[step], q2 = q[2 * step], q3 = q[k3 * step];
         const double d0 = sub(q1, q[0], rk), d1 = sub(q2, q1, rk), d2 = sub(q3, q2, rk);
         const double d3 = sub(q[k4 * step], q3, rk);
         const double t0 = mc_half_slope_d(d0, d1, rk), t1 = mc_half_slope_d(d1, d2, rk);
         const double t2 = mc_half_slope_d(d2, d3, rk);
-        double* qm = xs ? sQx + GBH_IX((v * M + line + ow) * (M + 2) + c0 + ow, 10 * QX)
-                        : sQy + GBH_IX((v * (M + 2) + c0 + ow) * M + line + ow, 10 * QX);
-        const int os = xs ? 1 : M;                    // next slope cell
-        const int op = 5 * QX;                        // plus states follow the minus states
+        // the base slot lies in the minus half; a partial triple stores no slot past its line
+        double* qm = xs ? sQx + GBH_IX((v * MY + wy0 + line) * (M + 2) + wx0 + c0, 5 * QXS)
+                        : sQy + GBH_IX((v * (MY + 2) + wy0 + c0) * M + wx0 + line, 5 * QYS);
         qm[0] = sub(q1, t0, rk);
         qm[op] = add(q1, t0, rk);
         if (two) {
@@ -257,23 +286,22 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     }
     __syncthreads();
 
-    // (C) HLLC on the x faces (i - 1/2, i in [0, M - 1]) and y faces (j - 1/2,
-    //     j in [0, M - 1]); the faces at M - 1/2 came with (B)
-    for (int f = tid; f < 2 * Mw * Mw; f += NT) {
-      const bool xf = f < Mw * Mw;
-      int i, j;                    // tile positions
+    // (C) HLLC on the x faces (i - 1/2, i in [wx0, wx1)) and y faces (j - 1/2,
+    //     j in [wy0, wy1)) of the window; the faces at wx1 - 1/2 and wy1 - 1/2
+    //     came with (B)
+    for (int f = tid; f < 2 * Wx * Wy; f += NT) {
+      const bool xf = f < Wx * Wy;
+      const int f2 = xf ? f : f - Wx * Wy;
+      const int i = f2 % Wx + wx0, j = f2 / Wx + wy0;   // band positions
       const double *ql, *qr;       // minus/plus state arrays, var stride vs
       int vs, ol, orr;
       if (xf) {
-        i = f % Mw + ow; j = f / Mw + ow;
-        vs = M * (M + 2);
+        vs = QXS;
         ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
         orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
-        const int f2 = f - Mw * Mw;
-        i = f2 % Mw + ow; j = f2 / Mw + ow;
-        vs = (M + 2) * M;
+        vs = QYS;
         ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
         orr = (j + 1) * M + i;                // minus state of cell j (slot j+1)
         ql = sQy; qr = sQy;
@@ -284,11 +312,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       double F[5];
       hllc_flux(wl, wr, e, F);
       if (xf) {
-        double* o = sFx + GBH_IX(j * (M + 1) + i, FX);
-        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+        double* o = sFx + GBH_IX(j * (M + 1) + i, FXS);
+        o[0] = F[0]; o[vn * FXS] = F[1]; o[vt * FXS] = F[2]; o[3 * FXS] = F[3]; o[4 * FXS] = F[4];
       } else {
-        double* o = sFy + GBH_IX(j * M + i, FX);
-        o[0] = F[0]; o[vn * FX] = F[1]; o[vt * FX] = F[2]; o[3 * FX] = F[3]; o[4 * FX] = F[4];
+        double* o = sFy + GBH_IX(j * M + i, FYS);
+        o[0] = F[0]; o[vn * FYS] = F[1]; o[vt * FYS] = F[2]; o[3 * FYS] = F[3]; o[4 * FYS] = F[4];
       }
     }
     __syncthreads();
@@ -299,12 +327,12 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (cj + L.g)) * L.nxp + (ci + L.g);
     // in an outer plane of a ring stage only the window's cells are updated
     // (the others are never read again and their fluxes were not formed)
-    const bool upd = !outer || (tx >= 2 && tx < M - 2 && ty >= 2 && ty < M - 2);
+    const bool upd = !outer || (tx >= wx0 && tx < wx1 && ty >= wy0 && ty < wy1);
     double out[5];
 #pragma unroll
     for (int v = 0; v < 5 && upd; ++v) {
-      const double fx = sub(sFx[GBH_IX((v * M + ty) * (M + 1) + tx + 1, 5 * FX)], sFx[(v * M + ty) * (M + 1) + tx], rk);
-      const double fy = sub(sFy[GBH_IX((v * (M + 1) + ty + 1) * M + tx, 5 * FX)], sFy[(v * (M + 1) + ty) * M + tx], rk);
+      const double fx = sub(sFx[GBH_IX((v * MY + ty) * (M + 1) + tx + 1, 5 * FXS)], sFx[(v * MY + ty) * (M + 1) + tx], rk);
+      const double fy = sub(sFy[GBH_IX((v * (MY + 1) + ty + 1) * M + tx, 5 * FYS)], sFy[(v * (MY + 1) + ty) * M + tx], rk);
       const long long o = GBH_IX(base + v * L.vstride, (long long)L.nblocks * L.bstride);
       double r = fma(-dtx, fx, __ldg(a.Uin + o));
       r = fma(-dty, fy, r);
@@ -323,16 +351,16 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       const int t2k = DIM3 ? k : 0;
       if (ci == 0 && fsl[FACE_XM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[GBH_IX(fsl[FACE_XM] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * M + ty) * (M + 1) + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_XM] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * MY + ty) * (M + 1) + tx];
       if (ci == N - 1 && fsl[FACE_XP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[GBH_IX(fsl[FACE_XP] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * M + ty) * (M + 1) + tx + 1];
+          a.flux_reg[GBH_IX(fsl[FACE_XP] * ss + (v * n2 + t2k) * N + cj, a.flux_reg_len)] = sFx[(v * MY + ty) * (M + 1) + tx + 1];
       if (cj == 0 && fsl[FACE_YM] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[GBH_IX(fsl[FACE_YM] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (M + 1) + ty) * M + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_YM] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (MY + 1) + ty) * M + tx];
       if (cj == N - 1 && fsl[FACE_YP] >= 0)
         for (int v = 0; v < 5; ++v)
-          a.flux_reg[GBH_IX(fsl[FACE_YP] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (M + 1) + ty + 1) * M + tx];
+          a.flux_reg[GBH_IX(fsl[FACE_YP] * ss + (v * n2 + t2k) * N + ci, a.flux_reg_len)] = sFy[(v * (MY + 1) + ty + 1) * M + tx];
       if (DIM3 && k == 0 && fsl[FACE_ZM] >= 0)
         for (int v = 0; v < 5; ++v) a.flux_reg[GBH_IX(fsl[FACE_ZM] * ss + (v * n2 + cj) * N + ci, a.flux_reg_len)] = Fzm[v];
       if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
@@ -363,58 +391,82 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   }
 }
 
-// Work list: items (block, z-chunk) in order; each CTA processes
+// CTAs per SM the register budget is sized for: an unsplit interior tile
+// (256 threads at N = 16) two, a band of it four; a ring tile one, a band
+// of it two.
+template <int E, int S>
+constexpr int min_ctas() { return (E == 0 ? 2 : 1) * S; }
+
+// Work list: items (block, z-chunk, band) in order; each CTA processes
 // `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
 // grid makes the kernel persistent).  No CTA waits on another.
-template <int N, bool DIM3, int E>
-__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E), E == 0 ? 2 : 1) stage_kernel(const StageArgs a) {
+template <int N, bool DIM3, int E, int S>
+__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E) / S, min_ctas<E, S>()) stage_kernel(const StageArgs a) {
+  constexpr int NT = (N + 2 * E) * (N + 2 * E) / S;
   extern __shared__ double smem[];
-  __shared__ double s_red[E == 0 && N * N > 32 ? N * N / 32 : 1];
-  const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
+  __shared__ double s_red[E == 0 && NT > 32 ? NT / 32 : 1];
+  const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
   const int first = blockIdx.x * a.items_per_cta;
   const int last = min(nitems, first + a.items_per_cta);
   for (int item = first; item < last; ++item) {
-    stage_item<N, DIM3, E>(a, item, smem, s_red);
+    stage_item<N, DIM3, E, S>(a, item, smem, s_red);
     __syncthreads();
   }
 }
 
-template <int N, int E>
-size_t smem_for() {
+template <int N, int E, int S>
+constexpr size_t smem_for() {
   constexpr int M = N + 2 * E;
-  constexpr int P = M + 4;
-  return sizeof(double) * (5 * P * P + 4 * 5 * M * (M + 2) + 2 * 5 * M * (M + 1));
+  constexpr int MY = M / S;
+  return sizeof(double) * (5 * (MY + 4) * (M + 4) + 2 * 5 * MY * (M + 2) + 2 * 5 * (MY + 2) * M +
+                           5 * MY * (M + 1) + 5 * (MY + 1) * M);
 }
 
-template <int N, bool D3, int E>
+template <int N, bool D3, int E, int S>
 cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
-  const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks;
+  const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
   const int per = a.items_per_cta > 0 ? a.items_per_cta : 1;
   const unsigned grid = (unsigned)((nitems + per - 1) / per);
-  stage_kernel<N, D3, E><<<grid, (N + 2 * E) * (N + 2 * E), smem_for<N, E>(), s>>>(a);
+  stage_kernel<N, D3, E, S><<<grid, (N + 2 * E) * (N + 2 * E) / S, smem_for<N, E, S>(), s>>>(a);
   return cudaGetLastError();
 }
 
+template <int N, bool D3, int E, int S>
+cudaError_t prepare_one() {
+  return cudaFuncSetAttribute(stage_kernel<N, D3, E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_for<N, E, S>());
+}
+
+// The row-band split (S = 2) exists for N >= 8 (a band of at least 4 rows).
 template <int N, bool D3>
 cudaError_t prepare_t() {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<N, D3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_for<N, 0>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel<N, D3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_for<N, 2>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage_kernel<N, D3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_for<N, 4>());
+  cudaError_t e = prepare_one<N, D3, 0, 1>();
+  if (e == cudaSuccess) e = prepare_one<N, D3, 2, 1>();
+  if (e == cudaSuccess) e = prepare_one<N, D3, 4, 1>();
+  if constexpr (N >= 8) {
+    if (e == cudaSuccess) e = prepare_one<N, D3, 0, 2>();
+    if (e == cudaSuccess) e = prepare_one<N, D3, 2, 2>();
+    if (e == cudaSuccess) e = prepare_one<N, D3, 4, 2>();
+  }
   return e;
+}
+
+template <int N, bool D3, int E>
+cudaError_t launch_s(const StageArgs& a, cudaStream_t s) {
+  if constexpr (N >= 8) {
+    if (a.ysplit == 2) return launch_t<N, D3, E, 2>(a, s);
+  }
+  if (a.ysplit != 1) return cudaErrorInvalidValue;
+  return launch_t<N, D3, E, 1>(a, s);
 }
 
 template <int E>
 cudaError_t launch_e(const StageArgs& a, cudaStream_t s) {
   const bool d3 = a.lay.ndim == 3;
   switch (a.lay.nx) {
-    case 4: return d3 ? launch_t<4, true, E>(a, s) : launch_t<4, false, E>(a, s);
-    case 8: return d3 ? launch_t<8, true, E>(a, s) : launch_t<8, false, E>(a, s);
-    case 16: return d3 ? launch_t<16, true, E>(a, s) : launch_t<16, false, E>(a, s);
+    case 4: return d3 ? launch_s<4, true, E>(a, s) : launch_s<4, false, E>(a, s);
+    case 8: return d3 ? launch_s<8, true, E>(a, s) : launch_s<8, false, E>(a, s);
+    case 16: return d3 ? launch_s<16, true, E>(a, s) : launch_s<16, false, E>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -425,9 +477,9 @@ GBH_CHECK_TAKE(check_take_stage)
 
 size_t stage_smem_bytes(int nx) {
   switch (nx) {
-    case 4: return smem_for<4, 0>();
-    case 8: return smem_for<8, 0>();
-    case 16: return smem_for<16, 0>();
+    case 4: return smem_for<4, 0, 1>();
+    case 8: return smem_for<8, 0, 1>();
+    case 16: return smem_for<16, 0, 1>();
     default: return 0;
   }
 }

@@ -214,6 +214,15 @@ class Hydro:
     def set_decomposition(self, kchunk: int, items_per_cta: int):
         self._check(self.lib.gbh_set_decomposition(self.ctx, int(kchunk), int(items_per_cta)))
 
+    def set_tile_split(self, ring: int, ysplit: int):
+        """Row bands per plane tile of the stage kernel for ring width 0, 2 or 4."""
+        self._check(self.lib.gbh_set_tile_split(self.ctx, int(ring), int(ysplit)))
+
+    def tile_split(self, ring: int = 0) -> int:
+        out = C.c_int(0)
+        self._check(self.lib.gbh_get_tile_split(self.ctx, int(ring), C.byref(out)))
+        return int(out.value)
+
     def set_telescoping(self, enable: bool = True):
         """Telescoping SSP-RK (one guard fill per step; needs nguard >= 2 * stages)."""
         self._check(self.lib.gbh_set_telescoping(self.ctx, int(bool(enable))))

@@ -187,6 +187,7 @@ def test_sod_like_256_gradient_vs_finite_differences(gb):
     idx = np.argwhere(mask(lat)[:, 0] > 0)
     pick = np.random.default_rng(11).choice(len(idx), 32, replace=False)
     rel = {1e-6: [], 1e-8: []}
+    comp = {1e-6: {}, 1e-8: {}}
     for var in (0, 1, 2, 4):
         gmax = np.max(np.abs(grad[:, var]))
         for p in pick:
@@ -199,6 +200,12 @@ def test_sod_like_256_gradient_vs_finite_differences(gb):
                 Wm[c] -= hh
                 fd = (J(Wp) - J(Wm)) / (2 * hh)
                 rel[step].append(abs(fd - grad[c]) / gmax)
+                comp[step].setdefault(var, []).append(abs(fd - grad[c]) / abs(grad[c]))
+    # per-component relative errors |fd - g| / |g| (median, 90th percentile, max per field)
+    for step in comp:
+        print(f"FD h={step:g} per-component relative error (median / p90 / max): " + "; ".join(
+            "%s %.1e / %.1e / %.1e" % ("rho u v w p".split()[v], np.median(x), np.percentile(x, 90), np.max(x))
+            for v, x in comp[step].items()))
     r6, r8 = np.array(rel[1e-6]), np.array(rel[1e-8])
     assert np.median(r6) <= 1e-5 and r6.max() <= 5e-3, (np.median(r6), r6.max())
     assert np.median(r8) <= 2e-6 and r8.max() <= 2e-4, (np.median(r8), r8.max())

@@ -118,3 +118,98 @@ def test_autotune_and_refined_decomposition(gb):
     db = hr.compute_dt(B)
     hr.advance(B, 3, db)
     assert torch.equal(da, db)
+
+
+def _split_case(case):
+    """(context factory, initial state, rings the case's steps use)"""
+    if case in ("3d", "telescoping_rk2", "telescoping_rk3", "2d"):
+        ng = 6 if case == "telescoping_rk3" else 4
+        lat = (wl.lattice_2d(3, 2, 16, 16, ng, bc=("periodic", "outflow")) if case == "2d" else
+               wl.lattice_3d(2, 3, 2, 16, 16, 16, ng, bc=("outflow", "periodic", "outflow")))
+        U0 = wl.random_state(lat, seed=61, rough=True)
+
+        def make():
+            h = gb_pkg().Hydro.from_lattice(lat)
+            if case == "telescoping_rk3":
+                h.set_rk_stages(3)
+            h.set_telescoping(case.startswith("telescoping"))
+            return h
+        rings = {"telescoping_rk2": (0, 2), "telescoping_rk3": (0, 2, 4)}.get(case, (0,))
+        return make, U0, rings, lat.interior_slices()
+    if case in ("two_level", "two_level_lbl"):
+        tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))
+        U0 = wl.sedov_two_level(tl)
+
+        def make():
+            h = gb_pkg().Hydro.from_two_level(tl)
+            h.set_telescoping(case == "two_level_lbl")
+            return h
+        return make, U0, ((0, 2) if case == "two_level_lbl" else (0,)), tl.coarse.interior_slices()
+    lats, U0 = small_ensemble()
+    return (lambda: gb_pkg().Hydro.from_batch(lats)), U0, (0,), lats[0].interior_slices()
+
+
+def gb_pkg():
+    import paper_2401_03378_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("case", ["3d", "2d", "telescoping_rk2", "telescoping_rk3", "two_level", "two_level_lbl",
+                                  "batched"])
+def test_tile_split_does_not_change_results(gb, case):
+    """The stage kernel's plane tile cut into two row bands (one CTA each), on
+    the interior stage and on every ring stage the mode uses, alone and with
+    z-chunks and several items per CTA: the same state and dt bit for bit."""
+    make, U0, rings, sl = _split_case(case)
+    zs, ys, xs = sl
+    results = []
+    for split, kc, ipc in ((1, 0, 1), (2, 0, 1), (2, 8, 3)):
+        h = make()
+        for r in rings:
+            h.set_tile_split(r, split)
+        if kc or ipc != 1:
+            h.set_decomposition(kc if h.ndim == 3 else 0, ipc)
+        assert all(h.tile_split(r) == split for r in rings)
+        U = dev(U0)
+        if h.refined:
+            h.fill_guardcells(U)
+        dt = h.compute_dt(U)
+        h.advance(U, 3, dt)
+        results.append((host(U)[:, :, zs, ys, xs], host(dt), h.floor_hits()))
+        h.close()
+    for U, dt, hits in results[1:]:
+        assert np.array_equal(U, results[0][0]) and np.array_equal(dt, results[0][1])
+        assert hits == results[0][2]
+
+
+def test_tile_split_rejections(gb):
+    h = gb.Hydro.from_lattice(wl.lattice_3d(2, 2, 2, 4, 4, 4, 4))
+    with pytest.raises(gb.GbhError):
+        h.set_tile_split(0, 2)          # bands of 2 rows are not built
+    h2 = gb.Hydro.from_lattice(wl.lattice_3d(2, 2, 2, 8, 8, 8, 4))
+    for ring, split in ((1, 1), (0, 3), (6, 1)):
+        with pytest.raises(gb.GbhError):
+            h2.set_tile_split(ring, split)
+    h2.set_tile_split(4, 2)
+    assert h2.tile_split(4) == 2 and h2.tile_split(0) == 1
+
+
+def test_autotune_picks_tile_splits_for_ring_stages(gb):
+    lat = wl.lattice_3d(2, 2, 2, 16, 16, 16, 6)
+    U0 = wl.sedov(lat)
+    h = gb.Hydro.from_lattice(lat)
+    h.set_rk_stages(3)
+    h.set_telescoping(True)
+    U = dev(U0)
+    h.autotune(U)
+    assert torch.equal(U, dev(U0))
+    assert all(h.tile_split(r) in (1, 2) for r in (0, 2, 4))
+    ref = gb.Hydro.from_lattice(lat)
+    ref.set_rk_stages(3)
+    ref.set_telescoping(True)
+    A, B = dev(U0), dev(U0)
+    da, db = h.compute_dt(A), ref.compute_dt(B)
+    h.advance(A, 2, da)
+    ref.advance(B, 2, db)
+    zs, ys, xs = lat.interior_slices()
+    assert torch.equal(A[:, :, zs, ys, xs], B[:, :, zs, ys, xs]) and torch.equal(da, db)

@@ -65,14 +65,23 @@ UNIFORM = [
 ]
 
 
-@pytest.mark.parametrize("lat,stages,tele", UNIFORM)
-def test_uniform_paths(gb, lat, stages, tele):
+def split_tiles(h, split):
+    """Row bands of the stage kernel's plane tile on every ring width."""
+    for ring in (0, 2, 4):
+        h.set_tile_split(ring, split)
+
+
+# the row-band split (2) exists for blocks of at least 8 cells per side
+@pytest.mark.parametrize("lat,stages,tele,split", [u + (s,) for u in UNIFORM for s in (1, 2)
+                                                   if s == 1 or u[0].n[0] >= 8])
+def test_uniform_paths(gb, lat, stages, tele, split):
     U0 = wl.random_state(lat, seed=61, rough=True)
 
     def make(checked):
         h = gb.Hydro.from_lattice(lat, checked=checked)
         h.set_rk_stages(stages)
         h.set_telescoping(tele)
+        split_tiles(h, split)
         return h
 
     def run(h):
@@ -108,8 +117,9 @@ def test_decompositions_and_graph(gb, kchunk, ipc):
     both(gb, make, run)
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("stages,tele,ng", [(2, False, 4), (2, True, 4), (3, False, 6), (3, True, 6)])
-def test_two_level_paths(gb, stages, tele, ng):
+def test_two_level_paths(gb, stages, tele, ng, split):
     tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, ng), (1, 1, 1), (3, 3, 3))
     U0 = wl.sedov_two_level(tl)
 
@@ -117,6 +127,7 @@ def test_two_level_paths(gb, stages, tele, ng):
         h = gb.Hydro.from_two_level(tl, checked=checked)
         h.set_rk_stages(stages)
         h.set_telescoping(tele)
+        split_tiles(h, split)
         return h
 
     def run(h):

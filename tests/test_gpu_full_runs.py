@@ -55,6 +55,14 @@ def host(T):
     return T.cpu().numpy()
 
 
+def report(name, err, dterr=None):
+    """One line with the measured figures (shown by pytest -rP)."""
+    line = f"PARITY {name}: rel Linf per variable " + " ".join("%.2e" % e for e in err)
+    if dterr is not None:
+        line += f"; dt history {dterr:.2e}"
+    print(line)
+
+
 def stepped(h, U, nsteps):
     """nsteps of hydro_step_cfl (the benchmark's loop); returns the dt of every step."""
     dt = h.compute_dt(U)
@@ -75,8 +83,9 @@ def test_sedov_3d_128_200_steps_whole_run(gb):
     hist, _ = stepped(h, Ug, 200)
     out = host(Ug)
     err = relerr_per_var(to_global(out, lat), to_global(ref, lat))
-    assert np.all(err <= TOL_RUN), err
     dterr = np.max(np.abs(hist[:, 0] / hist_o - 1))
+    report("Sedov 128^3 x 200", err, dterr)
+    assert np.all(err <= TOL_RUN), err
     assert dterr <= TOL_DT, dterr
     assert h.floor_hits() == hits_o == 0
     zs, ys, xs = lat.interior_slices()
@@ -96,8 +105,9 @@ def test_sedov_3d_256_50_steps_whole_run(gb):
     ref = U0
     hist_o, hits_o = Oracle(lat).run(ref, 50)
     err = relerr_per_var(to_global(out, lat), to_global(ref, lat))
-    assert np.all(err <= TOL_RUN), err
     dterr = np.max(np.abs(hist[:, 0] / hist_o - 1))
+    report("Sedov 256^3 x 50", err, dterr)
+    assert np.all(err <= TOL_RUN), err
     assert dterr <= TOL_DT, dterr
     assert h.floor_hits() == hits_o == 0
 
@@ -129,8 +139,9 @@ def test_refined_sedov_4096_plus_4096_50_steps_whole_run(gb):
     ref = U0
     hist_o, hits_o = Oracle2(tl).run(ref, 50)
     err = leaf_err(out, ref, tl)
-    assert np.all(err <= TOL_RUN), err
     dterr = np.max(np.abs(hist[:, 0] / hist_o - 1))
+    report("two-level Sedov 4096+4096 blocks x 50", err, dterr)
+    assert np.all(err <= TOL_RUN), err
     assert dterr <= TOL_DT, dterr
     assert h.floor_hits() == hits_o == 0
 
@@ -172,6 +183,7 @@ def test_ensemble_96_problems_100_steps_whole_run(gb):
         assert dterr <= TOL_DT, (i, dterr)
         worst_dt = max(worst_dt, dterr)
         assert hits_o == 0
+    report("96-problem ensemble x 100 (worst problem per variable)", worst, worst_dt)
     assert h.floor_hits() == 0
 
 
@@ -230,9 +242,11 @@ def test_sod_like_256_gradient_vs_oracle_adjoint(gb):
     for s in reversed(range(50)):
         lo = o.step_adjoint(states[s], run.dts[s], lo)
     e = relerr_per_var(to_global(lam0, lat), to_global(lo, lat))
-    assert np.all(e[[0, 1, 2, 4]] <= TOL_GRAD), e
     go = prim_to_cons_vjp_plain(W0, lo) * mask
     eW = relerr_per_var(to_global(gW, lat), to_global(go, lat))
+    report("gradient 256^2 x 50, conserved", e)
+    report("gradient 256^2 x 50, primitive", eW)
+    assert np.all(e[[0, 1, 2, 4]] <= TOL_GRAD), e
     assert np.all(eW[[0, 1, 2, 4]] <= TOL_GRAD), eW
     # w is identically zero in 2-D: its adjoint is round-off of the others'
     scale = np.max(np.abs(to_global(lo, lat)[[1, 2]]))

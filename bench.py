@@ -308,7 +308,7 @@ def run_gpu(args):
 
     # the decomposition the library's autotuner picks on this workload (the
     # timed loop below runs with it)
-    tuning = autotuned(h, U, (0,), ms_per_step)
+    tuning = autotuned(h, U, (0,), ms_per_step) if args.autotune else None
     dt = h.compute_dt(U)
     for _ in range(args.warmup):
         h.step_cfl(U, dt)
@@ -821,6 +821,9 @@ def main(argv=None):
     ap.add_argument("--no-repeats", dest="repeats", action="store_false",
                     help="skip the 5 x 10-step repeats after the timed loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the default decomposition without running the autotuner first "
+                         "(profiling runs: no trial launches before the captured ones)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         log("note: at least 3 warm-up steps are required; using 3")

@@ -393,6 +393,24 @@ int gbh_stage_kernel_time(gbh_ctx *ctx, double *ms_host, long long *launches_hos
  * (x2 flops for forms 0, 1 and 4).  GBH_ERR_INVAL for out-of-range arguments. */
 int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double *out_dev, void *stream);
 
+/* FP64 instruction-count probe of the stage kernel's arithmetic building
+ * blocks (not part of the method; for ncu's per-kernel instruction counters).
+ * fn: 0 = conserved -> primitive conversion of one cell, 1 = one x/y slope
+ * work item (three cells' MC slopes and face states) of one variable, 2 = one
+ * HLLC face, 3 = the 3-D flux-difference update of one variable, 4 = the
+ * second SSP-RK stage's combine of one variable, 5 = the CFL epilogue of one
+ * cell (conversion and 3-D signal speed), 6 = the z march's next slope and
+ * face states of one variable, 7 = the two face states of a block-boundary
+ * face, one variable.  Each of blocks*threads threads makes iters dependent
+ * calls on its 10 DEVICE doubles io_dev[10 t .. 10 t + 9] (a conserved state,
+ * or two primitive states for fn 2, and any finite values for the rest;
+ * overwritten with the chain's last inputs, which differ from the first ones
+ * in the last mantissa bit at most), chained through integer operations only, so
+ * the FP64 instructions of a launch divided by blocks*threads*iters are those
+ * of one call.  GBH_ERR_INVAL for out-of-range arguments. */
+#define GBH_OPCOUNT_FNS 8
+int gbh_op_count_probe(int fn, int blocks, int threads, int iters, double *io_dev, void *stream);
+
 /* Self-test of the FP64 reciprocal / reciprocal-square-root / square-root
  * building blocks the kernels use (hardware seed + one refinement step):
  * for n positive, normal, finite DEVICE doubles x_dev writes 6*n DEVICE

@@ -87,6 +87,7 @@ SIGNATURES = {
     "gbh_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "gbh_stage_kernel_time": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _vp]),
     "gbh_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _vp]),
+    "gbh_op_count_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "gbh_fastmath_selftest": (C.c_int, [_dp, _dp, C.c_longlong, _vp]),
     "gbh_bits_selftest": (C.c_int, [_dp, _dp, _dp, C.c_longlong, _vp]),
     "gbh_device_sm_count": (C.c_int, []),

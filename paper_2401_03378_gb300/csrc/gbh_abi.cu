@@ -1457,6 +1457,21 @@ int gbh_fp64_probe(int blocks, int threads, int iters, int lanes, int form, doub
   return GBH_OK;
 }
 
+int gbh_op_count_probe(int fn, int blocks, int threads, int iters, double* io_dev, void* stream) {
+  if (fn < 0 || fn >= GBH_OPCOUNT_FNS || blocks < 1 || threads < 1 || threads > 1024 || iters < 1 || !io_dev)
+    return set_err(nullptr, GBH_ERR_INVAL, "invalid probe arguments");
+  gbh_params p{};
+  p.gamma = 1.4;
+  p.small_rho = 1e-12;
+  p.small_p = 1e-14;
+  gbh::Layout L;
+  gbh::Eos eos;
+  gbh::layout_from_params(&p, &L, &eos);
+  cudaError_t e = gbh::launch_op_count(fn, blocks, threads, iters, eos, io_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_err(nullptr, GBH_ERR_CUDA, "probe launch: %s", cudaGetErrorString(e));
+  return GBH_OK;
+}
+
 int gbh_fastmath_selftest(const double* x_dev, double* out_dev, long long n, void* stream) {
   if (!x_dev || !out_dev || n < 1) return set_err(nullptr, GBH_ERR_INVAL, "invalid self-test arguments");
   cudaError_t e = gbh::launch_fastmath_selftest(x_dev, out_dev, n, (cudaStream_t)stream);

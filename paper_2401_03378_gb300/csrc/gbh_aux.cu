@@ -205,6 +205,72 @@ __global__ void fp64_probe_kernel(int iters, int lanes, long long zero, double* 
   out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = sum;
 }
 
+// FP64 instruction count of one call of each arithmetic building block of the
+// stage kernel, in the form the kernel uses (register constants, register-FMA
+// adds and multiplies).  Each thread makes `iters` dependent calls on the 10
+// doubles io[10 t .. 10 t + 9]; the next call's inputs take the low bit of
+// the XOR of every output of the last one into their last mantissa bits with
+// an integer XOR, so no part of a call can be hoisted or folded and the chain
+// adds no FP64 work: ncu's FP64 instruction counters of a launch divided by
+// threads x iters are the instructions of one call.
+template <int FN>
+__global__ void op_count_kernel(int iters, const Eos e0, double* io) {
+  const long long zt = thread_zero(e0);
+  const Eos e = reg_eos(e0, zt);
+  const Rk& rk = e.k;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double x[10];
+#pragma unroll
+  for (int v = 0; v < 10; ++v) x[v] = io[10 * t + v];
+  const double c1 = reg_const(0.3, zt), c2 = reg_const(0.2, zt), c3 = reg_const(0.1, zt);
+  long long fb = 0;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int v = 0; v < 10; ++v) x[v] = bitsd(dbits(x[v]) ^ (fb & 1));
+    fb = 0;
+    if constexpr (FN == 0) {          // cons -> prim of one cell
+      double W[5];
+      fb ^= cons_to_prim(x, W, e);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fb ^= dbits(W[v]);
+    } else if constexpr (FN == 1) {   // one x/y slope work item (three cells) of one variable
+      const double d0 = sub(x[1], x[0], rk), d1 = sub(x[2], x[1], rk), d2 = sub(x[3], x[2], rk);
+      const double d3 = sub(x[4], x[3], rk);
+      const double t0 = mc_half_slope_d(d0, d1, rk), t1 = mc_half_slope_d(d1, d2, rk);
+      const double t2 = mc_half_slope_d(d2, d3, rk);
+      const double q[6] = {sub(x[1], t0, rk), add(x[1], t0, rk), sub(x[2], t1, rk), add(x[2], t1, rk),
+                           sub(x[3], t2, rk), add(x[3], t2, rk)};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) fb ^= dbits(q[v]);
+    } else if constexpr (FN == 2) {   // one HLLC face
+      double F[5];
+      hllc_flux(x, x + 5, e, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fb ^= dbits(F[v]);
+    } else if constexpr (FN == 3) {   // the 3-D flux-difference update of one variable
+      double r = fma(-c1, sub(x[1], x[2], rk), x[0]);
+      r = fma(-c2, sub(x[3], x[4], rk), r);
+      r = fma(-c3, sub(x[5], x[6], rk), r);
+      fb ^= dbits(r);
+    } else if constexpr (FN == 4) {   // the second-stage combine of one variable
+      fb ^= dbits(half_any(add(x[1], x[0], rk)));
+    } else if constexpr (FN == 5) {   // CFL epilogue of one cell: cons -> prim and 3-D signal speed
+      double W[5], ir;
+      cons_to_prim_ir(x, W, e, ir);
+      fb ^= dbits(signal_speed_ir(W, ir, e, c1, c2, c3, true));
+    } else if constexpr (FN == 6) {   // z march: the next z slope and face states of one variable
+      const double dn = sub(x[1], x[0], rk);
+      const double tz = mc_half_slope_d(x[2], dn, rk);
+      fb ^= dbits(sub(x[0], tz, rk)) ^ dbits(add(x[0], tz, rk)) ^ dbits(dn);
+    } else {                           // the two face states of a block-boundary face, one variable
+      const double d0 = sub(x[1], x[0], rk), d1 = sub(x[2], x[1], rk), d2 = sub(x[3], x[2], rk);
+      fb ^= dbits(add(x[1], mc_half_slope_d(d0, d1, rk), rk)) ^ dbits(sub(x[2], mc_half_slope_d(d1, d2, rk), rk));
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 10; ++v) io[10 * t + v] = bitsd(dbits(x[v]) ^ (fb & 1));
+}
+
 // Self-test of the refined reciprocal / square roots: out[6][n] =
 // rcp_nr, 1.0/x, rsqrt_nr, 1.0/sqrt(x), sqrt_nr, sqrt(x).
 __global__ void fastmath_selftest_kernel(const double* x, double* out, long long n) {
@@ -309,6 +375,21 @@ cudaError_t launch_bits_selftest(const double* x, const double* y, double* out, 
 
 cudaError_t launch_fastmath_selftest(const double* x, double* out, long long n, cudaStream_t s) {
   fastmath_selftest_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(x, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_count(int fn, int blocks, int threads, int iters, const Eos& e, double* io, cudaStream_t s) {
+  switch (fn) {
+    case 0: op_count_kernel<0><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 1: op_count_kernel<1><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 2: op_count_kernel<2><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 3: op_count_kernel<3><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 4: op_count_kernel<4><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 5: op_count_kernel<5><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 6: op_count_kernel<6><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    case 7: op_count_kernel<7><<<blocks, threads, 0, s>>>(iters, e, io); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

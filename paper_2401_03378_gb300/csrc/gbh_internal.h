@@ -163,5 +163,6 @@ long long check_take_amr();
 long long check_take_adjoint();
 long long check_selftest();
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, int lanes, int form, double* out, cudaStream_t s);
+cudaError_t launch_op_count(int fn, int blocks, int threads, int iters, const Eos& e, double* io, cudaStream_t s);
 
 }  // namespace gbh

@@ -434,6 +434,21 @@ def test_fp64_probe_runs(gb):
         gb.fp64_probe(152 * 4, 256, 1000, out, 32, 5)
 
 
+def test_op_count_probe_runs(gb):
+    """Every building block of the instruction-count probe runs and keeps its
+    chained inputs finite (the chain only flips the last mantissa bit)."""
+    from paper_2401_03378_gb300.probe import OP_COUNT, op_count, op_count_inputs
+    for fn in OP_COUNT:
+        io = op_count(fn, 4, 64, 16)
+        ref = op_count_inputs(fn, 4 * 64)
+        got = host(io)
+        assert np.all(np.isfinite(got))
+        rel = np.abs(got / ref.numpy() - 1)
+        assert np.max(rel) <= 4 * np.finfo(float).eps
+    with pytest.raises(Exception):
+        op_count(8, 4, 64, 16)
+
+
 def test_refined_reciprocal_and_roots_within_two_ulp(gb):
     """The kernels' reciprocal, 1/sqrt and sqrt (hardware seed + one
     third-order refinement) stay within 2 ulp of the IEEE results over the

@@ -59,6 +59,14 @@ __device__ __forceinline__ bool corrected_cell(const StageArgs& a, int b, int i,
          (j == N - 1 && on(FACE_YP)) || (DIM3 && k == 0 && on(FACE_ZM)) || (DIM3 && k == nz - 1 && on(FACE_ZP));
 }
 
+// Threads of a stage CTA: one per column of the band, except the 2 x 2
+// corner columns of an unsplit ring-2 tile (N (N + 8), 384 = 12 whole warps at
+// N = 16, against 400 = 12.5).
+template <int N, int E, int S>
+constexpr int stage_threads() {
+  return E == 2 && S == 1 ? N * (N + 4 * E) : (N + 2 * E) * (N + 2 * E) / S;
+}
+
 // One work item: block `b` of the list (or of the lattice), z-chunk `chunk`
 // and row band `band` of the plane tile.  The (N+2E)-wide plane tile is cut
 // into S bands of MY = (N+2E)/S rows; a CTA of M*MY threads updates one band
@@ -68,7 +76,7 @@ template <int N, bool DIM3, int E, int S>
 __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red) {
   constexpr int M = N + 2 * E;              // plane tile width (the interior when E = 0)
   constexpr int MY = M / S;                 // rows of one band
-  constexpr int NT = M * MY;
+  constexpr int NT = stage_threads<N, E, S>();   // threads: one per updated column
   constexpr int PX = M + 4, PY = MY + 4;    // band with 2-deep x/y rims
   constexpr int QXS = MY * (M + 2);         // x face states of a band, per variable and side
   constexpr int QYS = (MY + 2) * M;         // y face states
@@ -85,7 +93,31 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   const int band = S == 1 ? 0 : item % S;
   const int rest = S == 1 ? item : item / S;
   const int y0 = band * MY;                 // first tile row of the band
-  const int tx = tid % M, ty = tid / M;     // band position; cell (tx - E, y0 + ty - E)
+  // The next stage reads a ring stage's output only in its own box (ring
+  // width E - 2) and the 2-deep face slabs around it, so the 2 x 2 columns at
+  // the corners of the tile, outside that box in both x and y, are never read.
+  // The ring-2 stage on the whole tile (S = 1) has no thread for them (its
+  // corners are exactly those 2 x 2 squares): they are not updated, and the
+  // primitives of their cells, which the slopes of the neighbouring rim cells
+  // need, are loaded with the rims.  The other columns are numbered row by
+  // row: the rows above the interior (its columns only), the interior rows
+  // (all columns), the rows below.  (At ring 4 the same 16 corner columns of
+  // 576 would leave 560 threads, not a whole number of warps; that tile keeps
+  // one thread per column.)
+  int tx, ty;                               // band position; cell (tx - E, y0 + ty - E)
+  if constexpr (E == 2 && S == 1) {
+    if (tid < E * N) {
+      ty = tid / N; tx = E + tid % N;
+    } else if (tid < E * N + N * M) {
+      const int r = tid - E * N;
+      ty = E + r / M; tx = r % M;
+    } else {
+      const int r = tid - E * N - N * M;
+      ty = E + N + r / N; tx = E + r % N;
+    }
+  } else {
+    tx = tid % M; ty = tid / M;
+  }
   const int ci = tx - E, cj = y0 + ty - E;
   const int slot_idx = rest / a.nchunks;
   const int chunk = rest - slot_idx * a.nchunks;
@@ -184,16 +216,24 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 #pragma unroll
     for (int v = 0; v < 5; ++v) sW[GBH_IX((v * PY + ty + 2) * PX + tx + 2, 5 * PY * PX)] = W0[v];
     if constexpr (S == 1) {
-      // the whole tile: all four rims on every plane except the outer planes
-      // of a ring stage, which read none (their window lies 2 cells inside)
-      for (int r = tid; r < (outer ? 0 : 8 * M); r += NT) {
+      // the whole tile: all four rims (and at ring 2 the 16 cells of the
+      // corner columns, which have no thread) on every plane except the
+      // outer planes of a ring stage, which read none (their window lies 2
+      // cells inside)
+      constexpr int NC = E == 2 ? 16 : 0;
+      for (int r = tid; r < (outer ? 0 : 8 * M + NC); r += NT) {
         const int q = r / (2 * M), t = r - q * 2 * M;
         const int depth = t / M, pos = t - depth * M;
         int i, j;
         if (q == 0) { i = -1 - depth; j = pos; }
         else if (q == 1) { i = M + depth; j = pos; }
         else if (q == 2) { i = pos; j = -1 - depth; }
-        else { i = pos; j = M + depth; }
+        else if (q == 3) { i = pos; j = M + depth; }
+        else {
+          const int c = r - 8 * M, cx = c % (2 * E), cy = c / (2 * E);
+          i = cx < E ? cx : N + cx;
+          j = cy < E ? cy : N + cy;
+        }
         double W[5];
         load_prim<N>(a, e, b, i - E, j - E, k, W);
 #pragma unroll
@@ -425,8 +465,8 @@ constexpr int min_ctas() { return (E == 0 ? 2 : 1) * S; }
 // `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
 // grid makes the kernel persistent).  No CTA waits on another.
 template <int N, bool DIM3, int E, int S>
-__global__ void __launch_bounds__((N + 2 * E) * (N + 2 * E) / S, min_ctas<E, S>()) stage_kernel(const StageArgs a) {
-  constexpr int NT = (N + 2 * E) * (N + 2 * E) / S;
+__global__ void __launch_bounds__(stage_threads<N, E, S>(), min_ctas<E, S>()) stage_kernel(const StageArgs a) {
+  constexpr int NT = stage_threads<N, E, S>();
   extern __shared__ double smem[];
   __shared__ double s_red[E == 0 && NT > 32 ? NT / 32 : 1];
   const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
@@ -451,7 +491,7 @@ cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
   const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
   const int per = a.items_per_cta > 0 ? a.items_per_cta : 1;
   const unsigned grid = (unsigned)((nitems + per - 1) / per);
-  stage_kernel<N, D3, E, S><<<grid, (N + 2 * E) * (N + 2 * E) / S, smem_for<N, E, S>(), s>>>(a);
+  stage_kernel<N, D3, E, S><<<grid, stage_threads<N, E, S>(), smem_for<N, E, S>(), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,9 @@ def measure(lanes: int, iters: int = 20000, per_sm: int = 8, threads: int = 256,
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
-    ops = 8.0 * iters * blocks * (threads // 32) * lanes
+    # the active lanes: the first `lanes` of every warp, the last (partial) warp included
+    active = (threads // 32) * lanes + min(lanes, threads % 32)
+    ops = 8.0 * iters * blocks * active
     return best, ops / (best * 1e-3)
 
 
@@ -80,6 +82,8 @@ def main(argv=None):
     ap.add_argument("--forms", default="1", help="comma list of 0..4 (%s)" % FORMS)
     ap.add_argument("--iters", type=int, default=20000)
     ap.add_argument("--clock-mhz", type=float, default=2070.0, help="SM clock for the per-clock figure")
+    ap.add_argument("--threads", default="256", help="comma list of threads per CTA")
+    ap.add_argument("--per-sm", type=int, default=8, help="CTAs per SM in the grid")
     ap.add_argument("--count", action="store_true", help="launch the instruction-count probe instead")
     args = ap.parse_args(argv)
     sms = sm_count()
@@ -90,12 +94,13 @@ def main(argv=None):
             torch.cuda.synchronize()
             print(f"op_count fn={fn} ({name}): calls={blocks * threads * iters}")
         return
-    for form in [int(x) for x in args.forms.split(",")]:
-        for lanes in [int(x) for x in args.lanes.split(",")]:
-            ms, ops = measure(lanes, args.iters, form=form)
-            per_clk = ops / sms / (args.clock_mhz * 1e6)
-            print(f"form={form} ({FORMS[form]:28s}) lanes={lanes:2d} ms={ms:9.3f} "
-                  f"G ops/s(active lanes)={ops / 1e9:8.2f} lanes/clk/SM={per_clk:6.3f}")
+    for threads in [int(x) for x in args.threads.split(",")]:
+        for form in [int(x) for x in args.forms.split(",")]:
+            for lanes in [int(x) for x in args.lanes.split(",")]:
+                ms, ops = measure(lanes, args.iters, per_sm=args.per_sm, threads=threads, form=form)
+                per_clk = ops / sms / (args.clock_mhz * 1e6)
+                print(f"threads={threads:4d} per_sm={args.per_sm} form={form} ({FORMS[form]:28s}) lanes={lanes:2d} "
+                      f"ms={ms:9.3f} G ops/s(active lanes)={ops / 1e9:8.2f} lanes/clk/SM={per_clk:6.3f}")
 
 
 if __name__ == "__main__":

@@ -40,7 +40,8 @@
 
 extern "C" {
 struct OrcAmr2 {
-  int lo[3], hi[3];  /* fine region in coarse-block units, [lo, hi) per dimension */
+  int lo[3], hi[3];  /* bounding box of the fine region in coarse-block units, [lo, hi) per dimension */
+  const unsigned char* refined;  /* [coarse blocks]: 1 where the block is refined; NULL: the whole box */
 };
 struct OrcGrid {
   int ndim;          /* 2 or 3 */
@@ -428,37 +429,61 @@ ll step_telescoping(const OrcGrid& G, double* U, double dt, int nstages = 2) {
 //     the coarse flux is replaced by the mean of the 2^(d-1) fine fluxes
 //     through it, in every RK stage, weighted like the stage's L term.
 // Layout: coarse blocks 0..n0-1 (the complete coarse lattice; covered blocks
-// hold restricted data), then fine blocks n0..n0+n1-1 (lattice over the fine
-// region, x fastest).  The fine region is a box of whole coarse blocks at
-// least one block away from the domain boundary.
+// hold restricted data), then fine blocks n0..n0+n1-1 (lattice over the
+// bounding box of the fine region, x fastest).  The refined coarse blocks are
+// any set of whole blocks (a box, an L, separate boxes) at least one block
+// away from the domain boundary; the fine lattice's blocks whose parent is not
+// refined do not exist (their slots in the array are skipped).
 struct Amr2 {
   OrcGrid C, F;
   int lo[3], hi[3];
   ll n0, n1;
+  std::vector<unsigned char> refined;   /* [n0] */
 };
 
-Amr2 make_amr2(const OrcGrid& C, const int lo[3], const int hi[3]) {
+Amr2 make_amr2(const OrcGrid& C, const OrcAmr2& R) {
   Amr2 A;
   A.C = C;
   A.F = C;
   for (int d = 0; d < 3; ++d) {
-    A.lo[d] = d < C.ndim ? lo[d] : 0;
-    A.hi[d] = d < C.ndim ? hi[d] : 1;
+    A.lo[d] = d < C.ndim ? R.lo[d] : 0;
+    A.hi[d] = d < C.ndim ? R.hi[d] : 1;
     A.F.nb[d] = d < C.ndim ? 2 * (A.hi[d] - A.lo[d]) : 1;
     A.F.dx[d] = C.dx[d] * 0.5;
     A.F.periodic[d] = 0;
   }
   A.n0 = (ll)C.nb[0] * C.nb[1] * C.nb[2];
   A.n1 = (ll)A.F.nb[0] * A.F.nb[1] * A.F.nb[2];
+  A.refined.assign(A.n0, 0);
+  const Geo gc(C);
+  for (ll b = 0; b < A.n0; ++b) {
+    int c[3];
+    gc.coords(b, c);
+    bool in = true;
+    for (int d = 0; d < 3; ++d) in = in && c[d] >= A.lo[d] && c[d] < A.hi[d];
+    A.refined[b] = in && (!R.refined || R.refined[b]);
+  }
   return A;
 }
 
+/* a coarse block covered by the fine level */
 bool covered(const Amr2& A, const Geo& gc, ll b) {
-  int c[3];
-  gc.coords(b, c);
-  for (int d = 0; d < 3; ++d)
-    if (c[d] < A.lo[d] || c[d] >= A.hi[d]) return false;
-  return true;
+  (void)gc;
+  return A.refined[b] != 0;
+}
+
+/* fine lattice block f exists: its parent coarse block is refined */
+bool fine_exists(const Amr2& A, const Geo& gc, const Geo& gf, ll f) {
+  int c[3], p[3];
+  gf.coords(f, c);
+  for (int d = 0; d < 3; ++d) p[d] = d < gc.ndim ? A.lo[d] + c[d] / 2 : 0;
+  return A.refined[p[0] + (ll)gc.nb[0] * (p[1] + (ll)gc.nb[1] * p[2])] != 0;
+}
+
+/* the fine block at lattice offset o from fine block f, or -1 where there is none */
+ll fine_neighbour(const Amr2& A, const Geo& gc, const Geo& gf, ll f, const int o[3]) {
+  const ll nb = gf.neighbour(f, o);
+  return nb >= 0 && fine_exists(A, gc, gf, nb) ? nb : -1;
 }
 
 int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -524,6 +549,7 @@ void amr2_fill_fine(const Amr2& A, double* U) {
   const int nd = A.C.ndim;
 #pragma omp parallel for schedule(dynamic, 1)
   for (ll f = 0; f < A.n1; ++f) {
+    if (!fine_exists(A, gc, gf, f)) continue;
     for (int k = 0; k < gf.p[2]; ++k)
       for (int j = 0; j < gf.p[1]; ++j)
         for (int i = 0; i < gf.p[0]; ++i) {
@@ -535,7 +561,7 @@ void amr2_fill_fine(const Amr2& A, double* U) {
             if (o[d]) interior = false;
           }
           if (interior) continue;
-          const ll nb = gf.neighbour(f, o);
+          const ll nb = fine_neighbour(A, gc, gf, f, o);
           if (nb >= 0) {
             for (int v = 0; v < 5; ++v)
               U[gf.at(A.n0 + f, v, k, j, i)] =
@@ -609,7 +635,7 @@ void record_cf_faces(const Amr2& A, const Geo& gc, const Geo& gf, ll t, const Wo
       if (t < A.n0) {
         const ll nb = gc.neighbour(t, o);
         if (nb >= 0 && covered(A, gc, nb)) record_face(gc, w, d, side, R.face[t * 6 + 2 * d + side]);
-      } else if (gf.neighbour(t - A.n0, o) < 0) {
+      } else if (fine_neighbour(A, gc, gf, t - A.n0, o) < 0) {
         record_face(gf, w, d, side, R.face[t * 6 + 2 * d + side]);
       }
     }
@@ -631,6 +657,7 @@ ll amr2_stage(const Amr2& A, const double* Uin, const double* Un, double* Uout, 
         if (covered(A, gc, t)) continue;
         hits += stage_block(A.C, gc, t, Uin, Un, Uout, dt, a, bcoef, w);
       } else {
+        if (!fine_exists(A, gc, gf, t - A.n0)) continue;
         hits += stage_block(A.F, gf, t, Uin, Un, Uout, dt, a, bcoef, w);
       }
       record_cf_faces(A, gc, gf, t, w, R);
@@ -656,7 +683,7 @@ ll amr2_level_telescoping(const Amr2& A, const Rk& r, int lev, std::vector<doubl
     w.resize(gc.cells);
 #pragma omp for schedule(dynamic, 1)
     for (ll t = b0; t < b1; ++t) {
-      if (!lev && covered(A, gc, t)) continue;
+      if (lev ? !fine_exists(A, gc, gf, t - A.n0) : covered(A, gc, t)) continue;
       for (int st = 0; st < r.S; ++st) {
         hits += stage_block(G, geo, t, X[st].data(), st ? X[0].data() : nullptr, X[st + 1].data(), dt, r.a[st],
                             r.b[st], w, 2 * (r.S - 1 - st));
@@ -695,8 +722,11 @@ void amr2_reflux(const Amr2& A, double* U, double dt, double coef, const FluxReg
             int T[3];                                 /* global coarse coordinates of the face cell's tangentials */
             T[t1] = c[t1] * gc.n[t1] + b1;
             T[t2] = c[t2] * gc.n[t2] + b2;
-            /* fine face position along d: first / last fine cell of the fine region */
-            const int fd = side ? 0 : gf.nb[d] * gf.n[d] - 1;
+            /* fine cell next to the face along d: the face lies at coarse
+             * cell coordinate X (between cells X - 1 and X); the fine region
+             * begins there (side 1) or ends there (side 0) */
+            const int X = (c[d] + side) * gc.n[d];
+            const int fd = 2 * (X - A.lo[d] * gc.n[d]) - (side ? 0 : 1);
             double fsum[5] = {0, 0, 0, 0, 0};
             for (int q2 = 0; q2 < (nd == 3 ? 2 : 1); ++q2)
               for (int q1 = 0; q1 < 2; ++q1) {
@@ -737,8 +767,9 @@ double amr2_compute_dt(const Amr2& A, const double* U) {
     const OrcGrid& G = lev ? A.F : A.C;
     const double idx = 1.0 / G.dx[0], idy = 1.0 / G.dx[1], idz = 1.0 / G.dx[2];
     const ll b0 = lev ? A.n0 : 0, b1 = lev ? A.n0 + A.n1 : A.n0;
+    const Geo gf(A.F);
     for (ll b = b0; b < b1; ++b) {
-      if (!lev && covered(A, gc, b)) continue;
+      if (lev ? !fine_exists(A, gc, gf, b - A.n0) : covered(A, gc, b)) continue;
       for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
         for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
           for (int i = gc.g[0]; i < gc.g[0] + gc.n[0]; ++i) {
@@ -778,8 +809,9 @@ ll amr2_step(const Amr2& A, double* U, double dt, int nstages = 2) {
     amr2_reflux(A, Y.data(), dt, r.b[st], R);
     std::swap(X, Y);
   }
+  const Geo gf(A.F);
   for (ll b = 0; b < A.n0 + A.n1; ++b) {
-    if (b < A.n0 && covered(A, gc, b)) continue;
+    if (b < A.n0 ? covered(A, gc, b) : !fine_exists(A, gc, gf, b - A.n0)) continue;
     for (int v = 0; v < 5; ++v)
       for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
         for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
@@ -814,8 +846,9 @@ ll amr2_step_telescoping(const Amr2& A, double* U, double dt, int nstages = 2) {
   for (int lev = 1; lev >= 0; --lev) hits += amr2_level_telescoping(A, r, lev, X, dt, R);
   double* out = X[r.S].data();
   for (int st = 0; st < r.S; ++st) amr2_reflux(A, out, dt, rk_weight(r, st), R[st]);
+  const Geo gf(A.F);
   for (ll b = 0; b < nblk; ++b) {
-    if (b < A.n0 && covered(A, gc, b)) continue;
+    if (b < A.n0 ? covered(A, gc, b) : !fine_exists(A, gc, gf, b - A.n0)) continue;
     for (int v = 0; v < 5; ++v)
       for (int k = gc.g[2]; k < gc.g[2] + gc.n[2]; ++k)
         for (int j = gc.g[1]; j < gc.g[1] + gc.n[1]; ++j)
@@ -1194,23 +1227,23 @@ long long orc_run(const OrcGrid* G, double* U, int nsteps, double* dt_hist, int 
 
 /* ---- two-level composite grid (coarse blocks first, then fine blocks) ---- */
 
-void orc2_restrict(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_restrict(make_amr2(*G, R->lo, R->hi), U); }
+void orc2_restrict(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_restrict(make_amr2(*G, *R), U); }
 
-void orc2_fill(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_prepare(make_amr2(*G, R->lo, R->hi), U); }
+void orc2_fill(const OrcGrid* G, const OrcAmr2* R, double* U) { amr2_prepare(make_amr2(*G, *R), U); }
 
 double orc2_compute_dt(const OrcGrid* G, const OrcAmr2* R, const double* U) {
-  return amr2_compute_dt(make_amr2(*G, R->lo, R->hi), U);
+  return amr2_compute_dt(make_amr2(*G, *R), U);
 }
 
 long long orc2_step(const OrcGrid* G, const OrcAmr2* R, double* U, double dt) {
-  return amr2_step(make_amr2(*G, R->lo, R->hi), U, dt);
+  return amr2_step(make_amr2(*G, *R), U, dt);
 }
 
 /* One stage without flux correction (reflux = 0) or with it (reflux = 1):
  * prepares Uin (restriction + guard fills) and writes the leaf blocks of Uout. */
 long long orc2_stage(const OrcGrid* G, const OrcAmr2* R, double* Uin, const double* Un, double* Uout, double dt,
                      double a, double b, int reflux) {
-  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  const Amr2 A = make_amr2(*G, *R);
   FluxReg reg;
   amr2_prepare(A, Uin);
   const ll hits = amr2_stage(A, Uin, Un, Uout, dt, a, b, reg);
@@ -1221,14 +1254,14 @@ long long orc2_stage(const OrcGrid* G, const OrcAmr2* R, double* Uin, const doub
 /* One level-by-level telescoping step; -1 if the grid has fewer than 4 guard cells. */
 long long orc2_step_telescoping(const OrcGrid* G, const OrcAmr2* R, double* U, double dt) {
   if (G->ng < 4) return -1;
-  return amr2_step_telescoping(make_amr2(*G, R->lo, R->hi), U, dt);
+  return amr2_step_telescoping(make_amr2(*G, *R), U, dt);
 }
 
 /* One step with nstages stages: all-levels non-telescoping, or (telescoping
  * != 0) level-by-level telescoping; -1 if invalid. */
 long long orc2_step_rk(const OrcGrid* G, const OrcAmr2* R, double* U, double dt, int nstages, int telescoping) {
   if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
-  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  const Amr2 A = make_amr2(*G, *R);
   return telescoping ? amr2_step_telescoping(A, U, dt, nstages) : amr2_step(A, U, dt, nstages);
 }
 
@@ -1237,7 +1270,7 @@ long long orc2_step_rk(const OrcGrid* G, const OrcAmr2* R, double* U, double dt,
 long long orc2_run(const OrcGrid* G, const OrcAmr2* R, double* U, int nsteps, double* dt_hist, int telescoping,
                    int nstages) {
   if ((nstages != 2 && nstages != 3) || (telescoping && G->ng < 2 * nstages)) return -1;
-  const Amr2 A = make_amr2(*G, R->lo, R->hi);
+  const Amr2 A = make_amr2(*G, *R);
   long long hits = 0;
   amr2_restrict(A, U);
   for (int s = 0; s < nsteps; ++s) {

@@ -18,7 +18,7 @@ _lib = None
 
 
 class OrcAmr2(C.Structure):
-    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3)]
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3), ("refined", C.c_void_p)]
 
 
 class OrcGrid(C.Structure):
@@ -219,7 +219,10 @@ class Oracle:
 
 
 class Oracle2:
-    """The oracle on a two-level composite grid (workloads.TwoLevel)."""
+    """The oracle on a two-level composite grid (workloads.TwoLevel).  Its
+    arrays hold the coarse lattice, then the fine lattice over the bounding box
+    of the refined blocks, including the slots of fine blocks that do not exist
+    (their parent is not refined), which it neither reads nor writes."""
 
     def __init__(self, tl, gamma=1.4, cfl=0.8, small_rho=1e-12, small_p=1e-14):
         self.tl = tl
@@ -228,6 +231,9 @@ class Oracle2:
         for d in range(3):
             self.r.lo[d] = tl.lo[d]
             self.r.hi[d] = tl.hi[d]
+        # the refined coarse blocks (all of the box when the grid names none)
+        self._mask = np.ascontiguousarray(tl.refined_mask(), dtype=np.uint8)
+        self.r.refined = self._mask.ctypes.data
         self.L = lib()
 
     def _chk(self, U):

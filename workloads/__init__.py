@@ -22,7 +22,7 @@ valid states for brute-force checks.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Tuple
+from typing import Optional, Tuple
 
 import numpy as np
 
@@ -272,18 +272,30 @@ def poison_guards(U: np.ndarray, lat: Lattice, value: float = np.nan, corners_on
 
 @dataclass(frozen=True)
 class TwoLevel:
-    """A complete coarse lattice plus a fine lattice at twice the resolution over
-    the box of coarse blocks [lo, hi) (at least one block from the domain edge).
-    Composite arrays hold the coarse blocks first, then the fine blocks."""
+    """A complete coarse lattice plus a fine level at twice the resolution over
+    a set of whole coarse blocks, each at least one block from the domain edge:
+    the box [lo, hi) of coarse blocks, or, when `refined` lists coarse block
+    coordinates, those blocks (an L shape, separate boxes, ...), of which
+    [lo, hi) is then the bounding box.
+
+    Composite arrays hold the coarse blocks first, then the fine lattice over
+    [lo, hi) block by block; fine blocks whose parent is not refined have slots
+    there too (the oracle's layout), and `gpu_blocks` lists the blocks of the
+    library's layout, which has no such slots."""
 
     coarse: Lattice
     lo: Tuple[int, int, int]
     hi: Tuple[int, int, int]
+    refined: Optional[Tuple[Tuple[int, int, int], ...]] = None
 
     def __post_init__(self):
         for d in range(self.coarse.ndim):
             if not (1 <= self.lo[d] < self.hi[d] <= self.coarse.nb[d] - 1):
-                raise ValueError("the fine region must be a box of coarse blocks away from the domain edge")
+                raise ValueError("the fine region must be made of coarse blocks away from the domain edge")
+        if self.refined is not None:
+            for c in self.refined:
+                if not all(self.lo[d] <= c[d] < self.hi[d] for d in range(3)):
+                    raise ValueError("refined blocks must lie in [lo, hi)")
 
     @property
     def fine(self) -> Lattice:
@@ -313,20 +325,49 @@ class TwoLevel:
 
     def covered(self, b: int) -> bool:
         c = self.coarse.block_coords(b)
-        return all(self.lo[d] <= c[d] < self.hi[d] for d in range(3))
+        if not all(self.lo[d] <= c[d] < self.hi[d] for d in range(3)):
+            return False
+        return self.refined is None or tuple(c) in self.refined
+
+    def refined_mask(self) -> np.ndarray:
+        """uint8 [n0]: 1 for every refined (covered) coarse block."""
+        return np.array([1 if self.covered(b) else 0 for b in range(self.n0)], dtype=np.uint8)
+
+    def fine_exists(self, f: int) -> bool:
+        """Fine lattice block f exists: its parent coarse block is refined."""
+        c = self.fine.block_coords(f)
+        nd = self.coarse.ndim
+        p = tuple(self.lo[d] + c[d] // 2 if d < nd else 0 for d in range(3))
+        return self.covered(p[0] + self.coarse.nb[0] * (p[1] + self.coarse.nb[1] * p[2]))
+
+    @property
+    def gpu_blocks(self) -> np.ndarray:
+        """Composite-array indices of the library's blocks: every coarse block,
+        then the fine blocks that exist, in fine-lattice order."""
+        fine = [self.n0 + f for f in range(self.n1) if self.fine_exists(f)]
+        return np.array(list(range(self.n0)) + fine, dtype=np.int64)
 
     @property
     def leaf_cells(self) -> int:
         c = self.coarse
         per = c.n[0] * c.n[1] * c.n[2]
         ncov = sum(1 for b in range(self.n0) if self.covered(b))
-        return (self.n0 - ncov + self.n1) * per
+        nfine = sum(1 for f in range(self.n1) if self.fine_exists(f))
+        return (self.n0 - ncov + nfine) * per
 
 
 def two_level(coarse: Lattice, lo, hi) -> TwoLevel:
     lo = tuple(lo) + (0,) * (3 - len(lo))
     hi = tuple(hi) + (1,) * (3 - len(hi))
     return TwoLevel(coarse, lo, hi)
+
+
+def two_level_blocks(coarse: Lattice, blocks) -> TwoLevel:
+    """Two-level grid refining the listed coarse blocks (coordinates (i, j[, k]))."""
+    cs = sorted({tuple(b) + (0,) * (3 - len(b)) for b in blocks})
+    lo = tuple(min(c[d] for c in cs) for d in range(3))
+    hi = tuple(max(c[d] for c in cs) + 1 for d in range(3))
+    return TwoLevel(coarse, lo, hi, tuple(cs))
 
 
 def two_level_state(tl: TwoLevel, prim_fn, gamma: float = 1.4):

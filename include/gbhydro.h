@@ -105,11 +105,11 @@ int gbh_create(const gbh_params *params, gbh_ctx **out);
  * hydro_compute_dt uses leaf cells only; hydro_fill_guardcells restricts and
  * then fills every guard cell (prolongation where the region is coarser).
  * hydro_stage / hydro_stage_guarded return GBH_ERR_UNSUPPORTED on such a
- * context.  Supported: exactly two levels, cubic (3-D) or square (2-D) blocks
- * of even size, fine blocks not on the domain boundary, and no coarse leaf
- * block bordering the refined region through more than one face (a box
- * qualifies; an L-shaped region, or two boxes one coarse block apart, give
- * GBH_ERR_UNSUPPORTED). */
+ * context.  The refined coarse blocks may form any region (a box, an L, a
+ * notch, separate boxes): a coarse cell next to several refined faces of its
+ * block takes every face's correction, in the face order x-, x+, y-, y+, z-,
+ * z+.  Supported: exactly two levels, cubic (3-D) or square (2-D) blocks of
+ * even size, fine blocks not on the domain boundary. */
 typedef struct gbh_refinement {
   const int32_t *parent;
   const int32_t *children;

@@ -53,6 +53,7 @@ struct gbh_ctx {
   double* d_flux_reg3 = nullptr;
   size_t flux_reg_doubles = 0;
   gbh::RefluxEntry* d_reflux = nullptr;
+  int* d_reflux_of = nullptr;       // [nblocks][6]: flux-correction entry of a coarse leaf face, or -1
   int2* d_cf_faces = nullptr;
   gbh::AmrArgs amr{};
   // batched ensembles (gbh_create_batched): per-block problem id, per-problem CFL accumulators
@@ -673,17 +674,13 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
         cf_faces.push_back(make_int2((int)b, f));
       }
   }
+  // one entry per coarse leaf face with refined blocks beyond it; a block can
+  // border the refined region through several faces (an L, a notch), and
+  // reflux_of names each face's entry so that a cell next to several of them
+  // takes all their corrections from one thread
+  std::vector<int> reflux_of(6 * (size_t)NB, -1);
   for (long long b = 0; b < NB; ++b) {
     if (par[4 * b] >= 0 || chl[8 * b] >= 0) continue;
-    // reflux_kernel corrects each cell next to a coarse-fine face from one
-    // thread per face cell: a block bordering the fine region through two faces
-    // would have its edge cells corrected by two threads at once
-    int cf = 0;
-    for (int f = 0; f < 2 * nd; ++f) cf += face[6 * b + f] >= 0 && chl[8 * face[6 * b + f]] >= 0;
-    if (cf > 1)
-      return set_err(nullptr, GBH_ERR_UNSUPPORTED,
-                     "coarse block %lld borders the refined region through %d faces; the flux correction "
-                     "supports one (refine a box, or boxes at least two coarse blocks apart)", b, cf);
     for (int f = 0; f < 2 * nd; ++f) {
       const int nb = face[6 * b + f];
       if (nb < 0 || chl[8 * nb] < 0) continue;
@@ -703,6 +700,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
             return set_err(nullptr, GBH_ERR_INVAL, "fine block %d facing coarse block %lld is not marked GBH_NBR_COARSER", ch, b);
           en.fine_slot[q1 + 2 * q2] = fs;
         }
+      reflux_of[6 * b + f] = (int)refl.size();
       refl.push_back(en);
     }
   }
@@ -727,6 +725,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   c->flux_reg_doubles = fstride * (size_t)(nslots ? nslots : 1);
   up((void**)&c->d_flux_reg, nullptr, sizeof(double) * c->flux_reg_doubles);
   up((void**)&c->d_reflux, refl.empty() ? nullptr : refl.data(), sizeof(gbh::RefluxEntry) * refl.size());
+  up((void**)&c->d_reflux_of, reflux_of.data(), sizeof(int) * reflux_of.size());
   up((void**)&c->d_cf_faces, cf_faces.empty() ? nullptr : cf_faces.data(), sizeof(int2) * cf_faces.size());
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? GBH_ERR_NOMEM : GBH_ERR_CUDA;
@@ -744,6 +743,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.fine = c->d_fine;
   A.nfine = (int)fine.size();
   A.reflux = c->d_reflux;
+  A.reflux_of = c->d_reflux_of;
   A.nreflux = (int)refl.size();
   A.cf_faces = c->d_cf_faces;
   A.ncf_faces = (int)cf_faces.size();
@@ -1098,6 +1098,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_flux_reg3);
   cudaFree(c->d_scratch2);
   cudaFree(c->d_reflux);
+  cudaFree(c->d_reflux_of);
   cudaFree(c->d_cf_faces);
   cudaFree(c->d_problem);
   cudaFree(c->d_adj_lamW);

@@ -211,11 +211,14 @@ __global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
 }
 
 // Flux correction on the coarse side of the fine-region boundary.  One
-// thread per (interface face, face cell); each corrected cell has a single
-// entry (gbh_create_refined refuses a coarse block bordering the refined
-// region through two faces).  With smax_acc (the last correction of a step),
-// the thread also forms the corrected cell's CFL signal-speed sum, which the
-// stage kernel's epilogue left out, and adds it to the step's max.
+// thread per (interface face, face cell).  A coarse cell next to several
+// corrected faces of its block (a block bordering the refined region through
+// two or three faces) is handled by the thread of the lowest of those faces,
+// which adds every face's correction in the order x-, x+, y-, y+, z-, z+ (one
+// writer per cell); the other threads leave it.  With smax_acc (the last
+// correction of a step), the thread then forms the corrected cell's CFL
+// signal-speed sum, which the stage kernel's epilogue left out, and adds it
+// to the step's max.
 __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrArgs a, const double* dt_dev,
                                                           double dt_val, double coef, unsigned long long* smax_acc) {
   const Layout& L = a.lay;
@@ -228,41 +231,60 @@ __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrAr
   const long long per = (long long)N * n2;
   const long long total = per * a.nreflux;
   const long long sstride = 5LL * N * n2;
+  const double nfine = L.ndim == 3 ? 0.25 : 0.5;
+  const int nfaces = 2 * L.ndim;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const RefluxEntry en = a.reflux[t / per];
+    const int* of = a.reflux_of + 6LL * en.block;
+    // the coarse cell next to this entry's face at face cell (t1, t2)
+    const int r = (int)(t % per);
+    int x[3];
+    {
+      const int d = en.face >> 1, side = en.face & 1;
+      const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+      x[d] = side ? N - 1 : 0;
+      x[t1d] = r % N;
+      x[t2d] = L.ndim == 3 ? r / N : 0;
+    }
+    auto touches = [&](int f) {   // the cell lies next to face f of the block and f is corrected
+      const int d = f >> 1;
+      return __ldg(of + f) >= 0 && x[d] == ((f & 1) ? N - 1 : 0);
+    };
+    int owner = -1;
+    for (int f = 0; f < nfaces && owner < 0; ++f)
+      if (touches(f)) owner = f;
+    if (owner != en.face) continue;
     // the time step of the block's problem (one entry unless batched)
     const double dt = dt_dev ? dt_dev[a.problem ? __ldg(a.problem + en.block) : 0] : dt_val;
-    const int r = (int)(t % per);
-    const int t1 = r % N, t2 = r / N;
-    const int d = en.face >> 1, side = en.face & 1;
-    // coarse cell adjacent to the face
-    int x[3];
-    const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
-    x[d] = side ? (d == 0 ? L.nx : d == 1 ? L.ny : L.nz) - 1 : 0;
-    x[t1d] = t1;
-    x[t2d] = L.ndim == 3 ? t2 : 0;
-    const int q1 = t1 / half, q2 = L.ndim == 3 ? t2 / half : 0;
-    const int fs = en.fine_slot[q1 + 2 * q2];
-    const int f1 = 2 * (t1 % half), f2 = L.ndim == 3 ? 2 * (t2 % half) : 0;
-    const double* Fc = a.flux_reg + (long long)en.coarse_slot * sstride;
-    const double* Ff = a.flux_reg + (long long)fs * sstride;
-    const double idx = __ldg(a.inv_dx + 3 * en.block + d);
-    const double nfine = L.ndim == 3 ? 0.25 : 0.5;
     double Uc[5];
-    for (int v = 0; v < 5; ++v) {
-      double fsum = 0.0;
-      for (int b2 = 0; b2 < (L.ndim == 3 ? 2 : 1); ++b2)
-        for (int b1 = 0; b1 < 2; ++b1)
-          fsum = __dadd_rn(fsum, Ff[GBH_IX((long long)fs * sstride + ((long long)v * n2 + f2 + b2) * N + f1 + b1,
-                                           a.flux_reg_len) - (long long)fs * sstride]);
-      const double fmean = __dmul_rn(fsum, nfine);
-      const double fc = Fc[GBH_IX((long long)en.coarse_slot * sstride + ((long long)v * n2 + (L.ndim == 3 ? t2 : 0)) * N + t1,
-                                  a.flux_reg_len) - (long long)en.coarse_slot * sstride];
-      const double corr = side ? __dsub_rn(fc, fmean) : __dsub_rn(fmean, fc);
-      const long long o = at(L, en.block, v, x[0], x[1], x[2]);
-      U[o] = Uc[v] = __dadd_rn(U[o], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
+    for (int v = 0; v < 5; ++v) Uc[v] = U[at(L, en.block, v, x[0], x[1], x[2])];
+    for (int f = 0; f < nfaces; ++f) {
+      if (!touches(f)) continue;
+      const RefluxEntry& eg = a.reflux[__ldg(of + f)];
+      const int d = f >> 1, side = f & 1;
+      const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+      const int t1 = x[t1d], t2 = L.ndim == 3 ? x[t2d] : 0;
+      const int q1 = t1 / half, q2 = L.ndim == 3 ? t2 / half : 0;
+      const int fs = eg.fine_slot[q1 + 2 * q2];
+      const int f1 = 2 * (t1 % half), f2 = L.ndim == 3 ? 2 * (t2 % half) : 0;
+      const double* Fc = a.flux_reg + (long long)eg.coarse_slot * sstride;
+      const double* Ff = a.flux_reg + (long long)fs * sstride;
+      const double idx = __ldg(a.inv_dx + 3 * en.block + d);
+      for (int v = 0; v < 5; ++v) {
+        double fsum = 0.0;
+        for (int b2 = 0; b2 < (L.ndim == 3 ? 2 : 1); ++b2)
+          for (int b1 = 0; b1 < 2; ++b1)
+            fsum = __dadd_rn(fsum, Ff[GBH_IX((long long)fs * sstride + ((long long)v * n2 + f2 + b2) * N + f1 + b1,
+                                             a.flux_reg_len) - (long long)fs * sstride]);
+        const double fmean = __dmul_rn(fsum, nfine);
+        const double fc = Fc[GBH_IX((long long)eg.coarse_slot * sstride + ((long long)v * n2 + t2) * N + t1,
+                                    a.flux_reg_len) - (long long)eg.coarse_slot * sstride];
+        const double corr = side ? __dsub_rn(fc, fmean) : __dsub_rn(fmean, fc);
+        Uc[v] = __dadd_rn(Uc[v], __dmul_rn(__dmul_rn(__dmul_rn(coef, dt), corr), idx));
+      }
     }
+    for (int v = 0; v < 5; ++v) U[at(L, en.block, v, x[0], x[1], x[2])] = Uc[v];
     if (smax_acc) {
       double W[5], ir;
       cons_to_prim_ir(Uc, W, e, ir);

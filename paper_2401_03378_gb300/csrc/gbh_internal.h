@@ -85,6 +85,7 @@ struct AmrArgs {
   const int2* cf_faces;  // (fine block, face) pairs whose face neighbour is on the coarser level
   int ncf_faces;
   const RefluxEntry* reflux;
+  const int* reflux_of;  // [nblocks][6]: entry of a coarse block's face in reflux, or -1
   int nreflux;
   double* flux_reg;
   long long flux_reg_len;  // doubles in flux_reg (checked build)

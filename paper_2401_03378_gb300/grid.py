@@ -48,10 +48,15 @@ def uniform_widths(nblocks: int, dx) -> np.ndarray:
     return w
 
 
-def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
+def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0, refined=None):
     """Tables of a two-level composite grid: the complete coarse lattice nb0
-    (blocks 0..n0-1) plus a fine lattice at half the cell width over the coarse
-    blocks [lo, hi) (blocks n0.., lexicographic over the fine lattice).
+    (blocks 0..n0-1) plus a fine level at half the cell width over refined
+    coarse blocks: every block of [lo, hi), or, if `refined` lists coarse block
+    coordinates, those blocks ([lo, hi) is then their bounding box).  The fine
+    blocks (n0..) are the children of the refined blocks, numbered in the order
+    of the fine lattice over [lo, hi) (x fastest), the children of blocks that
+    are not refined left out.  A fine face or edge with no fine block beyond it
+    faces the coarser level (GBH_NBR_COARSER).
 
     Returns (nbr, dx, parent, children) in the layout gbh_create_refined takes.
     """
@@ -62,10 +67,24 @@ def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
     n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
     nb1 = tuple(2 * (hi[d] - lo[d]) if d < nd else 1 for d in range(3))
     n0 = nb0[0] * nb0[1] * nb0[2]
-    n1 = nb1[0] * nb1[1] * nb1[2]
+    nlat = nb1[0] * nb1[1] * nb1[2]
+    ref = None if refined is None else {tuple(int(x) for x in c) + (0,) * (3 - len(c)) for c in refined}
+
+    def fine_coords(f):
+        return (f % nb1[0], (f // nb1[0]) % nb1[1], f // (nb1[0] * nb1[1]))
+
+    def parent_coords(f):
+        fc = fine_coords(f)
+        return tuple(lo[d] + fc[d] // 2 if d < nd else 0 for d in range(3))
+
+    exists = np.array([ref is None or parent_coords(f) in ref for f in range(nlat)], dtype=bool)
+    rank = np.full(nlat, -1, dtype=np.int64)
+    rank[exists] = np.arange(int(exists.sum()))
+    n1 = int(exists.sum())
     cnbr = neighbour_table(nd, nb0, periodic)
-    fnbr = neighbour_table(nd, nb1, (False, False, False)).astype(np.int64)
-    fnbr = np.where(fnbr >= 0, fnbr + n0, GBH_NBR_COARSER).astype(np.int32)
+    lat = neighbour_table(nd, nb1, (False, False, False)).astype(np.int64)[exists]
+    safe = np.where(lat >= 0, lat, 0)
+    fnbr = np.where((lat >= 0) & exists[safe], n0 + rank[safe], GBH_NBR_COARSER).astype(np.int32)
     nbr = np.concatenate([cnbr, fnbr], axis=0)
     dx = np.empty((n0 + n1, 3))
     dx[:n0] = np.asarray(dx0, dtype=np.float64)
@@ -73,22 +92,22 @@ def two_level_tables(ndim: int, nb0, n, lo, hi, periodic, dx0):
     parent = np.zeros((n0 + n1, 4), dtype=np.int32)
     parent[:n0, 0] = -1
     children = np.full((n0 + n1, 8), -1, dtype=np.int32)
-    for f in range(n1):
-        fc = (f % nb1[0], (f // nb1[0]) % nb1[1], f // (nb1[0] * nb1[1]))
-        pc = tuple(lo[d] + fc[d] // 2 if d < nd else 0 for d in range(3))
+    for f in np.flatnonzero(exists):
+        fc = fine_coords(f)
+        pc = parent_coords(f)
         pid = pc[0] + nb0[0] * (pc[1] + nb0[1] * pc[2])
         off = tuple((fc[d] % 2) * (n[d] // 2) if d < nd else 0 for d in range(3))
-        parent[n0 + f] = (pid, *off)
+        parent[n0 + rank[f]] = (pid, *off)
         oct_ = sum((fc[d] % 2) << d for d in range(nd))
-        children[pid, oct_] = n0 + f
+        children[pid, oct_] = n0 + rank[f]
     return nbr, dx, parent, children
 
 
 def batched_two_level_tables(grids):
     """Tables of independent two-level composite grids in one state array.
 
-    grids: sequence of (ndim, nb0, n, lo, hi, periodic, dx0), the arguments of
-    two_level_tables (same block shape).  The blocks of grid i (its coarse
+    grids: sequence of (ndim, nb0, n, lo, hi, periodic, dx0[, refined]), the
+    arguments of two_level_tables (same block shape).  The blocks of grid i (its coarse
     blocks, then its fine blocks) follow those of grid i-1.  Returns
     (nbr, dx, parent, children, problem) for gbh_create_refined_batched.
     """

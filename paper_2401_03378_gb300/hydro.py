@@ -95,11 +95,14 @@ class Hydro:
     @classmethod
     def from_two_level(cls, tl, **kw):
         """Two-level composite grid: any object with `coarse` (a lattice), `lo`, `hi`
-        (the fine region in coarse blocks), e.g. workloads.TwoLevel."""
+        (the fine region in coarse blocks, or the bounding box of `refined`, an
+        optional list of refined coarse block coordinates), e.g. workloads.TwoLevel.
+        The state holds the coarse blocks, then the children of the refined
+        blocks in fine-lattice order over [lo, hi)."""
         from .grid import two_level_tables
         c = tl.coarse
         nbr, dx, parent, children = two_level_tables(
-            c.ndim, c.nb, c.n, tl.lo, tl.hi, tuple(b == "periodic" for b in c.bc), c.dx)
+            c.ndim, c.nb, c.n, tl.lo, tl.hi, tuple(b == "periodic" for b in c.bc), c.dx, getattr(tl, "refined", None))
         return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children, **kw)
 
     @classmethod
@@ -113,7 +116,7 @@ class Hydro:
         c = tls[0].coarse
         nbr, dx, parent, children, problem = batched_two_level_tables(
             [(t.coarse.ndim, t.coarse.nb, t.coarse.n, t.lo, t.hi,
-              tuple(b == "periodic" for b in t.coarse.bc), t.coarse.dx) for t in tls])
+              tuple(b == "periodic" for b in t.coarse.bc), t.coarse.dx, getattr(t, "refined", None)) for t in tls])
         return cls(c.ndim, c.n, c.ng, nbr=nbr, dx=dx, parent=parent, children=children,
                    problem=problem, nproblems=len(tls), **kw)
 

@@ -297,18 +297,14 @@ def refined_tables(ndim, nb0, n, refined, dx0):
     return nbr, dx, parent, children
 
 
-def test_create_refined_rejects_a_coarse_block_on_two_refined_faces_without_gpu(lib):
-    """The flux correction runs one thread per coarse face cell, so a coarse
-    block next to the refined region through two faces (the inner corner of an
-    L-shaped region) is refused before anything touches the GPU; a box is not."""
+def test_create_refined_takes_any_region_without_gpu(lib):
+    """The tables of any set of refined coarse blocks (a box, an L whose inner
+    coarse block borders the fine region through two faces, a notch with three,
+    two boxes one coarse block apart) built by two_level_tables equal this
+    test's own construction, and they pass the context's table checks: without
+    a GPU the context allocation then fails, not the tables."""
     from paper_2401_03378_gb300 import _abi
     from paper_2401_03378_gb300.grid import two_level_tables
-    dx0 = (1 / 32, 1 / 32, 1.0)
-    box = [(x, y) for y in (1, 2) for x in (1, 2)]
-    mine = refined_tables(2, (4, 4), (8, 8), box, dx0)
-    ref = two_level_tables(2, (4, 4, 1), (8, 8, 1), (1, 1), (3, 3), (False, False, False), dx0)
-    for a, b in zip(mine, ref):
-        assert np.array_equal(a, b)
 
     def attempt(tables):
         keep = [np.ascontiguousarray(x) for x in tables]
@@ -326,16 +322,20 @@ def test_create_refined_rejects_a_coarse_block_on_two_refined_faces_without_gpu(
             lib.gbh_destroy(ctx)
         return rc, lib.gbh_last_error(None)
 
-    # L shape: coarse block (2, 2) borders (2, 1) across -y and (1, 2) across -x
-    rc, msg = attempt(refined_tables(2, (4, 4), (8, 8), [(1, 1), (2, 1), (1, 2)], dx0))
-    assert rc == -5 and b"coarse block 10 borders the refined region through 2 faces" in msg
-    # two boxes one coarse block apart in a 5 x 4 lattice: block (2, 1) sits between them
-    rc, msg = attempt(refined_tables(2, (5, 4), (8, 8), [(1, 1), (1, 2), (3, 1), (3, 2)], (1 / 40, 1 / 32, 1.0)))
-    assert rc == -5 and b"through 2 faces" in msg
-    # the box, and two boxes two coarse blocks apart, pass the table checks (without a GPU
-    # the context allocation then fails)
-    for tables in (mine, refined_tables(2, (8, 4), (8, 8), [(1, 1), (1, 2), (4, 1), (4, 2)], (1 / 64, 1 / 32, 1.0))):
-        rc, msg = attempt(tables)
+    regions = [((4, 4), [(x, y) for y in (1, 2) for x in (1, 2)]),            # box
+               ((4, 4), [(1, 1), (2, 1), (1, 2)]),                          # L
+               ((5, 4), [(1, 1), (2, 1), (3, 1), (1, 2), (3, 2)]),          # notch
+               ((5, 4), [(1, 1), (1, 2), (3, 1), (3, 2)]),                  # two boxes, one block apart
+               ((5, 5), [(1, 1), (3, 3)])]                                  # separate blocks
+    for nb0, blocks in regions:
+        dx0 = (1 / (8 * nb0[0]), 1 / (8 * nb0[1]), 1.0)
+        mine = refined_tables(2, nb0, (8, 8), blocks, dx0)
+        lo = (min(b[0] for b in blocks), min(b[1] for b in blocks))
+        hi = (max(b[0] for b in blocks) + 1, max(b[1] for b in blocks) + 1)
+        ref = two_level_tables(2, nb0 + (1,), (8, 8, 1), lo, hi, (False, False, False), dx0, blocks)
+        for x, y in zip(mine, ref):
+            assert np.array_equal(x, y)
+        rc, msg = attempt(mine)
         assert rc in (0, -2, -4) and b"faces" not in msg, msg
 
 

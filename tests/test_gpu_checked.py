@@ -117,11 +117,14 @@ def test_decompositions_and_graph(gb, kchunk, ipc):
     both(gb, make, run)
 
 
+@pytest.mark.parametrize("region", ["box", "tripod"])
 @pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("stages,tele,ng", [(2, False, 4), (2, True, 4), (3, False, 6), (3, True, 6)])
-def test_two_level_paths(gb, stages, tele, ng, split):
-    tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, ng), (1, 1, 1), (3, 3, 3))
-    U0 = wl.sedov_two_level(tl)
+def test_two_level_paths(gb, stages, tele, ng, split, region):
+    c = wl.lattice_3d(4, 4, 4, 8, 8, 8, ng)
+    tl = (wl.two_level(c, (1, 1, 1), (3, 3, 3)) if region == "box" else
+          wl.two_level_blocks(c, [(1, 1, 1), (2, 1, 1), (1, 2, 1), (1, 1, 2)]))
+    U0 = wl.sedov_two_level(tl)[tl.gpu_blocks]
 
     def make(checked):
         h = gb.Hydro.from_two_level(tl, checked=checked)

@@ -42,7 +42,7 @@ class CheckpointedRun:
 
     def backward(self, lam_final: torch.Tensor) -> torch.Tensor:
         lam = lam_final.clone().contiguous()
-        if self.h.nstages != 2:
+        if self.h.nstages != 2 or self.h.telescoping:
             return self._backward_recompute(lam)
         for start in reversed(range(0, self.nsteps, self.every)):
             end = min(start + self.every, self.nsteps)
@@ -61,8 +61,8 @@ class CheckpointedRun:
         return lam
 
     def _backward_recompute(self, lam: torch.Tensor) -> torch.Tensor:
-        """Three-stage contexts: the segment's states by hydro_step, each step's
-        adjoint recomputing its intermediate stages."""
+        """Three-stage and telescoping contexts: the segment's states by
+        hydro_step, each step's adjoint recomputing its intermediate stages."""
         for start in reversed(range(0, self.nsteps, self.every)):
             end = min(start + self.every, self.nsteps)
             states = [self.checkpoints[start].clone()]

@@ -78,6 +78,9 @@ struct gbh_ctx {
   double* d_adj_tmp = nullptr;
   double* d_adj_prim = nullptr;     // primitives of the state a VJP linearises about
   double* d_adj_tmp2 = nullptr;     // second intermediate adjoint (three stages)
+  double* d_adj_fill = nullptr;     // telescoping adjoint: the filled copy of Un
+  double* d_adj_tele = nullptr;     // telescoping adjoint: the adjoint of the filled state
+  size_t adj_slot_doubles = 0;      // size of d_adj_lamW
   // pipelined host-buffer step (hydro_step_host), set up on first use: chunks
   // of consecutive blocks, the highest chunk any face neighbour of a chunk
   // lives in, streams (copy in, stage 1, stage 2, copy out) and events
@@ -353,10 +356,22 @@ int reduce_dt(gbh_ctx* c, const double* U, double* dt_dev, double* hist, cudaStr
 int ensure_adjoint_buffers(gbh_ctx* c) {
   const size_t bytes = sizeof(double) * (size_t)state_elems(c->lay);
   cudaError_t e = cudaSuccess;
-  if (!c->d_adj_lamW) e = cudaMalloc(&c->d_adj_lamW, sizeof(double) * gbh::stage_vjp_scratch_doubles(c->lay));
+  // face slots: the interior faces, or in the telescoping mode the faces of
+  // the widest ring stage's box
+  const size_t slots = gbh::stage_vjp_scratch_doubles(c->lay, c->telescoping ? 2 * (c->nstages - 1) : 0);
+  if (c->d_adj_lamW && c->adj_slot_doubles < slots) {
+    cudaFree(c->d_adj_lamW);
+    c->d_adj_lamW = nullptr;
+  }
+  if (!c->d_adj_lamW) {
+    e = cudaMalloc(&c->d_adj_lamW, sizeof(double) * slots);
+    c->adj_slot_doubles = e == cudaSuccess ? slots : 0;
+  }
   if (e == cudaSuccess && !c->d_adj_tmp) e = cudaMalloc(&c->d_adj_tmp, bytes);
   if (e == cudaSuccess && !c->d_adj_prim) e = cudaMalloc(&c->d_adj_prim, bytes);
   if (e == cudaSuccess && c->nstages == 3 && !c->d_adj_tmp2) e = cudaMalloc(&c->d_adj_tmp2, bytes);
+  if (e == cudaSuccess && c->telescoping && !c->d_adj_fill) e = cudaMalloc(&c->d_adj_fill, bytes);
+  if (e == cudaSuccess && c->telescoping && !c->d_adj_tele) e = cudaMalloc(&c->d_adj_tele, bytes);
   if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
   return GBH_OK;
 }
@@ -373,7 +388,6 @@ gbh::StageArgs vjp_args(gbh_ctx* c, const double* U) {
 
 int adjoint_supported(gbh_ctx* c) {
   if (c->refined) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is not implemented on two-level contexts");
-  if (c->telescoping) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint is of the non-telescoping step");
   if (c->nproblems > 1) return set_err(c, GBH_ERR_UNSUPPORTED, "the adjoint takes one dt: not on batched contexts");
   return GBH_OK;
 }
@@ -995,6 +1009,56 @@ int hydro_stage_vjp(gbh_ctx* c, const double* U, const double* M, double scale, 
                                            (cudaStream_t)stream), "stage VJP launch");
 }
 
+// Adjoint of one telescoping step (Sec. 4.2, telescoping mode; readings C17,
+// C18).  Forward, recomputed: Uf = fill(Un) with all guard layers, then the
+// ring stages X_1 .. X_{S-1} (stage s updates the box of ring width
+// 2 (S - 1 - s) from its input's own cells), then U^{n+1} = a Uf + b (X_{S-1}
+// + dt L(X_{S-1})) on the interior.  Backward: with M the cotangent of
+// stage s's output on its box, the cotangent of its input is
+// b_s M + J_L(X_s)^T (b_s dt M), and a_s M goes to Uf directly; the last VJP
+// (stage 0, on Uf) adds the direct terms, and the reverse of the fill gives
+// dJ/dUn.  Every VJP reads the blocks' own padded cells (no halo gather).
+static int step_adjoint_telescoping(gbh_ctx* c, const double* Un, double dt, const double* lam, double* lam_prev,
+                                    cudaStream_t s) {
+  const RkCoef r = rk_coef(c->nstages);
+  const long long n = state_elems(c->lay);
+  int rc = cuda_err(c, cudaMemcpyAsync(c->d_adj_fill, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                    "cudaMemcpyAsync");
+  if (rc) return rc;
+  gbh::FillArgs F{c->d_adj_fill, c->d_nbr, c->d_face, c->lay};
+  if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
+  double* X[3] = {c->d_adj_fill, c->d_scratch, c->d_scratch2};
+  for (int st = 0; st + 1 < r.S; ++st) {
+    rc = stage_launch(c, X[st], st ? X[0] : nullptr, X[st + 1], nullptr, dt, r.a[st], r.b[st], false, false, s,
+                      2 * (r.S - 1 - st));
+    if (rc) return rc;
+  }
+  // cotangents of the stages' outputs: M[S] = lam (interior); M[s] = that of X_s
+  const double* M[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* cur[3] = {c->d_adj_tele, c->d_adj_tmp, c->d_adj_tmp2};
+  M[r.S] = lam;
+  for (int st = r.S - 1; st >= 0; --st) {
+    const int ring = 2 * (r.S - 1 - st);
+    const double* Xt[3];
+    double ct[3];
+    int rt[3];
+    int nt = 0;
+    Xt[nt] = M[st + 1]; ct[nt] = r.b[st]; rt[nt] = ring; ++nt;
+    if (st == 0)   // the direct terms a_s M_{s+1} of the later stages
+      for (int q = 1; q < r.S; ++q) {
+        Xt[nt] = M[q + 1]; ct[nt] = r.a[q]; rt[nt] = 2 * (r.S - 1 - q); ++nt;
+      }
+    gbh::StageArgs A = vjp_args(c, X[st]);
+    A.gather = 0;
+    rc = cuda_err(c, gbh::launch_stage_vjp_box(A, ring, M[st + 1], r.b[st] * dt, Xt, ct, rt, nt, c->d_adj_lamW,
+                                                c->d_adj_prim, cur[st], s), "box VJP launch");
+    if (rc) return rc;
+    M[st] = cur[st];
+  }
+  return cuda_err(c, gbh::launch_fill_vjp(c->lay, c->d_nbr, c->d_face, c->d_adj_tele, lam_prev, s),
+                  "fill VJP launch");
+}
+
 static int step_adjoint_common(gbh_ctx* c, const double* Un, const double* U1, double dt, const double* lam_next,
                                double* lam_prev, void* stream) {
   int rc = check_ctx(c);
@@ -1009,6 +1073,10 @@ static int step_adjoint_common(gbh_ctx* c, const double* Un, const double* U1, d
   if (U1 && lam_prev < U1 + n && U1 < lam_prev + n) return set_err(c, GBH_ERR_INVAL, "lam_prev must not overlap U1");
   if ((rc = ensure_adjoint_buffers(c))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->telescoping) {
+    if (U1) return set_err(c, GBH_ERR_UNSUPPORTED, "the stored-state adjoint is of the non-telescoping step");
+    return step_adjoint_telescoping(c, Un, dt, lam_next, lam_prev, s);
+  }
   if (c->nstages == 3) {
     if (U1) return set_err(c, GBH_ERR_UNSUPPORTED, "the stored-state adjoint is of the two-stage step");
     // forward: U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
@@ -1104,6 +1172,8 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_adj_lamW);
   cudaFree(c->d_adj_tmp);
   cudaFree(c->d_adj_prim);
+  cudaFree(c->d_adj_fill);
+  cudaFree(c->d_adj_tele);
   cudaFree(c->d_adj_tmp2);
   cudaFree(c->d_smax_own);
   drop_graph(c);

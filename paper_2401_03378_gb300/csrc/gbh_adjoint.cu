@@ -286,8 +286,9 @@ __device__ __forceinline__ void hllc_flux_vjp(const double WL[5], const double W
 struct FaceGeom {
   long long total;     // doubles in the slot buffer (checked build)
   long long base[3];   // offset of each dimension's slots in the buffer
-  int n[3];            // pencil length per dimension
+  int n[3];            // pencil length per dimension (the box's: n + 2E)
   int n1[3], n2[3];    // transverse extents per dimension
+  int ring[3];         // ring width per dimension (E; 0 in z of a 2-D grid): box position q is cell q - ring
 };
 
 __device__ __forceinline__ long long slot_index(const FaceGeom& G, int d, int b, int pen, int k, int s) {
@@ -306,7 +307,7 @@ __device__ __forceinline__ long long own_offset(const Layout& L, int b, int i, i
                 (long long)L.nblocks * L.bstride - 4 * L.vstride);
 }
 
-template <int N, int d>
+template <int N, int d, int E>
 __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G, const double* __restrict__ Wp,
                                           const double* __restrict__ M, double scale, double* __restrict__ C,
                                           long long t) {
@@ -317,8 +318,10 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   const long long npen = (long long)G.n1[d] * G.n2[d];
   const int pen = (int)(r % npen);
   const int b = (int)(r / npen);
-  const int p1 = pen % G.n1[d], p2 = pen / G.n1[d];
-  const int nd = G.n[d];
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  // transverse cells; E = 0: the interior pencils, no offsets (compile time)
+  const int p1 = pen % G.n1[d] - (E ? G.ring[t1] : 0), p2 = pen / G.n1[d] - (E ? G.ring[t2] : 0);
+  const int nd = G.n[d], Ed = E ? G.ring[d] : 0;
   const long long zt = thread_zero(a.eos);
   const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers
   const Rk& kr = e.k;
@@ -329,8 +332,9 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   int ci, cj, ck;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    // primitives of the stencil position (the halo gathered as in the stage kernel)
-    pencil_to_cell(d, k - 2 + s, p1, p2, ci, cj, ck);
+    // primitives of the stencil position (the halo gathered as in the stage
+    // kernel; in guard mode the block's own padded cells)
+    pencil_to_cell(d, k - 2 + s - Ed, p1, p2, ci, cj, ck);
     const long long o = cell_offset<N>(a, b, ci, cj, ck);
 #pragma unroll
     for (int v = 0; v < 5; ++v) W[s][v] = __ldg(Wp + o + v * L.vstride);
@@ -346,12 +350,12 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
   {
     double mk[5] = {0, 0, 0, 0, 0}, mk1[5] = {0, 0, 0, 0, 0};
     if (k < nd) {
-      pencil_to_cell(d, k, p1, p2, ci, cj, ck);
+      pencil_to_cell(d, k - Ed, p1, p2, ci, cj, ck);
       const long long o = own_offset(L, b, ci, cj, ck);
       for (int v = 0; v < 5; ++v) mk[v] = __ldg(M + o + v * L.vstride);
     }
     if (k > 0) {
-      pencil_to_cell(d, k - 1, p1, p2, ci, cj, ck);
+      pencil_to_cell(d, k - 1 - Ed, p1, p2, ci, cj, ck);
       const long long o = own_offset(L, b, ci, cj, ck);
       for (int v = 0; v < 5; ++v) mk1[v] = __ldg(M + o + v * L.vstride);
     }
@@ -383,7 +387,9 @@ __device__ __forceinline__ void face_work(const StageArgs& a, const FaceGeom& G,
     for (int v = 0; v < 5; ++v) out[s * 5 + v] = Cs[s][v];
 }
 
-template <int N>
+// E = 0: the interior faces (offsets known to be zero); E = 1: a box whose
+// ring widths G.ring are applied at run time.
+template <int N, int E>
 __global__ void __launch_bounds__(128, 4) vjp_face_kernel(const StageArgs a, const FaceGeom G,
                                                       const double* __restrict__ Wp, const double* __restrict__ M,
                                                       double scale, double* __restrict__ C) {
@@ -392,9 +398,9 @@ __global__ void __launch_bounds__(128, 4) vjp_face_kernel(const StageArgs a, con
   for (int d = 0; d < L.ndim; ++d) {
     const long long count = (long long)L.nblocks * G.n1[d] * G.n2[d] * (G.n[d] + 1);
     if (t < count) {
-      if (d == 0) face_work<N, 0>(a, G, Wp, M, scale, C, t);
-      else if (d == 1) face_work<N, 1>(a, G, Wp, M, scale, C, t);
-      else face_work<N, 2>(a, G, Wp, M, scale, C, t);
+      if (d == 0) face_work<N, 0, E>(a, G, Wp, M, scale, C, t);
+      else if (d == 1) face_work<N, 1, E>(a, G, Wp, M, scale, C, t);
+      else face_work<N, 2, E>(a, G, Wp, M, scale, C, t);
       return;
     }
     t -= count;
@@ -417,6 +423,25 @@ __global__ void vjp_prim_kernel(const StageArgs a, double* __restrict__ Wp) {
     const int j = (int)(r % L.ny);
     const int k = (int)(r / L.ny);
     const long long o = own_offset(L, b, i, j, k);
+    double U[5], W[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
+    cons_to_prim(U, W, e);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Wp[o + v * L.vstride] = W[v];
+  }
+}
+
+// Primitives of every padded cell of Uin into Wp (the box faces of a ring
+// stage read the block's own guard cells).
+__global__ void vjp_prim_padded_kernel(const StageArgs a, double* __restrict__ Wp) {
+  const Layout& L = a.lay;
+  const Eos e = reg_eos(a.eos, thread_zero(a.eos));
+  const long long total = (long long)L.nblocks * L.bstride / 5;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / L.vstride;
+    const long long o = b * L.bstride + (t - b * L.vstride);
     double U[5], W[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
@@ -494,6 +519,150 @@ __global__ void vjp_cell_kernel(const StageArgs a, const FaceGeom G, const doubl
   }
 }
 
+// ---- the padded-cell pass of a box VJP (guard mode) ---------------------------
+//
+// For the stage of ring width G.ring on the block's own padded cells (the
+// telescoping mode): every padded cell sums the slots of the box faces whose
+// stencils read it, in increasing face order per dimension (positions -2 ..
+// n + 2E + 1 of the pencils through it), applies the reverse of the EOS where
+// some face read it, and adds up to three linear terms, each on a box of its
+// own ring width (the cells where that term's array is defined):
+//   out = J^T (scale M) + sum_t [cell in box E_t] c_t X_t.
+// Every padded cell of out is written (0 where nothing reaches it).
+struct LinTerms {
+  const double* X[3];
+  double c[3];
+  int ring[3];
+  int n;
+};
+
+__device__ __forceinline__ bool in_box(const Layout& L, int E, int i, int j, int k) {
+  return i >= -E && i < L.nx + E && j >= -E && j < L.ny + E && (L.ndim == 2 || (k >= -E && k < L.nz + E));
+}
+
+__global__ void vjp_padded_cell_kernel(const StageArgs a, const FaceGeom G, const double* __restrict__ C,
+                                       const LinTerms T, double* out) {
+  const Layout& L = a.lay;
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers
+  const Rk& kr = e.k;
+  const long long per = (long long)L.nxp * L.nyp * L.nzp;
+  const long long total = per * L.nblocks;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    long long r = t % per;
+    const int i = (int)(r % L.nxp) - L.g;
+    r /= L.nxp;
+    const int j = (int)(r % L.nyp) - L.g;
+    const int k = (int)(r / L.nyp) - L.gz;
+    const int c[3] = {i, j, k};
+    double bW[5] = {0, 0, 0, 0, 0};
+    bool read = false;
+    for (int d = 0; d < L.ndim; ++d) {
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const int q1 = c[t1] + G.ring[t1], q2 = c[t2] + G.ring[t2];   // box pencil through the cell
+      if (q1 < 0 || q1 >= G.n[t1] || q2 < 0 || q2 >= G.n[t2]) continue;
+      const int q = c[d] + G.ring[d];                                 // box position along d
+      if (q < -2 || q > G.n[d] + 1) continue;
+      add_position(G, C, d, b, q1 + G.n1[d] * q2, q, bW, kr);
+      read = true;
+    }
+    const long long o = own_offset(L, b, i, j, k);
+    double bU[5] = {0, 0, 0, 0, 0};
+    if (read) {
+      double U[5], W[5];
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(a.Uin + o + v * L.vstride);
+      bool fr, fp;
+      cons_to_prim_flags(U, W, e, fr, fp);
+      prim_vjp(W, fr, fp, e, bW, bU);
+    }
+    for (int q = 0; q < T.n; ++q)
+      if (in_box(L, T.ring[q], i, j, k)) {
+        const double cq = reg_const(T.c[q], zt);
+        for (int v = 0; v < 5; ++v) bU[v] = fma(cq, T.X[q][o + v * L.vstride], bU[v]);
+      }
+    for (int v = 0; v < 5; ++v) out[o + v * L.vstride] = bU[v];
+  }
+}
+
+// ---- the reverse of the full guard fill (fill_kernel) -----------------------
+//
+// The fill copies interior cells into guard cells; its adjoint adds every
+// guard cell's adjoint to the interior cell it was copied from.  As a gather,
+// with one thread per interior cell s of block b and no atomics: per
+// dimension the guard cell's coordinate either equals s's (no offset), lies
+// across the face of the guard cell's block whose neighbour is b (s within
+// g of b's opposite face: a copy from the neighbour), or lies outside an
+// outflow face (s on that face: a clamped copy, any of the g guard
+// positions).  The guard cell's block is b's neighbour against the
+// neighbour offsets; each combination is checked against the tables the fill
+// used.  out = lam + the sum over the guard cells, on interior cells.
+__global__ void fill_vjp_kernel(const Layout L, const int* nbr, const int* face_nbr, const double* lam, double* out) {
+  const int nn = L.ndim == 3 ? 27 : 9;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  const int g[3] = {L.g, L.g, L.gz};
+  const long long per = (long long)L.nx * L.ny * L.nz;
+  const long long total = per * L.nblocks;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    long long r = t % per;
+    const int c[3] = {(int)(r % L.nx), (int)((r / L.nx) % L.ny), (int)(r / ((long long)L.nx * L.ny))};
+    double acc[5];
+    const long long os = own_offset(L, b, c[0], c[1], c[2]);
+    for (int v = 0; v < 5; ++v) acc[v] = lam[os + v * L.vstride];
+    // options per dimension: 0 the same coordinate, 1 / 2 a copy across the
+    // guard block's low / high face, 3 / 4 a clamp at its low / high outflow face
+    const int nopt[3] = {5, 5, L.ndim == 3 ? 5 : 1};
+    for (int oz = 0; oz < nopt[2]; ++oz)
+      for (int oy = 0; oy < nopt[1]; ++oy)
+        for (int ox = 0; ox < nopt[0]; ++ox) {
+          const int opt[3] = {ox, oy, oz};
+          if (ox == 0 && oy == 0 && oz == 0) continue;
+          int off[3] = {0, 0, 0};   // offset of b seen from the guard cell's block
+          int lo[3], hi[3];         // guard-cell coordinates in the guard block
+          bool ok = true;
+          for (int d = 0; d < 3 && ok; ++d) {
+            switch (opt[d]) {
+              case 0: lo[d] = hi[d] = c[d]; break;
+              case 1: ok = c[d] >= n[d] - g[d]; off[d] = -1; lo[d] = hi[d] = c[d] - n[d]; break;
+              case 2: ok = c[d] < g[d]; off[d] = 1; lo[d] = hi[d] = c[d] + n[d]; break;
+              case 3: ok = c[d] == 0; lo[d] = -g[d]; hi[d] = -1; break;
+              default: ok = c[d] == n[d] - 1; lo[d] = n[d]; hi[d] = n[d] + g[d] - 1; break;
+            }
+          }
+          if (!ok) continue;
+          // the guard cell's block: b's neighbour at -off
+          int gb = b;
+          if (off[0] || off[1] || off[2]) {
+            const int e = L.ndim == 3 ? (1 - off[2]) * 9 + (1 - off[1]) * 3 + (1 - off[0])
+                                      : (1 - off[1]) * 3 + (1 - off[0]);
+            gb = __ldg(nbr + (long long)nn * b + e);
+            if (gb < 0) continue;
+            const int eb = L.ndim == 3 ? (off[2] + 1) * 9 + (off[1] + 1) * 3 + (off[0] + 1)
+                                       : (off[1] + 1) * 3 + (off[0] + 1);
+            if (__ldg(nbr + (long long)nn * gb + eb) != b) continue;   // the fill would read another block
+          }
+          // the fill clamps exactly at gb's outflow faces
+          for (int d = 0; d < L.ndim && ok; ++d) {
+            if (opt[d] == 0) continue;
+            const int f = 2 * d + ((opt[d] == 2 || opt[d] == 4) ? 1 : 0);
+            const bool outflow = __ldg(face_nbr + 6 * gb + f) == GBH_BC_OUTFLOW;
+            ok = (opt[d] >= 3) == outflow;
+          }
+          if (!ok) continue;
+          for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+              for (int x = lo[0]; x <= hi[0]; ++x) {
+                const long long og = own_offset(L, gb, x, y, z);
+                for (int v = 0; v < 5; ++v) acc[v] += lam[og + v * L.vstride];
+              }
+        }
+    for (int v = 0; v < 5; ++v) out[os + v * L.vstride] = acc[v];
+  }
+}
+
 // out = a X + b Y on interior cells (state layout; out may alias X or Y).
 __global__ void axpby_kernel(const Layout L, double a, const double* X, double b, const double* Y, double* out) {
   const long long per = (long long)L.nx * L.ny * L.nz;
@@ -557,14 +726,21 @@ int grid_for(long long work) {
   return (int)(g < 1 ? 1 : g);
 }
 
-FaceGeom face_geom(const Layout& L) {
+// Faces of the box of ring width E around every block's interior (E = 0: the
+// interior itself), per dimension: pencils over the box's transverse extent,
+// n + 2E + 1 faces each.
+FaceGeom face_geom(const Layout& L, int E = 0) {
   FaceGeom G{};
-  const int n[3] = {L.nx, L.ny, L.nz};
+  int n[3] = {L.nx, L.ny, L.nz};
+  for (int d = 0; d < 3; ++d) {
+    G.ring[d] = d < L.ndim ? E : 0;
+    n[d] += 2 * G.ring[d];
+  }
   long long off = 0;
   for (int d = 0; d < 3; ++d) {
     G.n[d] = n[d];
-    G.n1[d] = d == 0 ? L.ny : L.nx;
-    G.n2[d] = d == 2 ? L.ny : L.nz;
+    G.n1[d] = d == 0 ? n[1] : n[0];
+    G.n2[d] = d == 2 ? n[1] : n[2];
     G.base[d] = off;
     if (d < L.ndim) off += (long long)L.nblocks * G.n1[d] * G.n2[d] * (n[d] + 1) * 20;
   }
@@ -576,15 +752,7 @@ FaceGeom face_geom(const Layout& L) {
 
 GBH_CHECK_TAKE(check_take_adjoint)
 
-size_t stage_vjp_scratch_doubles(const Layout& L) {
-  long long total = 0;
-  const int n[3] = {L.nx, L.ny, L.nz};
-  for (int d = 0; d < L.ndim; ++d) {
-    const long long n1 = d == 0 ? L.ny : L.nx, n2 = d == 2 ? L.ny : L.nz;
-    total += (long long)L.nblocks * n1 * n2 * (n[d] + 1) * 20;
-  }
-  return (size_t)total;
-}
+size_t stage_vjp_scratch_doubles(const Layout& L, int ring) { return (size_t)face_geom(L, ring).total; }
 
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,
                              const double* B, double cB, double* C, double* Wp, double* out, cudaStream_t s) {
@@ -597,14 +765,54 @@ cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, 
   for (int d = 0; d < L.ndim; ++d) faces += (long long)L.nblocks * G.n1[d] * G.n2[d] * (G.n[d] + 1);
   const unsigned grid = (unsigned)((faces + 127) / 128);
   switch (L.nx) {
-    case 4: vjp_face_kernel<4><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
-    case 8: vjp_face_kernel<8><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
-    case 16: vjp_face_kernel<16><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 4: vjp_face_kernel<4, 0><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 8: vjp_face_kernel<8, 0><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 16: vjp_face_kernel<16, 0><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vjp_cell_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(a, G, C, A, cA, B, cB, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_vjp_box(const StageArgs& a, int ring, const double* M, double scale, const double* const X[3],
+                                 const double c[3], const int rings[3], int nterms, double* C, double* Wp, double* out,
+                                 cudaStream_t s) {
+  const Layout& L = a.lay;
+  if (a.gather || ring < 0 || L.g < ring + 2 || nterms < 0 || nterms > 3) return cudaErrorInvalidValue;
+  const FaceGeom G = face_geom(L, ring);
+  // primitives of every padded cell the box faces read: all of them
+  vjp_prim_padded_kernel<<<grid_for((long long)L.nblocks * L.nxp * L.nyp * L.nzp), 256, 0, s>>>(a, Wp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  long long faces = 0;
+  for (int d = 0; d < L.ndim; ++d) faces += (long long)L.nblocks * G.n1[d] * G.n2[d] * (G.n[d] + 1);
+  const unsigned grid = (unsigned)((faces + 127) / 128);
+  // the ring is a run-time offset here (E = 1 selects it); the interior
+  // instantiation above keeps its compile-time zero offsets
+  switch (L.nx) {
+    case 4: vjp_face_kernel<4, 1><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 8: vjp_face_kernel<8, 1><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    case 16: vjp_face_kernel<16, 1><<<grid, 128, 0, s>>>(a, G, Wp, M, scale, C); break;
+    default: return cudaErrorInvalidValue;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  LinTerms T{};
+  T.n = nterms;
+  for (int q = 0; q < nterms; ++q) {
+    T.X[q] = X[q];
+    T.c[q] = c[q];
+    T.ring[q] = rings[q];
+  }
+  vjp_padded_cell_kernel<<<grid_for((long long)L.nblocks * L.nxp * L.nyp * L.nzp), 256, 0, s>>>(a, G, C, T, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_vjp(const Layout& L, const int* nbr, const int* face_nbr, const double* lam, double* out,
+                            cudaStream_t s) {
+  fill_vjp_kernel<<<grid_for((long long)L.nblocks * L.nx * L.ny * L.nz), 256, 0, s>>>(L, nbr, face_nbr, lam, out);
   return cudaGetLastError();
 }
 

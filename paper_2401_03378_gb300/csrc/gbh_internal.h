@@ -144,9 +144,21 @@ cudaError_t launch_dt_reduce_blocks(const DtArgs& a, const int* problem, cudaStr
 cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
                          cudaStream_t s);
 
-size_t stage_vjp_scratch_doubles(const Layout& L);   // face-slot buffer of launch_stage_vjp
+size_t stage_vjp_scratch_doubles(const Layout& L, int ring = 0);   // face-slot buffer of a (box) stage VJP
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,
                              const double* B, double cB, double* C, double* Wp, double* out, cudaStream_t s);
+// VJP of a stage of ring width `ring` that reads the block's own padded cells
+// (a.gather = 0, the telescoping mode): out = J_L(Uin)^T (scale M), with M
+// read on the box of that ring, plus nterms linear terms c_t X_t, each on the
+// box of ring width rings[t]; every padded cell of out is written.  C: face
+// slots (stage_vjp_scratch_doubles(L, ring)); Wp: a state-sized buffer.
+cudaError_t launch_stage_vjp_box(const StageArgs& a, int ring, const double* M, double scale, const double* const X[3],
+                                 const double c[3], const int rings[3], int nterms, double* C, double* Wp, double* out,
+                                 cudaStream_t s);
+// Reverse of the full guard fill: out = lam + the adjoints of the guard cells
+// the fill copies each interior cell into (interior cells of out only).
+cudaError_t launch_fill_vjp(const Layout& L, const int* nbr, const int* face_nbr, const double* lam, double* out,
+                            cudaStream_t s);
 cudaError_t launch_axpby(const Layout& L, double a, const double* X, double b, const double* Y, double* out,
                          cudaStream_t s);   // out = a X + b Y on interior cells
 cudaError_t launch_prim_to_cons(const Layout& L, const Eos& e, const double* W, double* U, const double* lamU,

@@ -85,6 +85,7 @@ class Hydro:
         self.ctx = ctx
         self.device = torch.cuda.current_device()
         self.nstages = 2
+        self.telescoping = False
 
     @classmethod
     def from_lattice(cls, lat, **kw):
@@ -229,6 +230,7 @@ class Hydro:
     def set_telescoping(self, enable: bool = True):
         """Telescoping SSP-RK (one guard fill per step; needs nguard >= 2 * stages)."""
         self._check(self.lib.gbh_set_telescoping(self.ctx, int(bool(enable))))
+        self.telescoping = bool(enable)
 
     def set_rk_stages(self, nstages: int):
         """2 (SSP-RK2, the default) or 3 (SSP-RK3) Shu-Osher stages per step."""

@@ -170,14 +170,18 @@ def test_batched_and_host_step(gb):
     assert violations(gb) == 0
 
 
-def test_adjoint(gb):
-    lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, 4, bc=("periodic", "outflow", "outflow"))
+@pytest.mark.parametrize("tele,stages,ng", [(False, 2, 4), (True, 2, 4), (True, 3, 6)])
+def test_adjoint(gb, tele, stages, ng):
+    lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, ng, bc=("periodic", "outflow", "outflow"))
     U0 = wl.random_state(lat, seed=62, rough=False)
     rng = np.random.default_rng(63)
     L0 = rng.normal(size=U0.shape)
 
     def make(checked):
-        return gb.Hydro.from_lattice(lat, checked=checked)
+        h = gb.Hydro.from_lattice(lat, checked=checked)
+        h.set_rk_stages(stages)
+        h.set_telescoping(tele)
+        return h
 
     def run(h):
         U, lam = dev(U0), dev(L0)

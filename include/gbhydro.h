@@ -184,9 +184,10 @@ int gbh_get_tile_split(gbh_ctx *ctx, int ring, int *ysplit);
  * from its own guard data with the fluxes through coarse-fine faces of each
  * stage kept, then the coarse side of the fine region corrected once with
  * weight 1/2 per stage, and the restriction.
- * Applies to hydro_step, hydro_step_cfl, hydro_advance(_graph/_host); not to
- * single stages, hydro_step_static or the adjoint (which returns
- * GBH_ERR_UNSUPPORTED while the mode is on).
+ * Applies to hydro_step, hydro_step_cfl, hydro_advance(_graph/_host) and, on
+ * uniform contexts, hydro_step_adjoint (the adjoint of the telescoping step);
+ * not to single stages, hydro_stage_vjp, hydro_step_static or
+ * hydro_step_adjoint_stored.
  * Errors: GBH_ERR_INVAL if nguard < 4; GBH_ERR_NOMEM if the second set of
  * flux registers (two-level contexts) cannot be allocated.  Drops a captured
  * graph. */
@@ -202,7 +203,8 @@ int gbh_set_telescoping(gbh_ctx *ctx, int enable);
  * Allocates a second scratch state (and flux registers) on first use.
  * Errors: GBH_ERR_INVAL for other values or too few guard cells for the
  * telescoping mode; GBH_ERR_NOMEM.  hydro_step_adjoint follows the stage
- * count; hydro_step_adjoint_stored is of the two-stage step only.  Drops a
+ * count; hydro_step_adjoint_stored is of the two-stage non-telescoping step
+ * only.  Drops a
  * captured graph. */
 int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
 
@@ -227,11 +229,15 @@ int hydro_advance_graph(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, voi
  *   neighbours as in hydro_stage).  A and B may be NULL; out may equal A or B
  *   but must not overlap U or M.
  * hydro_step_adjoint: given lam_next = dJ/dU^{n+1} of one hydro_step(Un, dt)
- *   with the context's stage count (2 or 3; the non-telescoping step),
- *   writes lam_prev = dJ/dU^n: the Shu-Osher recursion run backwards,
+ *   with the context's stage count (2 or 3) and mode, writes lam_prev =
+ *   dJ/dU^n: the Shu-Osher recursion run backwards,
  *   lam_{s-1} = b_s lam_s + J_L(U(s-1))^T (b_s dt lam_s), with U^n also
  *   collecting a_s lam_s from every stage (recomputes the intermediate
- *   stages; lam_prev may equal lam_next, must not overlap Un).
+ *   stages; lam_prev may equal lam_next, must not overlap Un).  In the
+ *   telescoping mode (Sec. 4.2) the recursion runs over the ring stages'
+ *   boxes on the filled state, and ends with the reverse of the one fill of
+ *   all guard layers: every guard cell's adjoint goes to the interior cell it
+ *   was copied from (a neighbour's, or the block's own at an outflow edge).
  * hydro_prim_to_cons: U = conserved(W) on interior cells, W = (rho, u, v, w, p)
  *   in the state layout; hydro_prim_to_cons_vjp: lamW = (dU/dW)^T lamU. */
 int hydro_stage_vjp(gbh_ctx *ctx, const double *U, const double *M, double scale, const double *A, double cA,
@@ -243,7 +249,7 @@ int hydro_step_adjoint(gbh_ctx *ctx, const double *Un, double dt, const double *
  * (DEVICE, e.g. kept while recomputing a checkpointed segment with
  * hydro_stage), which saves the stage the call would otherwise recompute.
  * U1 is read only; lam_prev must not overlap Un or U1.  Two-stage contexts
- * only (GBH_ERR_UNSUPPORTED otherwise). */
+ * only, non-telescoping (GBH_ERR_UNSUPPORTED otherwise). */
 int hydro_step_adjoint_stored(gbh_ctx *ctx, const double *Un, const double *U1, double dt, const double *lam_next,
                               double *lam_prev, void *stream);
 /* Conserved variables from primitive ones, the inverse of the calcEos

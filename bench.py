@@ -37,10 +37,14 @@ UNIT = "zone-updates/s"
 WORKLOAD = ("3D Sedov blast 256^3: 4096 blocks of 16^3 + 4 guard cells, FP64, gamma 1.4, CFL 0.8, "
             "SSP-RK2 (non-telescoping), MC-limited PLM, HLLC, CFL dt on device each step")
 # Algorithmic FP64 operations per zone-update (+, -, *, /, sqrt = 1 each),
-# counted on the oracle's arithmetic by oracle/opcount.cpp: stage 1 570,
-# stage 2 585 + 24 for the CFL signal speed of the new state.
+# counted on the oracle's arithmetic by oracle/opcount.cpp: stage 1 570 (its
+# 13 for the conversion of its input included), stage 2 585 + 11 for the CFL
+# signal speed of the new state.  calcEos runs once per stage: the primitives
+# of the new state serve the CFL speed and the next step's first stage, so
+# the conversion is counted once (the oracle converts the new state a second
+# time for its dt, 13 more: 1179 per zone-update).
 FLOPS_STAGE1 = 570
-FLOPS_STAGE2 = 585 + 24
+FLOPS_STAGE2 = 585 + 11
 # FP64 peak derived from the nominal GB300 rate (1.25 TFLOP/s) at 152 SMs and
 # 2070 MHz: 2 FP64 FMA lanes per SM per clock -> 152 * 2 * 2 * 2.07e9.
 FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2.07e9
@@ -326,8 +330,7 @@ def run_gpu(args):
     barrier()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
-            h.step_cfl(U, dt)
+        h.advance(U, args.steps, dt)      # K steps of one call (CFL dt on the device each step)
         e1.record(stream)
         barrier()
     secs = e0.elapsed_time(e1) / 1e3
@@ -341,8 +344,7 @@ def run_gpu(args):
     for _ in range(5 if args.repeats else 0):
         barrier()
         e0.record(stream)
-        for _ in range(10):
-            h.step_cfl(U, dt)
+        h.advance(U, 10, dt)
         e1.record(stream)
         barrier()
         reps.append(e0.elapsed_time(e1) / 10)

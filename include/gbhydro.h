@@ -208,6 +208,32 @@ int gbh_set_telescoping(gbh_ctx *ctx, int enable);
  * captured graph. */
 int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
 
+/* Primitive variables carried from stage to stage (Alg. "Intra stage
+ * calculations for Spark": calcEos runs once per stage, after updSoln, and
+ * its primitives are what the next stage's calcLims reads).  With the carry
+ * on, every stage of a call except its last leaves the primitive variables
+ * (rho, u, v, w, p, floors applied) of its output in one of two
+ * context-owned arrays of the state's size, and the next stage reads them
+ * instead of converting its input again; the first stage of a call converts
+ * the caller's state.  Within one call of hydro_step / hydro_step_cfl the
+ * first stage hands its primitives to the second; hydro_advance,
+ * hydro_advance_graph and hydro_advance_host carry them across their steps,
+ * and hydro_step_host from stage 1 to stage 2.  Results, dt and floor
+ * counts are bit for bit those of the carry off (a floor is counted by the
+ * stage whose output it is found in, once per interior cell and stage, as
+ * when the next stage converted).  Applies to uniform and batched contexts in
+ * the non-telescoping mode; telescoping steps, two-level contexts, single
+ * stages, the adjoint and hydro_step_static always convert.
+ * gbh_create / gbh_create_batched allocate the arrays (2 x
+ * gbh_state_bytes) and switch the carry on; if that allocation fails the
+ * carry stays off and the context is created all the same.
+ * gbh_set_prim_carry(ctx, 0) frees the arrays (synchronises the device);
+ * enable != 0 allocates them again (GBH_ERR_NOMEM if it cannot; no effect on
+ * a two-level context).  gbh_get_prim_carry writes 1 to *enabled when the
+ * carry is on.  Drops a captured graph. */
+int gbh_set_prim_carry(gbh_ctx *ctx, int enable);
+int gbh_get_prim_carry(gbh_ctx *ctx, int *enabled);
+
 /* (No counterpart in the paper: launch batching.)
  * nsteps calls of hydro_step_cfl captured once into a CUDA graph (on a
  * private stream; re-captured when U, dt_dev or nsteps change, or the

@@ -33,6 +33,10 @@ struct gbh_ctx {
   double* d_scratch = nullptr;     // U(1), one state
   double* d_scratch2 = nullptr;    // U(2) of three-stage SSP-RK (allocated by gbh_set_rk_stages)
   int nstages = 2;                 // SSP-RK stages (2 or 3)
+  // primitive variables carried from stage to stage on uniform grids (halo
+  // gathered): two arrays of the state's layout (gbh_set_prim_carry)
+  double* d_W[2] = {nullptr, nullptr};
+  bool prim_carry = false;
   unsigned long long* d_words = nullptr;  // [0] smax accumulator, [1] floor count, [2] check count
   // host-buffer path (allocated on first use)
   double* d_host_state = nullptr;
@@ -161,11 +165,14 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
 // many guard cells around the interior, from Uin's own guard cells.
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
                  double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, int ring = 0,
-                 double* flux_reg = nullptr, const int* list = nullptr, int nlist = 0) {
+                 double* flux_reg = nullptr, const int* list = nullptr, int nlist = 0,
+                 const double* Win = nullptr, double* Wout = nullptr) {
   gbh::StageArgs A{};
   A.Uin = Uin;
   A.Un = Un;
   A.Uout = Uout;
+  A.Win = Win;
+  A.Wout = Wout;
   A.face_nbr = c->d_face;
   A.inv_dx = c->d_inv_dx;
   A.dt_dev = dt_dev;
@@ -273,25 +280,48 @@ int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt
   return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
 }
 
+// Primitive variables carried through the stages of one entry-point call
+// (uniform grids, non-telescoping): `in` is the array holding the primitives
+// of the current state (-1: none, so the next stage converts on load); each
+// stage's epilogue writes those of its output into the other array, except
+// the call's last stage unless last_out.  A state handed in by the caller is
+// always converted on load.
+struct PrimChain {
+  int in = -1;
+  bool last_out = false;
+};
+
 // One SSP-RK step on a uniform (or batched) grid.  Non-telescoping: every
 // stage gathers its halo from the neighbours.  Telescoping (Sec. 4.2): one
 // guard fill of U (all layers), then stage s of S updates the interior
 // widened by 2 (S - s) cells from its input's own guard cells; no exchange
-// between the stages.  The last stage may carry the dt epilogue.
-int uniform_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
+// between the stages.  The last stage may carry the dt epilogue.  pc: the
+// call's primitive chain (non-telescoping; null or no arrays: every stage
+// converts on load).
+int uniform_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s,
+                 PrimChain* pc = nullptr) {
   const RkCoef r = rk_coef(c->nstages);
   int rc = GBH_OK;
   if (c->telescoping) {
     gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
     if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
   }
+  const bool carry = pc && !c->telescoping && c->prim_carry && c->d_W[0];
   const double* in = U;
   for (int st = 0; st < r.S; ++st) {
     double* out = stage_out(c, st, U);
     const bool last = st == r.S - 1;
     const int ring = c->telescoping ? 2 * (r.S - 1 - st) : 0;
+    const double* Win = nullptr;
+    double* Wout = nullptr;
+    if (carry) {
+      const int wo = (!last || pc->last_out) ? (pc->in == 0 ? 1 : 0) : -1;
+      if (pc->in >= 0) Win = c->d_W[pc->in];
+      if (wo >= 0) Wout = c->d_W[wo];
+      pc->in = wo;
+    }
     rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], !c->telescoping,
-                      last && dt_epilogue, s, ring);
+                      last && dt_epilogue, s, ring, nullptr, nullptr, 0, Win, Wout);
     if (rc) return rc;
     in = out;
   }
@@ -501,16 +531,38 @@ using gbh::validate_params;
 static int create_common(const gbh_params* p, gbh_ctx** out);
 extern "C" int gbh_destroy(gbh_ctx* c);
 
-static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s) {
+static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimChain* pc) {
   int rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, dt_dev, 0.0, true, s)
                                         : refined_step(c, U, dt_dev, 0.0, true, s))
-                      : uniform_step(c, U, dt_dev, 0.0, true, s);
+                      : uniform_step(c, U, dt_dev, 0.0, true, s, pc);
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
                   "dt finalize launch");
 }
 
 
+
+// The two arrays of the primitive carry (uniform contexts).  If they cannot
+// be allocated the carry stays off and every stage converts on load (the
+// results are the same bit for bit); returns whether it is on.
+static bool alloc_prim_buffers(gbh_ctx* c) {
+  if (c->refined) return false;
+  if (!c->d_W[0]) {
+    const size_t bytes = sizeof(double) * state_elems(c->lay);
+    double *w0 = nullptr, *w1 = nullptr;
+    if (cudaMalloc(&w0, bytes) != cudaSuccess || cudaMalloc(&w1, bytes) != cudaSuccess) {
+      cudaFree(w0);
+      cudaFree(w1);
+      cudaGetLastError();      // the failed allocation is not an error of the context
+      c->prim_carry = false;
+      return false;
+    }
+    c->d_W[0] = w0;
+    c->d_W[1] = w1;
+  }
+  c->prim_carry = true;
+  return true;
+}
 
 static int create_common(const gbh_params* p, gbh_ctx** out) {
   gbh_ctx* c = new (std::nothrow) gbh_ctx();
@@ -556,7 +608,9 @@ int gbh_create(const gbh_params* p, gbh_ctx** out) {
   *out = nullptr;
   int rc = validate_params(p, false);
   if (rc) return rc;
-  return create_common(p, out);
+  if ((rc = create_common(p, out))) return rc;
+  alloc_prim_buffers(*out);
+  return GBH_OK;
 }
 
 // Problem ids of a batched context: in range, and no neighbour (or, on two
@@ -781,6 +835,7 @@ int gbh_create_batched(const gbh_params* p, const int32_t* problem, int nproblem
     gbh_destroy(c);
     return rc;
   }
+  alloc_prim_buffers(c);
   *out = c;
   return GBH_OK;
 }
@@ -950,6 +1005,31 @@ int gbh_set_rk_stages(gbh_ctx* c, int nstages) {
   return GBH_OK;
 }
 
+int gbh_set_prim_carry(gbh_ctx* c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  drop_graph(c);
+  if (!enable) {
+    cudaError_t e = cudaDeviceSynchronize();   // no stage in flight may still use the arrays
+    cudaFree(c->d_W[0]);
+    cudaFree(c->d_W[1]);
+    c->d_W[0] = c->d_W[1] = nullptr;
+    c->prim_carry = false;
+    return cuda_err(c, e, "cudaDeviceSynchronize");
+  }
+  if (c->refined) return GBH_OK;
+  if (!alloc_prim_buffers(c)) return set_err(c, GBH_ERR_NOMEM, "primitive arrays: device allocation failed");
+  return GBH_OK;
+}
+
+int gbh_get_prim_carry(gbh_ctx* c, int* enabled) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!enabled) return set_err(c, GBH_ERR_INVAL, "enabled is NULL");
+  *enabled = c->prim_carry && c->d_W[0] ? 1 : 0;
+  return GBH_OK;
+}
+
 int gbh_set_decomposition(gbh_ctx* c, int kchunk, int items_per_cta) {
   if (!c) return set_err(nullptr, GBH_ERR_INVAL, "null context");
   if (items_per_cta < 1 || kchunk < 0 || (kchunk > 0 && (c->lay.ndim != 3 || kchunk < 2 || kchunk > c->lay.nz)))
@@ -972,7 +1052,11 @@ int hydro_advance_graph(gbh_ctx* c, double* U, int nsteps, double* dt_dev, void*
     if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(c, e, "begin capture");
-    for (int n = 0; n < nsteps && rc == GBH_OK; ++n) rc = step_cfl(c, U, dt_dev, c->cap_stream);
+    PrimChain pc;
+    for (int n = 0; n < nsteps && rc == GBH_OK; ++n) {
+      pc.last_out = n < nsteps - 1;
+      rc = step_cfl(c, U, dt_dev, c->cap_stream, &pc);
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (rc) {
@@ -1152,6 +1236,8 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_inv_dx);
   cudaFree(c->d_words);
   cudaFree(c->d_scratch);
+  cudaFree(c->d_W[0]);
+  cudaFree(c->d_W[1]);
   cudaFree(c->d_host_state);
   cudaFree(c->d_host_dt);
   cudaFree(c->d_host_hist);
@@ -1250,14 +1336,16 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if (c->refined)
     return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, false, s)
                           : refined_step(c, U, nullptr, dt, false, s);
-  return uniform_step(c, U, nullptr, dt, false, s);
+  PrimChain pc;
+  return uniform_step(c, U, nullptr, dt, false, s, &pc);
 }
 
 int hydro_step_cfl(gbh_ctx* c, double* U, double* dt_dev, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
-  return step_cfl(c, U, dt_dev, (cudaStream_t)stream);
+  PrimChain pc;
+  return step_cfl(c, U, dt_dev, (cudaStream_t)stream, &pc);
 }
 
 int hydro_advance(gbh_ctx* c, double* U, int nsteps, double* dt_dev, double* dt_hist_dev, void* stream) {
@@ -1266,14 +1354,16 @@ int hydro_advance(gbh_ctx* c, double* U, int nsteps, double* dt_dev, double* dt_
   if (nsteps < 0) return set_err(c, GBH_ERR_INVAL, "nsteps must be >= 0");
   if (!U || !dt_dev || !aligned8(U) || !aligned8(dt_dev)) return set_err(c, GBH_ERR_INVAL, "null or misaligned pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  PrimChain pc;
   for (int n = 0; n < nsteps; ++n) {
+    pc.last_out = n < nsteps - 1;
     if (dt_hist_dev) {
       rc = cuda_err(c, cudaMemcpyAsync(dt_hist_dev + (size_t)n * c->nproblems, dt_dev,
                                        sizeof(double) * c->nproblems, cudaMemcpyDeviceToDevice, s),
                     "dt history copy");
       if (rc) return rc;
     }
-    rc = step_cfl(c, U, dt_dev, s);
+    rc = step_cfl(c, U, dt_dev, s, &pc);
     if (rc) return rc;
   }
   return GBH_OK;
@@ -1389,9 +1479,10 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, s);
     if ((rc = cuda_err(c, e, "H2D copy"))) return rc;
     if (!given && (rc = reduce_dt(c, U, c->d_host_dt, nullptr, s))) return rc;
+    PrimChain pc;
     rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, c->d_host_dt, 0.0, true, s)
                                       : refined_step(c, U, c->d_host_dt, 0.0, true, s))
-                    : uniform_step(c, U, c->d_host_dt, 0.0, true, s);
+                    : uniform_step(c, U, c->d_host_dt, 0.0, true, s, &pc);
     if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
                            "dt finalize launch");
     if (rc) return rc;
@@ -1406,6 +1497,9 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
   // stage-1 launches still read U^n; chunk k goes back as soon as its stage 2
   // is done.  With dt given, copy-in, both stages and copy-out overlap.
   const int K = c->pipe_chunks;
+  // stage 1 leaves the primitives of U(1) for stage 2 (chunk k's stage 2 reads
+  // them only from the chunks whose stage 1 it waits for, like U(1) itself)
+  double* W1 = c->prim_carry ? c->d_W[0] : nullptr;
   cudaStream_t sin = c->pipe_stream[0], s1 = c->pipe_stream[1], s2 = c->pipe_stream[2], sout = c->pipe_stream[3];
   cudaEvent_t* ev_in = &c->pipe_ev[0];
   cudaEvent_t* ev_s1 = &c->pipe_ev[K];
@@ -1429,7 +1523,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
     if ((rc = cuda_err(c, cudaStreamWaitEvent(s1, ev_in[c->pipe_need[k]], 0), "event wait"))) return rc;
     rc = stage_launch(c, U, nullptr, c->d_scratch, c->d_host_dt, 0.0, 0.0, 1.0, true, false, s1, 0, nullptr,
-                      c->d_ident + first, cnt);
+                      c->d_ident + first, cnt, nullptr, W1);
     if (rc) return rc;
     if ((rc = cuda_err(c, cudaEventRecord(ev_s1[k], s1), "event record"))) return rc;
   }
@@ -1437,7 +1531,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
     if ((rc = cuda_err(c, cudaStreamWaitEvent(s2, ev_s1[c->pipe_need[k]], 0), "event wait"))) return rc;
     rc = stage_launch(c, c->d_scratch, U, c->d_pipe_out, c->d_host_dt, 0.0, 0.5, 0.5, true, true, s2, 0, nullptr,
-                      c->d_ident + first, cnt);
+                      c->d_ident + first, cnt, W1);
     if (rc) return rc;
     if ((rc = cuda_err(c, cudaEventRecord(ev_s2[k], s2), "event record"))) return rc;
   }

@@ -57,6 +57,11 @@ struct StageArgs {
   Eos eos;
   unsigned long long* smax_acc;     // if non-null: max signal-speed sum of Uout (bit pattern)
   unsigned long long* floor_count;  // floor applications on interior cells
+  // primitive variables carried from stage to stage (uniform grids, halo
+  // gathered; the layout of the state, interior cells only)
+  const double* Win;                // if non-null: the primitives of Uin (no floor counted on reading them)
+  double* Wout;                     // if non-null: the epilogue writes the primitives of Uout (and counts
+                                    // their floors)
   // two-level composite grids (all null on a uniform grid)
   const int* block_list;            // blocks to update (leaf blocks); null = all blocks
   int nlist;                        // entries of block_list

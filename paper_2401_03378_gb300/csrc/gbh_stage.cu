@@ -59,6 +59,26 @@ __device__ __forceinline__ bool corrected_cell(const StageArgs& a, int b, int i,
          (j == N - 1 && on(FACE_YP)) || (DIM3 && k == 0 && on(FACE_ZM)) || (DIM3 && k == nz - 1 && on(FACE_ZP));
 }
 
+// Primitives of a cell of the stage's input, in load_prim's addressing: read
+// from a.Win, where the epilogue of the stage that produced Uin left them
+// (calcEos of Alg. "Intra stage calculations for Spark" runs once per stage,
+// after updSoln; that stage also counted their floors), or converted from Uin
+// when the input comes from outside the stage sequence.  Ring stages read
+// guard cells, which carry no primitives, and always convert.
+template <int N, int E>
+__device__ __forceinline__ int stage_prim(const StageArgs& a, const Eos& e, int b, int i, int j, int k, double W[5]) {
+  if (E == 0 && a.Win) {
+    const long long o = cell_offset<N>(a, b, i, j, k);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) W[v] = __ldg(a.Win + o + v * a.lay.vstride);
+    return 0;
+  }
+  return load_prim<N>(a, e, b, i, j, k, W);
+}
+
+// Hint: fetch the line holding *p into L1 (PTX prefetch; no register, no wait).
+__device__ __forceinline__ void prefetch_l1(const double* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // Threads of a stage CTA: one per column of the band, except the 2 x 2
 // corner columns of an unsplit ring-2 tile (N (N + 8), 384 = 12 whole warps at
 // N = 16, against 400 = 12.5).
@@ -144,11 +164,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
-    load_prim<N>(a, e, b, ci, cj, k0 - 2, Wm2);
-    load_prim<N>(a, e, b, ci, cj, k0 - 1, Wm1);
-    const int h0 = load_prim<N>(a, e, b, ci, cj, k0, W0);
+    stage_prim<N, E>(a, e, b, ci, cj, k0 - 2, Wm2);
+    stage_prim<N, E>(a, e, b, ci, cj, k0 - 1, Wm1);
+    const int h0 = stage_prim<N, E>(a, e, b, ci, cj, k0, W0);
     if (counted(k0)) hits += h0;
-    const int h1 = load_prim<N>(a, e, b, ci, cj, k0 + 1, Wp1);
+    const int h1 = stage_prim<N, E>(a, e, b, ci, cj, k0 + 1, Wp1);
     if (counted(k0 + 1)) hits += h1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -166,15 +186,35 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     hllc_flux(wl, wr, e, f);
     Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
   } else {
-    const int h0 = load_prim<N>(a, e, b, ci, cj, 0, W0);
+    const int h0 = stage_prim<N, E>(a, e, b, ci, cj, 0, W0);
     if (col_in) hits += h0;
   }
 
   for (int k = k0; k < k1; ++k) {
     double Fzp[5], Wn[5], qpn[5];
+    if constexpr (E == 0) {
+      // Into L1 ahead of their use: the conserved operands of this plane's
+      // update (D), which nothing else reads when the primitives come from
+      // a.Win, and the z march's cell of the next iteration (plane k + 3 of
+      // this column, while it lies in the block): -0.7% per step.  (A ring
+      // stage reads its update operands two planes earlier with its
+      // primitives; the hint there measured 0.4% slower.)
+      const long long pb =
+          (long long)b * L.bstride + ((long long)(k + L.gz) * L.nyp + (cj + L.g)) * L.nxp + (ci + L.g);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        prefetch_l1(a.Uin + pb + v * L.vstride);
+        if (a.combine) prefetch_l1(a.Un + pb + v * L.vstride);
+      }
+      if (DIM3 && k + 3 < L.nz) {
+        const double* src = a.Win ? a.Win : a.Uin;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) prefetch_l1(src + pb + 3LL * L.nyp * L.nxp + v * L.vstride);
+      }
+    }
     if (DIM3) {
       // own column: primitives at k+2, face states of k+1, z flux at k + 1/2
-      const int hn = load_prim<N>(a, e, b, ci, cj, k + 2, Wn);
+      const int hn = stage_prim<N, E>(a, e, b, ci, cj, k + 2, Wn);
       if (counted(k + 2)) hits += hn;
       double qmz[5];
 #pragma unroll
@@ -235,7 +275,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
           j = cy < E ? cy : N + cy;
         }
         double W[5];
-        load_prim<N>(a, e, b, i - E, j - E, k, W);
+        stage_prim<N, E>(a, e, b, i - E, j - E, k, W);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sW[GBH_IX((v * PY + j + 2) * PX + i + 2, 5 * PY * PX)] = W[v];
       }
@@ -260,7 +300,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         }
         if (!need) continue;
         double W[5];
-        load_prim<N>(a, e, b, i - E, y0 + j - E, k, W);
+        stage_prim<N, E>(a, e, b, i - E, y0 + j - E, k, W);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sW[GBH_IX((v * PY + j + 2) * PX + i + 2, 5 * PY * PX)] = W[v];
       }
@@ -430,11 +470,19 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       if (DIM3 && k == L.nz - 1 && fsl[FACE_ZP] >= 0)
         for (int v = 0; v < 5; ++v) a.flux_reg[GBH_IX(fsl[FACE_ZP] * ss + (v * n2 + cj) * N + ci, a.flux_reg_len)] = Fzp[v];
     }
-    if (E == 0 && a.smax_acc) {
+    if (E == 0 && (a.smax_acc || a.Wout)) {
+      // calcEos of the new state: the CFL speed, and the next stage's primitives
       double W[5], ir;
-      cons_to_prim_ir(out, W, e, ir);
-      const double sp = signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3);
-      if (!corrected_cell<N, DIM3>(a, b, ci, cj, k, L.nz)) smax = fmax(smax, sp);
+      const int h = cons_to_prim_ir(out, W, e, ir);
+      if (a.Wout) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) a.Wout[GBH_IX(base + v * L.vstride, (long long)L.nblocks * L.bstride)] = W[v];
+        hits += h;
+      }
+      if (a.smax_acc) {
+        const double sp = signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3);
+        if (!corrected_cell<N, DIM3>(a, b, ci, cj, k, L.nz)) smax = fmax(smax, sp);
+      }
     }
 
     if (DIM3) {

@@ -237,6 +237,16 @@ class Hydro:
         self._check(self.lib.gbh_set_rk_stages(self.ctx, int(nstages)))
         self.nstages = int(nstages)
 
+    def set_prim_carry(self, enable: bool = True):
+        """Carry each stage's primitive variables to the next stage (on by default
+        on uniform contexts; the results do not depend on it, bit for bit)."""
+        self._check(self.lib.gbh_set_prim_carry(self.ctx, int(bool(enable))))
+
+    def prim_carry(self) -> bool:
+        out = C.c_int(0)
+        self._check(self.lib.gbh_get_prim_carry(self.ctx, C.byref(out)))
+        return bool(out.value)
+
     # -- adjoint ------------------------------------------------------------
     def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None, U1=None):
         """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen).

@@ -48,7 +48,9 @@ FLOPS_STAGE2 = 585 + 11
 # FP64 peak derived from the nominal GB300 rate (1.25 TFLOP/s) at 152 SMs and
 # 2070 MHz: 2 FP64 FMA lanes per SM per clock -> 152 * 2 * 2 * 2.07e9.
 FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2.07e9
-ALG_BYTES_PER_ZONE = 200  # stage 1: read U^n, write U1 (80 B); stage 2: read U1, U^n, write U^{n+1} (120 B)
+# stage 1: read U^n and its primitives, write U1 and its primitives (160 B);
+# stage 2: read U1, its primitives and U^n, write U^{n+1} and its primitives (200 B)
+ALG_BYTES_PER_ZONE = 360
 
 
 def log(*a):

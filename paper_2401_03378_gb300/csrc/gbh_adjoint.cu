@@ -110,11 +110,11 @@ __device__ __forceinline__ void prim_vjp(const double W[5], bool fr, bool fp, co
   bU[0] = fr ? 0.0 : fma(half_any(bp), k2, fma(-ir, uw, bW[0]));
 }
 
-// Reverse of hllc_flux (gbh_device.cuh): the forward is recomputed in the same
-// arrangement (one reciprocal square root of rho_L rho_R, the Roe sound speed
-// from w_L c_L^2 + w_R c_R^2 + (gamma-1)/2 w_L w_R |u_L - u_R|^2, the star
-// state through t = u_K + g), then (dF/dW)^T bF is accumulated step by step
-// in reverse.  Branches (the min / max of the wave-speed bounds, the side K,
+// Reverse of hllc_flux (gbh_device.cuh): the forward is recomputed from the
+// same formulas, grouped for the reverse sweep (one reciprocal square root of
+// rho_L rho_R, the Roe sound speed from w_L c_L^2 + w_R c_R^2 + (gamma-1)/2
+// w_L w_R |u_L - u_R|^2, the star state through t = u_K + g), then
+// (dF/dW)^T bF is accumulated step by step in reverse.  Branches (the min / max of the wave-speed bounds, the side K,
 // the fan) keep the forward's decisions and are taken by selects.
 __device__ __forceinline__ void hllc_flux_vjp(const double WL[5], const double WR[5], const Eos& e, const double bF[5],
                               double bWL[5], double bWR[5]) {

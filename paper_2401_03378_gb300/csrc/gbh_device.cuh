@@ -113,9 +113,11 @@ __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, 
                                                   double idy, double idz, bool dim3) {
   const Rk& k = e.k;
   const double c = sqrt_nr(mul(mul(e.gamma, W[4], k), ir, k), k);
-  double s = mul(add(fabs(W[1]), c, k), idx, k);
-  s = fma(add(fabs(W[2]), c, k), idy, s);
-  if (dim3) s = fma(add(fabs(W[3]), c, k), idz, s);
+  // sum_d (|u_d| + c) / dx_d = c (1/dx + 1/dy [+ 1/dz]) + |u| / dx + |v| / dy [+ |w| / dz]
+  const double isum = dim3 ? add(add(idx, idy, k), idz, k) : add(idx, idy, k);
+  double s = fma(fabs(W[1]), idx, mul(c, isum, k));
+  s = fma(fabs(W[2]), idy, s);
+  if (dim3) s = fma(fabs(W[3]), idz, s);
   return s;
 }
 
@@ -138,14 +140,16 @@ __device__ __forceinline__ double signal_speed_ir(const double W[5], double ir, 
 //
 // The Roe averages are evaluated in an algebraically equal form with fewer
 // FP64 operations.  One reciprocal square root q = 1/sqrt(rho_L rho_R) gives
-// 1/rho_L = rho_R q^2, 1/rho_R = rho_L q^2 and r = sqrt(rho_R / rho_L) =
-// rho_R q; the weights are w_L = 1 / (1 + r), w_R = r w_L; and, because
-// H_K = c_K^2 / (gamma-1) + |u_K|^2 / 2 and w_L + w_R = 1,
+// c_L^2 = gamma p_L / rho_L = p_L rho_R (gamma q^2), c_R^2 = p_R rho_L (gamma q^2)
+// and r = sqrt(rho_R / rho_L) = rho_R q; the weights are w_L = 1 / (1 + r),
+// w_R = r w_L; and, because H_K = c_K^2 / (gamma-1) + |u_K|^2 / 2 and
+// w_L + w_R = 1,
 //   c~^2 = (gamma-1) (H~ - |u~|^2 / 2) = w_L c_L^2 + w_R c_R^2
-//          + (gamma-1)/2 w_L w_R |u_L - u_R|^2,
+//          + (gamma-1)/2 w_L w_R |u_L - u_R|^2
+//        = w_L c_L^2 + w_R (c_R^2 + (gamma-1)/2 w_L |u_L - u_R|^2),
 // a sum of non-negative terms (no cancellation at high Mach number), so the
 // transverse Roe velocities and H~ are not formed.  h_K is formed for the
-// chosen side only, and u~ = u_L - w_R (u_L - u_R).  82 FP64 operations per face.
+// chosen side only, and u~ = u_L - w_R (u_L - u_R).  80 FP64 operations per face.
 __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5], const Eos& e,
                                           double F[5]) {
   const Rk& k = e.k;
@@ -153,9 +157,8 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
   const double rR = WR[0], uR = WR[1], vR = WR[2], wR = WR[3], pR = WR[4];
 
   const double q = rsqrt_nr(mul(rL, rR, k), k);          // 1/sqrt(rho_L rho_R)
-  const double q2 = mul(q, q, k);
-  const double iL = mul(rR, q2, k), iR = mul(rL, q2, k);   // 1/rho
-  const double cL2 = mul(mul(e.gamma, pL, k), iL, k), cR2 = mul(mul(e.gamma, pR, k), iR, k);   // c^2
+  const double gq2 = mul(mul(e.gamma, q, k), q, k);        // gamma / (rho_L rho_R)
+  const double cL2 = mul(mul(pL, rR, k), gq2, k), cR2 = mul(mul(pR, rL, k), gq2, k);   // c^2
   const double cL = sqrt_nr(cL2, k), cR = sqrt_nr(cR2, k);
 
   const double r = mul(rR, q, k);                          // sqrt(rho_R / rho_L)
@@ -163,7 +166,7 @@ __device__ __forceinline__ void hllc_flux(const double WL[5], const double WR[5]
   const double du = sub(uL, uR, k), dv = sub(vL, vR, k), dw = sub(wL, wR, k);
   const double ut = fma(-wr, du, uL);                      // w_L u_L + w_R u_R
   const double du2 = fma(dw, dw, fma(dv, dv, mul(du, du, k)));
-  const double ct = sqrt_nr(fma(mul(e.hgm1, mul(wl, wr, k), k), du2, fma(wl, cL2, mul(wr, cR2, k))), k);
+  const double ct = sqrt_nr(fma(wl, cL2, mul(wr, fma(mul(e.hgm1, wl, k), du2, cR2), k)), k);
 
   const double SL = min_d(sub(uL, cL, k), sub(ut, ct, k));
   const double SR = max_d(add(uR, cR, k), add(ut, ct, k));

@@ -322,6 +322,14 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     //     wx1 - 1/2 and y = wy1 - 1/2, each forming the two face states it
     //     needs from the primitives (the same arithmetic as the slope items):
     //     so (C) is exactly 2 Wx Wy faces (two full passes of an unsplit CTA).
+    //     In the inner planes of the unsplit ring-2 tile the next stage reads
+    //     the slab lines (the 2 + 2 rows and columns outside the interior)
+    //     only at the N interior positions, so these lines need no face past
+    //     position N + 2 (the face between tile cells N + 1 and N + 2, which
+    //     the list takes instead of their boundary face) and (C) skips their
+    //     faces outside [2, N + 2): (C) is then 2 N (N + 8) faces, exactly
+    //     two passes of the N (N + 8) threads.
+    const bool trim = E == 2 && S == 1 && !outer;
     const int TRX = (Wx + 4) / 3, TRY = (Wy + 4) / 3;   // triples per line (W + 2 slope cells)
     const int NSX = TRX * Wy, NSY = TRY * Wx;
     for (int s = rtid; s < NSX + NSY + Wy + Wx; s += NT) {
@@ -330,8 +338,10 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         const bool xf = f < Wy;
         const int line = xf ? f : f - Wy;                       // window row (x face) or column (y face)
         const int step = xf ? 1 : PX;
-        // positions wx1 - 2 .. wx1 + 1 along x (or wy1 - 2 .. wy1 + 1 along y)
-        const int first = xf ? (wy0 + line + 2) * PX + wx1 : wy1 * PX + wx0 + line + 2;
+        const bool slab = trim && (line < 2 || line >= M - 2);
+        const int pos = xf ? (slab ? M - 2 : wx1) : (slab ? M - 2 : wy1);   // the face pos - 1/2
+        // positions pos - 2 .. pos + 1 along x (or y)
+        const int first = xf ? (wy0 + line + 2) * PX + pos : pos * PX + wx0 + line + 2;
         double ql[5], qr[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -347,8 +357,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         double F[5];
         hllc_flux(wl, wr, e, F);
         const int fs = xf ? FXS : FYS;
-        double* o = xf ? sFx + GBH_IX((wy0 + line) * (M + 1) + wx1, FXS)
-                       : sFy + GBH_IX(wy1 * M + wx0 + line, FYS);
+        double* o = xf ? sFx + GBH_IX((wy0 + line) * (M + 1) + pos, FXS)
+                       : sFy + GBH_IX(pos * M + wx0 + line, FYS);
         o[0] = F[0]; o[vn * fs] = F[1]; o[vt * fs] = F[2]; o[3 * fs] = F[3]; o[4 * fs] = F[4];
         continue;
       }
@@ -391,20 +401,33 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     // (C) HLLC on the x faces (i - 1/2, i in [wx0, wx1)) and y faces (j - 1/2,
     //     j in [wy0, wy1)) of the window; the faces at wx1 - 1/2 and wy1 - 1/2
     //     came with (B)
-    for (int f = tid; f < 2 * Wx * Wy; f += NT) {
-      const bool xf = f < Wx * Wy;
+    // (in the inner planes of the ring-2 tile: N full lines of M faces, then
+    //     the 4 slab lines at positions [2, N + 2), per direction)
+    const int nper = trim ? N * (N + 8) : Wx * Wy;
+    for (int f = tid; f < 2 * nper; f += NT) {
+      const bool xf = f < nper;
       int i, j;                    // band positions
       const double *ql, *qr;       // minus/plus state arrays, var stride vs
       int vs, ol, orr;
+      int line = 0, pos = 0;       // trimmed mapping: face pos - 1/2 of line
+      if (trim) {
+        const int g = xf ? f : f - nper;
+        if (g < N * M) {
+          line = 2 + g / M; pos = g - (line - 2) * M;
+        } else {
+          const int h = g - N * M, sl = h / N;
+          line = sl < 2 ? sl : N + sl; pos = 2 + h - sl * N;
+        }
+      }
       if (xf) {
-        i = f % Wx + wx0; j = f / Wx + wy0;
+        if (trim) { i = pos; j = line; } else { i = f % Wx + wx0; j = f / Wx + wy0; }
         vs = QXS;
         ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
         orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
         const int f2 = f - Wx * Wy;
-        i = f2 % Wx + wx0; j = f2 / Wx + wy0;
+        if (trim) { i = line; j = pos; } else { i = f2 % Wx + wx0; j = f2 / Wx + wy0; }
         vs = QYS;
         ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
         orr = (j + 1) * M + i;                // minus state of cell j (slot j+1)

@@ -1,0 +1,95 @@
+"""Index maps of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), restated
+on the CPU: the thread -> column map, and the face lists of the inner planes.
+
+The telescoping variant's first stage (Sec. 4.2) updates the interior widened
+by 2 cells; the next stage reads that output in its own box and in the 2-deep
+slabs across its faces, never in the 2 x 2 corner columns.  The kernel
+launches N (N + 8) threads (no thread for a corner column) and, in the inner
+planes, forms only the faces the update of those columns reads: every face of
+the N interior lines, the faces at positions [2, N + 2] of the 4 slab lines.
+These tests check that the maps are one-to-one, cover exactly what the update
+reads, and give whole warps and exactly two passes of the face list."""
+import pytest
+
+E = 2
+
+
+def thread_columns(N):
+    """(tx, ty) tile position of each thread: rows above the interior (interior
+    columns only), the interior rows (all columns), the rows below."""
+    M = N + 2 * E
+    out = []
+    for tid in range(N * (N + 4 * E)):
+        if tid < E * N:
+            ty, tx = tid // N, E + tid % N
+        elif tid < E * N + N * M:
+            r = tid - E * N
+            ty, tx = E + r // M, r % M
+        else:
+            r = tid - E * N - N * M
+            ty, tx = E + N + r // N, E + r % N
+        out.append((tx, ty))
+    return out
+
+
+def face_list_c(N):
+    """Faces of phase (C) in the inner planes: ('x', i, j) is the x face
+    i - 1/2 of row j, ('y', i, j) the y face j - 1/2 of column i."""
+    M = N + 2 * E
+    nper = N * (N + 8)
+    out = []
+    for f in range(2 * nper):
+        xf = f < nper
+        g = f if xf else f - nper
+        if g < N * M:
+            line = 2 + g // M
+            pos = g - (line - 2) * M
+        else:
+            h = g - N * M
+            sl = h // N
+            line = sl if sl < 2 else N + sl
+            pos = 2 + h - sl * N
+        out.append(("x", pos, line) if xf else ("y", line, pos))
+    return out
+
+
+def boundary_faces_b(N):
+    """The faces the slope phase (B) solves: the tile's upper boundary face of
+    every line, or, on a slab line, the face at position N + 2."""
+    M = N + 2 * E
+    out = []
+    for f in range(2 * M):
+        xf = f < M
+        line = f if xf else f - M
+        pos = M - 2 if (line < 2 or line >= M - 2) else M
+        out.append(("x", pos, line) if xf else ("y", line, pos))
+    return out
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_threads_cover_the_columns_but_the_corners(N):
+    M = N + 2 * E
+    cols = thread_columns(N)
+    assert len(set(cols)) == len(cols) == N * (N + 8)
+    corner = {(x, y) for x in range(M) for y in range(M)
+              if not (E <= x < E + N) and not (E <= y < E + N)}
+    assert len(corner) == 4 * E * E
+    assert set(cols) == {(x, y) for x in range(M) for y in range(M)} - corner
+    if N == 16:
+        assert len(cols) == 384 and len(cols) % 32 == 0
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_face_lists_are_exactly_what_the_update_reads(N):
+    M = N + 2 * E
+    c, b = face_list_c(N), boundary_faces_b(N)
+    assert len(set(c)) == len(c) and len(set(b)) == len(b) and not set(c) & set(b)
+    for d, i, j in c + b:
+        assert 0 <= i <= M and 0 <= j <= M
+    need = set()
+    for tx, ty in thread_columns(N):
+        need |= {("x", tx, ty), ("x", tx + 1, ty), ("y", tx, ty), ("y", tx, ty + 1)}
+    assert set(c) | set(b) == need
+    # two full passes of the threads, against 2 M^2 faces (a third, partial pass) untrimmed
+    assert len(c) == 2 * len(thread_columns(N))
+    assert 2 * M * M > len(c)

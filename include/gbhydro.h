@@ -221,16 +221,18 @@ int gbh_set_rk_stages(gbh_ctx *ctx, int nstages);
  * and hydro_step_host from stage 1 to stage 2.  Results, dt and floor
  * counts are bit for bit those of the carry off (a floor is counted by the
  * stage whose output it is found in, once per interior cell and stage, as
- * when the next stage converted).  Applies to uniform and batched contexts in
- * the non-telescoping mode; telescoping steps, two-level contexts, single
- * stages, the adjoint and hydro_step_static always convert.
- * gbh_create / gbh_create_batched allocate the arrays (2 x
- * gbh_state_bytes) and switch the carry on; if that allocation fails the
- * carry stays off and the context is created all the same.
- * gbh_set_prim_carry(ctx, 0) frees the arrays (synchronises the device);
- * enable != 0 allocates them again (GBH_ERR_NOMEM if it cannot; no effect on
- * a two-level context).  gbh_get_prim_carry writes 1 to *enabled when the
- * carry is on.  Drops a captured graph. */
+ * when the next stage converted).  On two-level contexts (all-levels steps)
+ * the restriction, the prolongation and the flux correction also write the
+ * primitives of the cells they write (the correction counts the floors of the
+ * corrected value in place of the uncorrected one).  Applies to uniform,
+ * batched and two-level contexts in the non-telescoping mode; telescoping
+ * steps, single stages, the adjoint and hydro_step_static always convert.
+ * Every gbh_create* allocates the arrays (2 x gbh_state_bytes) and switches
+ * the carry on; if that allocation fails the carry stays off and the context
+ * is created all the same.  gbh_set_prim_carry(ctx, 0) frees the arrays
+ * (synchronises the device); enable != 0 allocates them again
+ * (GBH_ERR_NOMEM if it cannot).  gbh_get_prim_carry writes 1 to *enabled
+ * when the carry is on.  Drops a captured graph. */
 int gbh_set_prim_carry(gbh_ctx *ctx, int enable);
 int gbh_get_prim_carry(gbh_ctx *ctx, int *enabled);
 

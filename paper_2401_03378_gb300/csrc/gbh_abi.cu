@@ -223,15 +223,20 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
 // boundary.  Uin's covered blocks and fine guard cells are rewritten.  With
 // dt_epilogue (the last stage) the stage kernel and the correction also leave
 // the CFL signal-speed max of the leaf cells of Uout in the accumulator.
+// Win (the primitive carry): the primitives of Uin's leaf cells, to which the
+// restriction and the prolongation add those of the cells they write, so the
+// stage reads no conserved cell it would have to convert; Wout: where the
+// stage and the correction leave the primitives of Uout.
 int refined_stage(gbh_ctx* c, double* Uin, const double* Un, double* Uout, const double* dt_dev, double dt,
-                  double a, double b, bool dt_epilogue, cudaStream_t s) {
-  int rc = cuda_err(c, gbh::launch_restrict(Uin, c->amr, s), "restrict launch");
+                  double a, double b, bool dt_epilogue, cudaStream_t s, double* Win = nullptr,
+                  double* Wout = nullptr) {
+  int rc = cuda_err(c, gbh::launch_restrict(Uin, c->amr, s, Win), "restrict launch");
   if (rc) return rc;
-  rc = cuda_err(c, gbh::launch_prolong(Uin, c->amr, 2, true, s), "prolong launch");
+  rc = cuda_err(c, gbh::launch_prolong(Uin, c->amr, 2, true, s, Win), "prolong launch");
   if (rc) return rc;
-  rc = stage_launch(c, Uin, Un, Uout, dt_dev, dt, a, b, true, dt_epilogue, s);
+  rc = stage_launch(c, Uin, Un, Uout, dt_dev, dt, a, b, true, dt_epilogue, s, 0, nullptr, nullptr, 0, Win, Wout);
   if (rc) return rc;
-  return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, dt_epilogue ? c->d_smax : nullptr, s),
+  return cuda_err(c, gbh::launch_reflux(Uout, c->amr, dt_dev, dt, b, dt_epilogue ? c->d_smax : nullptr, s, Wout),
                   "reflux launch");
 }
 
@@ -263,33 +268,47 @@ double* stage_out(gbh_ctx* c, int s, double* U) {
 
 double* flux_regs(gbh_ctx* c, int s) { return s == 0 ? c->d_flux_reg : s == 1 ? c->d_flux_reg2 : c->d_flux_reg3; }
 
-// One SSP-RK step on a two-level grid, all-levels non-telescoping; ends with
-// the restriction of the new state so that covered coarse cells hold the
-// mean of their children.  dt_epilogue: the CFL max of the new leaf cells goes
-// into the accumulator (the restriction changes covered blocks only).
-int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s) {
-  const RkCoef r = rk_coef(c->nstages);
-  double* in = U;
-  for (int st = 0; st < r.S; ++st) {
-    double* out = stage_out(c, st, U);
-    int rc = refined_stage(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st],
-                           dt_epilogue && st == r.S - 1, s);
-    if (rc) return rc;
-    in = out;
-  }
-  return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
-}
-
 // Primitive variables carried through the stages of one entry-point call
-// (uniform grids, non-telescoping): `in` is the array holding the primitives
-// of the current state (-1: none, so the next stage converts on load); each
-// stage's epilogue writes those of its output into the other array, except
-// the call's last stage unless last_out.  A state handed in by the caller is
+// (non-telescoping steps): `in` is the array holding the primitives of the
+// current state (-1: none, so the next stage converts on load); each stage's
+// epilogue writes those of its output into the other array, except the
+// call's last stage unless last_out.  A state handed in by the caller is
 // always converted on load.
 struct PrimChain {
   int in = -1;
   bool last_out = false;
 };
+
+// The primitive arrays stage st of r reads and writes under the chain pc (null
+// when the carry is off), and the chain advanced past the stage.
+void chain_stage(gbh_ctx* c, PrimChain* pc, bool last, double** Win, double** Wout) {
+  *Win = *Wout = nullptr;
+  if (!pc || c->telescoping || !c->prim_carry || !c->d_W[0]) return;
+  const int wo = (!last || pc->last_out) ? (pc->in == 0 ? 1 : 0) : -1;
+  if (pc->in >= 0) *Win = c->d_W[pc->in];
+  if (wo >= 0) *Wout = c->d_W[wo];
+  pc->in = wo;
+}
+
+// One SSP-RK step on a two-level grid, all-levels non-telescoping; ends with
+// the restriction of the new state so that covered coarse cells hold the
+// mean of their children.  dt_epilogue: the CFL max of the new leaf cells goes
+// into the accumulator (the restriction changes covered blocks only).
+int refined_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt_epilogue, cudaStream_t s,
+                 PrimChain* pc = nullptr) {
+  const RkCoef r = rk_coef(c->nstages);
+  double* in = U;
+  for (int st = 0; st < r.S; ++st) {
+    double* out = stage_out(c, st, U);
+    double *Win, *Wout;
+    chain_stage(c, pc, st == r.S - 1, &Win, &Wout);
+    int rc = refined_stage(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st],
+                           dt_epilogue && st == r.S - 1, s, Win, Wout);
+    if (rc) return rc;
+    in = out;
+  }
+  return cuda_err(c, gbh::launch_restrict(U, c->amr, s), "restrict launch");
+}
 
 // One SSP-RK step on a uniform (or batched) grid.  Non-telescoping: every
 // stage gathers its halo from the neighbours.  Telescoping (Sec. 4.2): one
@@ -306,20 +325,13 @@ int uniform_step(gbh_ctx* c, double* U, const double* dt_dev, double dt, bool dt
     gbh::FillArgs F{U, c->d_nbr, c->d_face, c->lay};
     if ((rc = cuda_err(c, gbh::launch_fill(F, s), "fill kernel launch"))) return rc;
   }
-  const bool carry = pc && !c->telescoping && c->prim_carry && c->d_W[0];
   const double* in = U;
   for (int st = 0; st < r.S; ++st) {
     double* out = stage_out(c, st, U);
     const bool last = st == r.S - 1;
     const int ring = c->telescoping ? 2 * (r.S - 1 - st) : 0;
-    const double* Win = nullptr;
-    double* Wout = nullptr;
-    if (carry) {
-      const int wo = (!last || pc->last_out) ? (pc->in == 0 ? 1 : 0) : -1;
-      if (pc->in >= 0) Win = c->d_W[pc->in];
-      if (wo >= 0) Wout = c->d_W[wo];
-      pc->in = wo;
-    }
+    double *Win, *Wout;
+    chain_stage(c, pc, last, &Win, &Wout);
     rc = stage_launch(c, in, st ? U : nullptr, out, dt_dev, dt, r.a[st], r.b[st], !c->telescoping,
                       last && dt_epilogue, s, ring, nullptr, nullptr, 0, Win, Wout);
     if (rc) return rc;
@@ -533,7 +545,7 @@ extern "C" int gbh_destroy(gbh_ctx* c);
 
 static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimChain* pc) {
   int rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, dt_dev, 0.0, true, s)
-                                        : refined_step(c, U, dt_dev, 0.0, true, s))
+                                        : refined_step(c, U, dt_dev, 0.0, true, s, pc))
                       : uniform_step(c, U, dt_dev, 0.0, true, s, pc);
   if (rc) return rc;
   return cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, dt_dev, nullptr, s, c->nproblems),
@@ -546,7 +558,6 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimC
 // be allocated the carry stays off and every stage converts on load (the
 // results are the same bit for bit); returns whether it is on.
 static bool alloc_prim_buffers(gbh_ctx* c) {
-  if (c->refined) return false;
   if (!c->d_W[0]) {
     const size_t bytes = sizeof(double) * state_elems(c->lay);
     double *w0 = nullptr, *w1 = nullptr;
@@ -819,6 +830,8 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.flux_reg_len = (long long)c->flux_reg_doubles;
   A.inv_dx = c->d_inv_dx;
   A.eos = c->eos;
+  A.floor_count = c->d_words + 1;
+  alloc_prim_buffers(c);
   *out = c;
   return GBH_OK;
 }
@@ -1017,7 +1030,6 @@ int gbh_set_prim_carry(gbh_ctx* c, int enable) {
     c->prim_carry = false;
     return cuda_err(c, e, "cudaDeviceSynchronize");
   }
-  if (c->refined) return GBH_OK;
   if (!alloc_prim_buffers(c)) return set_err(c, GBH_ERR_NOMEM, "primitive arrays: device allocation failed");
   return GBH_OK;
 }
@@ -1333,10 +1345,10 @@ int hydro_step(gbh_ctx* c, double* U, double dt, void* stream) {
   if ((rc = check_dt(c, dt))) return rc;
   if (!U || !aligned8(U)) return set_err(c, GBH_ERR_INVAL, "null or misaligned state pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  PrimChain pc;
   if (c->refined)
     return c->telescoping ? refined_telescoping_step(c, U, nullptr, dt, false, s)
-                          : refined_step(c, U, nullptr, dt, false, s);
-  PrimChain pc;
+                          : refined_step(c, U, nullptr, dt, false, s, &pc);
   return uniform_step(c, U, nullptr, dt, false, s, &pc);
 }
 
@@ -1481,7 +1493,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     if (!given && (rc = reduce_dt(c, U, c->d_host_dt, nullptr, s))) return rc;
     PrimChain pc;
     rc = c->refined ? (c->telescoping ? refined_telescoping_step(c, U, c->d_host_dt, 0.0, true, s)
-                                      : refined_step(c, U, c->d_host_dt, 0.0, true, s))
+                                      : refined_step(c, U, c->d_host_dt, 0.0, true, s, &pc))
                     : uniform_step(c, U, c->d_host_dt, 0.0, true, s, &pc);
     if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
                            "dt finalize launch");

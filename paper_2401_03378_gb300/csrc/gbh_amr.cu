@@ -15,6 +15,12 @@
 //    fine region is replaced by the mean of the fine fluxes through it:
 //    U += b dt (F_c - mean F_f) / dx (low side of the face; opposite sign on
 //    the high side), b = the stage's weight of L.
+// With a primitive array W (the primitive carry between the stages of an
+// all-levels step), each kernel also writes the primitive variables of the
+// cells it writes, so that the next stage reads them for every cell of its
+// stencil: restricted covered cells, prolonged fine guard cells, corrected
+// coarse cells (the conversion of the stage kernel, no floor counted: these
+// cells are read as halo or were counted by the stage that produced them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,9 +44,17 @@ __device__ __forceinline__ long long at(const Layout& L, int b, int v, int i, in
                 (long long)L.nblocks * L.bstride);
 }
 
+// Primitives of the conserved vector Uc at state offset o (cell offset, variable 0).
+__device__ __forceinline__ void write_prim(double* W, const Layout& L, long long o, const double Uc[5], const Eos& e) {
+  double Wp[5];
+  cons_to_prim(Uc, Wp, e);
+  for (int v = 0; v < 5; ++v) W[GBH_IX(o + v * L.vstride, (long long)L.nblocks * L.bstride)] = Wp[v];
+}
+
 // Restriction: one thread per (covered block, interior cell); 5 variables.
-__global__ void restrict_kernel(double* U, const AmrArgs a) {
+__global__ void restrict_kernel(double* U, const AmrArgs a, double* W) {
   const Layout& L = a.lay;
+  const Eos e = reg_eos(a.eos, thread_zero(a.eos));
   const int n[3] = {L.nx, L.ny, L.nz};
   const int h[3] = {L.nx / 2, L.ny / 2, L.ndim == 3 ? L.nz / 2 : 1};
   const long long per = (long long)L.nx * L.ny * L.nz;
@@ -57,13 +71,16 @@ __global__ void restrict_kernel(double* U, const AmrArgs a) {
     const int oct = (i / h[0]) + 2 * (j / h[1]) + (L.ndim == 3 ? 4 * (k / h[2]) : 0);
     const int child = __ldg(a.children + 8 * cb + oct);
     const int fi = 2 * (i % h[0]), fj = 2 * (j % h[1]), fk = L.ndim == 3 ? 2 * (k % h[2]) : 0;
+    double Uc[5];
     for (int v = 0; v < 5; ++v) {
       double s = 0.0;
       for (int dz = 0; dz < (L.ndim == 3 ? 2 : 1); ++dz)
         for (int dy = 0; dy < 2; ++dy)
           for (int dx = 0; dx < 2; ++dx) s = __dadd_rn(s, U[at(L, child, v, fi + dx, fj + dy, fk + dz)]);
-      U[at(L, cb, v, i, j, k)] = __dmul_rn(s, w);
+      Uc[v] = __dmul_rn(s, w);
+      U[at(L, cb, v, i, j, k)] = Uc[v];
     }
+    if (W) write_prim(W, L, at(L, cb, 0, i, j, k), Uc, e);
   }
 }
 
@@ -97,8 +114,9 @@ __device__ __forceinline__ int floor_div2(int x) { return x >= 0 ? x / 2 : -((1 
 // coarser level (neighbour code GBH_NBR_COARSER).  One thread per (task,
 // cell): a task is one fine block; `depth` limits the guard depth and
 // `faces_only` restricts to the face slabs (what the stage kernel reads).
-__global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_only) {
+__global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_only, double* W) {
   const Layout& L = a.lay;
+  const Eos eo = reg_eos(a.eos, thread_zero(a.eos));
   const int n[3] = {L.nx, L.ny, L.nz};
   const int gg[3] = {depth, depth, L.ndim == 3 ? depth : 0};
   const int ex[3] = {n[0] + 2 * gg[0], n[1] + 2 * gg[1], n[2] + 2 * gg[2]};
@@ -143,6 +161,7 @@ __global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_
       om[d] = coarse_offset(a, parent, Pm[0], Pm[1], Pm[2]);
       op[d] = coarse_offset(a, parent, Pp[0], Pp[1], Pp[2]);
     }
+    double Uf[5];
     for (int v = 0; v < 5; ++v) {
       const long long vo = v * L.vstride;
       const double q0 = U[oc + vo];
@@ -151,16 +170,19 @@ __global__ void prolong_kernel(double* U, const AmrArgs a, int depth, int faces_
         const double h = mc_half_slope(U[om[d] + vo], q0, U[op[d] + vo]);   // sigma / 2
         val = __dadd_rn(val, __dmul_rn(0.5 * h, (double)s[d]));
       }
+      Uf[v] = val;
       U[at(L, fb, v, c[0], c[1], c[2])] = val;
     }
+    if (W) write_prim(W, L, at(L, fb, 0, c[0], c[1], c[2]), Uf, eo);
   }
 }
 
 // Prolongation into the 2-deep face slabs that the stage kernel reads, for a
 // list of (fine block, face) pairs whose face neighbour lies on the coarser
 // level: one thread per (pair, slab cell).
-__global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
+__global__ void prolong_faces_kernel(double* U, const AmrArgs a, double* W) {
   const Layout& L = a.lay;
+  const Eos eo = reg_eos(a.eos, thread_zero(a.eos));
   const int N = L.nx;
   const int n2 = L.ndim == 3 ? N : 1;
   const long long per = 2LL * N * n2;
@@ -197,6 +219,7 @@ __global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
       om[e] = coarse_offset(a, parent, Pm[0], Pm[1], Pm[2]);
       op[e] = coarse_offset(a, parent, Pp[0], Pp[1], Pp[2]);
     }
+    double Uf[5];
     for (int v = 0; v < 5; ++v) {
       const long long vo = v * L.vstride;
       const double q0 = U[oc + vo];
@@ -205,8 +228,10 @@ __global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
         const double h = mc_half_slope(U[om[e] + vo], q0, U[op[e] + vo]);
         val = __dadd_rn(val, __dmul_rn(0.5 * h, (double)sg[e]));
       }
+      Uf[v] = val;
       U[at(L, fb, v, c[0], c[1], c[2])] = val;
     }
+    if (W) write_prim(W, L, at(L, fb, 0, c[0], c[1], c[2]), Uf, eo);
   }
 }
 
@@ -220,7 +245,8 @@ __global__ void prolong_faces_kernel(double* U, const AmrArgs a) {
 // signal-speed sum, which the stage kernel's epilogue left out, and adds it
 // to the step's max.
 __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrArgs a, const double* dt_dev,
-                                                          double dt_val, double coef, unsigned long long* smax_acc) {
+                                                          double dt_val, double coef, unsigned long long* smax_acc,
+                                                          double* W) {
   const Layout& L = a.lay;
   const long long zt = thread_zero(a.eos);
   const Eos e = reg_eos(a.eos, zt);   // FP64 constants in per-thread registers (gbh_fastmath.cuh)
@@ -257,8 +283,8 @@ __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrAr
     if (owner != en.face) continue;
     // the time step of the block's problem (one entry unless batched)
     const double dt = dt_dev ? dt_dev[a.problem ? __ldg(a.problem + en.block) : 0] : dt_val;
-    double Uc[5];
-    for (int v = 0; v < 5; ++v) Uc[v] = U[at(L, en.block, v, x[0], x[1], x[2])];
+    double Uc[5], U0[5];   // corrected, and as the stage left it
+    for (int v = 0; v < 5; ++v) U0[v] = Uc[v] = U[at(L, en.block, v, x[0], x[1], x[2])];
     for (int f = 0; f < nfaces; ++f) {
       if (!touches(f)) continue;
       const RefluxEntry& eg = a.reflux[__ldg(of + f)];
@@ -285,6 +311,16 @@ __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrAr
       }
     }
     for (int v = 0; v < 5; ++v) U[at(L, en.block, v, x[0], x[1], x[2])] = Uc[v];
+    if (W) {
+      // the stage's epilogue converted (and counted) the uncorrected value
+      // for the next stage; replace it, and count the corrected value's floors
+      // instead, as a conversion of this cell by the next stage would
+      double W0[5], Wc[5];
+      const long long o = at(L, en.block, 0, x[0], x[1], x[2]);
+      const int h0 = cons_to_prim(U0, W0, e), h1 = cons_to_prim(Uc, Wc, e);
+      for (int v = 0; v < 5; ++v) W[GBH_IX(o + v * L.vstride, (long long)L.nblocks * L.bstride)] = Wc[v];
+      if (h1 != h0) atomicAdd(a.floor_count, (unsigned long long)(long long)(h1 - h0));
+    }
     if (smax_acc) {
       double W[5], ir;
       cons_to_prim_ir(Uc, W, e, ir);
@@ -309,30 +345,30 @@ __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrAr
 
 GBH_CHECK_TAKE(check_take_amr)
 
-cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s) {
+cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s, double* W) {
   if (a.ncovered == 0) return cudaSuccess;
-  restrict_kernel<<<grid_for((long long)a.ncovered * a.lay.nx * a.lay.ny * a.lay.nz), kThreads, 0, s>>>(U, a);
+  restrict_kernel<<<grid_for((long long)a.ncovered * a.lay.nx * a.lay.ny * a.lay.nz), kThreads, 0, s>>>(U, a, W);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s) {
+cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s, double* W) {
   if (a.nfine == 0) return cudaSuccess;
   if (faces_only && depth == 2 && a.cf_faces) {
     const long long per = 2LL * a.lay.nx * (a.lay.ndim == 3 ? a.lay.nx : 1);
-    prolong_faces_kernel<<<grid_for(per * a.ncf_faces), kThreads, 0, s>>>(U, a);
+    prolong_faces_kernel<<<grid_for(per * a.ncf_faces), kThreads, 0, s>>>(U, a, W);
     return cudaGetLastError();
   }
   const Layout& L = a.lay;
   const long long per = (long long)(L.nx + 2 * depth) * (L.ny + 2 * depth) * (L.ndim == 3 ? L.nz + 2 * depth : 1);
-  prolong_kernel<<<grid_for(per * a.nfine), kThreads, 0, s>>>(U, a, depth, faces_only ? 1 : 0);
+  prolong_kernel<<<grid_for(per * a.nfine), kThreads, 0, s>>>(U, a, depth, faces_only ? 1 : 0, W);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, double dt, double coef,
-                          unsigned long long* smax_acc, cudaStream_t s) {
+                          unsigned long long* smax_acc, cudaStream_t s, double* W) {
   if (a.nreflux == 0) return cudaSuccess;
   const long long per = (long long)a.lay.nx * (a.lay.ndim == 3 ? a.lay.nx : 1);
-  reflux_kernel<<<grid_for(per * a.nreflux), kThreads, 0, s>>>(U, a, dt_dev, dt, coef, smax_acc);
+  reflux_kernel<<<grid_for(per * a.nreflux), kThreads, 0, s>>>(U, a, dt_dev, dt, coef, smax_acc, W);
   return cudaGetLastError();
 }
 

@@ -97,15 +97,19 @@ struct AmrArgs {
   const double* inv_dx;
   const int* problem;      // [nblocks] problem of each block (batched two-level ensembles), or null
   Eos eos;                 // for the CFL signal speed of corrected cells
+  unsigned long long* floor_count;  // the stage kernel's floor counter
 };
 
-cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s);
-cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s);
+// W: if non-null, a primitive array of the state's layout; each launch also
+// writes the primitives of the cells it writes there.
+cudaError_t launch_restrict(double* U, const AmrArgs& a, cudaStream_t s, double* W = nullptr);
+cudaError_t launch_prolong(double* U, const AmrArgs& a, int depth, bool faces_only, cudaStream_t s,
+                           double* W = nullptr);
 // smax_acc: if non-null, the max CFL signal-speed sum of the corrected cells
 // (after their correction) goes into smax_acc[problem] (bit pattern), the part
 // of the step's CFL reduction that the stage kernel's epilogue leaves out.
 cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, double dt, double coef,
-                          unsigned long long* smax_acc, cudaStream_t s);
+                          unsigned long long* smax_acc, cudaStream_t s, double* W = nullptr);
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 

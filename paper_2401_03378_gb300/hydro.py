@@ -238,8 +238,8 @@ class Hydro:
         self.nstages = int(nstages)
 
     def set_prim_carry(self, enable: bool = True):
-        """Carry each stage's primitive variables to the next stage (on by default
-        on uniform contexts; the results do not depend on it, bit for bit)."""
+        """Carry each stage's primitive variables to the next stage (on by default;
+        the results do not depend on it, bit for bit; telescoping steps never carry)."""
         self._check(self.lib.gbh_set_prim_carry(self.ctx, int(bool(enable))))
 
     def prim_carry(self) -> bool:

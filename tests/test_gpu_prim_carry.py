@@ -1,9 +1,11 @@
 """The primitive carry (gbh_set_prim_carry): every stage's epilogue leaves the
 primitive variables of its output for the next stage, which then reads them
 instead of converting its input (calcEos once per stage, after updSoln, as in
-Alg. "Intra stage calculations for Spark").  With the carry on, every entry
-point gives the states, dt and dt histories of the carry off bit for bit, and
-the same floor counts; telescoping and two-level contexts never carry."""
+Alg. "Intra stage calculations for Spark"); on two-level grids the restriction,
+the prolongation and the flux correction add the primitives of the cells they
+write.  With the carry on, every entry point gives the states, dt and dt
+histories of the carry off bit for bit, and the same floor counts; telescoping
+steps never carry."""
 import numpy as np
 import pytest
 
@@ -155,7 +157,98 @@ def test_batched_ensemble_bitwise(gb):
     on_and_off(gb, lambda: gb.Hydro.from_batch(lats), U0)
 
 
-def test_telescoping_and_two_level_never_carry(gb):
+TWO_LEVEL = {
+    "box-3d": wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3)),
+    "L-2d": wl.two_level_blocks(wl.lattice_2d(5, 5, 8, 8, 4), [(1, 1), (2, 1), (3, 1), (1, 2), (1, 3)]),
+    "tripod-3d-periodic": wl.two_level_blocks(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4, bc="periodic"),
+                                              [(1, 1, 1), (2, 1, 1), (1, 2, 1), (1, 1, 2)]),
+    "box-2d-16": wl.two_level(wl.lattice_2d(4, 4, 16, 16, 4), (1, 1), (3, 3)),
+}
+
+
+def smooth_two_level(tl, seed):
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0, 2 * np.pi, 8)
+    nd = tl.coarse.ndim
+
+    def fn(X, Y, Z):
+        s = np.sin(2 * np.pi * X + ph[0]) * np.cos(2 * np.pi * Y + ph[1])
+        if nd == 3:
+            s = s * np.cos(2 * np.pi * Z + ph[2])
+        return (1 + 0.4 * s, 0.5 * np.sin(2 * np.pi * Y + ph[3]) + 0 * X, 0.4 * np.cos(2 * np.pi * X + ph[4]),
+                (0.3 * np.sin(2 * np.pi * X + ph[5]) if nd == 3 else 0 * X), 1 + 0.3 * s)
+    return wl.two_level_state(tl, fn)
+
+
+def floor_cells(tl, U, seed):
+    """Plant E = |m|^2 / (4 rho) (a negative pressure, floored) in a few coarse
+    leaf cells next to the refined region, whose flux correction changes them
+    after every stage, and in a few fine cells at the coarse-fine boundary."""
+    c = tl.coarse
+    nd, n = c.ndim, c.n[0]
+    zs, ys, xs = c.interior_slices()
+    rng = np.random.default_rng(seed)
+    picks = []
+    for b in range(tl.n0):
+        if tl.covered(b):
+            continue
+        bc = c.block_coords(b)
+        for d in range(nd):
+            for side in (0, 1):
+                nbc = list(bc)
+                nbc[d] += 1 if side else -1
+                if not (0 <= nbc[d] < c.nb[d]):
+                    continue
+                nb = nbc[0] + c.nb[0] * (nbc[1] + c.nb[1] * nbc[2])
+                if tl.covered(nb):
+                    cell = [int(rng.integers(n)) for _ in range(3)]
+                    if nd == 2:
+                        cell[2] = 0
+                    cell[d] = n - 1 if side else 0
+                    picks.append((b, cell))
+    for fb in [g for g in tl.gpu_blocks if g >= tl.n0][:3]:
+        picks.append((fb, [0, 0, 0]))
+    for b, (i, j, k) in picks[:6] + picks[-3:]:
+        kk = zs.start + k
+        cv = U[b, :, kk, ys.start + j, xs.start + i]
+        ke = 0.5 * (cv[1] ** 2 + cv[2] ** 2 + cv[3] ** 2) / cv[0]
+        U[b, 4, kk, ys.start + j, xs.start + i] = 0.5 * ke
+    return U
+
+
+@pytest.mark.parametrize("stages", [2, 3])
+@pytest.mark.parametrize("name", list(TWO_LEVEL))
+def test_two_level_every_entry_point_bitwise(gb, name, stages):
+    tl = TWO_LEVEL[name]
+    U0 = smooth_two_level(tl, 7)[tl.gpu_blocks]
+
+    def make():
+        h = gb.Hydro.from_two_level(tl)
+        h.set_rk_stages(stages)
+        return h
+    assert on_and_off(gb, make, U0) == [0] * 6
+
+
+@pytest.mark.parametrize("name", ["box-3d", "L-2d", "tripod-3d-periodic"])
+def test_two_level_floor_counts_equal_with_corrected_cells(gb, name):
+    """Floors planted in coarse cells that the flux correction changes: the
+    carry counts the corrected value's floors, as the next stage's conversion
+    would, so the counts of every entry point are those of the carry off."""
+    tl = TWO_LEVEL[name]
+    U = smooth_two_level(tl, 8)
+    U = floor_cells(tl, U, 9)
+    hits = on_and_off(gb, lambda: gb.Hydro.from_two_level(tl), U[tl.gpu_blocks], nsteps=3)
+    assert all(x > 0 for x in hits), hits
+
+
+def test_two_level_batched_bitwise(gb):
+    tls = [wl.two_level(wl.lattice_2d(4, 4, 8, 8, 4, bc="periodic"), (1, 1), (3, 3)),
+           wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))][:1] * 3
+    U0 = np.concatenate([smooth_two_level(t, 10 + i)[t.gpu_blocks] for i, t in enumerate(tls)])
+    on_and_off(gb, lambda: gb.Hydro.from_two_level_batch(tls), U0)
+
+
+def test_telescoping_never_carries(gb):
     lat = wl.lattice_3d(2, 2, 2, 8, 8, 8, 4)
     U0 = wl.random_state(lat, seed=5, rough=True)
 
@@ -164,12 +257,13 @@ def test_telescoping_and_two_level_never_carry(gb):
         h.set_telescoping(True)
         return h
     on_and_off(gb, make, U0)
-    tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))
-    h = gb.Hydro.from_two_level(tl)
-    assert not h.prim_carry()
-    h.set_prim_carry(True)
-    assert not h.prim_carry()
-    h.close()
+    tl = TWO_LEVEL["box-3d"]
+
+    def make2():
+        h = gb.Hydro.from_two_level(tl)
+        h.set_telescoping(True)
+        return h
+    on_and_off(gb, make2, smooth_two_level(tl, 11)[tl.gpu_blocks])
 
 
 def test_toggle_and_default(gb):

@@ -554,7 +554,7 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimC
 
 
 
-// The two arrays of the primitive carry (uniform contexts).  If they cannot
+// The two arrays of the primitive carry.  If they cannot
 // be allocated the carry stays off and every stage converts on load (the
 // results are the same bit for bit); returns whether it is on.
 static bool alloc_prim_buffers(gbh_ctx* c) {

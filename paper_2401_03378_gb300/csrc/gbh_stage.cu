@@ -24,10 +24,12 @@
 //  - all FP64 arithmetic is register FMAs (gbh_fastmath.cuh);
 //  - the update of the plane reads its x/y fluxes from shared memory and its
 //    z fluxes from registers and writes Uout.
-// Optional epilogue (second RK stage): max over the CTA of the CFL signal
-// speed of Uout, one 64-bit atomicMax per CTA on the bit pattern of the
-// non-negative double (on two-level grids without the cells the flux
-// correction changes afterwards).
+// Optional epilogue: calcEos of Uout (the conversion to primitive variables),
+// which the next stage of the call reads from a.Wout instead of converting
+// its input again; at the last RK stage, the max over the CTA of the CFL
+// signal speed of Uout from the same conversion, one 64-bit atomicMax per CTA
+// on the bit pattern of the non-negative double (on two-level grids without
+// the cells the flux correction changes afterwards).
 //
 // Telescoping mode (Sec. 4.2): the earlier stages also update a ring of E
 // guard cells around the interior (E = 2 (S - s) for stage s of S), from the

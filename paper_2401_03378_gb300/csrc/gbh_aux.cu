@@ -12,9 +12,12 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// fill_guardcells (Sec. 4.2).  One thread per (block, padded cell); interior
-// cells are skipped.  The value of a guard cell is resolved directly, without
-// passes that depend on one another:
+// fill_guardcells (Sec. 4.2).  Work items are (block, padded z plane), a CTA
+// each in turn; the CTA's threads take the plane's guard cells only: the whole
+// plane in a z guard plane, else the g rows below and above the interior rows
+// and the g-cell x guards of the interior rows (32-bit index arithmetic; rows
+// are contiguous in x, so the copies are coalesced).  The value of a guard
+// cell is resolved directly, without passes that depend on one another:
 //  1. for each dimension d in which the cell lies outside the block and the
 //     block's face in that direction is an outflow edge, its coordinate is
 //     clamped to the nearest interior index (outflow is applied in the order
@@ -23,49 +26,56 @@ constexpr int kThreads = 256;
 //     interior cell of the neighbour block at that offset (full table).
 // Every source is an interior cell, so the in-place fill has no read/write
 // overlap.  An offset with no neighbour and no outflow face is left untouched.
-__global__ void fill_kernel(const FillArgs a) {
+__global__ void __launch_bounds__(kThreads) fill_kernel(const FillArgs a) {
   const Layout& L = a.lay;
-  const long long cells = (long long)L.nzp * L.nyp * L.nxp;
-  const long long total = cells * L.nblocks;
   const int nn = L.ndim == 3 ? 27 : 9;
   const int n[3] = {L.nx, L.ny, L.nz};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / cells);
-    long long r = t - (long long)b * cells;
-    const int ii = (int)(r % L.nxp);
-    r /= L.nxp;
-    const int jj = (int)(r % L.nyp);
-    const int kk = (int)(r / L.nyp);
-    int c[3] = {ii - L.g, jj - L.g, kk - L.gz};
-    int o[3];
-    bool interior = true;
-    for (int d = 0; d < 3; ++d) {
-      o[d] = c[d] < 0 ? -1 : (c[d] >= n[d] ? 1 : 0);
-      if (o[d] != 0) interior = false;
-    }
-    if (interior) continue;
-    for (int d = 0; d < L.ndim; ++d) {
-      if (o[d] == 0) continue;
-      const int f = 2 * d + (o[d] > 0 ? 1 : 0);
-      if (__ldg(a.face_nbr + 6 * b + f) == -1) {   // outflow face
-        c[d] = o[d] < 0 ? 0 : n[d] - 1;
-        o[d] = 0;
+  const int nitems = L.nblocks * L.nzp;
+  const int full = 2 * L.g * L.nxp;            // cells of the 2g full rows of an interior plane
+  const long long lim = (long long)L.nblocks * L.bstride - 4 * L.vstride;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int b = item / L.nzp, kk = item - b * L.nzp;
+    const int cz = kk - L.gz;
+    const bool zguard = cz < 0 || cz >= n[2];
+    const int ncell = zguard ? L.nyp * L.nxp : full + L.ny * 2 * L.g;
+    for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+      int ii, jj;
+      if (zguard) {
+        jj = q / L.nxp;
+        ii = q - jj * L.nxp;
+      } else if (q < full) {
+        const int r = q / L.nxp;
+        jj = r < L.g ? r : L.ny + r;
+        ii = q - r * L.nxp;
+      } else {
+        const int r = q - full, row = r / (2 * L.g), side = r - row * 2 * L.g;
+        jj = L.g + row;
+        ii = side < L.g ? side : L.nx + side;
       }
-    }
-    int src = b;
-    if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
-      const int e = L.ndim == 3 ? (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
-      src = __ldg(a.nbr + (long long)nn * b + e);
-      if (src < 0) continue;
-      for (int d = 0; d < 3; ++d) c[d] -= o[d] * n[d];
-    }
-    const long long lim = (long long)L.nblocks * L.bstride - 4 * L.vstride;
-    const long long so = GBH_IX(
-        (long long)src * L.bstride + ((long long)(c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g), lim);
-    const long long dof = GBH_IX((long long)b * L.bstride + ((long long)kk * L.nyp + jj) * L.nxp + ii, lim);
+      int c[3] = {ii - L.g, jj - L.g, cz};
+      int o[3];
+      for (int d = 0; d < 3; ++d) o[d] = c[d] < 0 ? -1 : (c[d] >= n[d] ? 1 : 0);
+      for (int d = 0; d < L.ndim; ++d) {
+        if (o[d] == 0) continue;
+        const int f = 2 * d + (o[d] > 0 ? 1 : 0);
+        if (__ldg(a.face_nbr + 6 * b + f) == -1) {   // outflow face
+          c[d] = o[d] < 0 ? 0 : n[d] - 1;
+          o[d] = 0;
+        }
+      }
+      int src = b;
+      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+        const int e = L.ndim == 3 ? (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1) : (o[1] + 1) * 3 + (o[0] + 1);
+        src = __ldg(a.nbr + nn * b + e);
+        if (src < 0) continue;
+        for (int d = 0; d < 3; ++d) c[d] -= o[d] * n[d];
+      }
+      const long long so = GBH_IX(
+          (long long)src * L.bstride + ((c[2] + L.gz) * L.nyp + (c[1] + L.g)) * L.nxp + (c[0] + L.g), lim);
+      const long long dof = GBH_IX((long long)b * L.bstride + (kk * L.nyp + jj) * L.nxp + ii, lim);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) a.U[dof + v * L.vstride] = a.U[so + v * L.vstride];
+      for (int v = 0; v < 5; ++v) a.U[dof + v * L.vstride] = a.U[so + v * L.vstride];
+    }
   }
 }
 
@@ -338,8 +348,8 @@ long long check_selftest() {
 }
 
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
-  const long long work = (long long)a.lay.nblocks * a.lay.nzp * a.lay.nyp * a.lay.nxp;
-  fill_kernel<<<grid_for(work, kThreads), kThreads, 0, s>>>(a);
+  const long long items = (long long)a.lay.nblocks * a.lay.nzp;
+  fill_kernel<<<(int)(items < 152LL * 16 ? items : 152LL * 16), kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
-"""Index maps of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), restated
-on the CPU: the thread -> column map, and the face lists of the inner planes.
+"""Index maps of the kernels, restated on the CPU: the thread -> column map and the
+face lists of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), and the
+guard-cell enumeration of the fill kernel (gbh_aux.cu).
 
 The telescoping variant's first stage (Sec. 4.2) updates the interior widened
 by 2 cells; the next stage reads that output in its own box and in the 2-deep
@@ -93,3 +94,42 @@ def test_face_lists_are_exactly_what_the_update_reads(N):
     # two full passes of the threads, against 2 M^2 faces (a third, partial pass) untrimmed
     assert len(c) == 2 * len(thread_columns(N))
     assert 2 * M * M > len(c)
+
+
+def fill_plane_cells(n, g, nd, kk):
+    """Cells (jj, ii) the fill kernel's threads take in padded plane kk."""
+    nxp = n + 2 * g
+    gz = g if nd == 3 else 0
+    nz = n if nd == 3 else 1
+    cz = kk - gz
+    zguard = cz < 0 or cz >= nz
+    full = 2 * g * nxp
+    out = []
+    for q in range(nxp * nxp if zguard else full + n * 2 * g):
+        if zguard:
+            jj, ii = divmod(q, nxp)
+        elif q < full:
+            r = q // nxp
+            jj, ii = (r if r < g else n + r), q - r * nxp
+        else:
+            row, side = divmod(q - full, 2 * g)
+            jj, ii = g + row, (side if side < g else n + side)
+        out.append((jj, ii))
+    return out
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+@pytest.mark.parametrize("n,g", [(4, 2), (8, 3), (16, 4), (8, 6)])
+def test_fill_enumeration_covers_each_guard_cell_once(nd, n, g):
+    """The guard fill (Sec. 4.2) takes, per (block, padded z plane), exactly the
+    plane's guard cells: the whole plane outside the interior z range, else the
+    g full rows below and above the interior rows and the g-cell x guards."""
+    nxp = n + 2 * g
+    gz = g if nd == 3 else 0
+    nzp = n + 2 * gz if nd == 3 else 1
+    got = [(kk,) + c for kk in range(nzp) for c in fill_plane_cells(n, g, nd, kk)]
+    assert len(got) == len(set(got))
+    inside = lambda x: g <= x < g + n
+    want = {(kk, jj, ii) for kk in range(nzp) for jj in range(nxp) for ii in range(nxp)
+            if not (inside(ii) and inside(jj) and (kk - gz >= 0 and kk - gz < (n if nd == 3 else 1)))}
+    assert set(got) == want

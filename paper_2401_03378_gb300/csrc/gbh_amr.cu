@@ -330,13 +330,13 @@ __global__ void __launch_bounds__(kThreads) reflux_kernel(double* U, const AmrAr
       if (a.problem)
         atomicMax(smax_acc + __ldg(a.problem + en.block), (unsigned long long)__double_as_longlong(sp));
       else
-        smax = fmax(smax, sp);
+        smax = max_nonneg(smax, sp);
     }
   }
   if (smax_acc && !a.problem) {
     // one accumulator: warp max, one atomic per warp (every lane of the warp
     // reaches this point: the block size is a multiple of 32)
-    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    for (int o = 16; o > 0; o >>= 1) smax = max_nonneg(smax, __shfl_xor_sync(0xffffffffu, smax, o));
     if ((threadIdx.x & 31) == 0) atomicMax(smax_acc, (unsigned long long)__double_as_longlong(smax));
   }
 }

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_kernel(const DtArgs a) {
     const double s = signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * b), zt),
                                      reg_const(__ldg(a.inv_dx + 3 * b + 1), zt),
                                      reg_const(__ldg(a.inv_dx + 3 * b + 2), zt), d3);
-    smax = fmax(smax, s);
+    smax = max_nonneg(smax, s);
   }
   __shared__ double red[kThreads / 32];
   const double m = block_max<kThreads>(smax, red);
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) dt_reduce_blocks_kernel(const DtArgs
       for (int v = 0; v < 5; ++v) U[v] = __ldg(a.U + o + v * L.vstride);
       double ir;
       cons_to_prim_ir(U, W, e, ir);
-      smax = fmax(smax, signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * b), zt),
+      smax = max_nonneg(smax, signal_speed_ir(W, ir, e, reg_const(__ldg(a.inv_dx + 3 * b), zt),
                                         reg_const(__ldg(a.inv_dx + 3 * b + 1), zt),
                                         reg_const(__ldg(a.inv_dx + 3 * b + 2), zt), d3));
     }

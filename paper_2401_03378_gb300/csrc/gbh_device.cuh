@@ -83,6 +83,17 @@ __device__ __forceinline__ double mc_half_slope_d(double dm, double dp, const Rk
 // x / 2 for a positive normal x >= 2^-1021 (one off the exponent field)
 __device__ __forceinline__ double half_pos(double x) { return bitsd(dbits(x) - (1LL << 52)); }
 
+// max(a, b) of non-negative doubles on the integer pipe (their bit patterns
+// order like their values; fmax is an FP64-pipe instruction).  A NaN operand
+// is passed over, as fmax passes it over.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  constexpr unsigned long long kInf = 0x7ff0000000000000ULL;
+  unsigned long long x = (unsigned long long)dbits(a), y = (unsigned long long)dbits(b);
+  x = x > kInf ? 0ULL : x;
+  y = y > kInf ? 0ULL : y;
+  return bitsd((long long)(x > y ? x : y));
+}
+
 // Maximum over the NT threads of a CTA (NT a power of two) of non-negative
 // values: xor shuffles within each warp (over the lanes the CTA has), then
 // the warps' maxima through s_warp[NT/32] and one more warp of shuffles.  The
@@ -92,7 +103,7 @@ __device__ __forceinline__ double block_max(double v, double* s_warp) {
   constexpr int WL = NT < 32 ? NT : 32;
   constexpr unsigned mask = WL == 32 ? 0xffffffffu : ((1u << WL) - 1u);
 #pragma unroll
-  for (int o = WL / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
+  for (int o = WL / 2; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(mask, v, o));
   if constexpr (NT > 32) {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -101,7 +112,7 @@ __device__ __forceinline__ double block_max(double v, double* s_warp) {
     if (warp == 0) {
       v = lane < NW ? s_warp[lane] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      for (int o = 16; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
     }
   }
   return v;

@@ -506,7 +506,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
       }
       if (a.smax_acc) {
         const double sp = signal_speed_ir(W, ir, e, reg_const(idx, zt), reg_const(idy, zt), reg_const(idz, zt), DIM3);
-        if (!corrected_cell<N, DIM3>(a, b, ci, cj, k, L.nz)) smax = fmax(smax, sp);
+        if (!corrected_cell<N, DIM3>(a, b, ci, cj, k, L.nz)) smax = max_nonneg(smax, sp);
       }
     }
 

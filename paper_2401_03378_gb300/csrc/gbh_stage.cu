@@ -95,7 +95,8 @@ constexpr int stage_threads() {
 // (S = 1: the whole tile).  Uses the caller's shared memory; ends with the
 // per-item atomics.
 template <int N, bool DIM3, int E, int S>
-__device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red) {
+__device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red,
+                                           double* s_dt) {
   constexpr int M = N + 2 * E;              // plane tile width (the interior when E = 0)
   constexpr int MY = M / S;                 // rows of one band
   constexpr int NT = stage_threads<N, E, S>();   // threads: one per updated column
@@ -157,7 +158,14 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   const long long zt = thread_zero(a.eos);
   const Eos e = reg_eos(a.eos, zt);
   const Rk& rk = e.k;
-  const double dtx = reg_const(dt * idx, zt), dty = reg_const(dt * idy, zt), dtz = reg_const(dt * idz, zt);
+  // dt/dx, dt/dy, dt/dz: formed once per item by thread 0 and read back in
+  // the update, after the plane's barriers (three FP64 multiplies per thread
+  // otherwise, which an item of one 2-D plane pays per cell)
+  if (tid == 0) {
+    s_dt[0] = dt * idx;
+    s_dt[1] = dt * idy;
+    s_dt[2] = DIM3 ? dt * idz : 0.0;
+  }
 
   int hits = 0;
   double smax = 0.0;
@@ -458,6 +466,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     // (the others are never read again and their fluxes were not formed)
     const bool upd = !outer || (tx >= wx0 && tx < wx1 && ty >= wy0 && ty < wy1);
     double out[5];
+    const double dtx = reg_const(s_dt[0], zt), dty = reg_const(s_dt[1], zt), dtz = reg_const(s_dt[2], zt);
 #pragma unroll
     for (int v = 0; v < 5 && upd; ++v) {
       const double fx = sub(sFx[GBH_IX((v * MY + ty) * (M + 1) + tx + 1, 5 * FXS)], sFx[(v * MY + ty) * (M + 1) + tx], rk);
@@ -542,11 +551,12 @@ __global__ void __launch_bounds__(stage_threads<N, E, S>(), min_ctas<E, S>()) st
   constexpr int NT = stage_threads<N, E, S>();
   extern __shared__ double smem[];
   __shared__ double s_red[E == 0 && NT > 32 ? NT / 32 : 1];
+  __shared__ double s_dt[3];
   const int nitems = (a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
   const int first = blockIdx.x * a.items_per_cta;
   const int last = min(nitems, first + a.items_per_cta);
   for (int item = first; item < last; ++item) {
-    stage_item<N, DIM3, E, S>(a, item, smem, s_red);
+    stage_item<N, DIM3, E, S>(a, item, smem, s_red, s_dt);
     __syncthreads();
   }
 }

@@ -415,7 +415,10 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     traffic = measured_traffic(zones)
     roof = {
-        "kernel": "gbh stage_kernel<16,3D> (both SSP-RK2 stages, fused halo gather, dt epilogue)",
+        "kernel": ("gbh face_flux_kernel<16,3D> + stage_kernel<16,3D> per stage, timed together (both SSP-RK2 "
+                   "stages: each block face solved once in the pre-pass, fused halo gather, dt epilogue)"
+                   if h.face_prepass() else
+                   "gbh stage_kernel<16,3D> (both SSP-RK2 stages, fused halo gather, dt epilogue)"),
         "bound": "alu",
         "achieved": achieved / 1e12,
         "peak": FP64_PEAK_NOMINAL / 1e12,
@@ -449,7 +452,7 @@ def run_gpu(args):
         "data": "synthetic (seeded Sedov initial condition)",
         "config": bench_config(lat),
         "parallelism": f"replicas x{world}",
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (5 if h.face_prepass() else 3) * args.steps,
         "autotune": tuning,
         "clocks": clocks,
         "repeats": repeats,
@@ -522,6 +525,7 @@ def run_variants(args, gb, torch, barrier, ms_headline):
         stage_ms, _ = h.stage_kernel_time()
         h.set_kernel_timing(False)
         nbad = h.check_state(U)
+        pre = h.face_prepass() and not tele      # the face pre-pass runs before halo-gathering stages
         h.close()
         del U
         torch.cuda.empty_cache()
@@ -531,7 +535,8 @@ def run_variants(args, gb, torch, barrier, ms_headline):
                      "steps": args.variant_steps, "ms_per_step": ms,
                      "stage_kernels_ms_per_step": stage_ms / args.variant_steps,
                      "over_headline_step": ms / ms_headline,
-                     "launches_per_step": stages + 1 + (1 if tele else 0), "unphysical_cells": nbad,
+                     "launches_per_step": stages + 1 + (1 if tele else 0) + (stages if pre else 0),
+                     "unphysical_cells": nbad,
                      "autotune": tuning}
     out["workload"] = f"{WORKLOAD} -- stepper variants (nguard as listed)"
     return out

@@ -64,6 +64,8 @@ SIGNATURES = {
     "gbh_set_rk_stages": (C.c_int, [_vp, C.c_int]),
     "gbh_set_prim_carry": (C.c_int, [_vp, C.c_int]),
     "gbh_get_prim_carry": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "gbh_set_face_prepass": (C.c_int, [_vp, C.c_int]),
+    "gbh_get_face_prepass": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "hydro_advance_graph": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "hydro_stage_vjp": (C.c_int, [_vp, _dp, _dp, C.c_double, _dp, C.c_double, _dp, C.c_double, _dp, _vp]),
     "hydro_step_adjoint": (C.c_int, [_vp, _dp, C.c_double, _dp, _dp, _vp]),

@@ -37,6 +37,10 @@ struct gbh_ctx {
   // gathered): two arrays of the state's layout (gbh_set_prim_carry)
   double* d_W[2] = {nullptr, nullptr};
   bool prim_carry = false;
+  // the face pre-pass of the interior stages (gbh_set_face_prepass): the
+  // fluxes through every block face, [nblocks][6][5][nx * nx (3-D) or nx]
+  double* d_bflux = nullptr;
+  bool face_prepass = false;
   unsigned long long* d_words = nullptr;  // [0] smax accumulator, [1] floor count, [2] check count
   // host-buffer path (allocated on first use)
   double* d_host_state = nullptr;
@@ -196,6 +200,8 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   }
   A.items_per_cta = c->items_per_cta;
   A.ysplit = (ring == 0 || ring == 2 || ring == 4) ? c->ysplit[ring / 2] : 1;
+  const bool prepass = c->face_prepass && c->d_bflux && ring == 0 && gather && !c->refined && !list &&
+                       A.ysplit == 1 && A.nchunks == 1;
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
@@ -210,6 +216,11 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   cudaEvent_t stop;
   int rc = record_start(c, s, &stop);
   if (rc) return rc;
+  if (prepass) {
+    // each block face solved once, then read by the stage
+    if ((rc = cuda_err(c, gbh::launch_face_fluxes(A, c->d_bflux, s), "face pre-pass launch"))) return rc;
+    A.bflux = c->d_bflux;
+  }
   rc = cuda_err(c, ring > 0 ? gbh::launch_stage_ring(A, ring, s) : gbh::launch_stage(A, s), "stage kernel launch");
   if (rc) return rc;
   if (stop) rc = cuda_err(c, cudaEventRecord(stop, s), "cudaEventRecord");
@@ -557,6 +568,25 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimC
 // The two arrays of the primitive carry.  If they cannot
 // be allocated the carry stays off and every stage converts on load (the
 // results are the same bit for bit); returns whether it is on.
+// The face pre-pass buffer (uniform contexts); off if it cannot be allocated.
+// Switched on at creation for 3-D contexts only: in 2-D a block plane has few
+// boundary faces for what the extra launch costs (the 96-problem 2-D ensemble
+// measured 1.2% slower with it, the 256^3 3-D step 3.3% faster).
+static bool alloc_face_buffer(gbh_ctx* c, bool at_create = false) {
+  if (c->refined || (at_create && c->lay.ndim != 3)) return false;
+  if (!c->d_bflux) {
+    const size_t nf = (size_t)c->lay.nx * (c->lay.ndim == 3 ? c->lay.nx : 1);
+    if (cudaMalloc(&c->d_bflux, sizeof(double) * 6 * 5 * nf * (size_t)c->lay.nblocks) != cudaSuccess) {
+      c->d_bflux = nullptr;
+      cudaGetLastError();
+      c->face_prepass = false;
+      return false;
+    }
+  }
+  c->face_prepass = true;
+  return true;
+}
+
 static bool alloc_prim_buffers(gbh_ctx* c) {
   if (!c->d_W[0]) {
     const size_t bytes = sizeof(double) * state_elems(c->lay);
@@ -621,6 +651,7 @@ int gbh_create(const gbh_params* p, gbh_ctx** out) {
   if (rc) return rc;
   if ((rc = create_common(p, out))) return rc;
   alloc_prim_buffers(*out);
+  alloc_face_buffer(*out, true);
   return GBH_OK;
 }
 
@@ -849,6 +880,7 @@ int gbh_create_batched(const gbh_params* p, const int32_t* problem, int nproblem
     return rc;
   }
   alloc_prim_buffers(c);
+  alloc_face_buffer(c, true);
   *out = c;
   return GBH_OK;
 }
@@ -1031,6 +1063,27 @@ int gbh_set_prim_carry(gbh_ctx* c, int enable) {
     return cuda_err(c, e, "cudaDeviceSynchronize");
   }
   if (!alloc_prim_buffers(c)) return set_err(c, GBH_ERR_NOMEM, "primitive arrays: device allocation failed");
+  return GBH_OK;
+}
+
+int gbh_set_face_prepass(gbh_ctx* c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  drop_graph(c);
+  if (!enable) {
+    c->face_prepass = false;
+    return GBH_OK;
+  }
+  if (c->refined) return GBH_OK;
+  if (!alloc_face_buffer(c)) return set_err(c, GBH_ERR_NOMEM, "face pre-pass buffer: device allocation failed");
+  return GBH_OK;
+}
+
+int gbh_get_face_prepass(gbh_ctx* c, int* enabled) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!enabled) return set_err(c, GBH_ERR_INVAL, "enabled is NULL");
+  *enabled = c->face_prepass && c->d_bflux ? 1 : 0;
   return GBH_OK;
 }
 
@@ -1250,6 +1303,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_scratch);
   cudaFree(c->d_W[0]);
   cudaFree(c->d_W[1]);
+  cudaFree(c->d_bflux);
   cudaFree(c->d_host_state);
   cudaFree(c->d_host_dt);
   cudaFree(c->d_host_hist);

@@ -94,7 +94,7 @@ constexpr int stage_threads() {
 // into S bands of MY = (N+2E)/S rows; a CTA of M*MY threads updates one band
 // (S = 1: the whole tile).  Uses the caller's shared memory; ends with the
 // per-item atomics.
-template <int N, bool DIM3, int E, int S>
+template <int N, bool DIM3, int E, int S, bool BF = false>
 __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double* smem, double* s_red,
                                            double* s_dt) {
   constexpr int M = N + 2 * E;              // plane tile width (the interior when E = 0)
@@ -172,9 +172,16 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   double W0[5], Wp1[5], qpz[5], Fzm[5];     // column state carried along z
   double dz1[5];                            // Wp1 - W0 (the next z slope's left difference)
 
+  // the face pre-pass solved the block's faces (the interior stage on whole
+  // blocks: the host takes this kernel only for items of one whole block, so
+  // the z march starts at the block's bottom face and ends at its top face)
+  constexpr bool bf = BF && E == 0 && S == 1;
+  const double* bfb = bf ? a.bflux + (long long)b * 6 * 5 * (N * (DIM3 ? N : 1)) : nullptr;
+  constexpr int NF = N * (DIM3 ? N : 1);      // faces of one block face
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
-    stage_prim<N, E>(a, e, b, ci, cj, k0 - 2, Wm2);
+    constexpr bool bottom = bf;                // the z face -1/2 comes from the pre-pass
+    if (!bottom) stage_prim<N, E>(a, e, b, ci, cj, k0 - 2, Wm2);
     stage_prim<N, E>(a, e, b, ci, cj, k0 - 1, Wm1);
     const int h0 = stage_prim<N, E>(a, e, b, ci, cj, k0, W0);
     if (counted(k0)) hits += h0;
@@ -183,18 +190,23 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double d0 = sub(W0[v], Wm1[v], rk);
-      qpm1[v] = add(Wm1[v], mc_half_slope_d(sub(Wm1[v], Wm2[v], rk), d0, rk), rk);
+      if (!bottom) qpm1[v] = add(Wm1[v], mc_half_slope_d(sub(Wm1[v], Wm2[v], rk), d0, rk), rk);
       dz1[v] = sub(Wp1[v], W0[v], rk);
       const double t = mc_half_slope_d(d0, dz1[v], rk);
       qm0[v] = sub(W0[v], t, rk);
       qpz[v] = add(W0[v], t, rk);
     }
-    // z face k0 - 1/2; rotated order (rho, w, u, v, p)
-    double wl[5] = {qpm1[0], qpm1[3], qpm1[1], qpm1[2], qpm1[4]};
-    double wr[5] = {qm0[0], qm0[3], qm0[1], qm0[2], qm0[4]};
-    double f[5];
-    hllc_flux(wl, wr, e, f);
-    Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
+    if (bottom) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fzm[v] = bfb[(FACE_ZM * 5 + v) * NF + cj * N + ci];
+    } else {
+      // z face k0 - 1/2; rotated order (rho, w, u, v, p)
+      double wl[5] = {qpm1[0], qpm1[3], qpm1[1], qpm1[2], qpm1[4]};
+      double wr[5] = {qm0[0], qm0[3], qm0[1], qm0[2], qm0[4]};
+      double f[5];
+      hllc_flux(wl, wr, e, f);
+      Fzm[0] = f[0]; Fzm[1] = f[2]; Fzm[2] = f[3]; Fzm[3] = f[1]; Fzm[4] = f[4];
+    }
   } else {
     const int h0 = stage_prim<N, E>(a, e, b, ci, cj, 0, W0);
     if (col_in) hits += h0;
@@ -222,7 +234,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         for (int v = 0; v < 5; ++v) prefetch_l1(src + pb + 3LL * L.nyp * L.nxp + v * L.vstride);
       }
     }
-    if (DIM3) {
+    if (DIM3 && bf && k == L.nz - 1) {
+      // the z face nz - 1/2 comes from the pre-pass
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fzp[v] = bfb[(FACE_ZP * 5 + v) * NF + cj * N + ci];
+    } else if (DIM3) {
       // own column: primitives at k+2, face states of k+1, z flux at k + 1/2
       const int hn = stage_prim<N, E>(a, e, b, ci, cj, k + 2, Wn);
       if (counted(k + 2)) hits += hn;
@@ -342,7 +358,22 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     const bool trim = E == 2 && S == 1 && !outer;
     const int TRX = (Wx + 4) / 3, TRY = (Wy + 4) / 3;   // triples per line (W + 2 slope cells)
     const int NSX = TRX * Wy, NSY = TRY * Wx;
-    for (int s = rtid; s < NSX + NSY + Wy + Wx; s += NT) {
+    for (int s = rtid; s < NSX + NSY + (bf ? 2 : 1) * (Wy + Wx); s += NT) {
+      if (bf && s >= NSX + NSY) {
+        // the block's boundary faces from the pre-pass: x faces 0 and N of
+        // each row, y faces 0 and N of each column (plane k)
+        const int f = s - NSX - NSY;
+        const bool xf = f < 2 * N;
+        const int side = (xf ? f : f - 2 * N) / N, line = (xf ? f : f - 2 * N) % N;
+        const int face = xf ? FACE_XM + side : FACE_YM + side;
+        const double* src = bfb + face * 5 * NF + line + (DIM3 ? N * k : 0);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (xf) sFx[GBH_IX((v * MY + line) * (M + 1) + side * N, 5 * FXS)] = src[v * NF];
+          else sFy[GBH_IX((v * (MY + 1) + side * N) * M + line, 5 * FYS)] = src[v * NF];
+        }
+        continue;
+      }
       if (s >= NSX + NSY) {
         const int f = s - NSX - NSY;
         const bool xf = f < Wy;
@@ -413,7 +444,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
     //     came with (B)
     // (in the inner planes of the ring-2 tile: N full lines of M faces, then
     //     the 4 slab lines at positions [2, N + 2), per direction)
-    const int nper = trim ? N * (N + 8) : Wx * Wy;
+    // (with the pre-pass: the N - 1 inner faces of each line only)
+    const int nper = trim ? N * (N + 8) : bf ? (N - 1) * N : Wx * Wy;
     for (int f = tid; f < 2 * nper; f += NT) {
       const bool xf = f < nper;
       int i, j;                    // band positions
@@ -430,14 +462,18 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
         }
       }
       if (xf) {
-        if (trim) { i = pos; j = line; } else { i = f % Wx + wx0; j = f / Wx + wy0; }
+        if (trim) { i = pos; j = line; }
+        else if (bf) { i = f % (N - 1) + 1; j = f / (N - 1); }
+        else { i = f % Wx + wx0; j = f / Wx + wy0; }
         vs = QXS;
         ol = 5 * vs + j * (M + 2) + i;        // plus state of cell i-1 (slot i)
         orr = j * (M + 2) + i + 1;            // minus state of cell i (slot i+1)
         ql = sQx; qr = sQx;
       } else {
-        const int f2 = f - Wx * Wy;
-        if (trim) { i = line; j = pos; } else { i = f2 % Wx + wx0; j = f2 / Wx + wy0; }
+        const int f2 = f - nper;
+        if (trim) { i = line; j = pos; }
+        else if (bf) { i = f2 % N; j = f2 / N + 1; }
+        else { i = f2 % Wx + wx0; j = f2 / Wx + wy0; }
         vs = QYS;
         ol = 5 * vs + j * M + i;              // plus state of cell j-1 (slot j)
         orr = (j + 1) * M + i;                // minus state of cell j (slot j+1)
@@ -537,6 +573,67 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   }
 }
 
+// The face pre-pass: one thread per (block, face, face cell).  The flux
+// through a face is solved once: by the block on its high side (x = N - 1/2,
+// y = N - 1/2, z = nz - 1/2, which also writes it into the neighbour's slot
+// for that neighbour's low face), and, where a block has no neighbour on a
+// low side (an outflow edge), by that block.  Face states as the stage
+// kernel forms them (the plus state of the cell below the face, the minus
+// state of the cell above, MC slopes of the primitives, the same arithmetic
+// and halo addressing), the same HLLC, the same rotations: the stage reads
+// the same bits it would have formed.
+template <int N, bool DIM3>
+__global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, double* __restrict__ out) {
+  constexpr int NF = N * (DIM3 ? N : 1);
+  constexpr int NFACES = DIM3 ? 6 : 4;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)a.lay.nblocks * NFACES * NF) return;
+  const int b = (int)(t / (NFACES * NF));
+  const int r = (int)(t - (long long)b * NFACES * NF);
+  const int face = r / NF, tt = r - face * NF;
+  const int d = face >> 1, side = face & 1;
+  const int nb = __ldg(a.face_nbr + 6 * b + face);
+  if (side == 0 && nb >= 0) return;             // solved by the neighbour, as its high face
+  const long long zt = thread_zero(a.eos);
+  const Eos e = reg_eos(a.eos, zt);
+  const Rk& rk = e.k;
+  // the cell coordinates along the normal: two below the face, two above
+  const int p0 = side ? N - 2 : -2;
+  const int t1 = tt % N, t2 = DIM3 ? tt / N : 0;
+  double Q[4][5];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int i, j, k;
+    if (d == 0) { i = p0 + c; j = t1; k = t2; }
+    else if (d == 1) { i = t1; j = p0 + c; k = t2; }
+    else { i = t1; j = t2; k = p0 + c; }
+    stage_prim<N, 0>(a, e, b, i, j, k, Q[c]);
+  }
+  double ql[5], qr[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double d0 = sub(Q[1][v], Q[0][v], rk), d1 = sub(Q[2][v], Q[1][v], rk), d2 = sub(Q[3][v], Q[2][v], rk);
+    ql[v] = add(Q[1][v], mc_half_slope_d(d0, d1, rk), rk);   // plus state of the cell below
+    qr[v] = sub(Q[2][v], mc_half_slope_d(d1, d2, rk), rk);   // minus state of the cell above
+  }
+  // rotated order: the normal momentum second (x: rho u v w p; y: rho v u w p; z: rho w u v p)
+  const int vn = d + 1, va = d == 0 ? 2 : 1, vb = d == 2 ? 2 : 3;
+  double wl[5] = {ql[0], ql[vn], ql[va], ql[vb], ql[4]};
+  double wr[5] = {qr[0], qr[vn], qr[va], qr[vb], qr[4]};
+  double F[5];
+  hllc_flux(wl, wr, e, F);
+  double G[5];
+  G[0] = F[0]; G[vn] = F[1]; G[va] = F[2]; G[vb] = F[3]; G[4] = F[4];
+  double* o = out + ((long long)b * 6 + face) * 5 * NF + tt;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v * NF] = G[v];
+  if (side == 1 && nb >= 0) {
+    double* on = out + ((long long)nb * 6 + (face - 1)) * 5 * NF + tt;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) on[v * NF] = G[v];
+  }
+}
+
 // CTAs per SM the register budget is sized for: an unsplit interior tile
 // (256 threads at N = 16) two, a band of it four; a ring tile one, a band
 // of it two.
@@ -546,7 +643,7 @@ constexpr int min_ctas() { return (E == 0 ? 2 : 1) * S; }
 // Work list: items (block, z-chunk, band) in order; each CTA processes
 // `items_per_cta` consecutive items (1 = one CTA per item; a machine-sized
 // grid makes the kernel persistent).  No CTA waits on another.
-template <int N, bool DIM3, int E, int S>
+template <int N, bool DIM3, int E, int S, bool BF = false>
 __global__ void __launch_bounds__(stage_threads<N, E, S>(), min_ctas<E, S>()) stage_kernel(const StageArgs a) {
   constexpr int NT = stage_threads<N, E, S>();
   extern __shared__ double smem[];
@@ -556,7 +653,7 @@ __global__ void __launch_bounds__(stage_threads<N, E, S>(), min_ctas<E, S>()) st
   const int first = blockIdx.x * a.items_per_cta;
   const int last = min(nitems, first + a.items_per_cta);
   for (int item = first; item < last; ++item) {
-    stage_item<N, DIM3, E, S>(a, item, smem, s_red, s_dt);
+    stage_item<N, DIM3, E, S, BF>(a, item, smem, s_red, s_dt);
     __syncthreads();
   }
 }
@@ -569,18 +666,18 @@ constexpr size_t smem_for() {
                            5 * MY * (M + 1) + 5 * (MY + 1) * M);
 }
 
-template <int N, bool D3, int E, int S>
+template <int N, bool D3, int E, int S, bool BF = false>
 cudaError_t launch_t(const StageArgs& a, cudaStream_t s) {
   const long long nitems = (long long)(a.block_list ? a.nlist : a.lay.nblocks) * a.nchunks * S;
   const int per = a.items_per_cta > 0 ? a.items_per_cta : 1;
   const unsigned grid = (unsigned)((nitems + per - 1) / per);
-  stage_kernel<N, D3, E, S><<<grid, stage_threads<N, E, S>(), smem_for<N, E, S>(), s>>>(a);
+  stage_kernel<N, D3, E, S, BF><<<grid, stage_threads<N, E, S>(), smem_for<N, E, S>(), s>>>(a);
   return cudaGetLastError();
 }
 
-template <int N, bool D3, int E, int S>
+template <int N, bool D3, int E, int S, bool BF = false>
 cudaError_t prepare_one() {
-  return cudaFuncSetAttribute(stage_kernel<N, D3, E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(stage_kernel<N, D3, E, S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_for<N, E, S>());
 }
 
@@ -588,6 +685,7 @@ cudaError_t prepare_one() {
 template <int N, bool D3>
 cudaError_t prepare_t() {
   cudaError_t e = prepare_one<N, D3, 0, 1>();
+  if (e == cudaSuccess) e = prepare_one<N, D3, 0, 1, true>();
   if (e == cudaSuccess) e = prepare_one<N, D3, 2, 1>();
   if (e == cudaSuccess) e = prepare_one<N, D3, 4, 1>();
   if constexpr (N >= 8) {
@@ -604,6 +702,9 @@ cudaError_t launch_s(const StageArgs& a, cudaStream_t s) {
     if (a.ysplit == 2) return launch_t<N, D3, E, 2>(a, s);
   }
   if (a.ysplit != 1) return cudaErrorInvalidValue;
+  if constexpr (E == 0) {
+    if (a.bflux) return launch_t<N, D3, 0, 1, true>(a, s);
+  }
   return launch_t<N, D3, E, 1>(a, s);
 }
 
@@ -642,6 +743,19 @@ cudaError_t stage_prepare(int nx, int ndim) {
 }
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0>(a, s); }
+
+cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s) {
+  const bool d3 = a.lay.ndim == 3;
+  const long long total = (long long)a.lay.nblocks * (d3 ? 6 : 4) * a.lay.nx * (d3 ? a.lay.nx : 1);
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  switch (a.lay.nx) {
+    case 4: d3 ? face_flux_kernel<4, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<4, false><<<grid, 256, 0, s>>>(a, out); break;
+    case 8: d3 ? face_flux_kernel<8, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<8, false><<<grid, 256, 0, s>>>(a, out); break;
+    case 16: d3 ? face_flux_kernel<16, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<16, false><<<grid, 256, 0, s>>>(a, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stage_ring(const StageArgs& a, int ring, cudaStream_t s) {
   if (a.gather || a.smax_acc || a.lay.g < ring + 2) return cudaErrorInvalidValue;

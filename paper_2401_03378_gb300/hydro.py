@@ -247,6 +247,16 @@ class Hydro:
         self._check(self.lib.gbh_get_prim_carry(self.ctx, C.byref(out)))
         return bool(out.value)
 
+    def set_face_prepass(self, enable: bool = True):
+        """Solve every block face once in a pre-pass before each interior stage
+        (on by default on 3-D uniform contexts; the results do not depend on it, bit for bit)."""
+        self._check(self.lib.gbh_set_face_prepass(self.ctx, int(bool(enable))))
+
+    def face_prepass(self) -> bool:
+        out = C.c_int(0)
+        self._check(self.lib.gbh_get_face_prepass(self.ctx, C.byref(out)))
+        return bool(out.value)
+
     # -- adjoint ------------------------------------------------------------
     def step_adjoint(self, Un, dt: float, lam_next, lam_prev=None, U1=None):
         """dJ/dU^n of step(Un, dt) from dJ/dU^{n+1} (dt held fixed, forward branches frozen).

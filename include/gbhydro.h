@@ -246,7 +246,7 @@ int gbh_get_prim_carry(gbh_ctx *ctx, int *enabled);
  * instead of solving each shared face in both blocks.  Results, dt and
  * floor counts are bit for bit those without it (the same face states and
  * HLLC arithmetic).  gbh_create / gbh_create_batched allocate its buffer
- * ([nblocks][6][5][nxb nyb] doubles) and switch it on for 3-D contexts (off
+ * ([nblocks][6][5][nxb max(nxb, nzb)] doubles) and switch it on for 3-D contexts (off
  * if that allocation fails); 2-D contexts start with it off (enable
  * allocates [nblocks][6][5][nxb] doubles).  enable = 0 switches it off (the
  * buffer stays); no effect on two-level contexts.  GBH_ERR_NOMEM if enable

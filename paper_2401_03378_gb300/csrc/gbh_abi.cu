@@ -575,7 +575,7 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimC
 static bool alloc_face_buffer(gbh_ctx* c, bool at_create = false) {
   if (c->refined || (at_create && c->lay.ndim != 3)) return false;
   if (!c->d_bflux) {
-    const size_t nf = (size_t)c->lay.nx * (c->lay.ndim == 3 ? c->lay.nx : 1);
+    const size_t nf = (size_t)c->lay.nx * (c->lay.ndim == 3 ? (c->lay.nz > c->lay.nx ? c->lay.nz : c->lay.nx) : 1);
     if (cudaMalloc(&c->d_bflux, sizeof(double) * 6 * 5 * nf * (size_t)c->lay.nblocks) != cudaSuccess) {
       c->d_bflux = nullptr;
       cudaGetLastError();

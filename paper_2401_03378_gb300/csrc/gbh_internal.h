@@ -60,8 +60,9 @@ struct StageArgs {
   // primitive variables carried from stage to stage (uniform grids, halo
   // gathered; the layout of the state, interior cells only)
   // the fluxes through the blocks' faces, formed before the stage by the face
-  // pre-pass ([nblocks][6][5][N * N2], tangential index fastest: x faces
-  // j + N k, y faces i + N k, z faces i + N j); null: the stage forms them
+  // pre-pass ([nblocks][6][5][NF], NF = N max(N, nz) in 3-D and N in 2-D,
+  // tangential index fastest: x faces j + N k, y faces i + N k, z faces
+  // i + N j); null: the stage forms them
   const double* bflux;
   const double* Win;                // if non-null: the primitives of Uin (no floor counted on reading them)
   double* Wout;                     // if non-null: the epilogue writes the primitives of Uout (and counts
@@ -118,7 +119,7 @@ cudaError_t launch_reflux(double* U, const AmrArgs& a, const double* dt_dev, dou
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 // The face pre-pass of an interior stage (uniform grid, halo gathered): the
 // fluxes through every block face, each face solved once, into out ([nblocks]
-// [6][5][N * N2]); the stage then reads them through a.bflux.
+// [6][5][NF] as StageArgs::bflux); the stage then reads them through a.bflux.
 cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s);
 
 // Telescoping mode (Sec. 4.2): a stage that updates the interior widened by

@@ -176,8 +176,10 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   // blocks: the host takes this kernel only for items of one whole block, so
   // the z march starts at the block's bottom face and ends at its top face)
   constexpr bool bf = BF && E == 0 && S == 1;
-  const double* bfb = bf ? a.bflux + (long long)b * 6 * 5 * (N * (DIM3 ? N : 1)) : nullptr;
-  constexpr int NF = N * (DIM3 ? N : 1);      // faces of one block face
+  // faces per block face in the buffer: N max(N, nz) in 3-D (x and y faces
+  // have N nz, z faces N N), N in 2-D
+  const int NF = DIM3 ? N * (L.nz > N ? L.nz : N) : N;
+  const double* bfb = bf ? a.bflux + (long long)b * 6 * 5 * NF : nullptr;
   if (DIM3) {
     double Wm2[5], Wm1[5], qpm1[5], qm0[5];
     constexpr bool bottom = bf;                // the z face -1/2 comes from the pre-pass
@@ -584,7 +586,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 // the same bits it would have formed.
 template <int N, bool DIM3>
 __global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, double* __restrict__ out) {
-  constexpr int NF = N * (DIM3 ? N : 1);
+  const int nz = a.lay.nz;
+  const int NF = DIM3 ? N * (nz > N ? nz : N) : N;   // slots per block face (x, y faces: N nz; z faces: N N)
   constexpr int NFACES = DIM3 ? 6 : 4;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)a.lay.nblocks * NFACES * NF) return;
@@ -592,6 +595,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, doubl
   const int r = (int)(t - (long long)b * NFACES * NF);
   const int face = r / NF, tt = r - face * NF;
   const int d = face >> 1, side = face & 1;
+  if (DIM3 && tt / N >= (d == 2 ? N : nz)) return;  // past the face's extent
   const int nb = __ldg(a.face_nbr + 6 * b + face);
   if (side == 0 && nb >= 0) return;             // solved by the neighbour, as its high face
   const long long zt = thread_zero(a.eos);
@@ -746,7 +750,8 @@ cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0
 
 cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s) {
   const bool d3 = a.lay.ndim == 3;
-  const long long total = (long long)a.lay.nblocks * (d3 ? 6 : 4) * a.lay.nx * (d3 ? a.lay.nx : 1);
+  const long long total =
+      (long long)a.lay.nblocks * (d3 ? 6 : 4) * a.lay.nx * (d3 ? (a.lay.nz > a.lay.nx ? a.lay.nz : a.lay.nx) : 1);
   const unsigned grid = (unsigned)((total + 255) / 256);
   switch (a.lay.nx) {
     case 4: d3 ? face_flux_kernel<4, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<4, false><<<grid, 256, 0, s>>>(a, out); break;

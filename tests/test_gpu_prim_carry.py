@@ -36,6 +36,8 @@ LATTICES = {
     "3d-16-outflow": wl.lattice_3d(2, 2, 2, 16, 16, 16, 4),
     "3d-8-mixed": wl.lattice_3d(3, 2, 2, 8, 8, 8, 4, bc=("periodic", "outflow", "periodic")),
     "3d-4-periodic": wl.lattice_3d(3, 3, 2, 4, 4, 4, 4, bc="periodic"),
+    "3d-16x16x8": wl.lattice_3d(2, 2, 3, 16, 16, 8, 4),
+    "3d-8x8x12-mixed": wl.lattice_3d(3, 2, 2, 8, 8, 12, 6, bc=("periodic", "outflow", "periodic")),
     "2d-16-outflow": wl.lattice_2d(4, 3, 16, 16, 4),
     "2d-8-mixed-ng2": wl.lattice_2d(3, 3, 8, 8, 2, bc=("periodic", "outflow")),
 }

@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, doubl
   const Eos e = reg_eos(a.eos, zt);
   const Rk& rk = e.k;
   // the cell coordinates along the normal: two below the face, two above
-  const int p0 = side ? N - 2 : -2;
+  const int p0 = side ? (d == 2 ? nz : N) - 2 : -2;
   const int t1 = tt % N, t2 = DIM3 ? tt / N : 0;
   double Q[4][5];
 #pragma unroll

@@ -238,19 +238,20 @@ int gbh_get_prim_carry(gbh_ctx *ctx, int *enabled);
 
 /* Face pre-pass (not a choice the paper makes; how the blocks of the
  * concurrent-data pattern, Sec. 3.2, share their boundary work).  Each
- * interior stage that gathers its halo over all blocks of a uniform or
- * batched context (ring 0, one row band, whole blocks, every block) first runs a kernel
+ * interior stage that gathers its halo (ring 0, one row band, whole blocks;
+ * uniform, batched and two-level contexts, all-levels steps) first runs a kernel
  * that solves the flux through every block face once: the block on the high
  * side of a face solves it for both blocks, and a block solves its low face
- * itself only at an outflow edge.  The stage kernel then reads those fluxes
+ * itself only where it has no face neighbour (an outflow edge, a face onto
+ * the coarser level).  The stage kernel then reads those fluxes
  * instead of solving each shared face in both blocks.  Results, dt and
  * floor counts are bit for bit those without it (the same face states and
- * HLLC arithmetic).  gbh_create / gbh_create_batched allocate its buffer
- * ([nblocks][6][5][nxb max(nxb, nzb)] doubles) and switch it on for 3-D contexts (off
+ * HLLC arithmetic).  Every gbh_create* allocates its buffer ([nblocks][6]
+ * [5][nxb max(nxb, nzb)] doubles) and switches it on for 3-D contexts (off
  * if that allocation fails); 2-D contexts start with it off (enable
  * allocates [nblocks][6][5][nxb] doubles).  enable = 0 switches it off (the
- * buffer stays); no effect on two-level contexts.  GBH_ERR_NOMEM if enable
- * != 0 and the buffer cannot be allocated.  Drops a captured graph. */
+ * buffer stays).  GBH_ERR_NOMEM if enable != 0 and the buffer cannot be
+ * allocated.  Drops a captured graph. */
 int gbh_set_face_prepass(gbh_ctx *ctx, int enable);
 int gbh_get_face_prepass(gbh_ctx *ctx, int *enabled);
 

@@ -200,8 +200,8 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   }
   A.items_per_cta = c->items_per_cta;
   A.ysplit = (ring == 0 || ring == 2 || ring == 4) ? c->ysplit[ring / 2] : 1;
-  const bool prepass = c->face_prepass && c->d_bflux && ring == 0 && gather && !c->refined && !list &&
-                       A.ysplit == 1 && A.nchunks == 1;
+  const bool prepass = c->face_prepass && c->d_bflux && ring == 0 && gather && !list && A.ysplit == 1 &&
+                       A.nchunks == 1;
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
@@ -573,7 +573,7 @@ static int step_cfl(gbh_ctx* c, double* U, double* dt_dev, cudaStream_t s, PrimC
 // boundary faces for what the extra launch costs (the 96-problem 2-D ensemble
 // measured 1.2% slower with it, the 256^3 3-D step 3.3% faster).
 static bool alloc_face_buffer(gbh_ctx* c, bool at_create = false) {
-  if (c->refined || (at_create && c->lay.ndim != 3)) return false;
+  if (at_create && c->lay.ndim != 3) return false;
   if (!c->d_bflux) {
     const size_t nf = (size_t)c->lay.nx * (c->lay.ndim == 3 ? (c->lay.nz > c->lay.nx ? c->lay.nz : c->lay.nx) : 1);
     if (cudaMalloc(&c->d_bflux, sizeof(double) * 6 * 5 * nf * (size_t)c->lay.nblocks) != cudaSuccess) {
@@ -863,6 +863,7 @@ int gbh_create_refined(const gbh_params* p, const gbh_refinement* r, gbh_ctx** o
   A.eos = c->eos;
   A.floor_count = c->d_words + 1;
   alloc_prim_buffers(c);
+  alloc_face_buffer(c, true);
   *out = c;
   return GBH_OK;
 }
@@ -1074,7 +1075,6 @@ int gbh_set_face_prepass(gbh_ctx* c, int enable) {
     c->face_prepass = false;
     return GBH_OK;
   }
-  if (c->refined) return GBH_OK;
   if (!alloc_face_buffer(c)) return set_err(c, GBH_ERR_NOMEM, "face pre-pass buffer: device allocation failed");
   return GBH_OK;
 }

@@ -578,8 +578,9 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
 // The face pre-pass: one thread per (block, face, face cell).  The flux
 // through a face is solved once: by the block on its high side (x = N - 1/2,
 // y = N - 1/2, z = nz - 1/2, which also writes it into the neighbour's slot
-// for that neighbour's low face), and, where a block has no neighbour on a
-// low side (an outflow edge), by that block.  Face states as the stage
+// for that neighbour's low face), and, where a block has no face neighbour
+// on a low side (an outflow edge, or on a two-level grid a face whose halo is
+// the block's own prolonged guard cells), by that block.  Face states as the stage
 // kernel forms them (the plus state of the cell below the face, the minus
 // state of the cell above, MC slopes of the primitives, the same arithmetic
 // and halo addressing), the same HLLC, the same rotations: the stage reads

@@ -1,6 +1,6 @@
 """The face pre-pass (gbh_set_face_prepass): before each interior stage of a
-uniform or batched context a kernel solves the flux through every block face
-once, and the stage reads those fluxes instead of solving each shared face in
+uniform, batched or two-level context a kernel solves the flux through every
+block face once, and the stage reads those fluxes instead of solving each shared face in
 both blocks.  Every entry point gives the states, dt, dt histories and floor
 counts of the pre-pass off, bit for bit: the same face states and HLLC
 arithmetic on the same halo."""
@@ -88,9 +88,33 @@ def test_batched_and_other_contexts(gb):
     on_and_off(make, wl.random_state(lat, seed=85, rough=True))
     assert gb.Hydro.from_lattice(lat).face_prepass()                    # on by default in 3-D
     assert not gb.Hydro.from_lattice(wl.lattice_2d(2, 2, 8, 8, 4)).face_prepass()   # off in 2-D
-    tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))
-    h = gb.Hydro.from_two_level(tl)
-    assert not h.face_prepass()
-    h.set_face_prepass(True)
-    assert not h.face_prepass()
-    h.close()
+
+
+TWO_LEVEL = [wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3)),
+             wl.two_level_blocks(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4, bc="periodic"),
+                                 [(1, 1, 1), (2, 1, 1), (1, 2, 1), (1, 1, 2)]),
+             wl.two_level(wl.lattice_3d(4, 4, 3, 16, 16, 16, 4, bc=("periodic", "outflow", "outflow")),
+                          (1, 1, 1), (3, 3, 2))]
+
+
+@pytest.mark.parametrize("stages", [2, 3])
+@pytest.mark.parametrize("ti", range(len(TWO_LEVEL)), ids=["box", "tripod-periodic", "16-mixed"])
+def test_two_level_bitwise(gb, ti, stages):
+    """All-levels two-level steps: same-level faces solved once, faces onto the
+    coarser level by each side from its own halo (the fine block's prolonged
+    guard cells), the flux registers filled from the pre-pass fluxes."""
+    from tests.test_gpu_prim_carry import smooth_two_level
+    tl = TWO_LEVEL[ti]
+
+    def make():
+        h = gb.Hydro.from_two_level(tl)
+        h.set_rk_stages(stages)
+        return h
+    assert on_and_off(make, smooth_two_level(tl, 12)[tl.gpu_blocks]) == [0] * 6
+
+
+def test_two_level_batched_bitwise(gb):
+    from tests.test_gpu_prim_carry import smooth_two_level
+    tls = [wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))] * 3
+    U0 = np.concatenate([smooth_two_level(t, 20 + i)[t.gpu_blocks] for i, t in enumerate(tls)])
+    on_and_off(lambda: gb.Hydro.from_two_level_batch(tls), U0)

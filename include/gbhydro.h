@@ -412,6 +412,22 @@ int hydro_advance_host(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist
  * hydro_step_cfl's bit for bit. */
 int hydro_step_host(gbh_ctx *ctx, double *U_host, double *dt_host, void *stream);
 
+/* hydro_step_host for a host state that holds the interior cells only:
+ * U_host (HOST, pinned or pageable) is laid out as
+ *     U_host[nblocks][5][nzb][nyb][nxb]   (x fastest)
+ * with the variables of the state layout, and is replaced by the new state in
+ * the same layout.  Guard cells are not inputs of a step (every stage fills
+ * them from neighbour interiors or the boundary conditions), so only interior
+ * bytes cross the host link: at 16^3 blocks with 4 guard cells 4096 of 13824
+ * cells per variable.  Each chunk of blocks is copied into a context-owned
+ * device staging buffer (one interior-sized array, allocated on first use)
+ * and scattered into the padded device state by a kernel on the copy stream;
+ * the new state is gathered and copied back the same way.  dt_host, the
+ * chunks, the step forms that run unpipelined, errors and synchronisation are
+ * those of hydro_step_host, and the interior results equal hydro_step_cfl's
+ * bit for bit. */
+int hydro_step_host_interior(gbh_ctx *ctx, double *U_host, double *dt_host, void *stream);
+
 /* Number of block chunks hydro_step_host pipelines (1..64); 0 (the default)
  * picks the fewest chunks of at most two resident CTAs per SM, one wave of the
  * stage kernel each.  GBH_ERR_INVAL outside [0, 64]. */

@@ -85,6 +85,7 @@ SIGNATURES = {
     "hydro_advance": (C.c_int, [_vp, _dp, C.c_int, _dp, _dp, _vp]),
     "hydro_advance_host": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "hydro_step_host": (C.c_int, [_vp, _dp, _dp, _vp]),
+    "hydro_step_host_interior": (C.c_int, [_vp, _dp, _dp, _vp]),
     "gbh_set_host_pipeline": (C.c_int, [_vp, C.c_int]),
     "hydro_check_state": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), _vp]),
     "hydro_floor_hits": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),

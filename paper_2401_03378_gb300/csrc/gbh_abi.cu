@@ -102,6 +102,7 @@ struct gbh_ctx {
   int* d_ident = nullptr;           // identity block list
   double* d_pipe_out = nullptr;     // the new state
   double* d_pipe_dt = nullptr;      // its CFL dt
+  double* d_pipe_int = nullptr;     // interior-only staging (hydro_step_host_interior)
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -167,10 +168,13 @@ int record_start(gbh_ctx* c, cudaStream_t s, cudaEvent_t* stop) {
 
 // One stage launch.  ring > 0: the telescoping form that also updates that
 // many guard cells around the interior, from Uin's own guard cells.
+// range_first >= 0: `list` is the identity list of blocks [range_first,
+// range_first + nlist), one of a sequence of consecutive ranges whose stages
+// run in block order on one stream (the face pre-pass then serves it too).
 int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, const double* dt_dev,
                  double dt, double a, double b, bool gather, bool dt_epilogue, cudaStream_t s, int ring = 0,
                  double* flux_reg = nullptr, const int* list = nullptr, int nlist = 0,
-                 const double* Win = nullptr, double* Wout = nullptr) {
+                 const double* Win = nullptr, double* Wout = nullptr, int range_first = -1) {
   gbh::StageArgs A{};
   A.Uin = Uin;
   A.Un = Un;
@@ -200,8 +204,8 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   }
   A.items_per_cta = c->items_per_cta;
   A.ysplit = (ring == 0 || ring == 2 || ring == 4) ? c->ysplit[ring / 2] : 1;
-  const bool prepass = c->face_prepass && c->d_bflux && ring == 0 && gather && !list && A.ysplit == 1 &&
-                       A.nchunks == 1;
+  const bool prepass = c->face_prepass && c->d_bflux && ring == 0 && gather && (!list || range_first >= 0) &&
+                       A.ysplit == 1 && A.nchunks == 1;
   if (c->refined) {
     A.block_list = c->d_active;
     A.nlist = c->nactive;
@@ -218,7 +222,8 @@ int stage_launch(gbh_ctx* c, const double* Uin, const double* Un, double* Uout, 
   if (rc) return rc;
   if (prepass) {
     // each block face solved once, then read by the stage
-    if ((rc = cuda_err(c, gbh::launch_face_fluxes(A, c->d_bflux, s), "face pre-pass launch"))) return rc;
+    const int lo = list ? range_first : 0, hi = list ? range_first + nlist : -1;
+    if ((rc = cuda_err(c, gbh::launch_face_fluxes(A, c->d_bflux, s, lo, hi), "face pre-pass launch"))) return rc;
     A.bflux = c->d_bflux;
   }
   rc = cuda_err(c, ring > 0 ? gbh::launch_stage_ring(A, ring, s) : gbh::launch_stage(A, s), "stage kernel launch");
@@ -1338,6 +1343,7 @@ int gbh_destroy(gbh_ctx* c) {
   cudaFree(c->d_ident);
   cudaFree(c->d_pipe_out);
   cudaFree(c->d_pipe_dt);
+  cudaFree(c->d_pipe_int);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
   return GBH_OK;
@@ -1465,12 +1471,21 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
   return cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
 }
 
+// Doubles of one block in the interior-only layout [5][nz][ny][nx].
+static long long interior_cells(const Layout& L) { return 5LL * L.nx * L.ny * L.nz; }
+
 // Buffers, chunks, streams and events of the pipelined host-buffer step.
-static int pipe_setup(gbh_ctx* c) {
+static int pipe_setup(gbh_ctx* c, bool interior) {
   const size_t bytes = sizeof(double) * state_elems(c->lay);
   const int NB = c->lay.nblocks;
   cudaError_t e = cudaSuccess;
   if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
+  if (e == cudaSuccess && interior && !c->d_pipe_int) {
+    // the interior-only form writes the interior of d_host_state alone: its
+    // guard cells get defined values once (the steps never read them)
+    e = cudaMalloc(&c->d_pipe_int, sizeof(double) * interior_cells(c->lay) * NB);
+    if (e == cudaSuccess) e = cudaMemset(c->d_host_state, 0, bytes);
+  }
   if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double) * c->nproblems);
   if (e == cudaSuccess && !c->d_pipe_out) {
     e = cudaMalloc(&c->d_pipe_out, bytes);
@@ -1525,23 +1540,55 @@ static int pipe_setup(gbh_ctx* c) {
   return GBH_OK;
 }
 
-int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
+// hydro_step_host (interior = false: U_host in the padded state layout) and
+// hydro_step_host_interior (interior = true: U_host holds the interior cells
+// only, [nblocks][5][nz][ny][nx]; each chunk is copied into the staging buffer
+// d_pipe_int and scattered into the padded device state by a kernel on the
+// copy stream, and gathered back the same way, so only interior bytes cross
+// the host link).  The staging region of chunk k is read by its scatter
+// before its stage-1 launch and written by its gather after its stage-2
+// launch, which waits (through the stage-1 events) for that scatter: one
+// buffer serves both directions.
+static int host_step(gbh_ctx* c, double* U_host, double* dt_host, void* stream, bool interior) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U_host || !dt_host) return set_err(c, GBH_ERR_INVAL, "U_host and dt_host must be non-null");
   const bool given = dt_host[0] > 0.0;
   for (int p = 0; given && p < c->nproblems; ++p)
     if ((rc = check_dt(c, dt_host[p]))) return rc;
-  if ((rc = pipe_setup(c))) return rc;
+  if ((rc = pipe_setup(c, interior))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bstride = sizeof(double) * (size_t)c->lay.bstride;
+  const Layout& L = c->lay;
+  const size_t bstride = sizeof(double) * (size_t)L.bstride;
+  const long long cells = interior_cells(L);
   const size_t dtb = sizeof(double) * c->nproblems;
   double* U = c->d_host_state;
+  // blocks [first, first + cnt) of the host state into the padded device state dst
+  auto copy_in = [&](double* dst, int first, int cnt, cudaStream_t st) -> cudaError_t {
+    if (!interior)
+      return cudaMemcpyAsync(dst + (size_t)first * L.bstride, U_host + (size_t)first * L.bstride,
+                             bstride * (size_t)cnt, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(c->d_pipe_int + first * cells, U_host + first * cells,
+                                    sizeof(double) * cells * cnt, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = gbh::launch_interior_copy(dst, c->d_pipe_int, L, first, cnt, true, st);
+    return e;
+  };
+  // the same blocks of the padded device state src back into the host state
+  auto copy_out = [&](double* src, int first, int cnt, cudaStream_t st) -> cudaError_t {
+    if (!interior)
+      return cudaMemcpyAsync(U_host + (size_t)first * L.bstride, src + (size_t)first * L.bstride,
+                             bstride * (size_t)cnt, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = gbh::launch_interior_copy(src, c->d_pipe_int, L, first, cnt, false, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(U_host + first * cells, c->d_pipe_int + first * cells, sizeof(double) * cells * cnt,
+                          cudaMemcpyDeviceToHost, st);
+    return e;
+  };
   cudaError_t e = cudaSuccess;
   if (c->refined || c->telescoping || c->nstages != 2) {
     // the other step forms exchange data across the whole state between their
     // stages: copy in, step, copy out
-    e = cudaMemcpyAsync(U, U_host, bstride * c->lay.nblocks, cudaMemcpyHostToDevice, s);
+    e = copy_in(U, 0, L.nblocks, s);
     if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, s);
     if ((rc = cuda_err(c, e, "H2D copy"))) return rc;
     if (!given && (rc = reduce_dt(c, U, c->d_host_dt, nullptr, s))) return rc;
@@ -1552,7 +1599,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     if (!rc) rc = cuda_err(c, gbh::launch_dt_finalize(c->d_smax, c->cfl, c->d_pipe_dt, nullptr, s, c->nproblems),
                            "dt finalize launch");
     if (rc) return rc;
-    e = cudaMemcpyAsync(U_host, U, bstride * c->lay.nblocks, cudaMemcpyDeviceToHost, s);
+    e = copy_out(U, 0, L.nblocks, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt_host, c->d_pipe_dt, dtb, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_err(c, e, "host step");
@@ -1562,6 +1609,11 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
   // is done up to need[k]; stage 2 writes a separate state so that later
   // stage-1 launches still read U^n; chunk k goes back as soon as its stage 2
   // is done.  With dt given, copy-in, both stages and copy-out overlap.
+  // The face pre-pass runs per chunk (stage_launch's block range): a chunk's
+  // stage reads only slots written by the pre-pass of its own chunk or of an
+  // earlier one on the same stream, and the stage-2 pre-pass of chunk k writes
+  // only slots of blocks in chunks up to need[k], whose stage-1 launches it
+  // waits for; every writer of a slot in a stage writes the same face's bits.
   const int K = c->pipe_chunks;
   // stage 1 leaves the primitives of U(1) for stage 2 (chunk k's stage 2 reads
   // them only from the chunks whose stage 1 it waits for, like U(1) itself)
@@ -1575,9 +1627,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->pipe_mark[0], 0);
   if (e == cudaSuccess && given) e = cudaMemcpyAsync(c->d_host_dt, dt_host, dtb, cudaMemcpyHostToDevice, sin);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
-    const size_t off = (size_t)c->pipe_first[k] * c->lay.bstride;
-    const size_t n = bstride * (size_t)(c->pipe_first[k + 1] - c->pipe_first[k]);
-    e = cudaMemcpyAsync(U + off, U_host + off, n, cudaMemcpyHostToDevice, sin);
+    e = copy_in(U, c->pipe_first[k], c->pipe_first[k + 1] - c->pipe_first[k], sin);
     if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], sin);
   }
   if ((rc = cuda_err(c, e, "H2D copies"))) return rc;
@@ -1589,7 +1639,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
     if ((rc = cuda_err(c, cudaStreamWaitEvent(s1, ev_in[c->pipe_need[k]], 0), "event wait"))) return rc;
     rc = stage_launch(c, U, nullptr, c->d_scratch, c->d_host_dt, 0.0, 0.0, 1.0, true, false, s1, 0, nullptr,
-                      c->d_ident + first, cnt, nullptr, W1);
+                      c->d_ident + first, cnt, nullptr, W1, first);
     if (rc) return rc;
     if ((rc = cuda_err(c, cudaEventRecord(ev_s1[k], s1), "event record"))) return rc;
   }
@@ -1597,7 +1647,7 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     const int first = c->pipe_first[k], cnt = c->pipe_first[k + 1] - first;
     if ((rc = cuda_err(c, cudaStreamWaitEvent(s2, ev_s1[c->pipe_need[k]], 0), "event wait"))) return rc;
     rc = stage_launch(c, c->d_scratch, U, c->d_pipe_out, c->d_host_dt, 0.0, 0.5, 0.5, true, true, s2, 0, nullptr,
-                      c->d_ident + first, cnt, W1);
+                      c->d_ident + first, cnt, W1, nullptr, first);
     if (rc) return rc;
     if ((rc = cuda_err(c, cudaEventRecord(ev_s2[k], s2), "event record"))) return rc;
   }
@@ -1606,10 +1656,8 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
     return rc;
   e = cudaEventRecord(c->pipe_mark[1], s2);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
-    const size_t off = (size_t)c->pipe_first[k] * c->lay.bstride;
-    const size_t n = bstride * (size_t)(c->pipe_first[k + 1] - c->pipe_first[k]);
     e = cudaStreamWaitEvent(sout, ev_s2[k], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(U_host + off, c->d_pipe_out + off, n, cudaMemcpyDeviceToHost, sout);
+    if (e == cudaSuccess) e = copy_out(c->d_pipe_out, c->pipe_first[k], c->pipe_first[k + 1] - c->pipe_first[k], sout);
   }
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, c->pipe_mark[1], 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dt_host, c->d_pipe_dt, dtb, cudaMemcpyDeviceToHost, sout);
@@ -1623,6 +1671,14 @@ int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->pipe_mark[2], 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_err(c, e, "host step");
+}
+
+int hydro_step_host(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
+  return host_step(c, U_host, dt_host, stream, false);
+}
+
+int hydro_step_host_interior(gbh_ctx* c, double* U_host, double* dt_host, void* stream) {
+  return host_step(c, U_host, dt_host, stream, true);
 }
 
 int hydro_check_state(gbh_ctx* c, const double* U, long long* nbad_host, void* stream) {

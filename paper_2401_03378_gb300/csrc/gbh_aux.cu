@@ -185,6 +185,31 @@ __global__ void __launch_bounds__(kThreads) check_kernel(const double* U, const 
   if (bad) atomicAdd(count, bad);
 }
 
+// Interior cells between the padded and the interior-only layouts of the nb
+// blocks that start at `padded` and `interior`: one thread per cell,
+// consecutive threads along x, so both sides read and write whole rows of nx
+// doubles (coalesced).  The launcher keeps 5 nx ny nz nb below 2^30, so the
+// cell index and its decomposition are 32-bit.
+__global__ void __launch_bounds__(kThreads) interior_copy_kernel(double* padded, double* interior, const Layout L,
+                                                                 int nb, bool to_padded) {
+  const unsigned per = (unsigned)(L.nx * L.ny * L.nz), cells = 5u * per, total = cells * (unsigned)nb;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const unsigned bl = t / cells;
+    unsigned r = t - bl * cells;
+    const unsigned v = r / per;
+    r -= v * per;
+    const unsigned i = r % (unsigned)L.nx;
+    r /= (unsigned)L.nx;
+    const unsigned j = r % (unsigned)L.ny, k = r / (unsigned)L.ny;
+    const long long o = (long long)bl * L.bstride + (long long)v * L.vstride +
+                        ((long long)(k + L.gz) * L.nyp + (j + L.g)) * L.nxp + (i + L.g);
+    if (to_padded)
+      padded[GBH_IX(o, (long long)nb * L.bstride)] = interior[GBH_IX(t, total)];
+    else
+      interior[GBH_IX(t, total)] = padded[GBH_IX(o, (long long)nb * L.bstride)];
+  }
+}
+
 // 8 independent FMA chains per thread; the multiplier and addend keep the
 // values bounded (fixed point 1.0).  Only the first `lanes` lanes of each
 // warp run the chains (to measure how the FP64 pipe charges partial warps).
@@ -351,6 +376,20 @@ cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
   const long long items = (long long)a.lay.nblocks * a.lay.nzp;
   fill_kernel<<<(int)(items < 152LL * 16 ? items : 152LL * 16), kThreads, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_interior_copy(double* padded, double* interior, const Layout& L, int b0, int nb,
+                                 bool to_padded, cudaStream_t s) {
+  const long long cells = 5LL * L.nx * L.ny * L.nz;
+  const long long per_launch = (1LL << 30) / cells > 0 ? (1LL << 30) / cells : 1;
+  for (long long b = b0; b < (long long)b0 + nb; b += per_launch) {
+    const int n = (int)((long long)b0 + nb - b < per_launch ? (long long)b0 + nb - b : per_launch);
+    interior_copy_kernel<<<grid_for(cells * n, kThreads), kThreads, 0, s>>>(padded + b * L.bstride,
+                                                                           interior + b * cells, L, n, to_padded);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_dt_reduce(const DtArgs& a, cudaStream_t s) {

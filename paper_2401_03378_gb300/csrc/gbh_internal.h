@@ -120,7 +120,12 @@ cudaError_t launch_stage(const StageArgs& a, cudaStream_t s);
 // The face pre-pass of an interior stage (uniform grid, halo gathered): the
 // fluxes through every block face, each face solved once, into out ([nblocks]
 // [6][5][NF] as StageArgs::bflux); the stage then reads them through a.bflux.
-cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s);
+// Blocks [lo, hi) (hi < 0: all): the faces of a stage over that range of a
+// sequence of such ranges in block order.  A block's low face is solved by its
+// neighbour, as that block's high face, when the neighbour is below hi (in
+// this range or an earlier one), else by the block itself; a high face is
+// written into the neighbour's slot when the neighbour is at or above lo.
+cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s, int lo = 0, int hi = -1);
 
 // Telescoping mode (Sec. 4.2): a stage that updates the interior widened by
 // `ring` cells (0, 2 or 4) from the block's own guard cells (gather = 0),
@@ -161,6 +166,13 @@ cudaError_t launch_dt_reduce_blocks(const DtArgs& a, const int* problem, cudaStr
 
 cudaError_t launch_check(const double* U, Layout lay, Eos eos, unsigned long long* count,
                          cudaStream_t s);
+
+// Interior cells of blocks [b0, b0 + nb) between the padded state layout and
+// the interior-only layout [nblocks][5][nz][ny][nx] (the same block origin b0
+// in both): to_padded = true scatters `interior` into the interior cells of
+// `padded`, false gathers them.  Guard cells are neither read nor written.
+cudaError_t launch_interior_copy(double* padded, double* interior, const Layout& L, int b0, int nb,
+                                 bool to_padded, cudaStream_t s);
 
 size_t stage_vjp_scratch_doubles(const Layout& L, int ring = 0);   // face-slot buffer of a (box) stage VJP
 cudaError_t launch_stage_vjp(const StageArgs& a, const double* M, double scale, const double* A, double cA,

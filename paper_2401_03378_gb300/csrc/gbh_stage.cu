@@ -575,30 +575,37 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int item, double*
   }
 }
 
-// The face pre-pass: one thread per (block, face, face cell).  The flux
-// through a face is solved once: by the block on its high side (x = N - 1/2,
-// y = N - 1/2, z = nz - 1/2, which also writes it into the neighbour's slot
-// for that neighbour's low face), and, where a block has no face neighbour
-// on a low side (an outflow edge, or on a two-level grid a face whose halo is
-// the block's own prolonged guard cells), by that block.  Face states as the stage
+// The face pre-pass: one thread per (block, face, face cell) over blocks
+// [lo, hi).  The flux through a face is solved once: by the block on its high
+// side (x = N - 1/2, y = N - 1/2, z = nz - 1/2, which also writes it into the
+// neighbour's slot for that neighbour's low face), and, where a block has no
+// face neighbour on a low side (an outflow edge, or on a two-level grid a face
+// whose halo is the block's own prolonged guard cells), by that block.  When
+// the stage runs over consecutive block ranges in order (the host-buffer
+// pipeline), a low face whose neighbour lies in a later range (a periodic
+// wrap) is solved by the block itself, and a high face is written into the
+// neighbour's slot only when the neighbour is in this range or a later one
+// (an earlier range's stage has already read its slots).  Face states as the stage
 // kernel forms them (the plus state of the cell below the face, the minus
 // state of the cell above, MC slopes of the primitives, the same arithmetic
 // and halo addressing), the same HLLC, the same rotations: the stage reads
 // the same bits it would have formed.
 template <int N, bool DIM3>
-__global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, double* __restrict__ out, int lo,
+                                                        int hi) {
   const int nz = a.lay.nz;
   const int NF = DIM3 ? N * (nz > N ? nz : N) : N;   // slots per block face (x, y faces: N nz; z faces: N N)
   constexpr int NFACES = DIM3 ? 6 : 4;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)a.lay.nblocks * NFACES * NF) return;
-  const int b = (int)(t / (NFACES * NF));
-  const int r = (int)(t - (long long)b * NFACES * NF);
+  if (t >= (long long)(hi - lo) * NFACES * NF) return;
+  const int bl = (int)(t / (NFACES * NF));
+  const int r = (int)(t - (long long)bl * NFACES * NF);
+  const int b = lo + bl;
   const int face = r / NF, tt = r - face * NF;
   const int d = face >> 1, side = face & 1;
   if (DIM3 && tt / N >= (d == 2 ? N : nz)) return;  // past the face's extent
   const int nb = __ldg(a.face_nbr + 6 * b + face);
-  if (side == 0 && nb >= 0) return;             // solved by the neighbour, as its high face
+  if (side == 0 && nb >= 0 && nb < hi) return;  // solved by the neighbour, as its high face
   const long long zt = thread_zero(a.eos);
   const Eos e = reg_eos(a.eos, zt);
   const Rk& rk = e.k;
@@ -632,7 +639,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const StageArgs a, doubl
   double* o = out + ((long long)b * 6 + face) * 5 * NF + tt;
 #pragma unroll
   for (int v = 0; v < 5; ++v) o[v * NF] = G[v];
-  if (side == 1 && nb >= 0) {
+  if (side == 1 && nb >= lo) {
     double* on = out + ((long long)nb * 6 + (face - 1)) * 5 * NF + tt;
 #pragma unroll
     for (int v = 0; v < 5; ++v) on[v * NF] = G[v];
@@ -749,15 +756,18 @@ cudaError_t stage_prepare(int nx, int ndim) {
 
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t s) { return launch_e<0>(a, s); }
 
-cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s) {
+cudaError_t launch_face_fluxes(const StageArgs& a, double* out, cudaStream_t s, int lo, int hi) {
   const bool d3 = a.lay.ndim == 3;
+  if (hi < 0) hi = a.lay.nblocks;
+  if (lo < 0 || lo > hi || hi > a.lay.nblocks) return cudaErrorInvalidValue;
+  if (lo == hi) return cudaSuccess;
   const long long total =
-      (long long)a.lay.nblocks * (d3 ? 6 : 4) * a.lay.nx * (d3 ? (a.lay.nz > a.lay.nx ? a.lay.nz : a.lay.nx) : 1);
+      (long long)(hi - lo) * (d3 ? 6 : 4) * a.lay.nx * (d3 ? (a.lay.nz > a.lay.nx ? a.lay.nz : a.lay.nx) : 1);
   const unsigned grid = (unsigned)((total + 255) / 256);
   switch (a.lay.nx) {
-    case 4: d3 ? face_flux_kernel<4, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<4, false><<<grid, 256, 0, s>>>(a, out); break;
-    case 8: d3 ? face_flux_kernel<8, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<8, false><<<grid, 256, 0, s>>>(a, out); break;
-    case 16: d3 ? face_flux_kernel<16, true><<<grid, 256, 0, s>>>(a, out) : face_flux_kernel<16, false><<<grid, 256, 0, s>>>(a, out); break;
+    case 4: d3 ? face_flux_kernel<4, true><<<grid, 256, 0, s>>>(a, out, lo, hi) : face_flux_kernel<4, false><<<grid, 256, 0, s>>>(a, out, lo, hi); break;
+    case 8: d3 ? face_flux_kernel<8, true><<<grid, 256, 0, s>>>(a, out, lo, hi) : face_flux_kernel<8, false><<<grid, 256, 0, s>>>(a, out, lo, hi); break;
+    case 16: d3 ? face_flux_kernel<16, true><<<grid, 256, 0, s>>>(a, out, lo, hi) : face_flux_kernel<16, false><<<grid, 256, 0, s>>>(a, out, lo, hi); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -54,6 +54,7 @@ class Hydro:
         self.nguard = int(nguard)
         gz = self.nguard if ndim == 3 else 0
         self.shape = (self.nblocks, 5, nz + 2 * gz, ny + 2 * self.nguard, nx + 2 * self.nguard)
+        self.interior_shape = (self.nblocks, 5, nz, ny, nx)
         p = _abi.GbhParams()
         p.ndim, p.nxb, p.nyb, p.nzb = self.ndim, nx, ny, nz
         p.nguard, p.nblocks = self.nguard, self.nblocks
@@ -297,7 +298,8 @@ class Hydro:
                                                     self._state(lamW, "lamW"), _stream_handle()))
         return lamW
 
-    def _host_state(self, U_host) -> int:
+    def _host_state(self, U_host, shape=None) -> int:
+        shape = self.shape if shape is None else shape
         if isinstance(U_host, torch.Tensor):
             if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous():
                 raise TypeError("U_host must be a contiguous float64 CPU tensor")
@@ -306,8 +308,8 @@ class Hydro:
             if U_host.dtype != np.float64 or not U_host.flags.c_contiguous:
                 raise TypeError("U_host must be a C-contiguous float64 array")
             ptr = U_host.ctypes.data
-        if tuple(U_host.shape) != self.shape:
-            raise ValueError(f"U_host must have shape {self.shape}")
+        if tuple(U_host.shape) != shape:
+            raise ValueError(f"U_host must have shape {shape}")
         return ptr
 
     def step_host(self, U_host, dt_host):
@@ -319,6 +321,17 @@ class Hydro:
             raise TypeError("dt_host must be a contiguous float64 array with one entry per problem")
         self._check(self.lib.hydro_step_host(self.ctx, self._host_state(U_host), dt_host.ctypes.data,
                                              _stream_handle()))
+        return U_host
+
+    def step_host_interior(self, U_host, dt_host):
+        """step_host for a host state of the interior cells only, shape
+        interior_shape = (nblocks, 5, nz, ny, nx): only those bytes cross the
+        host link.  dt_host as in step_host; returns U_host."""
+        if not (isinstance(dt_host, np.ndarray) and dt_host.dtype == np.float64 and dt_host.size >= self.nproblems
+                and dt_host.flags.c_contiguous):
+            raise TypeError("dt_host must be a contiguous float64 array with one entry per problem")
+        self._check(self.lib.hydro_step_host_interior(self.ctx, self._host_state(U_host, self.interior_shape),
+                                                      dt_host.ctypes.data, _stream_handle()))
         return U_host
 
     def set_host_pipeline(self, chunks: int = 0):

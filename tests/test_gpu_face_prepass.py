@@ -118,3 +118,33 @@ def test_two_level_batched_bitwise(gb):
     tls = [wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))] * 3
     U0 = np.concatenate([smooth_two_level(t, 20 + i)[t.gpu_blocks] for i, t in enumerate(tls)])
     on_and_off(lambda: gb.Hydro.from_two_level_batch(tls), U0)
+
+
+@pytest.mark.parametrize("chunks", [0, 3, 5, 64])
+@pytest.mark.parametrize("interior", [False, True])
+def test_host_pipeline_chunks_bitwise(gb, chunks, interior):
+    """The pipelined host-buffer steps run the face pre-pass per chunk of
+    consecutive blocks: a low face whose neighbour lies in a later chunk (here
+    the periodic wraps in x, y and z) is solved by the block itself, a high
+    face is written into the neighbour's slot only for a neighbour in this or
+    a later chunk.  States and dt equal hydro_step_cfl's with the pre-pass off,
+    for chunks of one block, uneven chunks and the default chunking."""
+    lat = wl.lattice_3d(4, 4, 4, 8, 8, 8, 4, bc="periodic")
+    U0 = wl.random_state(lat, seed=86, rough=True)
+    hd, hh = gb.Hydro.from_lattice(lat), gb.Hydro.from_lattice(lat)
+    hd.set_face_prepass(False)
+    hh.set_host_pipeline(chunks)
+    assert hh.face_prepass()
+    sl = (slice(None), slice(None)) + tuple(lat.interior_slices())
+    D = torch.from_numpy(U0.copy()).cuda()
+    dt = hd.compute_dt(D)
+    Uh = torch.from_numpy(np.ascontiguousarray(U0[sl]) if interior else U0.copy()).pin_memory()
+    dth = np.zeros(1)
+    for _ in range(3):
+        hd.step_cfl(D, dt)
+        (hh.step_host_interior if interior else hh.step_host)(Uh, dth)
+        got = Uh.numpy() if interior else Uh.numpy()[sl]
+        assert np.array_equal(D.cpu().numpy()[sl], got)
+        assert np.array_equal(dt.cpu().numpy(), dth)
+    hd.close()
+    hh.close()

@@ -332,6 +332,59 @@ def test_step_host_equals_device_steps_bitwise(gb, kind):
         assert np.array_equal(host(dt), dth)
 
 
+@pytest.mark.parametrize("kind", ["3d", "2d_many_chunks", "periodic_z", "batched", "pageable", "telescoping",
+                                  "three_stages", "two_level"])
+def test_step_host_interior_equals_device_steps_bitwise(gb, kind):
+    """hydro_step_host_interior (a host state of the interior cells only; staged,
+    scattered into the padded device state and gathered back chunk by chunk)
+    gives hydro_step_cfl's interior bits and dt, call after call, pipelined
+    and in the step forms that run unpipelined (telescoping, three stages,
+    two levels), from pinned and from pageable host memory."""
+    if kind == "batched":
+        probs = wl.ensemble(count=5, seed=4, choices=(64, 128))
+        lats = [l for l, _ in probs]
+        U0 = np.concatenate([u for _, u in probs])
+        make = lambda: gb.Hydro.from_batch(lats)
+    elif kind == "two_level":
+        from tests.test_gpu_prim_carry import smooth_two_level
+        tl = wl.two_level(wl.lattice_3d(4, 4, 4, 8, 8, 8, 4), (1, 1, 1), (3, 3, 3))
+        U0 = smooth_two_level(tl, 31)[tl.gpu_blocks]
+        make = lambda: gb.Hydro.from_two_level(tl)
+    else:
+        lat = {"3d": wl.lattice_3d(16, 8, 8, 8, 8, 8, 4),
+               "2d_many_chunks": wl.lattice_2d(64, 64, 8, 8, 4),
+               "periodic_z": wl.lattice_3d(8, 8, 16, 8, 8, 8, 4, bc=("outflow", "outflow", "periodic")),
+               "pageable": wl.lattice_3d(8, 8, 8, 16, 16, 16, 4),
+               "telescoping": wl.lattice_3d(8, 8, 16, 8, 8, 8, 4),
+               "three_stages": wl.lattice_3d(8, 8, 8, 8, 8, 8, 4)}[kind]
+        U0 = wl.sedov(lat) if lat.ndim == 3 else wl.sod(lat)
+        make = lambda: gb.Hydro.from_lattice(lat)
+    hd, hh = make(), make()
+    if kind == "telescoping":
+        hd.set_telescoping(True)
+        hh.set_telescoping(True)
+    if kind == "three_stages":
+        hd.set_rk_stages(3)
+        hh.set_rk_stages(3)
+    n = hh.interior_shape
+    gz = hh.nguard if hh.ndim == 3 else 0
+    g = hh.nguard
+    interior = lambda A: A[:, :, gz:gz + n[2], g:g + n[3], g:g + n[4]]
+    D = dev(U0)
+    dt = hd.compute_dt(D)
+    Ui = np.ascontiguousarray(interior(U0))
+    Uh = Ui.copy() if kind == "pageable" else torch.from_numpy(Ui).pin_memory()
+    dth = np.zeros(hh.nproblems)
+    for _ in range(3):
+        hd.step_cfl(D, dt)
+        hh.step_host_interior(Uh, dth)
+        got = Uh if kind == "pageable" else Uh.numpy()
+        assert np.array_equal(interior(host(D)), got)
+        assert np.array_equal(host(dt), dth)
+    with pytest.raises(ValueError):
+        hh.step_host_interior(np.zeros(hh.shape), dth)     # the padded shape is not this call's layout
+
+
 @pytest.mark.parametrize("drift", [4.0, -4.0, 0.0])
 def test_supersonic_faces(gb, drift):
     """Rough states with velocities drift + U(-3, 3) in every direction (Mach up

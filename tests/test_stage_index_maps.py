@@ -1,6 +1,7 @@
 """Index maps of the kernels, restated on the CPU: the thread -> column map and the
-face lists of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), and the
-guard-cell enumeration of the fill kernel (gbh_aux.cu).
+face lists of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), the
+guard-cell enumeration of the fill kernel and the cell map of the interior
+scatter / gather (gbh_aux.cu).
 
 The telescoping variant's first stage (Sec. 4.2) updates the interior widened
 by 2 cells; the next stage reads that output in its own box and in the 2-deep
@@ -133,3 +134,61 @@ def test_fill_enumeration_covers_each_guard_cell_once(nd, n, g):
     want = {(kk, jj, ii) for kk in range(nzp) for jj in range(nxp) for ii in range(nxp)
             if not (inside(ii) and inside(jj) and (kk - gz >= 0 and kk - gz < (n if nd == 3 else 1)))}
     assert set(got) == want
+
+
+def interior_copy_launches(nblocks, n, g, nd, b0, nb):
+    """The launcher's split of blocks [b0, b0 + nb) (at most 2^30 cells per
+    launch) and, per launch, the kernel's map from the cell index t to the
+    offset in the padded blocks and in the interior-only blocks."""
+    nx = ny = n
+    nz = n if nd == 3 else 1
+    gz = g if nd == 3 else 0
+    nxp, nyp, nzp = nx + 2 * g, ny + 2 * g, nz + 2 * gz
+    vstride = nxp * nyp * nzp
+    bstride = 5 * vstride
+    per = nx * ny * nz
+    cells = 5 * per
+    per_launch = max((1 << 30) // cells, 1)
+    out = []
+    b = b0
+    while b < b0 + nb:
+        cnt = min(per_launch, b0 + nb - b)
+        total = cells * cnt
+        assert total < (1 << 30) + cells and total + 152 * 16 * 256 < (1 << 32)
+        for t in range(total):
+            bl, r = divmod(t, cells)
+            v, r = divmod(r, per)
+            i, r = r % nx, r // nx
+            j, k = r % ny, r // ny
+            o = bl * bstride + v * vstride + ((k + gz) * nyp + (j + g)) * nxp + (i + g)
+            assert 0 <= o < cnt * bstride
+            out.append((b * bstride + o, b * cells + t))
+        b += cnt
+    return out, (nxp, nyp, nzp, bstride, cells)
+
+
+@pytest.mark.parametrize("nd,n,g,nblocks,b0,nb", [(3, 4, 2, 5, 1, 3), (3, 8, 4, 3, 0, 3), (2, 16, 4, 7, 2, 4),
+                                                   (2, 4, 3, 6, 5, 1)])
+def test_interior_copy_maps_each_interior_cell_once(nd, n, g, nblocks, b0, nb):
+    """hydro_step_host_interior's scatter / gather: every interior cell of the
+    chunk's blocks once, no guard cell, the interior-only index in layout
+    order [block][var][z][y][x] and inside the chunk's range on both sides."""
+    pairs, (nxp, nyp, nzp, bstride, cells) = interior_copy_launches(nblocks, n, g, nd, b0, nb)
+    gz = g if nd == 3 else 0
+    nz = n if nd == 3 else 1
+    pads = [p for p, _ in pairs]
+    ints = [c for _, c in pairs]
+    assert ints == list(range(b0 * cells, (b0 + nb) * cells))
+    assert len(set(pads)) == len(pads)
+    want = set()
+    for b in range(b0, b0 + nb):
+        for v in range(5):
+            for k in range(nz):
+                for j in range(n):
+                    for i in range(n):
+                        want.add(b * bstride + v * nxp * nyp * nzp + ((k + gz) * nyp + j + g) * nxp + i + g)
+    assert set(pads) == want
+    # consecutive cells along x are consecutive on both sides (whole rows)
+    for (p0, c0), (p1, c1) in zip(pairs, pairs[1:]):
+        if c1 % n:
+            assert p1 == p0 + 1 and c1 == c0 + 1

@@ -1613,7 +1613,7 @@ static int host_step(gbh_ctx* c, double* U_host, double* dt_host, void* stream, 
   // stage reads only slots written by the pre-pass of its own chunk or of an
   // earlier one on the same stream, and the stage-2 pre-pass of chunk k writes
   // only slots of blocks in chunks up to need[k], whose stage-1 launches it
-  // waits for; every writer of a slot in a stage writes the same face's bits.
+  // waits for; in each stage every slot has exactly one writer.
   const int K = c->pipe_chunks;
   // stage 1 leaves the primitives of U(1) for stage 2 (chunk k's stage 2 reads
   // them only from the chunks whose stage 1 it waits for, like U(1) itself)

@@ -394,6 +394,14 @@ int hydro_advance(gbh_ctx *ctx, double *U, int nsteps, double *dt_dev, double *d
  * into dt_hist_host (nsteps doubles, may be NULL).  Synchronises the stream. */
 int hydro_advance_host(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist_host, void *stream);
 
+/* hydro_advance_host for a host state of the interior cells only, laid out
+ * as in hydro_step_host_interior (U_host[nblocks][5][nzb][nyb][nxb], HOST,
+ * in and out): copied into the context-owned interior-only staging array,
+ * scattered into the padded device state, advanced, gathered and copied
+ * back.  Arguments, errors and synchronisation otherwise as
+ * hydro_advance_host; the interior results are the same bits. */
+int hydro_advance_host_interior(gbh_ctx *ctx, double *U_host, int nsteps, double *dt_hist_host, void *stream);
+
 /* One step of a state in HOST memory with the copies overlapped with the
  * stages (one hydro_step_cfl in effect).  dt_host (HOST, [nproblems]) is in
  * and out: if dt_host[0] > 0 it is the step's time step (every entry must be

@@ -84,6 +84,7 @@ SIGNATURES = {
     "hydro_step_cfl": (C.c_int, [_vp, _dp, _dp, _vp]),
     "hydro_advance": (C.c_int, [_vp, _dp, C.c_int, _dp, _dp, _vp]),
     "hydro_advance_host": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
+    "hydro_advance_host_interior": (C.c_int, [_vp, _dp, C.c_int, _dp, _vp]),
     "hydro_step_host": (C.c_int, [_vp, _dp, _dp, _vp]),
     "hydro_step_host_interior": (C.c_int, [_vp, _dp, _dp, _vp]),
     "gbh_set_host_pipeline": (C.c_int, [_vp, C.c_int]),

@@ -1441,14 +1441,34 @@ int hydro_advance(gbh_ctx* c, double* U, int nsteps, double* dt_dev, double* dt_
   return GBH_OK;
 }
 
-int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_host, void* stream) {
+// Doubles of one block in the interior-only layout [5][nz][ny][nx].
+static long long interior_cells(const Layout& L) { return 5LL * L.nx * L.ny * L.nz; }
+
+// The interior-only staging array of the host-buffer calls (allocated on first
+// use).  Those calls write the interior of d_host_state alone: its guard cells
+// get defined values once (the steps never read them).
+static cudaError_t ensure_interior_staging(gbh_ctx* c) {
+  if (c->d_pipe_int) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&c->d_pipe_int, sizeof(double) * interior_cells(c->lay) * c->lay.nblocks);
+  if (e == cudaSuccess) e = cudaMemset(c->d_host_state, 0, sizeof(double) * state_elems(c->lay));
+  return e;
+}
+
+// hydro_advance_host (interior = false: U_host in the padded state layout) and
+// hydro_advance_host_interior (interior = true: [nblocks][5][nz][ny][nx], staged
+// in d_pipe_int and scattered into / gathered from the padded device state).
+static int advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_host, void* stream,
+                        bool interior) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!U_host || nsteps < 0) return set_err(c, GBH_ERR_INVAL, "U_host must be non-null and nsteps >= 0");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(double) * state_elems(c->lay);
+  const Layout& L = c->lay;
+  const size_t bytes = sizeof(double) * state_elems(L);
+  const size_t ibytes = sizeof(double) * interior_cells(L) * L.nblocks;
   cudaError_t e = cudaSuccess;
   if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
+  if (e == cudaSuccess && interior) e = ensure_interior_staging(c);
   if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double) * c->nproblems);
   if (e == cudaSuccess && nsteps > c->host_hist_cap) {
     cudaFree(c->d_host_hist);
@@ -1457,13 +1477,23 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
     if (e == cudaSuccess) c->host_hist_cap = nsteps;
   }
   if (e != cudaSuccess) return set_err(c, GBH_ERR_NOMEM, "device allocation failed: %s", cudaGetErrorString(e));
-  if ((rc = cuda_err(c, cudaMemcpyAsync(c->d_host_state, U_host, bytes, cudaMemcpyHostToDevice, s), "H2D copy")))
-    return rc;
+  if (interior) {
+    e = cudaMemcpyAsync(c->d_pipe_int, U_host, ibytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = gbh::launch_interior_copy(c->d_host_state, c->d_pipe_int, L, 0, L.nblocks, true, s);
+  } else {
+    e = cudaMemcpyAsync(c->d_host_state, U_host, bytes, cudaMemcpyHostToDevice, s);
+  }
+  if ((rc = cuda_err(c, e, "H2D copy"))) return rc;
   if ((rc = hydro_compute_dt(c, c->d_host_state, c->d_host_dt, stream))) return rc;
   if ((rc = hydro_advance(c, c->d_host_state, nsteps, c->d_host_dt, nsteps ? c->d_host_hist : nullptr, stream)))
     return rc;
-  if ((rc = cuda_err(c, cudaMemcpyAsync(U_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, s), "D2H copy")))
-    return rc;
+  if (interior) {
+    e = gbh::launch_interior_copy(c->d_host_state, c->d_pipe_int, L, 0, L.nblocks, false, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U_host, c->d_pipe_int, ibytes, cudaMemcpyDeviceToHost, s);
+  } else {
+    e = cudaMemcpyAsync(U_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, s);
+  }
+  if ((rc = cuda_err(c, e, "D2H copy"))) return rc;
   if (dt_hist_host && nsteps > 0 &&
       (rc = cuda_err(c, cudaMemcpyAsync(dt_hist_host, c->d_host_hist, sizeof(double) * nsteps * c->nproblems,
                                         cudaMemcpyDeviceToHost, s), "D2H dt copy")))
@@ -1471,8 +1501,13 @@ int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_h
   return cuda_err(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
 }
 
-// Doubles of one block in the interior-only layout [5][nz][ny][nx].
-static long long interior_cells(const Layout& L) { return 5LL * L.nx * L.ny * L.nz; }
+int hydro_advance_host(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_host, void* stream) {
+  return advance_host(c, U_host, nsteps, dt_hist_host, stream, false);
+}
+
+int hydro_advance_host_interior(gbh_ctx* c, double* U_host, int nsteps, double* dt_hist_host, void* stream) {
+  return advance_host(c, U_host, nsteps, dt_hist_host, stream, true);
+}
 
 // Buffers, chunks, streams and events of the pipelined host-buffer step.
 static int pipe_setup(gbh_ctx* c, bool interior) {
@@ -1480,12 +1515,7 @@ static int pipe_setup(gbh_ctx* c, bool interior) {
   const int NB = c->lay.nblocks;
   cudaError_t e = cudaSuccess;
   if (!c->d_host_state) e = cudaMalloc(&c->d_host_state, bytes);
-  if (e == cudaSuccess && interior && !c->d_pipe_int) {
-    // the interior-only form writes the interior of d_host_state alone: its
-    // guard cells get defined values once (the steps never read them)
-    e = cudaMalloc(&c->d_pipe_int, sizeof(double) * interior_cells(c->lay) * NB);
-    if (e == cudaSuccess) e = cudaMemset(c->d_host_state, 0, bytes);
-  }
+  if (e == cudaSuccess && interior) e = ensure_interior_staging(c);
   if (e == cudaSuccess && !c->d_host_dt) e = cudaMalloc(&c->d_host_dt, sizeof(double) * c->nproblems);
   if (e == cudaSuccess && !c->d_pipe_out) {
     e = cudaMalloc(&c->d_pipe_out, bytes);

@@ -338,9 +338,10 @@ class Hydro:
         """Block chunks of step_host (0: the fewest chunks of one stage-kernel wave each)."""
         self._check(self.lib.gbh_set_host_pipeline(self.ctx, int(chunks)))
 
-    def advance_host(self, U_host, nsteps: int, dt_hist_host=None):
-        """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state shape."""
-        ptr = self._host_state(U_host)
+    def advance_host(self, U_host, nsteps: int, dt_hist_host=None, interior: bool = False):
+        """U_host: a float64 CPU tensor (pinned or not) or numpy array of the state
+        shape (interior=True: of interior_shape, the interior cells only)."""
+        ptr = self._host_state(U_host, self.interior_shape if interior else None)
         h = None
         if dt_hist_host is not None:
             need = int(nsteps) * self.nproblems
@@ -353,7 +354,8 @@ class Hydro:
                         or dt_hist_host.numel() < need):
                     raise ValueError(f"dt_hist_host must be a contiguous float64 CPU tensor of >= {need} values")
                 h = dt_hist_host.data_ptr()
-        self._check(self.lib.hydro_advance_host(self.ctx, ptr, int(nsteps), h, _stream_handle()))
+        fn = self.lib.hydro_advance_host_interior if interior else self.lib.hydro_advance_host
+        self._check(fn(self.ctx, ptr, int(nsteps), h, _stream_handle()))
         return U_host
 
     def check_state(self, U) -> int:

@@ -265,6 +265,17 @@ def test_repeatable_and_step_variants_agree(gb):
     h.advance_host(Uh, 5, hist_h)
     assert np.array_equal(Uh[:, :, zs, ys, xs], res[0][:, :, zs, ys, xs])
     assert np.array_equal(hist_h, hh)
+    # and with a host state of the interior cells only (pageable, then pinned)
+    for pinned in (False, True):
+        Ui = np.ascontiguousarray(U[:, :, zs, ys, xs])
+        Ui = torch.from_numpy(Ui).pin_memory() if pinned else Ui
+        hist_i = np.zeros(5)
+        h.advance_host(Ui, 5, hist_i, interior=True)
+        got = Ui.numpy() if pinned else Ui
+        assert np.array_equal(got, res[0][:, :, zs, ys, xs])
+        assert np.array_equal(hist_i, hh)
+    with pytest.raises(ValueError):
+        h.advance_host(U.copy(), 5, None, interior=True)       # the padded shape is not that layout
 
 
 def test_checkpoint_resume_bitwise(gb, tmp_path):

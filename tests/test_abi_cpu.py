@@ -110,6 +110,13 @@ def test_create_rejects_bad_tables_without_gpu(lib):
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.hydro_step(None, None, 1.0, None) == -1
     assert lib.gbh_destroy(None) == 0
+    # the host-buffer entry points check the context before any CUDA call
+    dt = (C.c_double * 1)(0.0)
+    assert lib.hydro_step_host(None, None, dt, None) == -1
+    assert lib.hydro_step_host_interior(None, None, dt, None) == -1
+    assert lib.hydro_advance_host(None, None, 1, None, None) == -1
+    assert lib.hydro_advance_host_interior(None, None, 1, None, None) == -1
+    assert b"null context" in lib.gbh_last_error(None)
 
 
 @pytest.mark.parametrize("ndim,nb,per", [

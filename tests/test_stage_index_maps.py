@@ -1,7 +1,8 @@
 """Index maps of the kernels, restated on the CPU: the thread -> column map and the
-face lists of the stage kernel's unsplit ring-2 tile (gbh_stage.cu), the
-guard-cell enumeration of the fill kernel and the cell map of the interior
-scatter / gather (gbh_aux.cu).
+face lists of the stage kernel's unsplit ring-2 tile, the face pre-pass's
+thread -> face-cell map and its slots against the stage kernel's reads
+(gbh_stage.cu), the guard-cell enumeration of the fill kernel and the cell map
+of the interior scatter / gather (gbh_aux.cu).
 
 The telescoping variant's first stage (Sec. 4.2) updates the interior widened
 by 2 cells; the next stage reads that output in its own box and in the 2-deep
@@ -192,3 +193,56 @@ def test_interior_copy_maps_each_interior_cell_once(nd, n, g, nblocks, b0, nb):
     for (p0, c0), (p1, c1) in zip(pairs, pairs[1:]):
         if c1 % n:
             assert p1 == p0 + 1 and c1 == c0 + 1
+
+
+def prepass_thread_cells(N, nz, nblocks, lo, hi):
+    """The face pre-pass's thread map over blocks [lo, hi) (face_flux_kernel,
+    3-D): (block, face, cell coordinates i, j, k of the face's cell index, slot
+    index tt) per thread that solves a face, before the neighbour rules."""
+    NF = N * max(N, nz)
+    out = []
+    for t in range((hi - lo) * 6 * NF):
+        bl, r = divmod(t, 6 * NF)
+        b = lo + bl
+        face, tt = divmod(r, NF)
+        d = face >> 1
+        if tt // N >= (N if d == 2 else nz):
+            continue
+        t1, t2 = tt % N, tt // N
+        ijk = {0: ("-", t1, t2), 1: (t1, "-", t2), 2: (t1, t2, "-")}[d]
+        out.append((b, face, ijk, tt))
+    return out, NF
+
+
+def stage_read_slot(N, face, i, j, k):
+    """Slot index the stage kernel reads for a face cell: x faces row j of plane
+    k (j + N k), y faces column i of plane k (i + N k), z faces (i + N j)."""
+    d = face >> 1
+    return {0: j + N * k, 1: i + N * k, 2: i + N * j}[d]
+
+
+@pytest.mark.parametrize("N,nz,nblocks,lo,hi", [(16, 16, 3, 0, 3), (16, 8, 4, 1, 3), (8, 12, 5, 2, 5), (4, 4, 2, 0, 1)])
+def test_prepass_slots_match_the_stage_reads(N, nz, nblocks, lo, hi):
+    """Every face cell of the range's blocks has one thread, its slot is the
+    one the stage kernel reads for that cell, and slots stay inside
+    [nblocks][6][5][N max(N, nz)] (non-cubic blocks too)."""
+    cells, NF = prepass_thread_cells(N, nz, nblocks, lo, hi)
+    keys = [(b, f, ijk) for b, f, ijk, _ in cells]
+    assert len(keys) == len(set(keys))
+    want = set()
+    for b in range(lo, hi):
+        for f in range(6):
+            d = f >> 1
+            ext = {0: (N, nz), 1: (N, nz), 2: (N, N)}[d]
+            for t2 in range(ext[1]):
+                for t1 in range(ext[0]):
+                    want.add((b, f, {0: ("-", t1, t2), 1: (t1, "-", t2), 2: (t1, t2, "-")}[d]))
+    assert set(keys) == want
+    total = nblocks * 6 * 5 * NF
+    for b, f, (i, j, k), tt in cells:
+        ii = 0 if i == "-" else i
+        jj = 0 if j == "-" else j
+        kk = 0 if k == "-" else k
+        assert stage_read_slot(N, f, ii, jj, kk) == tt
+        for v in range(5):
+            assert 0 <= ((b * 6 + f) * 5 + v) * NF + tt < total

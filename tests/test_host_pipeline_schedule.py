@@ -119,7 +119,22 @@ def hb(a, b):
     (3, (16, 16, 16), (False, False, False), 0),  # the benchmark: 13 waves of 304 and 144
 ])
 def test_chunked_prepass_slots_are_ready_and_not_overwritten(ndim, nb, periodic, wanted):
-    face = face_table(ndim, nb, periodic)
+    check_schedule(face_table(ndim, nb, periodic), ndim, wanted)
+
+
+@pytest.mark.parametrize("wanted", [0, 3, 7, 25])
+def test_batched_problems_schedule(wanted):
+    """A batched context's face table: independent lattices one after another
+    (block ids offset), periodic wraps inside each problem."""
+    parts, off = [], 0
+    for nb, per in (((3, 3, 2), (True, True, True)), ((2, 4, 3), (False, True, True)), ((1, 2, 2), (True, True, True))):
+        f = face_table(3, nb, per)
+        parts.append(np.where(f >= 0, f + off, f))
+        off += f.shape[0]
+    check_schedule(np.concatenate(parts), 3, wanted)
+
+
+def check_schedule(face, ndim, wanted):
     NB = face.shape[0]
     first = chunks(NB, wanted)
     K = len(first) - 1
